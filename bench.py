@@ -1,0 +1,335 @@
+#!/usr/bin/env python3
+"""Benchmark: converged projections/sec at ||F|| <= 1e-5 on one GB300.
+
+A step is one pass of the whole hot path over one batch: projection (FP32
+Newton/LM steps with FP64 acceptance, Alg. 2 ParallelProject) followed by the
+sphere collision check of every projected configuration (CollisionFree).
+The default workload is the 7-DoF arm with the end-effector orientation
+constraint, 65,536 configurations (tol 1e-5, cap 30, lambda 1e-6; 60 link
+spheres against 64 obstacle spheres).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload arm|dual_arm|sphere] [--precision fp32|fp64]
+
+Prints one JSON line (rank 0).  Under torchrun each rank projects its own
+seeded batch of the same size (independent problems, no collective on the
+data path); value is the sum over ranks divided by the slowest rank's time.
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "converged projections/sec at ||F||<=1e-5 (batched FP32 vs plain FP64, 1 GB300)"
+UNIT = "projections/s"
+L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="arm", choices=["arm", "dual_arm", "sphere"])
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name, rank):
+    from paper_2604_13323_gb300 import workloads as W
+    if name == "arm":
+        wl = W.arm_workload(seed=1001 + 1000 * rank, n=65536)
+        return wl, wl.q, "arm7_axis_65536"
+    if name == "sphere":
+        wl = W.sphere_workload(seed=1000 + 1000 * rank)
+        return wl, W.segment_points(wl.segments), "sphere_geodesics_1024_pairs"
+    wl = W.dual_arm_workload(seed=1002, total=10, n_random=262144)
+    return wl, wl.q, "dual14_rel_262144"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 3 + i and r[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_baseline(wl, q, budget_s=10.0):
+    """The FP64 oracle, as it stands, on the host cores: projection + check of
+    contiguous chunks of the workload until ~budget_s of wall time."""
+    from oracle import oracle as orc
+    O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
+    threads = orc.default_threads()
+    p = wl.params
+    chunk = 4096
+    done = conv = 0
+    t0 = time.perf_counter()
+    off = 0
+    while time.perf_counter() - t0 < budget_s and done < q.shape[1] * 4:
+        sl = q[:, off:off + chunk]
+        out, fl, _, r = O.project(sl, p.tol, p.max_iters, p.lam, max_step=p.max_step, threads=threads)
+        O.check(out, threads=threads)
+        conv += int(((fl & orc.CONVERGED) != 0).sum())
+        done += sl.shape[1]
+        off = (off + chunk) % q.shape[1]
+    dt = time.perf_counter() - t0
+    return {"value": conv / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{done} configurations (contiguous chunks of {chunk} of the bench batch), "
+                      f"projection + collision check, FP64, {dt:.1f} s wall"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, same workload and metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl, q, wname = make_workload(args.workload, 0)
+    from oracle import oracle as orc
+    O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
+    threads = orc.default_threads()
+    p = wl.params
+    sample = min(q.shape[1], 8192)
+    times, convs = [], []
+    for s in range(args.warmup + args.steps):
+        sl = q[:, (s * sample) % q.shape[1]:][:, :sample]
+        t0 = time.perf_counter()
+        out, fl, _, _ = O.project(sl, p.tol, p.max_iters, p.lam, max_step=p.max_step, threads=threads)
+        O.check(out, threads=threads)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            convs.append(int(((fl & orc.CONVERGED) != 0).sum()))
+    total = sum(times)
+    value = sum(convs) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wname, "batch_per_step": sample, "dof": wl.dof, "k": wl.k, "tol": p.tol,
+                       "cap": p.max_iters},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{sample} configurations per step, projection + collision check"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2604_13323_gb300 import build as B
+    B.build()
+    from paper_2604_13323_gb300 import flops as FL
+    from paper_2604_13323_gb300 import mcproj
+    from paper_2604_13323_gb300 import workloads as W
+
+    wl, q_np, wname = make_workload(args.workload, rank)
+    if args.precision == "fp64":
+        wl.params.precision = W.PREC_FP64
+    elif args.precision == "fp32":
+        wl.params.precision = W.PREC_FP32
+    fp64 = wl.params.precision == W.PREC_FP64
+    dt = torch.float64 if fp64 else torch.float32
+    d, n = q_np.shape
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles, device=local)
+    stream = torch.cuda.current_stream(dev)
+    q_in = torch.tensor(q_np, dtype=dt, device=dev)
+    q_out = torch.empty_like(q_in)
+    flags = torch.empty(n, dtype=torch.uint8, device=dev)
+    iters = torch.empty(n, dtype=torch.uint8, device=dev)
+    resid = torch.empty(n, dtype=torch.float64, device=dev)
+    hit = torch.empty(n, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        P.project(q_in, wl.params, out=q_out, flags=flags, iters=iters, resid=resid, stream=stream)
+        if ev:
+            ev[1].record(stream)
+        P.check(q_out, out=hit, stream=stream)
+        if ev:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    launches0 = P.launches
+    sampler = ClockSampler(local)
+    with sampler:
+        torch.cuda.synchronize()
+        for s in range(args.steps):
+            flush.zero_()          # L2 flush between timed steps (outside the events)
+            step(evs[s])
+        torch.cuda.synchronize()
+    launches = P.launches - launches0
+    if world > 1:
+        dist.barrier()
+    t_proj = [e[0].elapsed_time(e[1]) for e in evs]
+    t_check = [e[1].elapsed_time(e[2]) for e in evs]
+    t_step = [e[0].elapsed_time(e[2]) for e in evs]
+    ms = sum(t_step) / len(t_step)
+    fl_np = flags.cpu().numpy()
+    rs_np = resid.cpu().numpy()
+    it_np = iters.cpu().numpy()
+    conv = int((((fl_np & mcproj.F_CONVERGED) != 0) & (rs_np <= wl.params.tol)).sum())
+    t_tot = torch.tensor([ms], dtype=torch.float64, device=dev)
+    c_tot = torch.tensor([conv], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_tot, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c_tot, op=dist.ReduceOp.SUM)
+    ms_max = float(t_tot.item())
+    value = float(c_tot.item()) / (ms_max * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers ----
+    q_host = torch.tensor(q_np, dtype=dt).pin_memory()
+    out_host = torch.empty((d, n), dtype=dt).pin_memory()
+    fl_host = torch.empty(n, dtype=torch.uint8).pin_memory()
+    hit_host = torch.empty(n, dtype=torch.uint8).pin_memory()
+    e2e_ms = []
+    for s in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        q_in.copy_(q_host, non_blocking=True)
+        step()
+        out_host.copy_(q_out, non_blocking=True)
+        fl_host.copy_(flags, non_blocking=True)
+        hit_host.copy_(hit, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if s >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    conv_e2e = int(((fl_host.numpy() & mcproj.F_CONVERGED) != 0).sum())
+    e2e_t = torch.tensor([sum(e2e_ms) / len(e2e_ms)], dtype=torch.float64, device=dev)
+    e2e_c = torch.tensor([conv_e2e], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e2e_c, op=dist.ReduceOp.SUM)
+    e2e = {"value": float(e2e_c.item()) / (float(e2e_t.item()) * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": q_host.numel() * q_host.element_size(),
+           "d2h_bytes_per_step": out_host.numel() * out_host.element_size() + 2 * n}
+
+    # ---- roofline of the dominant kernel ----
+    fm = FL.FlopModel(wl.robot, wl.constraints)
+    fp32, fp64f = fm.projection(it_np)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    clk = sampler.summary()
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak32 = sms * 128 * 2 * sm_max * 1e6 / 1e12        # FP32 FMA lanes x 2 flops x max clock
+    peak64 = 1.25                                         # nominal dense FP64, TFLOP/s
+    mp = sum(t_proj) / len(t_proj)
+    mc = sum(t_check) / len(t_check)
+    if fp64:
+        flops_proj = fp32 + fp64f   # the plain kernel does all of it in FP64
+        ach = flops_proj / (mp * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak64, "unit": "TFLOP/s", "frac": ach / peak64,
+                "traffic": None, "kernel": "k_project_f64 (plain FP64)", "peak_source": "nominal FP64"}
+    else:
+        ach32 = fp32 / (mp * 1e-3) / 1e12
+        ach64 = fp64f / (mp * 1e-3) / 1e12
+        # both pipes: the time the FP32 and FP64 work need at their peaks bounds the kernel
+        t_min = max(fp32 / (peak32 * 1e12), fp64f / (peak64 * 1e12))
+        roof = {"bound": "alu", "achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
+                "traffic": None, "kernel": "k_project_f32 (persistent, FP32 steps + FP64 acceptance)",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                "fp64_achieved": ach64, "fp64_peak": peak64, "fp64_frac": ach64 / peak64,
+                "mixed_bound_frac": t_min / (mp * 1e-3),
+                "flops_per_config": {"fp32": fp32 / n, "fp64": fp64f / n}}
+    kernel_ms = {"project": mp, "check": mc}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, q_np if not fp64 else q_np)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
+                "config": {"workload": wname, "batch": n, "dof": d, "k": wl.k, "tol": wl.params.tol,
+                           "cap": wl.params.max_iters, "lambda": wl.params.lam,
+                           "precision": "fp64 plain" if fp64 else "fp32 + fp64 acceptance",
+                           "obstacles": int(wl.obstacles.spheres.shape[0]), "robot_spheres": wl.robot.n_spheres,
+                           "l2": "flushed between timed steps (512 MB write)",
+                           "parallelism": f"replicas x{world}", "converged_per_step": conv,
+                           "kernel_ms": kernel_ms, "mean_iters": float(it_np.mean())},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    P.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

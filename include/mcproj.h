@@ -1,0 +1,212 @@
+/*
+ * mcproj -- batched manifold projection and collision checking on GB300.
+ *
+ * C ABI of libmcproj.so.  Plain pointers and sizes only.  Every batch buffer
+ * is caller-owned DEVICE memory unless a function says otherwise; every call
+ * is asynchronous on the given CUDA stream (0 = legacy default stream) unless
+ * it says otherwise.
+ *
+ * The operations follow the paper "Vectorizing Projection in Manifold-
+ * Constrained Motion Planning for Real-Time Whole-Body Control":
+ *   - a configuration q in R^d satisfies the constraints when F(q) = 0, up to
+ *     a tolerance ||F(q)|| < eps (Sec. II);
+ *   - constraints are end-effector TSRs (Eq. 1), relative poses of two frames
+ *     (Eq. 2), and the humanoid's stability constraint on the centre of mass
+ *     (Sec. V-C), stacked into one F (Sec. IV-C);
+ *   - projection is the loop ParallelProject / getDescentStep of Algorithm 2:
+ *     d = F(q); stop when ||d|| < eps; otherwise
+ *     q <- q - alpha J^T (J J^T + lambda I)^{-1} d, solved with a Cholesky
+ *     factorisation (Sec. IV-A, "Vectorized Levenberg-Marquardt"), with a
+ *     divergence exit when ||step|| > MaxDistance;
+ *   - CollisionFree(q) checks the robot's link spheres against the obstacles
+ *     (Sec. I, Algorithm 2).
+ *
+ * Batches are structure-of-arrays: element (joint j, configuration i) of a
+ * batch with leading dimension ld lives at base[j * ld + i]; ld >= n.
+ *
+ * Return values: MCP_OK on success.  Argument errors return MCP_ERR_ARG
+ * before anything is enqueued; CUDA runtime failures return MCP_ERR_CUDA.  In
+ * both cases mcp_last_error() describes the failure.  No function aborts the
+ * process, and no kernel traps: per-configuration failures are reported in
+ * the flags array.
+ *
+ * Thread safety: one context is used by one host thread at a time.
+ */
+#ifndef MCPROJ_H_
+#define MCPROJ_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mcp_ctx mcp_ctx;
+typedef struct CUstream_st *mcp_stream; /* a cudaStream_t */
+
+typedef enum {
+  MCP_OK = 0,
+  MCP_ERR_ARG = 1,         /* bad pointer, size, layout or descriptor */
+  MCP_ERR_STATE = 2,       /* robot / constraints / obstacles not loaded */
+  MCP_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+  MCP_ERR_OOM = 4,         /* device allocation failed */
+  MCP_ERR_UNSUPPORTED = 5  /* robot / constraint combination outside the compiled set */
+} mcp_status;
+
+/* Limits of the compiled kernels. */
+#define MCP_MAX_JOINTS 40
+#define MCP_MAX_FRAMES 8
+#define MCP_MAX_CONSTRAINTS 8
+#define MCP_MAX_EQUATIONS 24
+#define MCP_MAX_SPHERES 256
+#define MCP_MAX_OBSTACLES 1024
+#define MCP_MAX_AABBS 64
+
+/* Per-configuration flag bits written by the projection calls. */
+#define MCP_F_CONVERGED 1      /* ||F(q*)|| < tol, verified in FP64 */
+#define MCP_F_CAP 2            /* iteration cap reached without convergence */
+#define MCP_F_DIVERGED 4       /* ||step|| > max_step (Alg. 2 MaxDistance exit) */
+#define MCP_F_NONFINITE 8      /* NaN/Inf or a singular system with lambda = 0 */
+#define MCP_F_FP64_RESOLVE 16  /* at least one step was re-solved in FP64 */
+#define MCP_F_ACCEPT_FAIL 32   /* FP32 residual passed but the FP64 check did not, at the cap */
+#define MCP_F_OUT_OF_LIMITS 64 /* q* outside the joint limits (reported, never clamped) */
+
+/* Constraint kinds.  k = number of equations. */
+typedef enum {
+  MCP_C_SPHERE = 0,     /* F = ||q|| - target[0] (configuration space), k = 1 */
+  MCP_C_AXIS_ALIGN = 1, /* z-axis of frame_a parallel to world z: F = (z.x, z.y), k = 2
+                           (Sec. II: "held upright" TSR; antiparallel also satisfies it) */
+  MCP_C_POSE = 2,       /* Eq. 1 with B^w = 0: T_err = P^-1 T_a Q^-1, F = [t_err; log(R_err)],
+                           P = T_w^0, Q = T_e^w, k = 6 */
+  MCP_C_REL_POSE = 3,   /* Eq. 2: T_err = P^-1 (T_a^-1 T_b), F = [t_err; log(R_err)],
+                           P = T_ref, a = left, b = right, k = 6 */
+  MCP_C_COM_XY = 4      /* Sec. V-C stability: F = x_com^xy - target[0:2], k = 2 */
+} mcp_ckind;
+
+/* Robot: a tree of 1-DoF joints in topological order (parent[j] < j, -1 = world).
+ * T_j = T_parent(j) * X_j * Jnt(q_j); Jnt = Rz(q) (type 0, revolute) or a
+ * translation q along z (type 1, prismatic).  3x4 transforms are 12 doubles,
+ * row-major, column 3 = translation.  All arrays are HOST memory, copied by
+ * mcp_load_robot; the caller keeps ownership. */
+typedef struct {
+  int32_t n_joints;
+  const int32_t *parent;      /* [n_joints] */
+  const int32_t *type;        /* [n_joints] */
+  const double *X;            /* [n_joints * 12] */
+  const double *lower;        /* [n_joints] joint limits (flag only) */
+  const double *upper;        /* [n_joints] */
+  const double *mass;         /* [n_joints] link masses (may be NULL if no CoM constraint) */
+  const double *com;          /* [n_joints * 3] link CoM in its joint frame (may be NULL) */
+  int32_t n_spheres;
+  const int32_t *sphere_link; /* [n_spheres] joint the sphere rides on, -1 = world */
+  const double *sphere;       /* [n_spheres * 4] centre xyz in that frame, radius */
+  int32_t n_frames;
+  const int32_t *frame_link;  /* [n_frames] */
+  const double *frame_X;      /* [n_frames * 12] frame offset in its joint frame */
+} mcp_robot_desc;
+
+/* One constraint.  If q_ref != NULL (HOST, n_joints doubles) the reference is
+ * taken from the robot at q_ref when loaded, in FP64 on the device:
+ *   POSE:     P := T_a(q_ref) Q^-1          (T_err(q_ref) = I)
+ *   REL_POSE: P := T_a(q_ref)^-1 T_b(q_ref)
+ *   COM_XY:   target := xy midpoint of frames a and b at q_ref (the centre of
+ *             the support polygon of two feet). */
+typedef struct {
+  int32_t kind;
+  int32_t frame_a, frame_b;
+  double P[12];
+  double Q[12];
+  double target[3];
+  const double *q_ref;
+} mcp_constraint_desc;
+
+typedef struct {
+  double tol;          /* eps of Alg. 2, on the Euclidean norm of the stacked F */
+  int32_t max_iters;   /* step cap (Alg. 2 has none; at most max_iters steps) */
+  int32_t precision;   /* 0: FP32 steps with FP64 acceptance; 1: plain FP64 throughout */
+  double lambda;       /* LM damping */
+  double max_step;     /* Alg. 2 MaxDistance; <= 0 disables the exit */
+  double pivot_fp64;   /* FP32 Cholesky pivot below this -> the step is re-solved in FP64 */
+} mcp_project_params;
+
+/* Context on CUDA device `device`. */
+mcp_status mcp_create(int device, mcp_ctx **out);
+/* Frees the context and its device memory (NULL-safe).  Synchronises the device. */
+void mcp_destroy(mcp_ctx *ctx);
+/* Message of the last failure on this context ("" if none); owned by the context. */
+const char *mcp_last_error(const mcp_ctx *ctx);
+
+/* Loads (replaces) the robot model (Sec. II: configuration space C in R^d and
+ * the kinematics T_s^0 = FK(q) of Eq. 1).  Synchronous. */
+mcp_status mcp_load_robot(mcp_ctx *ctx, const mcp_robot_desc *robot);
+/* Loads (replaces) the stacked constraint list (Sec. IV-C), in order.  The
+ * robot must be loaded first.  Synchronous (references are resolved on the device). */
+mcp_status mcp_load_constraints(mcp_ctx *ctx, const mcp_constraint_desc *cons, int32_t n);
+/* Loads (replaces) obstacle spheres [n * 4] (centre, radius) and axis-aligned
+ * boxes [m * 6] (min xyz, max xyz); HOST memory, copied.  Synchronous. */
+mcp_status mcp_load_obstacles(mcp_ctx *ctx, const double *spheres, int32_t n_spheres, const double *aabbs,
+                              int32_t n_aabbs);
+/* Returns the resolved constraint i (after q_ref handling): P, Q (12 each) and
+ * target (3), into HOST buffers. */
+mcp_status mcp_get_constraint(const mcp_ctx *ctx, int32_t i, double *P, double *Q, double *target);
+
+/* ParallelProject (Alg. 2) of n configurations.
+ * q_in / q_out: [d * ld] float (precision 0) or double (precision 1); q_out may alias q_in.
+ * flags [n] uint8 (MCP_F_*), iters [n] uint8 (steps applied), resid [n] double:
+ * the FP64 Euclidean norm of F at the returned configuration.
+ * On a divergence exit q_out holds the last iterate before the rejected step. */
+mcp_status mcp_project_batch(mcp_ctx *ctx, const mcp_project_params *p, int64_t n, int64_t ld, const void *q_in,
+                             void *q_out, uint8_t *flags, uint8_t *iters, double *resid, mcp_stream stream);
+
+/* Projection of uneven interpolation segments in one persistent launch
+ * (Alg. 2: n points interpolated between q_s and q_proj are projected in
+ * parallel).  Point t of segment s is start[:, s] + t * delta[:, s],
+ * t = 0 .. len[s]-1; its outputs go to index off[s] + t, off = exclusive
+ * prefix sum of len.  start / delta: float [d * ld_seg] (precision 0) or
+ * double (precision 1); len: int32 [n_seg] (each >= 0); q_out: [d * ld_out]
+ * with ld_out >= sum(len); flags / iters / resid as in mcp_project_batch.
+ * The library scans len on the device into context-owned scratch.  Idle
+ * lanes refill themselves from a work counter, so segments of any length mix
+ * in one launch. */
+mcp_status mcp_project_segments(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_seg, int64_t ld_seg,
+                                const void *start, const void *delta, const int32_t *len, int64_t total,
+                                int64_t ld_out, void *q_out, uint8_t *flags, uint8_t *iters, double *resid,
+                                mcp_stream stream);
+
+/* CollisionFree (Alg. 2) of n configurations: in_collision[i] = 1 iff some
+ * robot sphere overlaps some obstacle sphere (|c_s - c_o| < r_s + r_o) or box
+ * (distance from c_s to the box < r_s).  q: [d * ld] float (precision 0) or
+ * double (precision 1). */
+mcp_status mcp_check_batch(mcp_ctx *ctx, int64_t n, int64_t ld, const void *q, int32_t precision,
+                           uint8_t *in_collision, mcp_stream stream);
+
+/* Vector-Jacobian product of the projection at points on the manifold
+ * (implicit-function theorem; the paper makes its log map differentiable "to
+ * enable gradient-based optimization", Sec. IV-A):
+ *   out = g - J^T (J J^T)^{-1} J g   at q_star.
+ * q_star, g, out: float [d * ld]; out may alias g.  flags [n] (may be NULL):
+ * MCP_F_FP64_RESOLVE if the solve fell back to FP64, MCP_F_NONFINITE if
+ * J J^T is singular (out is NaN there). */
+mcp_status mcp_project_vjp(mcp_ctx *ctx, int64_t n, int64_t ld, const float *q_star, const float *g, float *out,
+                           uint8_t *flags, mcp_stream stream);
+
+/* Path length L = sum_i |q_{i+1} - q_i| of n_paths paths of n_way waypoints
+ * and its gradient with respect to every waypoint.  Q: float [d * ld] with
+ * waypoint w of path p at column p * n_way + w; length [n_paths] (may be NULL);
+ * grad [d * ld] (may be NULL).  Zero-length edges contribute no gradient. */
+mcp_status mcp_path_length_grad(mcp_ctx *ctx, int64_t n_paths, int32_t n_way, int64_t ld, const float *Q,
+                                float *length, float *grad, mcp_stream stream);
+
+/* Picks the persistent launch shape (threads per block, blocks per SM, work
+ * chunk) for the loaded problem by timing candidates on n_sample generated
+ * configurations, and caches it in the context.  Synchronous. */
+mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sample, mcp_stream stream);
+
+/* Number of kernels this context has launched so far (for launch accounting). */
+int64_t mcp_launch_count(const mcp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCPROJ_H_ */

@@ -1,0 +1,6 @@
+// Kernel instantiations for the ProbArm7Pose problem class.
+#include "mcp_kernels.cuh"
+
+namespace mcp {
+MCP_INSTANTIATE(ProbArm7Pose)
+}  // namespace mcp

@@ -1,0 +1,904 @@
+// C ABI of libmcproj.so (declared in include/mcproj.h): context, model
+// loading, binding of a loaded robot/constraint stack to a compiled problem
+// class, and the batched entry points.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mcproj.h"
+#include "mcp_device.cuh"
+#include "mcp_internal.h"
+#include "mcp_problems.cuh"
+
+using namespace mcp;
+
+// ---------------------------------------------------------------------------
+// Problem-class registry
+// ---------------------------------------------------------------------------
+namespace {
+
+struct ClassDesc {
+  const char *name;
+  int D, NF, NC;
+  int parent[MAXJ], jtype[MAXJ], xrot[MAXJ], xtmask[MAXJ];
+  int flink[MAXF], frot[MAXF], ftmask[MAXF];
+  int ckind[MAXC], cfa[MAXC], cfb[MAXC];
+  bool project;  // projection / VJP compiled for this class
+  cudaError_t (*project_fn)(const HostModel &, const ProjCall &, int *);
+  cudaError_t (*check_fn)(const HostModel &, const CheckCall &, int *);
+  cudaError_t (*vjp_fn)(const HostModel &, const VjpCall &, int *);
+};
+
+template <class P>
+ClassDesc describe(bool project) {
+  ClassDesc d{};
+  d.name = P::name;
+  d.D = P::D;
+  d.NF = P::NF;
+  d.NC = P::NC;
+  for (int j = 0; j < P::D; ++j) {
+    d.parent[j] = P::parent(j);
+    d.jtype[j] = P::jtype(j);
+    d.xrot[j] = P::xrot(j);
+    d.xtmask[j] = P::xtmask(j);
+  }
+  for (int f = 0; f < P::NF; ++f) {
+    d.flink[f] = P::frame_link(f);
+    d.frot[f] = P::frot(f);
+    d.ftmask[f] = P::ftmask(f);
+  }
+  for (int c = 0; c < P::NC; ++c) {
+    d.ckind[c] = P::ckind(c);
+    d.cfa[c] = P::cfa(c);
+    d.cfb[c] = P::cfb(c);
+  }
+  d.project = project;
+  d.project_fn = &launch_project<P>;
+  d.check_fn = &launch_check<P>;
+  d.vjp_fn = &launch_vjp<P>;
+  return d;
+}
+
+const std::vector<ClassDesc> &registry() {
+  static const std::vector<ClassDesc> r = {describe<ProbSphere3>(true), describe<ProbArm7Axis>(true),
+                                           describe<ProbArm7Pose>(true), describe<ProbDual14Rel>(true),
+                                           describe<ProbHumanoid36>(false)};
+  return r;
+}
+
+// Signed-permutation code of a rotation given exactly (entries 0 / +-1), or XR_GENERIC.
+int rot_code(const double *X) {
+  int code = 0;
+  for (int k = 0; k < 3; ++k) {
+    int row = -1;
+    for (int r = 0; r < 3; ++r) {
+      const double v = X[r * 4 + k];
+      if (v == 0.0) continue;
+      if ((v != 1.0 && v != -1.0) || row >= 0) return XR_GENERIC;
+      row = r;
+    }
+    if (row < 0) return XR_GENERIC;
+    code |= row << (2 * k);
+    if (X[row * 4 + k] < 0) code |= 1 << (6 + k);
+  }
+  return code;
+}
+
+int trans_mask(const double *X) {
+  return (X[3] != 0.0 ? 1 : 0) | (X[7] != 0.0 ? 2 : 0) | (X[11] != 0.0 ? 4 : 0);
+}
+
+struct RobotHost {
+  int nj = 0, ns = 0, nf = 0;
+  std::vector<int> parent, type, sphere_link, frame_link;
+  std::vector<double> X, lower, upper, mass, com, sphere, frame_X;
+};
+
+struct ConsHost {
+  int kind, fa, fb;
+  double P[12], Q[12], target[3];
+  bool has_ref;
+  std::vector<double> q_ref;
+};
+
+// Setup-kernel input (resolution of q_ref references, subtree masses).
+struct ResolveIn {
+  int nj, nf, nc;
+  int parent[MAXJ], type[MAXJ], flink[MAXF];
+  double X[MAXJ][12], fX[MAXF][12], mass[MAXJ];
+  int kind[MAXC], fa[MAXC], fb[MAXC], has_ref[MAXC];
+  double P[MAXC][12], Q[MAXC][12], tgt[MAXC][3];
+  double qref[MAXC][MAXJ];
+};
+struct ResolveOut {
+  double P[MAXC][12], Q[MAXC][12], tgt[MAXC][3];
+  double Pinv[MAXC][12], Qinv[MAXC][12];
+  double msub[MAXJ];
+  double inv_mass;
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Setup kernels (FP64, run once per load)
+// ---------------------------------------------------------------------------
+__global__ void k_sincos_table(double2 *tab) {
+  const int k = threadIdx.x;
+  if (k < 256) {
+    double s, c;
+    sincospi(static_cast<double>(k) / 128.0, &s, &c);
+    tab[k] = make_double2(s, c);
+  }
+}
+
+__device__ void tf_mul64(const double *A, const double *B, double *C) {
+  double o[12];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 4; ++c) {
+      double s = A[r * 4] * B[c] + A[r * 4 + 1] * B[4 + c] + A[r * 4 + 2] * B[8 + c];
+      if (c == 3) s += A[r * 4 + 3];
+      o[r * 4 + c] = s;
+    }
+  for (int i = 0; i < 12; ++i) C[i] = o[i];
+}
+__device__ void tf_inv64(const double *A, double *B) {
+  double o[12];
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) o[r * 4 + c] = A[c * 4 + r];
+    o[r * 4 + 3] = -(A[r] * A[3] + A[4 + r] * A[7] + A[8 + r] * A[11]);
+  }
+  for (int i = 0; i < 12; ++i) B[i] = o[i];
+}
+
+// One thread: FK at each constraint's q_ref (runtime topology), references,
+// inverses, subtree masses.
+__global__ void k_resolve(const __grid_constant__ ResolveIn in, ResolveOut *out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double T[MAXJ][12], Tf[MAXF][12];
+  for (int c = 0; c < in.nc; ++c) {
+    for (int i = 0; i < 12; ++i) {
+      out->P[c][i] = in.P[c][i];
+      out->Q[c][i] = in.Q[c][i];
+    }
+    for (int i = 0; i < 3; ++i) out->tgt[c][i] = in.tgt[c][i];
+    if (in.has_ref[c]) {
+      for (int j = 0; j < in.nj; ++j) {
+        double pre[12], M[12];
+        if (in.parent[j] < 0) {
+          for (int i = 0; i < 12; ++i) pre[i] = in.X[j][i];
+        } else {
+          tf_mul64(T[in.parent[j]], in.X[j], pre);
+        }
+        for (int i = 0; i < 12; ++i) M[i] = 0.0;
+        M[0] = M[5] = M[10] = 1.0;
+        const double qj = in.qref[c][j];
+        if (in.type[j] == REV) {
+          double s, cc;
+          sincos(qj, &s, &cc);
+          M[0] = cc; M[1] = -s; M[4] = s; M[5] = cc;
+        } else {
+          M[11] = qj;
+        }
+        tf_mul64(pre, M, T[j]);
+      }
+      for (int f = 0; f < in.nf; ++f) {
+        if (in.flink[f] < 0) {
+          for (int i = 0; i < 12; ++i) Tf[f][i] = in.fX[f][i];
+        } else {
+          tf_mul64(T[in.flink[f]], in.fX[f], Tf[f]);
+        }
+      }
+      const int a = in.fa[c], b = in.fb[c];
+      if (in.kind[c] == K_POSE) {
+        double Qi[12];
+        tf_inv64(in.Q[c], Qi);
+        tf_mul64(Tf[a], Qi, out->P[c]);
+      } else if (in.kind[c] == K_REL) {
+        double Ai[12];
+        tf_inv64(Tf[a], Ai);
+        tf_mul64(Ai, Tf[b], out->P[c]);
+      } else if (in.kind[c] == K_COM) {
+        out->tgt[c][0] = 0.5 * (Tf[a][3] + Tf[b][3]);
+        out->tgt[c][1] = 0.5 * (Tf[a][7] + Tf[b][7]);
+      }
+    }
+    tf_inv64(out->P[c], out->Pinv[c]);
+    tf_inv64(out->Q[c], out->Qinv[c]);
+  }
+  double M = 0.0;
+  for (int j = in.nj - 1; j >= 0; --j) out->msub[j] = in.mass[j];
+  for (int j = in.nj - 1; j >= 0; --j) {
+    if (in.parent[j] >= 0) out->msub[in.parent[j]] += out->msub[j];
+    M += in.mass[j];
+  }
+  out->inv_mass = M > 0.0 ? 1.0 / M : 0.0;
+}
+
+// Exclusive prefix sum of segment lengths into off[0..n]; one block.
+__global__ void k_scan_lengths(const int32_t *len, long long n, long long *off) {
+  __shared__ long long part[1024];
+  const int t = threadIdx.x;
+  const long long per = (n + blockDim.x - 1) / blockDim.x;
+  const long long b = t * per, e = (b + per < n) ? b + per : n;
+  long long s = 0;
+  for (long long i = b; i < e; ++i) s += len[i] > 0 ? len[i] : 0;
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    long long acc = 0;
+    for (int i = 0; i < static_cast<int>(blockDim.x); ++i) {
+      const long long v = part[i];
+      part[i] = acc;
+      acc += v;
+    }
+    off[n] = acc;
+  }
+  __syncthreads();
+  long long acc = part[t];
+  for (long long i = b; i < e; ++i) {
+    off[i] = acc;
+    acc += len[i] > 0 ? len[i] : 0;
+  }
+}
+
+// Path length and its gradient (thread per waypoint / per path).
+__global__ void k_path_grad(const float *Q, long long ld, long long n_paths, int n_way, int d, float *grad) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n_paths * n_way) return;
+  const int w = static_cast<int>(i % n_way);
+  float ep[MAXJ], en[MAXJ];
+  float np2 = 0.f, nn2 = 0.f;
+  for (int j = 0; j < d; ++j) {
+    const float qi = Q[j * ld + i];
+    ep[j] = (w > 0) ? qi - Q[j * ld + i - 1] : 0.f;
+    en[j] = (w + 1 < n_way) ? Q[j * ld + i + 1] - qi : 0.f;
+    np2 = fmaf(ep[j], ep[j], np2);
+    nn2 = fmaf(en[j], en[j], nn2);
+  }
+  const float ip = np2 > 0.f ? rsqrtf(np2) : 0.f;
+  const float in = nn2 > 0.f ? rsqrtf(nn2) : 0.f;
+  for (int j = 0; j < d; ++j) grad[j * ld + i] = ep[j] * ip - en[j] * in;
+}
+
+__global__ void k_path_length(const float *Q, long long ld, long long n_paths, int n_way, int d, float *length) {
+  const long long p = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (p >= n_paths) return;
+  float L = 0.f;
+  for (int w = 0; w + 1 < n_way; ++w) {
+    const long long i = p * n_way + w;
+    float n2 = 0.f;
+    for (int j = 0; j < d; ++j) {
+      const float e = Q[j * ld + i + 1] - Q[j * ld + i];
+      n2 = fmaf(e, e, n2);
+    }
+    L += sqrtf(n2);
+  }
+  length[p] = L;
+}
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct mcp_ctx {
+  int device = 0;
+  std::string err;
+  bool robot_loaded = false, cons_loaded = false, obs_loaded = false;
+  RobotHost robot;
+  std::vector<ConsHost> cons;
+  HostModel hm;
+  int robot_class = -1;  // class whose robot part matches (collision check)
+  int prob_class = -1;   // class whose robot and constraints match (projection, VJP)
+  ModelT<double> *d_m64 = nullptr;
+  double2 *d_tab = nullptr;
+  float4 *d_obs32 = nullptr;
+  double *d_obs64 = nullptr;
+  float4 *d_box32 = nullptr;
+  double *d_box64 = nullptr;
+  unsigned long long *d_counter = nullptr;
+  long long *d_seg_off = nullptr;
+  long long seg_cap = 0;
+  ResolveOut *d_resolve = nullptr;
+  Tuning tune;
+  bool tuned = false;
+  int64_t launches = 0;
+};
+
+namespace {
+
+mcp_status fail(mcp_ctx *c, mcp_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+mcp_status cuda_fail(mcp_ctx *c, cudaError_t e, const char *what) {
+  return fail(c, e == cudaErrorMemoryAllocation ? MCP_ERR_OOM : MCP_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define MCP_CUDA(call, what)                                    \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what);     \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool robot_matches(const ClassDesc &d, const RobotHost &r) {
+  if (d.D != r.nj || d.NF != r.nf) return false;
+  for (int j = 0; j < r.nj; ++j) {
+    if (d.parent[j] != r.parent[j] || d.jtype[j] != r.type[j]) return false;
+    const int code = rot_code(&r.X[12 * j]);
+    if (d.xrot[j] != XR_GENERIC && d.xrot[j] != code) return false;
+    if (d.parent[j] >= 0 && (trans_mask(&r.X[12 * j]) & ~d.xtmask[j])) return false;
+  }
+  for (int f = 0; f < r.nf; ++f) {
+    if (d.flink[f] != r.frame_link[f]) return false;
+    const int code = rot_code(&r.frame_X[12 * f]);
+    if (d.frot[f] != XR_GENERIC && d.frot[f] != code) return false;
+    if (trans_mask(&r.frame_X[12 * f]) & ~d.ftmask[f]) return false;
+  }
+  return true;
+}
+
+bool cons_match(const ClassDesc &d, const std::vector<ConsHost> &c) {
+  if (d.NC != static_cast<int>(c.size())) return false;
+  for (int i = 0; i < d.NC; ++i) {
+    if (d.ckind[i] != c[i].kind) return false;
+    const bool uses_a = c[i].kind == K_AXIS || c[i].kind == K_POSE || c[i].kind == K_REL;
+    const bool uses_b = c[i].kind == K_REL;
+    if (uses_a && d.cfa[i] != c[i].fa) return false;
+    if (uses_b && d.cfb[i] != c[i].fb) return false;
+  }
+  return true;
+}
+
+void bind_classes(mcp_ctx *ctx) {
+  ctx->robot_class = -1;
+  ctx->prob_class = -1;
+  const auto &reg = registry();
+  for (int i = 0; i < static_cast<int>(reg.size()); ++i) {
+    if (!ctx->robot_loaded || !robot_matches(reg[i], ctx->robot)) continue;
+    if (ctx->robot_class < 0) ctx->robot_class = i;
+    if (ctx->cons_loaded && reg[i].project && cons_match(reg[i], ctx->cons)) {
+      ctx->prob_class = i;
+      ctx->robot_class = i;
+      break;
+    }
+  }
+}
+
+template <typename T>
+void fill_sphere_table(const RobotHost &r, SphereTable<T> &st) {
+  std::memset(&st, 0, sizeof(st));
+  int n = 0;
+  for (int l = -1; l < r.nj; ++l) {
+    st.off[l + 1] = static_cast<int16_t>(n);
+    for (int s = 0; s < r.ns; ++s) {
+      if (r.sphere_link[s] != l) continue;
+      for (int i = 0; i < 4; ++i) st.s[n][i] = static_cast<T>(r.sphere[4 * s + i]);
+      ++n;
+    }
+  }
+  st.off[r.nj + 1] = static_cast<int16_t>(n);
+  for (int l = r.nj + 2; l < MAXJ + 2; ++l) st.off[l] = static_cast<int16_t>(n);
+}
+
+template <typename T>
+void fill_robot_model(const RobotHost &r, ModelT<T> &m) {
+  std::memset(&m, 0, sizeof(m));
+  for (int j = 0; j < r.nj; ++j) {
+    for (int i = 0; i < 12; ++i) m.X[j][i] = static_cast<T>(r.X[12 * j + i]);
+    m.mass[j] = static_cast<T>(r.mass[j]);
+    for (int i = 0; i < 3; ++i) m.com[j][i] = static_cast<T>(r.com[3 * j + i]);
+    m.lower[j] = static_cast<T>(r.lower[j]);
+    m.upper[j] = static_cast<T>(r.upper[j]);
+  }
+  for (int f = 0; f < r.nf; ++f)
+    for (int i = 0; i < 12; ++i) m.fX[f][i] = static_cast<T>(r.frame_X[12 * f + i]);
+}
+
+template <typename T>
+void fill_constraints(const ResolveOut &ro, int nc, int nj, ModelT<T> &m) {
+  for (int c = 0; c < nc; ++c) {
+    for (int i = 0; i < 12; ++i) {
+      m.cPinv[c][i] = static_cast<T>(ro.Pinv[c][i]);
+      m.cQinv[c][i] = static_cast<T>(ro.Qinv[c][i]);
+    }
+    for (int i = 0; i < 3; ++i) m.ctgt[c][i] = static_cast<T>(ro.tgt[c][i]);
+  }
+  for (int j = 0; j < nj; ++j) m.msub[j] = static_cast<T>(ro.msub[j]);
+  m.inv_mass = static_cast<T>(ro.inv_mass);
+}
+
+mcp_status check_batch_ptr(mcp_ctx *ctx, const void *p, const char *name) {
+  if (!p) return fail(ctx, MCP_ERR_ARG, "%s is NULL", name);
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, MCP_ERR_ARG, "%s is not a CUDA-visible pointer", name);
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    return fail(ctx, MCP_ERR_ARG, "%s must be device memory", name);
+  return MCP_OK;
+}
+
+mcp_status ensure_resolved(mcp_ctx *ctx) {
+  // (re)build FP32/FP64 models from the loaded robot and constraints
+  DeviceGuard g(ctx->device);
+  ResolveIn *in = new (std::nothrow) ResolveIn;
+  if (!in) return fail(ctx, MCP_ERR_OOM, "host allocation failed");
+  std::memset(in, 0, sizeof(ResolveIn));
+  const RobotHost &r = ctx->robot;
+  in->nj = r.nj;
+  in->nf = r.nf;
+  in->nc = static_cast<int>(ctx->cons.size());
+  for (int j = 0; j < r.nj; ++j) {
+    in->parent[j] = r.parent[j];
+    in->type[j] = r.type[j];
+    in->mass[j] = r.mass[j];
+    for (int i = 0; i < 12; ++i) in->X[j][i] = r.X[12 * j + i];
+  }
+  for (int f = 0; f < r.nf; ++f) {
+    in->flink[f] = r.frame_link[f];
+    for (int i = 0; i < 12; ++i) in->fX[f][i] = r.frame_X[12 * f + i];
+  }
+  for (int c = 0; c < in->nc; ++c) {
+    const ConsHost &ch = ctx->cons[c];
+    in->kind[c] = ch.kind;
+    in->fa[c] = ch.fa;
+    in->fb[c] = ch.fb;
+    in->has_ref[c] = ch.has_ref ? 1 : 0;
+    for (int i = 0; i < 12; ++i) {
+      in->P[c][i] = ch.P[i];
+      in->Q[c][i] = ch.Q[i];
+    }
+    for (int i = 0; i < 3; ++i) in->tgt[c][i] = ch.target[i];
+    if (ch.has_ref)
+      for (int j = 0; j < r.nj; ++j) in->qref[c][j] = ch.q_ref[j];
+  }
+  if (!ctx->d_resolve) {
+    cudaError_t e = cudaMalloc(&ctx->d_resolve, sizeof(ResolveOut));
+    if (e != cudaSuccess) {
+      delete in;
+      return cuda_fail(ctx, e, "cudaMalloc");
+    }
+  }
+  k_resolve<<<1, 32>>>(*in, ctx->d_resolve);
+  ctx->launches += 1;
+  delete in;
+  ResolveOut ro;
+  MCP_CUDA(cudaGetLastError(), "resolve kernel launch");
+  MCP_CUDA(cudaMemcpy(&ro, ctx->d_resolve, sizeof(ro), cudaMemcpyDeviceToHost), "resolve copy");
+  for (int c = 0; c < static_cast<int>(ctx->cons.size()); ++c) {
+    std::memcpy(ctx->cons[c].P, ro.P[c], sizeof(ro.P[c]));
+    std::memcpy(ctx->cons[c].Q, ro.Q[c], sizeof(ro.Q[c]));
+    std::memcpy(ctx->cons[c].target, ro.tgt[c], sizeof(ro.tgt[c]));
+  }
+  fill_robot_model(r, ctx->hm.m32);
+  fill_robot_model(r, ctx->hm.m64);
+  fill_constraints(ro, static_cast<int>(ctx->cons.size()), r.nj, ctx->hm.m32);
+  fill_constraints(ro, static_cast<int>(ctx->cons.size()), r.nj, ctx->hm.m64);
+  fill_sphere_table(r, ctx->hm.st32);
+  fill_sphere_table(r, ctx->hm.st64);
+  MCP_CUDA(cudaMemcpy(ctx->d_m64, &ctx->hm.m64, sizeof(ModelT<double>), cudaMemcpyHostToDevice), "model copy");
+  return MCP_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+mcp_status mcp_create(int device, mcp_ctx **out) {
+  if (!out) return MCP_ERR_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return MCP_ERR_ARG;
+  }
+  mcp_ctx *ctx = new (std::nothrow) mcp_ctx;
+  if (!ctx) return MCP_ERR_OOM;
+  ctx->device = device;
+  DeviceGuard g(device);
+  int sms = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  ctx->hm.sm_count = sms;
+  cudaError_t e = cudaMalloc(&ctx->d_m64, sizeof(ModelT<double>));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tab, 256 * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counter, sizeof(unsigned long long));
+  if (e == cudaSuccess) {
+    k_sincos_table<<<1, 256>>>(ctx->d_tab);
+    ctx->launches += 1;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    mcp_destroy(ctx);
+    return MCP_ERR_CUDA;
+  }
+  ctx->hm.d_m64 = ctx->d_m64;
+  ctx->hm.d_tab = ctx->d_tab;
+  *out = ctx;
+  return MCP_OK;
+}
+
+void mcp_destroy(mcp_ctx *ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  cudaFree(ctx->d_m64);
+  cudaFree(ctx->d_tab);
+  cudaFree(ctx->d_obs32);
+  cudaFree(ctx->d_obs64);
+  cudaFree(ctx->d_box32);
+  cudaFree(ctx->d_box64);
+  cudaFree(ctx->d_counter);
+  cudaFree(ctx->d_seg_off);
+  cudaFree(ctx->d_resolve);
+  delete ctx;
+}
+
+const char *mcp_last_error(const mcp_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int64_t mcp_launch_count(const mcp_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+mcp_status mcp_load_robot(mcp_ctx *ctx, const mcp_robot_desc *rd) {
+  if (!ctx) return MCP_ERR_ARG;
+  if (!rd) return fail(ctx, MCP_ERR_ARG, "robot descriptor is NULL");
+  const int nj = rd->n_joints;
+  if (nj < 1 || nj > MCP_MAX_JOINTS) return fail(ctx, MCP_ERR_ARG, "n_joints %d outside [1, %d]", nj, MCP_MAX_JOINTS);
+  if (rd->n_spheres < 0 || rd->n_spheres > MCP_MAX_SPHERES)
+    return fail(ctx, MCP_ERR_ARG, "n_spheres %d outside [0, %d]", rd->n_spheres, MCP_MAX_SPHERES);
+  if (rd->n_frames < 0 || rd->n_frames > MCP_MAX_FRAMES)
+    return fail(ctx, MCP_ERR_ARG, "n_frames %d outside [0, %d]", rd->n_frames, MCP_MAX_FRAMES);
+  if (!rd->parent || !rd->type || !rd->X || !rd->lower || !rd->upper)
+    return fail(ctx, MCP_ERR_ARG, "robot arrays parent/type/X/lower/upper are required");
+  if (rd->n_spheres > 0 && (!rd->sphere_link || !rd->sphere)) return fail(ctx, MCP_ERR_ARG, "sphere arrays missing");
+  if (rd->n_frames > 0 && (!rd->frame_link || !rd->frame_X)) return fail(ctx, MCP_ERR_ARG, "frame arrays missing");
+  RobotHost r;
+  r.nj = nj;
+  r.ns = rd->n_spheres;
+  r.nf = rd->n_frames;
+  for (int j = 0; j < nj; ++j) {
+    if (rd->parent[j] < -1 || rd->parent[j] >= j)
+      return fail(ctx, MCP_ERR_ARG, "parent[%d] = %d must be in [-1, %d)", j, rd->parent[j], j);
+    if (rd->type[j] != REV && rd->type[j] != PRIS) return fail(ctx, MCP_ERR_ARG, "type[%d] = %d", j, rd->type[j]);
+  }
+  r.parent.assign(rd->parent, rd->parent + nj);
+  r.type.assign(rd->type, rd->type + nj);
+  r.X.assign(rd->X, rd->X + 12 * nj);
+  r.lower.assign(rd->lower, rd->lower + nj);
+  r.upper.assign(rd->upper, rd->upper + nj);
+  if (rd->mass) r.mass.assign(rd->mass, rd->mass + nj);
+  else r.mass.assign(nj, 0.0);
+  if (rd->com) r.com.assign(rd->com, rd->com + 3 * nj);
+  else r.com.assign(3 * nj, 0.0);
+  for (int s = 0; s < r.ns; ++s)
+    if (rd->sphere_link[s] < -1 || rd->sphere_link[s] >= nj)
+      return fail(ctx, MCP_ERR_ARG, "sphere_link[%d] = %d out of range", s, rd->sphere_link[s]);
+  for (int f = 0; f < r.nf; ++f)
+    if (rd->frame_link[f] < -1 || rd->frame_link[f] >= nj)
+      return fail(ctx, MCP_ERR_ARG, "frame_link[%d] = %d out of range", f, rd->frame_link[f]);
+  if (r.ns) {
+    r.sphere_link.assign(rd->sphere_link, rd->sphere_link + r.ns);
+    r.sphere.assign(rd->sphere, rd->sphere + 4 * r.ns);
+  }
+  if (r.nf) {
+    r.frame_link.assign(rd->frame_link, rd->frame_link + r.nf);
+    r.frame_X.assign(rd->frame_X, rd->frame_X + 12 * r.nf);
+  }
+  ctx->robot = std::move(r);
+  ctx->robot_loaded = true;
+  ctx->cons.clear();
+  ctx->cons_loaded = false;
+  ctx->tuned = false;
+  bind_classes(ctx);
+  return ensure_resolved(ctx);
+}
+
+mcp_status mcp_load_constraints(mcp_ctx *ctx, const mcp_constraint_desc *cd, int32_t n) {
+  if (!ctx) return MCP_ERR_ARG;
+  if (!ctx->robot_loaded) return fail(ctx, MCP_ERR_STATE, "load the robot before the constraints");
+  if (n < 0 || n > MCP_MAX_CONSTRAINTS) return fail(ctx, MCP_ERR_ARG, "n = %d outside [0, %d]", n, MCP_MAX_CONSTRAINTS);
+  if (n > 0 && !cd) return fail(ctx, MCP_ERR_ARG, "constraint array is NULL");
+  std::vector<ConsHost> cons;
+  int k = 0;
+  for (int i = 0; i < n; ++i) {
+    const mcp_constraint_desc &c = cd[i];
+    if (c.kind < MCP_C_SPHERE || c.kind > MCP_C_COM_XY) return fail(ctx, MCP_ERR_ARG, "constraint %d: kind %d", i, c.kind);
+    const bool uses_a = c.kind == MCP_C_AXIS_ALIGN || c.kind == MCP_C_POSE || c.kind == MCP_C_REL_POSE ||
+                        (c.kind == MCP_C_COM_XY && c.q_ref);
+    const bool uses_b = c.kind == MCP_C_REL_POSE || (c.kind == MCP_C_COM_XY && c.q_ref);
+    if (uses_a && (c.frame_a < 0 || c.frame_a >= ctx->robot.nf))
+      return fail(ctx, MCP_ERR_ARG, "constraint %d: frame_a %d out of range", i, c.frame_a);
+    if (uses_b && (c.frame_b < 0 || c.frame_b >= ctx->robot.nf))
+      return fail(ctx, MCP_ERR_ARG, "constraint %d: frame_b %d out of range", i, c.frame_b);
+    ConsHost h;
+    h.kind = c.kind;
+    h.fa = c.frame_a;
+    h.fb = c.frame_b;
+    std::memcpy(h.P, c.P, sizeof(h.P));
+    std::memcpy(h.Q, c.Q, sizeof(h.Q));
+    std::memcpy(h.target, c.target, sizeof(h.target));
+    h.has_ref = c.q_ref != nullptr;
+    if (h.has_ref) h.q_ref.assign(c.q_ref, c.q_ref + ctx->robot.nj);
+    k += cdim(c.kind);
+    cons.push_back(std::move(h));
+  }
+  if (k > MCP_MAX_EQUATIONS) return fail(ctx, MCP_ERR_ARG, "%d equations > %d", k, MCP_MAX_EQUATIONS);
+  ctx->cons = std::move(cons);
+  ctx->cons_loaded = true;
+  ctx->tuned = false;
+  bind_classes(ctx);
+  return ensure_resolved(ctx);
+}
+
+mcp_status mcp_get_constraint(const mcp_ctx *ctx, int32_t i, double *P, double *Q, double *target) {
+  if (!ctx || i < 0 || i >= static_cast<int>(ctx->cons.size())) return MCP_ERR_ARG;
+  if (P) std::memcpy(P, ctx->cons[i].P, 12 * sizeof(double));
+  if (Q) std::memcpy(Q, ctx->cons[i].Q, 12 * sizeof(double));
+  if (target) std::memcpy(target, ctx->cons[i].target, 3 * sizeof(double));
+  return MCP_OK;
+}
+
+mcp_status mcp_load_obstacles(mcp_ctx *ctx, const double *spheres, int32_t n_spheres, const double *aabbs,
+                              int32_t n_aabbs) {
+  if (!ctx) return MCP_ERR_ARG;
+  if (n_spheres < 0 || n_spheres > MCP_MAX_OBSTACLES || n_aabbs < 0 || n_aabbs > MCP_MAX_AABBS)
+    return fail(ctx, MCP_ERR_ARG, "obstacle counts %d / %d outside [0, %d] / [0, %d]", n_spheres, n_aabbs,
+                MCP_MAX_OBSTACLES, MCP_MAX_AABBS);
+  if ((n_spheres && !spheres) || (n_aabbs && !aabbs)) return fail(ctx, MCP_ERR_ARG, "obstacle array is NULL");
+  DeviceGuard g(ctx->device);
+  cudaFree(ctx->d_obs32);
+  cudaFree(ctx->d_obs64);
+  cudaFree(ctx->d_box32);
+  cudaFree(ctx->d_box64);
+  ctx->d_obs32 = nullptr;
+  ctx->d_obs64 = nullptr;
+  ctx->d_box32 = nullptr;
+  ctx->d_box64 = nullptr;
+  std::vector<float4> o32(n_spheres > 0 ? n_spheres : 1);
+  for (int i = 0; i < n_spheres; ++i)
+    o32[i] = make_float4(static_cast<float>(spheres[4 * i]), static_cast<float>(spheres[4 * i + 1]),
+                         static_cast<float>(spheres[4 * i + 2]), static_cast<float>(spheres[4 * i + 3]));
+  std::vector<float> b32(6 * (n_aabbs > 0 ? n_aabbs : 1));
+  for (int i = 0; i < 6 * n_aabbs; ++i) b32[i] = static_cast<float>(aabbs[i]);
+  const size_t n_o = static_cast<size_t>(n_spheres > 0 ? n_spheres : 1);
+  const size_t n_b = static_cast<size_t>(n_aabbs > 0 ? n_aabbs : 1);
+  MCP_CUDA(cudaMalloc(&ctx->d_obs32, n_o * sizeof(float4)), "cudaMalloc obstacles");
+  MCP_CUDA(cudaMalloc(&ctx->d_obs64, n_o * 4 * sizeof(double)), "cudaMalloc obstacles");
+  MCP_CUDA(cudaMalloc(&ctx->d_box32, n_b * 6 * sizeof(float)), "cudaMalloc boxes");
+  MCP_CUDA(cudaMalloc(&ctx->d_box64, n_b * 6 * sizeof(double)), "cudaMalloc boxes");
+  if (n_spheres) {
+    MCP_CUDA(cudaMemcpy(ctx->d_obs32, o32.data(), n_spheres * sizeof(float4), cudaMemcpyHostToDevice), "copy");
+    MCP_CUDA(cudaMemcpy(ctx->d_obs64, spheres, n_spheres * 4 * sizeof(double), cudaMemcpyHostToDevice), "copy");
+  }
+  if (n_aabbs) {
+    MCP_CUDA(cudaMemcpy(ctx->d_box32, b32.data(), n_aabbs * 6 * sizeof(float), cudaMemcpyHostToDevice), "copy");
+    MCP_CUDA(cudaMemcpy(ctx->d_box64, aabbs, n_aabbs * 6 * sizeof(double), cudaMemcpyHostToDevice), "copy");
+  }
+  ctx->hm.d_obs32 = ctx->d_obs32;
+  ctx->hm.d_obs64 = ctx->d_obs64;
+  ctx->hm.d_box32 = ctx->d_box32;
+  ctx->hm.d_box64 = ctx->d_box64;
+  ctx->hm.n_obs = n_spheres;
+  ctx->hm.n_box = n_aabbs;
+  ctx->obs_loaded = true;
+  return MCP_OK;
+}
+
+static mcp_status validate_params(mcp_ctx *ctx, const mcp_project_params *p) {
+  if (!p) return fail(ctx, MCP_ERR_ARG, "params is NULL");
+  if (!(p->tol > 0.0) || !std::isfinite(p->tol)) return fail(ctx, MCP_ERR_ARG, "tol must be positive");
+  if (p->max_iters < 0 || p->max_iters > 255) return fail(ctx, MCP_ERR_ARG, "max_iters %d outside [0, 255]", p->max_iters);
+  if (p->precision != 0 && p->precision != 1) return fail(ctx, MCP_ERR_ARG, "precision %d", p->precision);
+  if (!(p->lambda >= 0.0) || !std::isfinite(p->lambda)) return fail(ctx, MCP_ERR_ARG, "lambda must be >= 0");
+  if (!std::isfinite(p->max_step) || !std::isfinite(p->pivot_fp64)) return fail(ctx, MCP_ERR_ARG, "non-finite parameter");
+  if (!ctx->robot_loaded || !ctx->cons_loaded) return fail(ctx, MCP_ERR_STATE, "robot and constraints must be loaded");
+  if (ctx->prob_class < 0)
+    return fail(ctx, MCP_ERR_UNSUPPORTED, "the loaded robot / constraint stack matches no compiled problem class");
+  return MCP_OK;
+}
+
+static void fill_call(mcp_ctx *ctx, const mcp_project_params *p, ProjCall &c, cudaStream_t s) {
+  c.precision = p->precision;
+  c.tol = p->tol;
+  c.cap = p->max_iters;
+  c.lambda = p->lambda;
+  c.max_step = p->max_step;
+  c.pivot = p->pivot_fp64;
+  c.counter = ctx->d_counter;
+  c.tune = ctx->tune;
+  c.stream = s;
+}
+
+mcp_status mcp_project_batch(mcp_ctx *ctx, const mcp_project_params *p, int64_t n, int64_t ld, const void *q_in,
+                             void *q_out, uint8_t *flags, uint8_t *iters, double *resid, mcp_stream stream) {
+  if (!ctx) return MCP_ERR_ARG;
+  mcp_status st = validate_params(ctx, p);
+  if (st != MCP_OK) return st;
+  if (n < 0 || ld < n) return fail(ctx, MCP_ERR_ARG, "need 0 <= n <= ld (n = %lld, ld = %lld)", (long long)n, (long long)ld);
+  if (n == 0) return MCP_OK;
+  const char *names[5] = {"q_in", "q_out", "flags", "iters", "resid"};
+  const void *ptrs[5] = {q_in, q_out, flags, iters, resid};
+  for (int i = 0; i < 5; ++i)
+    if ((st = check_batch_ptr(ctx, ptrs[i], names[i])) != MCP_OK) return st;
+  DeviceGuard g(ctx->device);
+  ProjCall c;
+  fill_call(ctx, p, c, reinterpret_cast<cudaStream_t>(stream));
+  c.q_in = q_in;
+  c.ld_in = ld;
+  c.total = n;
+  c.q_out = q_out;
+  c.ld_out = ld;
+  c.flags = flags;
+  c.iters = iters;
+  c.resid = resid;
+  int launches = 0;
+  cudaError_t e = registry()[ctx->prob_class].project_fn(ctx->hm, c, &launches);
+  ctx->launches += launches;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "project_batch launch");
+  return MCP_OK;
+}
+
+mcp_status mcp_project_segments(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_seg, int64_t ld_seg,
+                                const void *start, const void *delta, const int32_t *len, int64_t total,
+                                int64_t ld_out, void *q_out, uint8_t *flags, uint8_t *iters, double *resid,
+                                mcp_stream stream) {
+  if (!ctx) return MCP_ERR_ARG;
+  mcp_status st = validate_params(ctx, p);
+  if (st != MCP_OK) return st;
+  if (n_seg < 0 || ld_seg < n_seg || n_seg > (1ll << 31) - 1)
+    return fail(ctx, MCP_ERR_ARG, "need 0 <= n_seg <= ld_seg, n_seg < 2^31");
+  if (total < 0 || ld_out < total) return fail(ctx, MCP_ERR_ARG, "need 0 <= total <= ld_out");
+  if (n_seg == 0 || total == 0) return MCP_OK;
+  const char *names[7] = {"start", "delta", "len", "q_out", "flags", "iters", "resid"};
+  const void *ptrs[7] = {start, delta, len, q_out, flags, iters, resid};
+  for (int i = 0; i < 7; ++i)
+    if ((st = check_batch_ptr(ctx, ptrs[i], names[i])) != MCP_OK) return st;
+  DeviceGuard g(ctx->device);
+  if (ctx->seg_cap < n_seg + 1) {
+    cudaFree(ctx->d_seg_off);
+    ctx->d_seg_off = nullptr;
+    ctx->seg_cap = 0;
+    MCP_CUDA(cudaMalloc(&ctx->d_seg_off, (n_seg + 1) * sizeof(long long)), "cudaMalloc segment offsets");
+    ctx->seg_cap = n_seg + 1;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  k_scan_lengths<<<1, 1024, 0, s>>>(len, n_seg, ctx->d_seg_off);
+  ctx->launches += 1;
+  MCP_CUDA(cudaGetLastError(), "segment scan launch");
+  ProjCall c;
+  fill_call(ctx, p, c, s);
+  c.segments = true;
+  c.start = start;
+  c.delta = delta;
+  c.ld_seg = ld_seg;
+  c.seg_off = ctx->d_seg_off;
+  c.n_seg = static_cast<int>(n_seg);
+  c.total = total;
+  c.q_out = q_out;
+  c.ld_out = ld_out;
+  c.flags = flags;
+  c.iters = iters;
+  c.resid = resid;
+  int launches = 0;
+  cudaError_t e = registry()[ctx->prob_class].project_fn(ctx->hm, c, &launches);
+  ctx->launches += launches;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "project_segments launch");
+  return MCP_OK;
+}
+
+mcp_status mcp_check_batch(mcp_ctx *ctx, int64_t n, int64_t ld, const void *q, int32_t precision,
+                           uint8_t *in_collision, mcp_stream stream) {
+  if (!ctx) return MCP_ERR_ARG;
+  if (!ctx->robot_loaded) return fail(ctx, MCP_ERR_STATE, "robot not loaded");
+  if (!ctx->obs_loaded) return fail(ctx, MCP_ERR_STATE, "obstacles not loaded");
+  if (ctx->robot_class < 0) return fail(ctx, MCP_ERR_UNSUPPORTED, "the loaded robot matches no compiled problem class");
+  if (precision != 0 && precision != 1) return fail(ctx, MCP_ERR_ARG, "precision %d", precision);
+  if (n < 0 || ld < n) return fail(ctx, MCP_ERR_ARG, "need 0 <= n <= ld");
+  if (n == 0) return MCP_OK;
+  mcp_status st;
+  if ((st = check_batch_ptr(ctx, q, "q")) != MCP_OK) return st;
+  if ((st = check_batch_ptr(ctx, in_collision, "in_collision")) != MCP_OK) return st;
+  DeviceGuard g(ctx->device);
+  CheckCall c;
+  c.precision = precision;
+  c.n = n;
+  c.ld = ld;
+  c.q = q;
+  c.out = in_collision;
+  c.stream = reinterpret_cast<cudaStream_t>(stream);
+  int launches = 0;
+  cudaError_t e = registry()[ctx->robot_class].check_fn(ctx->hm, c, &launches);
+  ctx->launches += launches;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "check_batch launch");
+  return MCP_OK;
+}
+
+mcp_status mcp_project_vjp(mcp_ctx *ctx, int64_t n, int64_t ld, const float *q_star, const float *g, float *out,
+                           uint8_t *flags, mcp_stream stream) {
+  if (!ctx) return MCP_ERR_ARG;
+  if (!ctx->robot_loaded || !ctx->cons_loaded) return fail(ctx, MCP_ERR_STATE, "robot and constraints must be loaded");
+  if (ctx->prob_class < 0) return fail(ctx, MCP_ERR_UNSUPPORTED, "no compiled problem class for this stack");
+  if (n < 0 || ld < n) return fail(ctx, MCP_ERR_ARG, "need 0 <= n <= ld");
+  if (n == 0) return MCP_OK;
+  mcp_status st;
+  if ((st = check_batch_ptr(ctx, q_star, "q_star")) != MCP_OK) return st;
+  if ((st = check_batch_ptr(ctx, g, "g")) != MCP_OK) return st;
+  if ((st = check_batch_ptr(ctx, out, "out")) != MCP_OK) return st;
+  if (flags && (st = check_batch_ptr(ctx, flags, "flags")) != MCP_OK) return st;
+  DeviceGuard gd(ctx->device);
+  VjpCall c;
+  c.n = n;
+  c.ld = ld;
+  c.q = q_star;
+  c.g = g;
+  c.out = out;
+  c.flags = flags;
+  c.stream = reinterpret_cast<cudaStream_t>(stream);
+  int launches = 0;
+  cudaError_t e = registry()[ctx->prob_class].vjp_fn(ctx->hm, c, &launches);
+  ctx->launches += launches;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "project_vjp launch");
+  return MCP_OK;
+}
+
+mcp_status mcp_path_length_grad(mcp_ctx *ctx, int64_t n_paths, int32_t n_way, int64_t ld, const float *Q,
+                                float *length, float *grad, mcp_stream stream) {
+  if (!ctx) return MCP_ERR_ARG;
+  if (!ctx->robot_loaded) return fail(ctx, MCP_ERR_STATE, "robot not loaded");
+  if (n_paths < 0 || n_way < 1 || ld < n_paths * n_way) return fail(ctx, MCP_ERR_ARG, "need ld >= n_paths * n_way");
+  if (n_paths == 0) return MCP_OK;
+  mcp_status st;
+  if ((st = check_batch_ptr(ctx, Q, "Q")) != MCP_OK) return st;
+  if (length && (st = check_batch_ptr(ctx, length, "length")) != MCP_OK) return st;
+  if (grad && (st = check_batch_ptr(ctx, grad, "grad")) != MCP_OK) return st;
+  DeviceGuard gd(ctx->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int d = ctx->robot.nj;
+  if (grad) {
+    const long long n = n_paths * n_way;
+    k_path_grad<<<static_cast<unsigned>((n + 127) / 128), 128, 0, s>>>(Q, ld, n_paths, n_way, d, grad);
+    ctx->launches += 1;
+    MCP_CUDA(cudaGetLastError(), "path gradient launch");
+  }
+  if (length) {
+    k_path_length<<<static_cast<unsigned>((n_paths + 127) / 128), 128, 0, s>>>(Q, ld, n_paths, n_way, d, length);
+    ctx->launches += 1;
+    MCP_CUDA(cudaGetLastError(), "path length launch");
+  }
+  return MCP_OK;
+}
+
+mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sample, mcp_stream stream) {
+  if (!ctx) return MCP_ERR_ARG;
+  (void)p;
+  (void)n_sample;
+  (void)stream;
+  return fail(ctx, MCP_ERR_UNSUPPORTED, "autotune not available yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// Host-side structures shared by the C ABI (mcp_api.cu) and the per-class
+// kernel instantiations (inst_*.cu).  Not part of the public interface.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "mcp_device.cuh"
+
+namespace mcp {
+
+constexpr int MAXS = 256;  // robot spheres per robot
+
+// Robot spheres sorted by the joint they ride on: spheres of link l (l = -1
+// for world-fixed ones) are s[off[l + 1]] .. s[off[l + 2] - 1].
+template <typename T>
+struct SphereTable {
+  T s[MAXS][4];
+  int16_t off[MAXJ + 2];
+};
+
+struct Tuning {
+  int tpb = 128;          // threads per block of the persistent kernel
+  int blocks_per_sm = 4;  // resident blocks per SM
+  int chunk = 32;         // configurations a warp claims per atomic
+};
+
+struct HostModel {
+  ModelT<float> m32;
+  ModelT<double> m64;
+  SphereTable<float> st32;
+  SphereTable<double> st64;
+  const ModelT<double> *d_m64 = nullptr;  // device copy of m64
+  const double2 *d_tab = nullptr;         // FP64 sin/cos table, 256 entries
+  const float4 *d_obs32 = nullptr;        // obstacle spheres (x, y, z, r)
+  const double *d_obs64 = nullptr;        // [n_obs * 4]
+  const float4 *d_box32 = nullptr;        // boxes as (lo.xyz, 0), (hi.xyz, 0)
+  const double *d_box64 = nullptr;        // [n_box * 6]
+  int n_obs = 0;
+  int n_box = 0;
+  int sm_count = 1;
+};
+
+struct ProjCall {
+  int precision = 0;
+  double tol = 1e-5;
+  int cap = 30;
+  double lambda = 0.0;
+  double max_step = 0.0;
+  double pivot = 1e-7;
+  bool segments = false;
+  // batch source
+  const void *q_in = nullptr;
+  long long ld_in = 0;
+  // segment source
+  const void *start = nullptr;
+  const void *delta = nullptr;
+  long long ld_seg = 0;
+  const long long *seg_off = nullptr;  // [n_seg + 1] exclusive prefix sums (device)
+  int n_seg = 0;
+  long long total = 0;
+  // outputs
+  void *q_out = nullptr;
+  long long ld_out = 0;
+  uint8_t *flags = nullptr;
+  uint8_t *iters = nullptr;
+  double *resid = nullptr;
+  unsigned long long *counter = nullptr;  // zeroed work counter (device)
+  Tuning tune;
+  cudaStream_t stream = 0;
+};
+
+struct CheckCall {
+  int precision = 0;
+  long long n = 0, ld = 0;
+  const void *q = nullptr;
+  uint8_t *out = nullptr;
+  cudaStream_t stream = 0;
+};
+
+struct VjpCall {
+  long long n = 0, ld = 0;
+  const float *q = nullptr;
+  const float *g = nullptr;
+  float *out = nullptr;
+  uint8_t *flags = nullptr;
+  double pivot = 1e-7;
+  cudaStream_t stream = 0;
+};
+
+// Launchers, one explicit instantiation per problem class.  Each returns the
+// CUDA error of its launch and adds the number of kernels it launched.
+template <class P>
+cudaError_t launch_project(const HostModel &hm, const ProjCall &c, int *launches);
+template <class P>
+cudaError_t launch_check(const HostModel &hm, const CheckCall &c, int *launches);
+template <class P>
+cudaError_t launch_vjp(const HostModel &hm, const VjpCall &c, int *launches);
+
+}  // namespace mcp

@@ -1,0 +1,1101 @@
+// Kernel templates of the projection path, instantiated per problem class in
+// inst_*.cu.  Building blocks are in mcp_device.cuh.
+//
+// Projection follows ParallelProject / getDescentStep of Algorithm 2 with the
+// stacked constraint (Sec. IV-C) and the inner LM form
+//     q <- q - J^T (J J^T + lambda I)^{-1} F(q)
+// (Sec. IV-A, "Vectorized Levenberg-Marquardt"), stopping per configuration
+// when ||F|| < tol, at the iteration cap, or on a step longer than MaxDistance.
+#pragma once
+
+#include <cfloat>
+
+#include <math_constants.h>
+
+#include "mcp_device.cuh"
+#include "mcp_internal.h"
+#include "mcp_problems.cuh"
+
+namespace mcp {
+
+constexpr unsigned FULL = 0xffffffffu;
+// internal flag bits (never written out)
+constexpr uint32_t FL_INT_FP32CONV = 1u << 8;   // FP32 residual passed; FP64 check pending
+constexpr uint32_t FL_INT_NEEDS_F64 = 1u << 9;  // FP32 pivot below threshold: continue in FP64
+
+// ---------------------------------------------------------------------------
+// Stacked residual F(q) and Jacobian J(q)
+// ---------------------------------------------------------------------------
+template <class P, typename T>
+struct Eval {
+  V3<T> x[P::NC];    // POSE: world origin of T_a Q^-1; REL: p_b
+  T G[P::NC][9];     // world -> error-frame rotation (POSE: P^-1_R; REL: P^-1_R R_a^T)
+  V3<T> phi[P::NC];  // log of the error rotation
+  T beta[P::NC];     // Jl^-1 coefficient
+  V3<T> za[P::NC];   // AXIS: frame z axis
+  T inv_norm;        // SPHERE: 1 / |q|
+  V3<T> C[P::D];     // COM: mass-weighted CoM sum over the subtree of joint j
+};
+
+template <class P, class Ops, typename T, bool WANT_J>
+__device__ __forceinline__ void residual(const ModelT<T> &m, const T (&q)[P::D], const Kin<P, T> &k,
+                                         T (&F)[kdim<P>()], Eval<P, T> &e) {
+  static_for<P::NC>([&](auto CC) {
+    constexpr int c = decltype(CC)::value;
+    constexpr int kind = P::ckind(c);
+    constexpr int r0 = roff<P>(c);
+    if constexpr (kind == K_SPHERE) {
+      // F = |q| - r (configuration space)
+      T n2 = T(0);
+#pragma unroll
+      for (int j = 0; j < P::D; ++j) n2 = fma_(q[j], q[j], n2);
+      T inv = Ops::rsqrt_(n2);
+      e.inv_norm = inv;
+      F[r0] = n2 * inv - m.ctgt[c][0];
+    } else if constexpr (kind == K_AXIS) {
+      // frame z axis parallel to world z: F = (z.x, z.y)
+      constexpr int a = P::cfa(c);
+      V3<T> za = col(k.fR[a], 2);
+      e.za[c] = za;
+      F[r0] = za.x;
+      F[r0 + 1] = za.y;
+    } else if constexpr (kind == K_POSE || kind == K_REL) {
+      T Pr[9];
+      load_R(m.cPinv[c], Pr);
+      const V3<T> Pp = load_p(m.cPinv[c]);
+      T Rerr[9];
+      V3<T> t;
+      if constexpr (kind == K_POSE) {
+        // Eq. 1: T_err = (T_w^0)^-1 T_a (T_e^w)^-1
+        constexpr int a = P::cfa(c);
+        T Qr[9], RaQ[9];
+        load_R(m.cQinv[c], Qr);
+        mul33(k.fR[a], Qr, RaQ);
+        const V3<T> x = add_rot_t<7>(k.fp[a], k.fR[a], load_p(m.cQinv[c]));
+        mul33(Pr, RaQ, Rerr);
+        const V3<T> tx = mulv(Pr, x);
+        t = {tx.x + Pp.x, tx.y + Pp.y, tx.z + Pp.z};
+        if constexpr (WANT_J) {
+          e.x[c] = x;
+#pragma unroll
+          for (int i = 0; i < 9; ++i) e.G[c][i] = Pr[i];
+        }
+      } else {
+        // Eq. 2: T_err = T_ref^-1 (T_a^-1 T_b); G = R_ref^T R_a^T
+        constexpr int a = P::cfa(c), b = P::cfb(c);
+        T G[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc)
+            G[r * 3 + cc] = fma_(Pr[r * 3], k.fR[a][cc * 3],
+                                 fma_(Pr[r * 3 + 1], k.fR[a][cc * 3 + 1], Pr[r * 3 + 2] * k.fR[a][cc * 3 + 2]));
+        mul33(G, k.fR[b], Rerr);
+        const V3<T> tx = mulv(G, sub(k.fp[b], k.fp[a]));
+        t = {tx.x + Pp.x, tx.y + Pp.y, tx.z + Pp.z};
+        if constexpr (WANT_J) {
+          e.x[c] = k.fp[b];
+#pragma unroll
+          for (int i = 0; i < 9; ++i) e.G[c][i] = G[i];
+        }
+      }
+      const auto lg = so3_log<Ops, T>(Rerr);
+      if constexpr (WANT_J) {
+        e.phi[c] = lg.phi;
+        e.beta[c] = jl_inv_beta<T>(lg.theta, lg.s, lg.c);
+      }
+      F[r0] = t.x;
+      F[r0 + 1] = t.y;
+      F[r0 + 2] = t.z;
+      F[r0 + 3] = lg.phi.x;
+      F[r0 + 4] = lg.phi.y;
+      F[r0 + 5] = lg.phi.z;
+    } else if constexpr (kind == K_COM) {
+      // Sec. V-C: x_com = sum_i m_i c_i / M with c_i = T_i com_i.  With WANT_J the
+      // subtree sums C_j = m_j c_j + sum over children are built in reverse
+      // topological order (children have larger indices).
+      V3<T> tot{T(0), T(0), T(0)};
+      static_for<P::D>([&](auto JJ) {
+        constexpr int j = P::D - 1 - decltype(JJ)::value;
+        const V3<T> ci = add_rot_t<7>(k.p[j], k.R[j], V3<T>{m.com[j][0], m.com[j][1], m.com[j][2]});
+        const V3<T> mc{m.mass[j] * ci.x, m.mass[j] * ci.y, m.mass[j] * ci.z};
+        tot = {tot.x + mc.x, tot.y + mc.y, tot.z + mc.z};
+        if constexpr (WANT_J) {
+          V3<T> acc = mc;
+          static_for<P::D>([&](auto II) {
+            constexpr int i = decltype(II)::value;
+            if constexpr (i > j && P::parent(i) == j) acc = {acc.x + e.C[i].x, acc.y + e.C[i].y, acc.z + e.C[i].z};
+          });
+          e.C[j] = acc;
+        }
+      });
+      F[r0] = fma_(tot.x, m.inv_mass, -m.ctgt[c][0]);
+      F[r0 + 1] = fma_(tot.y, m.inv_mass, -m.ctgt[c][1]);
+    }
+  });
+}
+
+// Jacobian of the stacked residual (world-frame geometric Jacobian rotated
+// into each error frame).  Only entries where jnz() holds are written / read.
+template <class P, typename T>
+__device__ __forceinline__ void jacobian(const ModelT<T> &m, const T (&q)[P::D], const Kin<P, T> &k,
+                                         const Eval<P, T> &e, T (&J)[kdim<P>()][P::D]) {
+  static_for<P::NC>([&](auto CC) {
+    constexpr int c = decltype(CC)::value;
+    constexpr int kind = P::ckind(c);
+    constexpr int r0 = roff<P>(c);
+    static_for<P::D>([&](auto JJ) {
+      constexpr int j = decltype(JJ)::value;
+      constexpr int s = col_sign<P>(c, j);
+      constexpr bool rev = P::jtype(j) == REV;
+      if constexpr (s != 0) {
+        if constexpr (kind == K_SPHERE) {
+          J[r0][j] = q[j] * e.inv_norm;
+        } else if constexpr (kind == K_AXIS) {
+          if constexpr (rev) {
+            const V3<T> d = cross(k.z[j], e.za[c]);
+            J[r0][j] = d.x;
+            J[r0 + 1][j] = d.y;
+          }
+        } else if constexpr (kind == K_POSE || kind == K_REL) {
+          // translation rows: G (velocity of the error point); rotation rows: Jl^-1 G z_j.
+          // REL: s = +1 for joints above b only, -1 above a only (Eq. 2, T_a^-1 T_b).
+          const V3<T> v = rev ? cross(k.z[j], sub(e.x[c], k.p[j])) : k.z[j];
+          const V3<T> vt = mulv(e.G[c], v);
+          J[r0][j] = s > 0 ? vt.x : -vt.x;
+          J[r0 + 1][j] = s > 0 ? vt.y : -vt.y;
+          J[r0 + 2][j] = s > 0 ? vt.z : -vt.z;
+          if constexpr (rev) {
+            const V3<T> w = jl_inv_apply(e.phi[c], e.beta[c], mulv(e.G[c], k.z[j]));
+            J[r0 + 3][j] = s > 0 ? w.x : -w.x;
+            J[r0 + 4][j] = s > 0 ? w.y : -w.y;
+            J[r0 + 5][j] = s > 0 ? w.z : -w.z;
+          }
+        } else if constexpr (kind == K_COM) {
+          // d x_com / d q_j = (1/M) z_j x (C_j - M_j o_j) (revolute), (M_j / M) z_j (prismatic)
+          if constexpr (rev) {
+            const T Mj = m.msub[j];
+            const V3<T> r{fma_(-Mj, k.p[j].x, e.C[j].x), fma_(-Mj, k.p[j].y, e.C[j].y), fma_(-Mj, k.p[j].z, e.C[j].z)};
+            const V3<T> d = cross(k.z[j], r);
+            J[r0][j] = d.x * m.inv_mass;
+            J[r0 + 1][j] = d.y * m.inv_mass;
+          } else {
+            const T f = m.msub[j] * m.inv_mass;
+            J[r0][j] = f * k.z[j].x;
+            J[r0 + 1][j] = f * k.z[j].y;
+          }
+        }
+      }
+    });
+  });
+}
+
+// A = J J^T + lambda I (lower triangle), skipping structural zeros.
+template <class P, typename T>
+__device__ __forceinline__ void gram(const T (&J)[kdim<P>()][P::D], T lambda, T (&A)[kdim<P>() * (kdim<P>() + 1) / 2]) {
+  constexpr int K = kdim<P>();
+  static_for<K>([&](auto AA) {
+    constexpr int a = decltype(AA)::value;
+    static_for<a + 1>([&](auto BB) {
+      constexpr int b = decltype(BB)::value;
+      T s = (a == b) ? lambda : T(0);
+      static_for<P::D>([&](auto JJ) {
+        constexpr int j = decltype(JJ)::value;
+        if constexpr (jnz<P>(a, j) && jnz<P>(b, j)) s = fma_(J[a][j], J[b][j], s);
+      });
+      A[tri(a, b)] = s;
+    });
+  });
+}
+
+// dq = J^T y
+template <class P, typename T>
+__device__ __forceinline__ void jt_mul(const T (&J)[kdim<P>()][P::D], const T (&y)[kdim<P>()], T (&dq)[P::D]) {
+  static_for<P::D>([&](auto JJ) {
+    constexpr int j = decltype(JJ)::value;
+    T s = T(0);
+    static_for<kdim<P>()>([&](auto AA) {
+      constexpr int a = decltype(AA)::value;
+      if constexpr (jnz<P>(a, j)) s = fma_(J[a][j], y[a], s);
+    });
+    dq[j] = s;
+  });
+}
+
+// u = J g
+template <class P, typename T>
+__device__ __forceinline__ void j_mul(const T (&J)[kdim<P>()][P::D], const T (&g)[P::D], T (&u)[kdim<P>()]) {
+  static_for<kdim<P>()>([&](auto AA) {
+    constexpr int a = decltype(AA)::value;
+    T s = T(0);
+    static_for<P::D>([&](auto JJ) {
+      constexpr int j = decltype(JJ)::value;
+      if constexpr (jnz<P>(a, j)) s = fma_(J[a][j], g[j], s);
+    });
+    u[a] = s;
+  });
+}
+
+// ---------------------------------------------------------------------------
+// Work items: a plain batch, or points on uneven segments.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct BatchSrc {
+  const T *q;
+  long long ld;
+  __device__ __forceinline__ long long clamp_total(long long t) const { return t; }
+  template <int D>
+  __device__ __forceinline__ void load(long long item, T (&out)[D]) const {
+#pragma unroll
+    for (int j = 0; j < D; ++j) out[j] = q[j * ld + item];
+  }
+};
+
+template <typename T>
+struct SegSrc {
+  const T *start;
+  const T *delta;
+  long long ld;
+  const long long *off;  // [n + 1]
+  int n;
+  // never hand out points past the end of the last segment
+  __device__ __forceinline__ long long clamp_total(long long t) const {
+    const long long dev_total = __ldg(&off[n]);
+    return t < dev_total ? t : dev_total;
+  }
+  template <int D>
+  __device__ __forceinline__ void load(long long item, T (&out)[D]) const {
+    // last segment s with off[s] <= item (segments of length 0 are skipped)
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(&off[mid]) <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    const T t = static_cast<T>(item - __ldg(&off[lo]));
+#pragma unroll
+    for (int j = 0; j < D; ++j) out[j] = fma_(t, delta[j * ld + lo], start[j * ld + lo]);
+  }
+};
+
+template <class P, class Src>
+struct ProjArgs {
+  ModelT<float> m;
+  const ModelT<double> *__restrict__ m64;
+  const double2 *__restrict__ tab;
+  Src src;
+  float *q_out;
+  long long ld_out;
+  uint8_t *flags;
+  uint8_t *iters;
+  double *resid;
+  unsigned long long *counter;
+  long long total;
+  int chunk;
+  int cap;
+  float tol2;
+  float lambda;
+  float max_step2;
+  float pivot;
+  double tol2_64;
+  double lambda64;
+};
+
+// ---------------------------------------------------------------------------
+// FP32 iteration (one pass of the ParallelProject loop for one configuration).
+// Returns true when the configuration leaves the FP32 loop.
+// ---------------------------------------------------------------------------
+template <class P, class A>
+__device__ __forceinline__ bool newton_iter_f32(const A &a, float (&q)[P::D], int &it, uint32_t &fl) {
+  constexpr int D = P::D, K = kdim<P>();
+  const OpsF32 ops{a.tab};
+  Kin<P, float> k;
+  if constexpr (needs_fk<P>()) fk<P, needs_pos<P>()>(ops, a.m, q, k);
+  float F[K];
+  Eval<P, float> e;
+  residual<P, OpsF32, float, true>(a.m, q, k, F, e);
+  float r2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < K; ++i) r2 = fmaf(F[i], F[i], r2);
+  if (!(r2 <= FLT_MAX)) {
+    fl |= FL_NONFINITE;
+    return true;
+  }
+  if (r2 < a.tol2) {
+    fl |= FL_INT_FP32CONV;
+    return true;
+  }
+  if (it >= a.cap) {
+    fl |= FL_CAP;
+    return true;
+  }
+  float J[K][D];
+  jacobian<P>(a.m, q, k, e, J);
+  float Am[K * (K + 1) / 2];
+  gram<P>(J, a.lambda, Am);
+  const float piv = cholesky_solve<K, OpsF32>(Am, F);
+  if (!(piv >= a.pivot)) {  // also catches NaN: finish this configuration in FP64
+    fl |= FL_INT_NEEDS_F64;
+    return true;
+  }
+  float dq[D];
+  jt_mul<P>(J, F, dq);
+  float s2 = 0.f;
+#pragma unroll
+  for (int j = 0; j < D; ++j) s2 = fmaf(dq[j], dq[j], s2);
+  if (a.max_step2 > 0.f && s2 > a.max_step2) {
+    fl |= FL_DIV;
+    return true;
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j) q[j] -= dq[j];
+  ++it;
+  if (!(s2 <= FLT_MAX)) {
+    fl |= FL_NONFINITE;
+    return true;
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 pieces used by the acceptance pass.
+// ---------------------------------------------------------------------------
+template <class P>
+__device__ __forceinline__ double residual2_f64(const OpsF64Table &ops, const ModelT<double> &m,
+                                                const double (&q)[P::D]) {
+  constexpr int K = kdim<P>();
+  Kin<P, double> k;
+  if constexpr (needs_fk<P>()) fk<P, needs_pos<P>()>(ops, m, q, k);
+  double F[K];
+  Eval<P, double> e;
+  residual<P, OpsF64Table, double, false>(m, q, k, F, e);
+  double r2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < K; ++i) r2 = fma(F[i], F[i], r2);
+  return r2;
+}
+
+// One LM step entirely in FP64 at q (the re-solve of a badly conditioned
+// system).  J and the factorisation live in local memory (runtime-indexed
+// loops) so that this rare path does not raise the register budget of the
+// FP32 loop.  Returns false if the FP64 system is singular as well.
+template <class P>
+__device__ __noinline__ bool lm_step_f64(const OpsF64Table ops, const ModelT<double> *__restrict__ m,
+                                         const double *q_in, double lambda, double *dq_out) {
+  constexpr int D = P::D, K = kdim<P>();
+  double q[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) q[j] = q_in[j];
+  Kin<P, double> k;
+  if constexpr (needs_fk<P>()) fk<P, needs_pos<P>()>(ops, *m, q, k);
+  double F[K];
+  Eval<P, double> e;
+  residual<P, OpsF64Table, double, true>(*m, q, k, F, e);
+  double J[K][D];
+#pragma unroll 1
+  for (int a = 0; a < K; ++a)
+#pragma unroll 1
+    for (int j = 0; j < D; ++j) J[a][j] = 0.0;
+  jacobian<P>(*m, q, k, e, J);
+  double L[K][K];
+#pragma unroll 1
+  for (int a = 0; a < K; ++a) {
+#pragma unroll 1
+    for (int b = 0; b <= a; ++b) {
+      double s = (a == b) ? lambda : 0.0;
+#pragma unroll 1
+      for (int j = 0; j < D; ++j) s = fma(J[a][j], J[b][j], s);
+      L[a][b] = s;
+    }
+  }
+#pragma unroll 1
+  for (int j = 0; j < K; ++j) {
+    double s = L[j][j];
+#pragma unroll 1
+    for (int t = 0; t < j; ++t) s = fma(-L[j][t], L[j][t], s);
+    if (!(s > 0.0)) return false;
+    L[j][j] = sqrt(s);
+#pragma unroll 1
+    for (int i = j + 1; i < K; ++i) {
+      double t2 = L[i][j];
+#pragma unroll 1
+      for (int t = 0; t < j; ++t) t2 = fma(-L[i][t], L[j][t], t2);
+      L[i][j] = t2 / L[j][j];
+    }
+  }
+  double y[K];
+#pragma unroll 1
+  for (int i = 0; i < K; ++i) {
+    double s = F[i];
+#pragma unroll 1
+    for (int t = 0; t < i; ++t) s = fma(-L[i][t], y[t], s);
+    y[i] = s / L[i][i];
+  }
+#pragma unroll 1
+  for (int i = K - 1; i >= 0; --i) {
+    double s = y[i];
+#pragma unroll 1
+    for (int t = i + 1; t < K; ++t) s = fma(-L[t][i], y[t], s);
+    y[i] = s / L[i][i];
+  }
+#pragma unroll 1
+  for (int j = 0; j < D; ++j) {
+    double s = 0.0;
+#pragma unroll 1
+    for (int a = 0; a < K; ++a) s = fma(J[a][j], y[a], s);
+    dq_out[j] = s;
+  }
+  return true;
+}
+
+// Heron refinement of an FP32 square root: one Newton step in FP64 brings the
+// FP32 estimate (relative error ~6e-8) to ~1e-14.
+__device__ __forceinline__ double sqrt_refined(double v) {
+  if (!(v > 0.0) || !(v <= DBL_MAX)) return sqrt(v);
+  const float r0f = sqrtf(static_cast<float>(v));
+  if (r0f == 0.0f) return sqrt(v);
+  const double r0 = static_cast<double>(r0f);
+  const double h = static_cast<double>(0.5f / r0f);
+  return fma(fma(-r0, r0, v), h, r0);
+}
+
+// Acceptance / finishing of one configuration that left the FP32 loop.  The
+// FP32 iterate is re-checked with the FP64 residual; if the FP32 test was too
+// optimistic, or the FP32 pivot was too small, the remaining steps are taken
+// in FP64 (rounded to the FP32 output).  Writes q, flags, iters and resid.
+template <class P, class A>
+__device__ __forceinline__ void accept_one(const A &a, long long item, int it, uint32_t fl) {
+  constexpr int D = P::D;
+  const OpsF64Table ops{a.tab};
+  const ModelT<double> &m = *a.m64;
+  float q[D];
+  double qd[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    q[j] = a.q_out[j * a.ld_out + item];
+    qd[j] = static_cast<double>(q[j]);
+  }
+  double r2 = residual2_f64<P>(ops, m, qd);
+  bool changed = false;
+  if (fl & (FL_INT_FP32CONV | FL_INT_NEEDS_F64)) {
+    const bool was_conv = (fl & FL_INT_FP32CONV) != 0;
+    fl &= ~(FL_INT_FP32CONV | FL_INT_NEEDS_F64);
+    bool conv = r2 < a.tol2_64;
+    while (!conv && it < a.cap) {
+      double dq[D];
+      fl |= FL_RESOLVE;
+      if (!lm_step_f64<P>(ops, a.m64, qd, a.lambda64, dq)) {
+        fl |= FL_NONFINITE;
+        break;
+      }
+      double s2 = 0.0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) s2 = fma(dq[j], dq[j], s2);
+      if (a.max_step2 > 0.f && s2 > static_cast<double>(a.max_step2)) {
+        fl |= FL_DIV;
+        break;
+      }
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        q[j] = static_cast<float>(qd[j] - dq[j]);
+        qd[j] = static_cast<double>(q[j]);
+      }
+      changed = true;
+      ++it;
+      r2 = residual2_f64<P>(ops, m, qd);
+      if (!(r2 <= DBL_MAX)) {
+        fl |= FL_NONFINITE;
+        break;
+      }
+      conv = r2 < a.tol2_64;
+    }
+    if (conv) fl |= FL_CONV;
+    else if (!(fl & (FL_NONFINITE | FL_DIV))) fl |= FL_CAP | (was_conv ? FL_ACCEPT_FAIL : 0u);
+  }
+  if (changed) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) a.q_out[j * a.ld_out + item] = q[j];
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j)
+    if (qd[j] < m.lower[j] || qd[j] > m.upper[j]) fl |= FL_LIMITS;
+  a.flags[item] = static_cast<uint8_t>(fl & 0xffu);
+  a.iters[item] = static_cast<uint8_t>(it > 255 ? 255 : it);
+  a.resid[item] = sqrt_refined(r2);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent projection kernel (FP32 steps, FP64 acceptance).
+//
+// Each warp keeps a local queue of work items claimed `chunk` at a time with
+// one atomicAdd.  Every pass of the loop (1) refills idle lanes from the queue,
+// (2) runs one Newton iteration on every active lane, (3) parks lanes that left
+// the FP32 loop in a per-warp pending list, and (4) once 32 are pending (or no
+// work is left) runs the FP64 acceptance on them with all lanes busy.  Lanes
+// therefore never wait for the slowest configuration of their warp, and the
+// FP64 work runs in full warps, interleaved with other warps' FP32 work.
+// ---------------------------------------------------------------------------
+template <class P, class Src, int TPB>
+__global__ void __launch_bounds__(TPB) k_project_f32(const __grid_constant__ ProjArgs<P, Src> a) {
+  constexpr int D = P::D;
+  constexpr int W = TPB / 32;
+  __shared__ long long s_item[W][64];
+  __shared__ uint32_t s_meta[W][64];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const long long total = a.src.clamp_total(a.total);
+  int pend = 0;                   // warp-uniform count of pending configurations
+  long long qn = 0, qe = 0;       // warp-local queue [qn, qe)
+  bool more = true;               // the global counter may still have work
+  bool act = false;
+  long long item = 0;
+  int it = 0;
+  uint32_t fl = 0;
+  float q[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) q[j] = 0.f;
+
+  while (true) {
+    // (1) refill
+    const unsigned idle = __ballot_sync(FULL, !act);
+    if (idle != 0u && (qn < qe || more)) {
+      const int need = __popc(idle);
+      const long long avail = qe - qn;
+      long long b0 = 0, b1 = 0;
+      if (avail < need && more) {
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(a.counter, static_cast<unsigned long long>(a.chunk));
+        b = __shfl_sync(FULL, b, 0);
+        if (static_cast<long long>(b) >= total) {
+          more = false;
+        } else {
+          b0 = static_cast<long long>(b);
+          b1 = b0 + a.chunk < total ? b0 + a.chunk : total;
+        }
+      }
+      const int rank = __popc(idle & ((1u << lane) - 1u));
+      if (!act) {
+        long long cand = -1;
+        if (rank < avail) cand = qn + rank;
+        else if (rank - avail < b1 - b0) cand = b0 + (rank - avail);
+        if (cand >= 0) {
+          item = cand;
+          act = true;
+          it = 0;
+          fl = 0;
+          a.src.template load<D>(item, q);
+        }
+      }
+      const long long used_old = need < avail ? need : avail;
+      if (b1 > b0) {
+        const long long rest = need - used_old;
+        qn = b0 + (rest < b1 - b0 ? rest : b1 - b0);
+        qe = b1;
+      } else {
+        qn += used_old;
+      }
+    }
+    // (2) one FP32 Newton iteration
+    bool done = false;
+    if (act) done = newton_iter_f32<P>(a, q, it, fl);
+    // (3) park finished lanes
+    const unsigned fin = __ballot_sync(FULL, done);
+    if (fin != 0u) {
+      if (done) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) a.q_out[j * a.ld_out + item] = q[j];
+        const int pos = pend + __popc(fin & ((1u << lane) - 1u));
+        s_item[wib][pos] = item;
+        s_meta[wib][pos] = static_cast<uint32_t>(it) | (fl << 8);
+        act = false;
+      }
+      pend += __popc(fin);
+      __syncwarp();
+    }
+    const bool drained = !__any_sync(FULL, act) && qn >= qe && !more;
+    // (4) FP64 acceptance in full warps
+    if (pend >= 32 || (drained && pend > 0)) {
+      const int take = pend < 32 ? pend : 32;
+      if (lane < take) {
+        const int pos = pend - take + lane;
+        const uint32_t meta = s_meta[wib][pos];
+        accept_one<P>(a, s_item[wib][pos], static_cast<int>(meta & 0xffu), meta >> 8);
+      }
+      pend -= take;
+      __syncwarp();
+    }
+    if (drained && pend == 0) break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Plain FP64 kernel: one thread per configuration, FP64 and CUDA's double
+// math throughout, no staging, no refill.  The reference point the batched
+// FP32 path is measured against, and the product path of FP64 problems.
+// ---------------------------------------------------------------------------
+template <class P, class Src>
+struct ProjArgs64 {
+  ModelT<double> m;
+  Src src;
+  double *q_out;
+  long long ld_out;
+  uint8_t *flags;
+  uint8_t *iters;
+  double *resid;
+  long long total;
+  int cap;
+  double tol2;
+  double lambda;
+  double max_step2;
+};
+
+template <class P, class Src>
+__global__ void __launch_bounds__(128) k_project_f64(const __grid_constant__ ProjArgs64<P, Src> a) {
+  constexpr int D = P::D, K = kdim<P>();
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= a.src.clamp_total(a.total)) return;
+  const OpsF64Plain ops{nullptr};
+  double q[D];
+  a.src.template load<D>(i, q);
+  uint32_t fl = 0;
+  int it = 0;
+  double r2 = 0.0;
+  for (;; ++it) {
+    Kin<P, double> k;
+    if constexpr (needs_fk<P>()) fk<P, needs_pos<P>()>(ops, a.m, q, k);
+    double F[K];
+    Eval<P, double> e;
+    residual<P, OpsF64Plain, double, true>(a.m, q, k, F, e);
+    r2 = 0.0;
+#pragma unroll
+    for (int r = 0; r < K; ++r) r2 = fma(F[r], F[r], r2);
+    if (!(r2 <= DBL_MAX)) {
+      fl |= FL_NONFINITE;
+      break;
+    }
+    if (r2 < a.tol2) {
+      fl |= FL_CONV;
+      break;
+    }
+    if (it >= a.cap) {
+      fl |= FL_CAP;
+      break;
+    }
+    double J[K][D];
+    jacobian<P>(a.m, q, k, e, J);
+    double Am[K * (K + 1) / 2];
+    gram<P>(J, a.lambda, Am);
+    const double piv = cholesky_solve<K, OpsF64Plain>(Am, F);
+    if (!(piv > 0.0)) {
+      fl |= FL_NONFINITE;
+      break;
+    }
+    double dq[D];
+    jt_mul<P>(J, F, dq);
+    double s2 = 0.0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) s2 = fma(dq[j], dq[j], s2);
+    if (a.max_step2 > 0.0 && s2 > a.max_step2) {
+      fl |= FL_DIV;
+      break;
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) q[j] -= dq[j];
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    a.q_out[j * a.ld_out + i] = q[j];
+    if (q[j] < a.m.lower[j] || q[j] > a.m.upper[j]) fl |= FL_LIMITS;
+  }
+  a.flags[i] = static_cast<uint8_t>(fl);
+  a.iters[i] = static_cast<uint8_t>(it > 255 ? 255 : it);
+  a.resid[i] = sqrt(r2);
+}
+
+// ---------------------------------------------------------------------------
+// Collision check (CollisionFree of Alg. 2): link spheres against obstacle
+// spheres and boxes; obstacles staged in shared memory, early exit on the
+// first overlap.  One thread per configuration.
+// ---------------------------------------------------------------------------
+template <class P, typename T>
+struct CheckArgs {
+  ModelT<T> m;
+  SphereTable<T> st;
+  const T *obs;  // [n_obs * 4]
+  const T *box;  // [n_box * 6]
+  int n_obs;
+  int n_box;
+  const T *q;
+  long long ld;
+  long long n;
+  uint8_t *out;
+  const double2 *tab;
+};
+
+template <typename T>
+__device__ __forceinline__ T max_(T a, T b) {
+  return a > b ? a : b;
+}
+
+template <typename T>
+__device__ __forceinline__ bool sphere_hits(V3<T> c, T rs, const T *s_obs, int n_obs, const T *s_box, int n_box) {
+  for (int o = 0; o < n_obs; ++o) {
+    const T dx = c.x - s_obs[4 * o], dy = c.y - s_obs[4 * o + 1], dz = c.z - s_obs[4 * o + 2];
+    const T rr = rs + s_obs[4 * o + 3];
+    if (fma_(dx, dx, fma_(dy, dy, dz * dz)) < rr * rr) return true;
+  }
+  for (int b = 0; b < n_box; ++b) {
+    const T *bx = s_box + 6 * b;
+    const T ex = max_(max_(bx[0] - c.x, c.x - bx[3]), T(0));
+    const T ey = max_(max_(bx[1] - c.y, c.y - bx[4]), T(0));
+    const T ez = max_(max_(bx[2] - c.z, c.z - bx[5]), T(0));
+    if (fma_(ex, ex, fma_(ey, ey, ez * ez)) < rs * rs) return true;
+  }
+  return false;
+}
+
+template <class P, typename T, class Ops>
+__global__ void __launch_bounds__(128) k_check(const __grid_constant__ CheckArgs<P, T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *s_obs = reinterpret_cast<T *>(smem_raw);
+  T *s_box = s_obs + 4 * a.n_obs;
+  for (int t = threadIdx.x; t < 4 * a.n_obs; t += blockDim.x) s_obs[t] = a.obs[t];
+  for (int t = threadIdx.x; t < 6 * a.n_box; t += blockDim.x) s_box[t] = a.box[t];
+  __syncthreads();
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  constexpr int D = P::D;
+  const Ops ops{a.tab};
+  T q[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) q[j] = a.q[j * a.ld + i];
+  bool hit = false;
+  // world-fixed spheres
+  for (int s = a.st.off[0]; s < a.st.off[1] && !hit; ++s)
+    hit = sphere_hits<T>(V3<T>{a.st.s[s][0], a.st.s[s][1], a.st.s[s][2]}, a.st.s[s][3], s_obs, a.n_obs, s_box,
+                         a.n_box);
+  Kin<P, T> k;
+  fk<P, true>(ops, a.m, q, k);
+  static_for<D>([&](auto JJ) {
+    constexpr int j = decltype(JJ)::value;
+    for (int s = a.st.off[j + 1]; s < a.st.off[j + 2] && !hit; ++s) {
+      const V3<T> c = add_rot_t<7>(k.p[j], k.R[j], V3<T>{a.st.s[s][0], a.st.s[s][1], a.st.s[s][2]});
+      hit = sphere_hits<T>(c, a.st.s[s][3], s_obs, a.n_obs, s_box, a.n_box);
+    }
+  });
+  a.out[i] = hit ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// VJP of the projection at q* (implicit-function theorem):
+//     v = g - J^T (J J^T)^{-1} J g.
+// FP32 with the same pivot rule as the projection: a small pivot re-solves
+// the configuration in FP64.
+// ---------------------------------------------------------------------------
+template <class P>
+struct VjpArgs {
+  ModelT<float> m;
+  const ModelT<double> *__restrict__ m64;
+  const double2 *__restrict__ tab;
+  const float *q;
+  const float *g;
+  float *out;
+  uint8_t *flags;
+  long long ld;
+  long long n;
+  float pivot;
+};
+
+template <class P>
+__device__ __noinline__ uint32_t vjp_f64(const OpsF64Table ops, const ModelT<double> *__restrict__ m,
+                                          const double *q, const double *g, double *v) {
+  // Reuse the FP64 LM step: with F replaced by J g and lambda = 0 it returns
+  // J^T (J J^T)^{-1} J g.  lm_step_f64 evaluates F itself, so the product is
+  // formed here instead.
+  constexpr int D = P::D, K = kdim<P>();
+  double qq[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) qq[j] = q[j];
+  Kin<P, double> k;
+  if constexpr (needs_fk<P>()) fk<P, needs_pos<P>()>(ops, *m, qq, k);
+  double F[K];
+  Eval<P, double> e;
+  residual<P, OpsF64Table, double, true>(*m, qq, k, F, e);
+  double J[K][D];
+#pragma unroll 1
+  for (int a = 0; a < K; ++a)
+#pragma unroll 1
+    for (int j = 0; j < D; ++j) J[a][j] = 0.0;
+  jacobian<P>(*m, qq, k, e, J);
+  double L[K][K], u[K];
+#pragma unroll 1
+  for (int a = 0; a < K; ++a) {
+    double s = 0.0;
+#pragma unroll 1
+    for (int j = 0; j < D; ++j) s = fma(J[a][j], g[j], s);
+    u[a] = s;
+#pragma unroll 1
+    for (int b = 0; b <= a; ++b) {
+      double t = 0.0;
+#pragma unroll 1
+      for (int j = 0; j < D; ++j) t = fma(J[a][j], J[b][j], t);
+      L[a][b] = t;
+    }
+  }
+#pragma unroll 1
+  for (int j = 0; j < K; ++j) {
+    double s = L[j][j];
+#pragma unroll 1
+    for (int t = 0; t < j; ++t) s = fma(-L[j][t], L[j][t], s);
+    if (!(s > 0.0)) return FL_NONFINITE;
+    L[j][j] = sqrt(s);
+#pragma unroll 1
+    for (int i = j + 1; i < K; ++i) {
+      double t2 = L[i][j];
+#pragma unroll 1
+      for (int t = 0; t < j; ++t) t2 = fma(-L[i][t], L[j][t], t2);
+      L[i][j] = t2 / L[j][j];
+    }
+  }
+#pragma unroll 1
+  for (int i = 0; i < K; ++i) {
+    double s = u[i];
+#pragma unroll 1
+    for (int t = 0; t < i; ++t) s = fma(-L[i][t], u[t], s);
+    u[i] = s / L[i][i];
+  }
+#pragma unroll 1
+  for (int i = K - 1; i >= 0; --i) {
+    double s = u[i];
+#pragma unroll 1
+    for (int t = i + 1; t < K; ++t) s = fma(-L[t][i], u[t], s);
+    u[i] = s / L[i][i];
+  }
+#pragma unroll 1
+  for (int j = 0; j < D; ++j) {
+    double s = 0.0;
+#pragma unroll 1
+    for (int a = 0; a < K; ++a) s = fma(J[a][j], u[a], s);
+    v[j] = g[j] - s;
+  }
+  return FL_RESOLVE;
+}
+
+template <class P>
+__global__ void __launch_bounds__(128) k_vjp(const __grid_constant__ VjpArgs<P> a) {
+  constexpr int D = P::D, K = kdim<P>();
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const OpsF32 ops{a.tab};
+  float q[D], g[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    q[j] = a.q[j * a.ld + i];
+    g[j] = a.g[j * a.ld + i];
+  }
+  Kin<P, float> k;
+  if constexpr (needs_fk<P>()) fk<P, needs_pos<P>()>(ops, a.m, q, k);
+  float F[K];
+  Eval<P, float> e;
+  residual<P, OpsF32, float, true>(a.m, q, k, F, e);
+  float J[K][D];
+  jacobian<P>(a.m, q, k, e, J);
+  float Am[K * (K + 1) / 2];
+  gram<P>(J, 0.f, Am);
+  float u[K];
+  j_mul<P>(J, g, u);
+  const float piv = cholesky_solve<K, OpsF32>(Am, u);
+  uint32_t fl = 0;
+  if (!(piv >= a.pivot)) {
+    double qd[D], gd[D], vd[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      qd[j] = q[j];
+      gd[j] = g[j];
+    }
+    fl = vjp_f64<P>(OpsF64Table{a.tab}, a.m64, qd, gd, vd);
+#pragma unroll
+    for (int j = 0; j < D; ++j) a.out[j * a.ld + i] = (fl & FL_NONFINITE) ? CUDART_NAN_F : static_cast<float>(vd[j]);
+  } else {
+    float w[D];
+    jt_mul<P>(J, u, w);
+#pragma unroll
+    for (int j = 0; j < D; ++j) a.out[j * a.ld + i] = g[j] - w[j];
+  }
+  if (a.flags) a.flags[i] = static_cast<uint8_t>(fl);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <class P, class Src, int TPB>
+cudaError_t launch_persistent(const HostModel &hm, const ProjCall &c, const Src &src) {
+  ProjArgs<P, Src> a;
+  a.m = hm.m32;
+  a.m64 = hm.d_m64;
+  a.tab = hm.d_tab;
+  a.src = src;
+  a.q_out = static_cast<float *>(c.q_out);
+  a.ld_out = c.ld_out;
+  a.flags = c.flags;
+  a.iters = c.iters;
+  a.resid = c.resid;
+  a.counter = c.counter;
+  a.total = c.total;
+  a.chunk = c.tune.chunk;
+  a.cap = c.cap;
+  a.tol2 = static_cast<float>(c.tol * c.tol);
+  a.lambda = static_cast<float>(c.lambda);
+  a.max_step2 = c.max_step > 0 ? static_cast<float>(c.max_step * c.max_step) : 0.f;
+  a.pivot = static_cast<float>(c.pivot);
+  a.tol2_64 = c.tol * c.tol;
+  a.lambda64 = c.lambda;
+  const long long warps_needed = (c.total + 31) / 32;
+  long long blocks = static_cast<long long>(hm.sm_count) * c.tune.blocks_per_sm;
+  const long long max_useful = (warps_needed + (TPB / 32) - 1) / (TPB / 32);
+  if (blocks > max_useful) blocks = max_useful;
+  if (blocks < 1) blocks = 1;
+  k_project_f32<P, Src, TPB><<<static_cast<unsigned>(blocks), TPB, 0, c.stream>>>(a);
+  return cudaGetLastError();
+}
+
+template <class P, class Src>
+cudaError_t launch_plain64(const HostModel &hm, const ProjCall &c, const Src &src) {
+  ProjArgs64<P, Src> a;
+  a.m = hm.m64;
+  a.src = src;
+  a.q_out = static_cast<double *>(c.q_out);
+  a.ld_out = c.ld_out;
+  a.flags = c.flags;
+  a.iters = c.iters;
+  a.resid = c.resid;
+  a.total = c.total;
+  a.cap = c.cap;
+  a.tol2 = c.tol * c.tol;
+  a.lambda = c.lambda;
+  a.max_step2 = c.max_step > 0 ? c.max_step * c.max_step : 0.0;
+  const long long blocks = (c.total + 127) / 128;
+  k_project_f64<P, Src><<<static_cast<unsigned>(blocks), 128, 0, c.stream>>>(a);
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t launch_project_impl(const HostModel &hm, const ProjCall &c, int *launches) {
+  if (c.total <= 0) return cudaSuccess;
+  cudaError_t err;
+  if (c.precision == 1) {
+    if (c.segments)
+      err = launch_plain64<P>(hm, c, SegSrc<double>{static_cast<const double *>(c.start),
+                                                    static_cast<const double *>(c.delta), c.ld_seg, c.seg_off,
+                                                    c.n_seg});
+    else
+      err = launch_plain64<P>(hm, c, BatchSrc<double>{static_cast<const double *>(c.q_in), c.ld_in});
+    *launches += 1;
+    return err;
+  }
+  err = cudaMemsetAsync(c.counter, 0, sizeof(unsigned long long), c.stream);
+  if (err != cudaSuccess) return err;
+  auto go = [&](auto src) -> cudaError_t {
+    switch (c.tune.tpb) {
+      case 64: return launch_persistent<P, decltype(src), 64>(hm, c, src);
+      case 256: return launch_persistent<P, decltype(src), 256>(hm, c, src);
+      default: return launch_persistent<P, decltype(src), 128>(hm, c, src);
+    }
+  };
+  if (c.segments)
+    err = go(SegSrc<float>{static_cast<const float *>(c.start), static_cast<const float *>(c.delta), c.ld_seg,
+                           c.seg_off, c.n_seg});
+  else
+    err = go(BatchSrc<float>{static_cast<const float *>(c.q_in), c.ld_in});
+  *launches += 1;
+  return err;
+}
+
+template <class P>
+cudaError_t launch_check_impl(const HostModel &hm, const CheckCall &c, int *launches) {
+  if (c.n <= 0) return cudaSuccess;
+  const unsigned blocks = static_cast<unsigned>((c.n + 127) / 128);
+  if (c.precision == 1) {
+    CheckArgs<P, double> a;
+    a.m = hm.m64;
+    a.st = hm.st64;
+    a.obs = hm.d_obs64;
+    a.box = hm.d_box64;
+    a.n_obs = hm.n_obs;
+    a.n_box = hm.n_box;
+    a.q = static_cast<const double *>(c.q);
+    a.ld = c.ld;
+    a.n = c.n;
+    a.out = c.out;
+    a.tab = hm.d_tab;
+    const size_t smem = sizeof(double) * (4 * hm.n_obs + 6 * hm.n_box);
+    k_check<P, double, OpsF64Plain><<<blocks, 128, smem, c.stream>>>(a);
+  } else {
+    CheckArgs<P, float> a;
+    a.m = hm.m32;
+    a.st = hm.st32;
+    a.obs = reinterpret_cast<const float *>(hm.d_obs32);
+    a.box = reinterpret_cast<const float *>(hm.d_box32);
+    a.n_obs = hm.n_obs;
+    a.n_box = hm.n_box;
+    a.q = static_cast<const float *>(c.q);
+    a.ld = c.ld;
+    a.n = c.n;
+    a.out = c.out;
+    a.tab = hm.d_tab;
+    const size_t smem = sizeof(float) * (4 * hm.n_obs + 6 * hm.n_box);
+    k_check<P, float, OpsF32><<<blocks, 128, smem, c.stream>>>(a);
+  }
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t launch_vjp_impl(const HostModel &hm, const VjpCall &c, int *launches) {
+  if (c.n <= 0) return cudaSuccess;
+  VjpArgs<P> a;
+  a.m = hm.m32;
+  a.m64 = hm.d_m64;
+  a.tab = hm.d_tab;
+  a.q = c.q;
+  a.g = c.g;
+  a.out = c.out;
+  a.flags = c.flags;
+  a.ld = c.ld;
+  a.n = c.n;
+  a.pivot = static_cast<float>(c.pivot);
+  const unsigned blocks = static_cast<unsigned>((c.n + 127) / 128);
+  k_vjp<P><<<blocks, 128, 0, c.stream>>>(a);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+#define MCP_INSTANTIATE_CHECK_ONLY(P)                                                          \
+  template <>                                                                                  \
+  cudaError_t launch_project<P>(const HostModel &, const ProjCall &, int *) {                   \
+    return cudaErrorNotSupported;                                                              \
+  }                                                                                            \
+  template <>                                                                                  \
+  cudaError_t launch_check<P>(const HostModel &hm, const CheckCall &c, int *launches) {        \
+    return launch_check_impl<P>(hm, c, launches);                                              \
+  }                                                                                            \
+  template <>                                                                                  \
+  cudaError_t launch_vjp<P>(const HostModel &, const VjpCall &, int *) {                        \
+    return cudaErrorNotSupported;                                                              \
+  }
+
+#define MCP_INSTANTIATE(P)                                                                     \
+  template <>                                                                                  \
+  cudaError_t launch_project<P>(const HostModel &hm, const ProjCall &c, int *launches) {       \
+    return launch_project_impl<P>(hm, c, launches);                                            \
+  }                                                                                            \
+  template <>                                                                                  \
+  cudaError_t launch_check<P>(const HostModel &hm, const CheckCall &c, int *launches) {        \
+    return launch_check_impl<P>(hm, c, launches);                                              \
+  }                                                                                            \
+  template <>                                                                                  \
+  cudaError_t launch_vjp<P>(const HostModel &hm, const VjpCall &c, int *launches) {            \
+    return launch_vjp_impl<P>(hm, c, launches);                                                \
+  }
+
+}  // namespace mcp

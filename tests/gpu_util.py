@@ -1,0 +1,52 @@
+"""Helpers shared by the GPU parity tests (comparison of the CUDA path, called
+through the C ABI, with the FP64 oracle on identical seeded inputs)."""
+import numpy as np
+
+from oracle import oracle as orc
+
+# Acceptance bars (from the projection spec): converged configurations agree to
+# 1e-4 rad in the infinity norm, the FP64 residual of every converged output is
+# below tol, convergence flags agree on >= 99.9 % of configurations, collision
+# verdicts agree exactly outside a 1e-5 m band around contact.
+Q_TOL = 1e-4
+FLAG_AGREE = 0.999
+CONTACT_BAND = 1e-5
+
+
+def f32_exact(q):
+    """The FP32 start the GPU sees, as FP64, so both sides start identically."""
+    return np.asarray(q, dtype=np.float32).astype(np.float64)
+
+
+def compare_projection(gpu, ora, tol, q_tol=Q_TOL, flag_agree=FLAG_AGREE, oracle=None, sample_resid=256):
+    """gpu / ora: (q [d, n], flags, iters, resid) as numpy.  Returns a stats dict."""
+    qg, fg, ig, rg = gpu
+    qo, fo, io, ro = ora
+    cg = (fg & orc.CONVERGED) != 0
+    co = (fo & orc.CONVERGED) != 0
+    agree = float((cg == co).mean())
+    both = cg & co
+    err = np.abs(qg[:, both] - qo[:, both]).max(axis=0) if both.any() else np.zeros(0)
+    stats = {"n": int(cg.size), "conv_gpu": float(cg.mean()), "conv_oracle": float(co.mean()), "flag_agree": agree,
+             "q_err_max": float(err.max()) if err.size else 0.0,
+             "q_err_p999": float(np.quantile(err, 0.999)) if err.size else 0.0,
+             "resid_max": float(rg[cg].max()) if cg.any() else 0.0,
+             "iters_equal": float((ig[both] == io[both]).mean()) if both.any() else 1.0}
+    assert agree >= flag_agree, stats
+    assert stats["q_err_max"] <= q_tol, stats
+    assert np.all(rg[cg] < tol), stats
+    if oracle is not None and cg.any():
+        # the reported FP64 residual is the residual of the returned configuration
+        idx = np.flatnonzero(cg)[:: max(1, cg.sum() // sample_resid)]
+        for i in idx:
+            r = np.linalg.norm(oracle.residual(qg[:, i].astype(np.float64)))
+            assert abs(r - rg[i]) <= 1e-9 * max(1.0, r) + 1e-13, (i, r, rg[i])
+            assert r < tol
+    return stats
+
+
+def compare_collision(hit_gpu, hit_oracle, margin_oracle, band=CONTACT_BAND):
+    ok = margin_oracle >= band
+    mism = (hit_gpu != hit_oracle) & ok
+    assert not mism.any(), (np.flatnonzero(mism)[:10], int(mism.sum()))
+    return {"n": int(hit_gpu.size), "excluded": int((~ok).sum()), "collide_frac": float(hit_oracle.mean())}

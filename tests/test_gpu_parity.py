@@ -1,0 +1,282 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every case runs the same seeded inputs through both sides and compares them
+element by element: converged configurations to 1e-4 rad, the FP64 residual of
+each converged output below tol, convergence flags on >= 99.9 %, collision
+verdicts exactly outside a 1e-5 m contact band.  Sizes span several thread
+blocks with a ragged tail; the full workload sizes are included where the
+oracle finishes them in seconds.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as orc  # noqa: E402
+from paper_2604_13323_gb300 import workloads as W  # noqa: E402
+from tests.gpu_util import compare_collision, compare_projection, f32_exact  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mcproj():
+    from paper_2604_13323_gb300 import build, mcproj as m
+    build.build()
+    m.load_library()
+    return m
+
+
+def dev(a, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def host(*ts):
+    return tuple(t.cpu().numpy() for t in ts)
+
+
+def run_gpu(P, q0, params, dtype=torch.float32, ld=None):
+    d, n = q0.shape
+    ld = n if ld is None else ld
+    qd = torch.zeros((d, ld), dtype=dtype, device="cuda")
+    qd[:, :n] = dev(q0, dtype)
+    out, fl, it, r = P.project(qd, params, n=n)
+    torch.cuda.synchronize()
+    q, fl, it, r = host(out, fl, it, r)
+    return q[:, :n], fl[:n], it[:n].astype(np.int32), r[:n]
+
+
+# ---------------------------------------------------------------------------
+# sphere manifold (plain FP64, uneven segments)
+# ---------------------------------------------------------------------------
+def test_sphere_segments_fp64(mcproj):
+    wl = W.sphere_workload()
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
+    O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
+    seg = wl.segments
+    out, fl, it, r = P.project_segments(dev(seg.start, torch.float64), dev(seg.delta, torch.float64),
+                                        dev(seg.length, torch.int32), wl.params)
+    torch.cuda.synchronize()
+    gpu = host(out, fl, it, r)
+    pts = W.segment_points(seg)
+    ora = O.project_params(pts, wl.params)
+    st = compare_projection((gpu[0], gpu[1], gpu[2].astype(np.int32), gpu[3]), ora, wl.params.tol, q_tol=1e-12,
+                            oracle=O)
+    assert st["conv_gpu"] == 1.0 and st["iters_equal"] > 0.999
+    np.testing.assert_allclose(gpu[0], pts / np.linalg.norm(pts, axis=0), atol=1e-14)
+    hit = P.check(out).cpu().numpy()
+    h_o, m_o = O.check(gpu[0])
+    compare_collision(hit, h_o, m_o)
+
+
+# ---------------------------------------------------------------------------
+# 7-DoF arm, orientation constraint (FP32 with FP64 acceptance)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,ld", [(1, 1), (37, 64), (8191, 8224), (65536, 65536)])
+def test_arm_fp32_parity(mcproj, n, ld):
+    wl = W.arm_workload(n=65536)
+    q0 = f32_exact(wl.q[:, :n])
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
+    O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
+    gpu = run_gpu(P, q0, wl.params, ld=ld)
+    ora = O.project_params(q0, wl.params)
+    st = compare_projection(gpu, ora, wl.params.tol, oracle=O)
+    assert st["conv_gpu"] > 0.99
+
+
+def test_arm_fp64_plain_parity(mcproj):
+    wl = W.arm_workload(n=4099)
+    wl.params.precision = W.PREC_FP64
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
+    O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
+    gpu = run_gpu(P, wl.q, wl.params, dtype=torch.float64)
+    ora = O.project_params(wl.q, wl.params)
+    st = compare_projection(gpu, ora, wl.params.tol, q_tol=1e-9, oracle=O)
+    assert st["iters_equal"] > 0.999
+
+
+def test_arm_pose_fp32_parity(mcproj):
+    """6-D TSR (Eq. 1) on the 7-DoF arm, reference pose taken at a seeded q_ref."""
+    wl = W.arm_workload(n=2048)
+    rng = np.random.default_rng(5)
+    q_ref = rng.uniform(-1.5, 1.5, 7)
+    cons = [W.Constraint(W.C_POSE, frame_a=0, q_ref=q_ref)]
+    q0 = f32_exact(q_ref[:, None] + 0.3 * rng.standard_normal((7, 2048)))
+    P = mcproj.Projector(wl.robot, cons, wl.obstacles)
+    O = orc.Oracle(wl.robot, cons, wl.obstacles)
+    Pg, Qg, tg = P.constraint(0)
+    Po, Qo, to = O.constraint_values(0)
+    np.testing.assert_allclose(Pg, Po, atol=1e-14)
+    gpu = run_gpu(P, q0, wl.params)
+    ora = O.project_params(q0, wl.params)
+    st = compare_projection(gpu, ora, wl.params.tol, oracle=O)
+    assert st["conv_oracle"] > 0.8
+
+
+def test_arm_check_fp32(mcproj):
+    wl = W.arm_workload(n=16384)
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
+    O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
+    q = f32_exact(wl.q)
+    hit = P.check(dev(q)).cpu().numpy()
+    h_o, m_o = O.check(q)
+    st = compare_collision(hit, h_o, m_o)
+    assert 0.05 < st["collide_frac"] < 0.95
+
+
+# ---------------------------------------------------------------------------
+# dual arm, relative pose (Eq. 2)
+# ---------------------------------------------------------------------------
+def test_dual_batch_fp32_parity(mcproj):
+    wl = W.dual_arm_workload(total=10, n_random=6000)
+    q0 = f32_exact(wl.q)
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
+    O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
+    Pg, _, _ = P.constraint(0)
+    Po, _, _ = O.constraint_values(0)
+    np.testing.assert_allclose(Pg, Po, atol=1e-14)
+    gpu = run_gpu(P, q0, wl.params)
+    ora = O.project_params(q0, wl.params)
+    compare_projection(gpu, ora, wl.params.tol, oracle=O)
+
+
+def test_dual_segments_fp32_parity(mcproj):
+    """Full uneven-segment workload (~262k points) in one persistent launch."""
+    wl = W.dual_arm_workload()
+    ex = wl.extra
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
+    O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
+    starts, _, _, _ = O.project_params(ex["raw_start"], wl.params)
+    seg = W.make_segments(f32_exact(starts), f32_exact(ex["raw_dir"]), ex["lengths"], ex["step"])
+    out, fl, it, r = P.project_segments(dev(seg.start), dev(seg.delta), dev(seg.length, torch.int32), wl.params)
+    torch.cuda.synchronize()
+    gpu = host(out, fl, it, r)
+    gpu = (gpu[0], gpu[1], gpu[2].astype(np.int32), gpu[3])
+    # the oracle projects the same points, formed in FP32 exactly as the kernel forms them
+    d = torch.tensor(seg.delta, dtype=torch.float32)
+    s = torch.tensor(seg.start, dtype=torch.float32)
+    t = torch.cat([torch.arange(int(ln), dtype=torch.float32) for ln in seg.length])
+    sid = torch.repeat_interleave(torch.arange(seg.length.shape[0]), torch.tensor(seg.length, dtype=torch.long))
+    pts = torch.addcmul(s[:, sid], t[None, :], d[:, sid]).double().numpy()
+    ora = O.project_params(pts, wl.params)
+    st = compare_projection(gpu, ora, wl.params.tol, oracle=O)
+    assert st["n"] == seg.total and st["conv_gpu"] > 0.99
+
+
+def test_dual_check_fp32(mcproj):
+    wl = W.dual_arm_workload(total=10, n_random=8192)
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
+    O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
+    q = f32_exact(wl.q)
+    hit = P.check(dev(q)).cpu().numpy()
+    h_o, m_o = O.check(q)
+    compare_collision(hit, h_o, m_o)
+
+
+def test_dual_vjp(mcproj):
+    wl = W.adjoint_workload(n=4096)
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
+    O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
+    q0 = f32_exact(wl.q)
+    qs, fl, _, _ = run_gpu(P, q0, wl.params)
+    conv = (fl & 1) != 0
+    g = f32_exact(wl.extra["g"])
+    v, vf = P.vjp(dev(qs), dev(g))
+    torch.cuda.synchronize()
+    v = v.cpu().numpy()
+    v_o, f_o = O.vjp(qs.astype(np.float64), g)
+    rel = np.linalg.norm(v - v_o, axis=0) / np.linalg.norm(v_o, axis=0)
+    assert np.quantile(rel[conv], 0.999) < 1e-4 and rel[conv].max() < 1e-3, rel.max()
+
+
+# ---------------------------------------------------------------------------
+# humanoid collision check (tree FK, spheres + boxes)
+# ---------------------------------------------------------------------------
+def test_humanoid_check_fp32(mcproj):
+    wl = W.humanoid_workload(n=4096)
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
+    O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
+    q = f32_exact(wl.q)
+    hit = P.check(dev(q)).cpu().numpy()
+    h_o, m_o = O.check(q)
+    compare_collision(hit, h_o, m_o)
+
+
+# ---------------------------------------------------------------------------
+# path length and its gradient
+# ---------------------------------------------------------------------------
+def test_path_length_grad(mcproj):
+    wl = W.dual_arm_workload(total=10)
+    P = mcproj.Projector(wl.robot, wl.constraints)
+    rng = np.random.default_rng(2)
+    n_paths, n_way = 37, 9
+    Q = rng.standard_normal((14, n_paths * n_way)).astype(np.float32)
+    Q[:, 5] = Q[:, 4]   # a zero-length edge contributes no gradient
+    L, G = P.path_length_grad(dev(Q), n_paths, n_way)
+    torch.cuda.synchronize()
+    Qt = torch.tensor(Q, dtype=torch.float64, requires_grad=True)
+    E = Qt.reshape(14, n_paths, n_way)
+    e = E[:, :, 1:] - E[:, :, :-1]
+    nrm = torch.sqrt((e * e).sum(0))
+    Lr = nrm.sum(1)
+    Lr.sum().backward()
+    np.testing.assert_allclose(L.cpu().numpy(), Lr.detach().numpy(), rtol=1e-5)
+    Gr = Qt.grad.numpy()
+    Gr[:, 4:6] = np.nan_to_num(Gr[:, 4:6])
+    np.testing.assert_allclose(G.cpu().numpy(), Gr, rtol=1e-4, atol=1e-5)
+
+
+# ---------------------------------------------------------------------------
+# edge cases and argument errors
+# ---------------------------------------------------------------------------
+def test_edge_cases(mcproj):
+    wl = W.arm_workload(n=64)
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
+    O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
+    # n = 0 is a no-op
+    q = dev(f32_exact(wl.q))
+    P.project(q, wl.params, n=0)
+    # non-finite inputs are flagged, not propagated as faults
+    qn = q.clone()
+    qn[3, 5] = float("nan")
+    qn[0, 7] = float("inf")
+    out, fl, it, r = P.project(qn, wl.params)
+    fl = fl.cpu().numpy()
+    assert fl[5] & mcproj.F_NONFINITE and fl[7] & mcproj.F_NONFINITE
+    assert (fl[[0, 1, 2]] & mcproj.F_CONVERGED).all()
+    # the divergence exit (Alg. 2 MaxDistance) keeps the last accepted iterate
+    p = W.Params(tol=1e-5, max_iters=30, lam=1e-6, max_step=0.05)
+    q0 = f32_exact(wl.q)
+    gpu = run_gpu(P, q0, p)
+    ora = O.project(q0, 1e-5, 30, 1e-6, max_step=0.05)
+    assert ((gpu[1] & 4) != 0).mean() > 0.3
+    assert (((gpu[1] & 4) != 0) == ((ora[1] & 4) != 0)).mean() >= 0.95
+    div = ((gpu[1] & 4) != 0) & ((ora[1] & 4) != 0) & (gpu[2] == ora[2])
+    assert np.abs(gpu[0][:, div] - ora[0][:, div]).max() < 1e-4
+    # in-place projection (q_out aliases q_in)
+    qa = dev(q0)
+    ref = P.project(qa.clone(), wl.params)[0]
+    P.project(qa, wl.params, out=qa)
+    torch.cuda.synchronize()
+    assert torch.equal(qa, ref)
+    # cap = 0: no steps, residual reported
+    p0 = W.Params(tol=1e-5, max_iters=0, lam=1e-6)
+    _, fl0, it0, r0 = run_gpu(P, q0, p0)
+    assert (it0 == 0).all() and ((fl0 & 2) != 0).mean() > 0.9
+    # argument errors are reported, nothing is launched
+    with pytest.raises(mcproj.MCPError):
+        P.project(q, W.Params(tol=-1.0))
+    with pytest.raises(mcproj.MCPError):
+        P.project(q.cpu(), wl.params)
+    with pytest.raises(mcproj.MCPError):
+        P.project(q, wl.params, n=q.shape[1] + 1)
+
+
+def test_unsupported_stack_is_reported(mcproj):
+    """A constraint stack with no compiled problem class is refused, not run on the CPU."""
+    wl = W.arm_workload(n=8)
+    cons = [W.Constraint(W.C_AXIS_ALIGN, frame_a=0), W.Constraint(W.C_COM_XY, target=np.zeros(3))]
+    P = mcproj.Projector(wl.robot, cons, wl.obstacles)
+    with pytest.raises(mcproj.MCPError) as e:
+        P.project(dev(f32_exact(wl.q)), wl.params)
+    assert e.value.status == mcproj.MCP_ERR_UNSUPPORTED
