@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--workload", default="arm", choices=["arm", "dual_arm", "sphere"])
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="fixed launch count for profilers: no time-padded warm-up, no CPU baseline, no e2e pass")
     return ap.parse_args()
 
 
@@ -117,7 +119,7 @@ def cpu_baseline(wl, q, budget_s=10.0):
     done = conv = 0
     t0 = time.perf_counter()
     off = 0
-    while time.perf_counter() - t0 < budget_s and done < q.shape[1] * 4:
+    while time.perf_counter() - t0 < budget_s:
         sl = q[:, off:off + chunk]
         out, fl, _, r = O.project(sl, p.tol, p.max_iters, p.lam, max_step=p.max_step, threads=threads)
         O.check(out, threads=threads)
@@ -210,16 +212,23 @@ def run_ours(args):
         if ev:
             ev[2].record(stream)
 
-    for _ in range(args.warmup):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    launches0 = P.launches
     sampler = ClockSampler(local)
     with sampler:
+        # warm-up: at least W steps and at least ~1.5 s of back-to-back load, so
+        # that the clock sampler sees the GPU under load around the timed steps
+        t0 = time.perf_counter()
+        w = 0
+        while w < args.warmup or (not args.profile and time.perf_counter() - t0 < 1.5):
+            flush.zero_()
+            step()
+            w += 1
+            if w % 64 == 0:
+                torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        launches0 = P.launches
         torch.cuda.synchronize()
         for s in range(args.steps):
             flush.zero_()          # L2 flush between timed steps (outside the events)
@@ -228,6 +237,10 @@ def run_ours(args):
     launches = P.launches - launches0
     if world > 1:
         dist.barrier()
+    pairs = torch.zeros(n, dtype=torch.int32, device=dev)
+    P.check(q_out, out=hit, pairs=pairs, stream=stream)   # untimed: counts the pairs the timed kernel tested
+    torch.cuda.synchronize()
+    pairs_total = float(pairs.double().sum().item())
     t_proj = [e[0].elapsed_time(e[1]) for e in evs]
     t_check = [e[1].elapsed_time(e[2]) for e in evs]
     t_step = [e[0].elapsed_time(e[2]) for e in evs]
@@ -250,7 +263,7 @@ def run_ours(args):
     fl_host = torch.empty(n, dtype=torch.uint8).pin_memory()
     hit_host = torch.empty(n, dtype=torch.uint8).pin_memory()
     e2e_ms = []
-    for s in range(args.warmup + args.steps):
+    for s in range(0 if args.profile else args.warmup + args.steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -264,12 +277,12 @@ def run_ours(args):
         if s >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
     conv_e2e = int(((fl_host.numpy() & mcproj.F_CONVERGED) != 0).sum())
-    e2e_t = torch.tensor([sum(e2e_ms) / len(e2e_ms)], dtype=torch.float64, device=dev)
+    e2e_t = torch.tensor([sum(e2e_ms) / max(1, len(e2e_ms))], dtype=torch.float64, device=dev)
     e2e_c = torch.tensor([conv_e2e], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
         dist.all_reduce(e2e_c, op=dist.ReduceOp.SUM)
-    e2e = {"value": float(e2e_c.item()) / (float(e2e_t.item()) * 1e-3), "unit": UNIT,
+    e2e = {"value": float(e2e_c.item()) / (float(e2e_t.item()) * 1e-3) if e2e_ms else None, "unit": UNIT,
            "h2d_bytes_per_step": q_host.numel() * q_host.element_size(),
            "d2h_bytes_per_step": out_host.numel() * out_host.element_size() + 2 * n}
 
@@ -284,6 +297,10 @@ def run_ours(args):
     peak64 = 1.25                                         # nominal dense FP64, TFLOP/s
     mp = sum(t_proj) / len(t_proj)
     mc = sum(t_check) / len(t_check)
+    # collision: FK with translations + per sphere block transform + 4 FMA per pair tested
+    check_flops = n * (fm.fk_positions() + 25 * wl.robot.n_spheres) + 8.0 * pairs_total
+    check_roof = {"kernel": "k_check_f32", "achieved": check_flops / (mc * 1e-3) / 1e12,
+                  "pairs_per_config": pairs_total / n}
     if fp64:
         flops_proj = fp32 + fp64f   # the plain kernel does all of it in FP64
         ach = flops_proj / (mp * 1e-3) / 1e12
@@ -301,9 +318,16 @@ def run_ours(args):
                 "mixed_bound_frac": t_min / (mp * 1e-3),
                 "flops_per_config": {"fp32": fp32 / n, "fp64": fp64f / n}}
     kernel_ms = {"project": mp, "check": mc}
+    roof["check"] = check_roof
+    roof["check"]["frac"] = check_roof["achieved"] / peak32
+    if mc > mp and not fp64:   # the dominant kernel carries the headline roofline
+        roof = {"bound": "alu", "achieved": check_roof["achieved"], "peak": peak32, "unit": "TFLOP/s",
+                "frac": check_roof["achieved"] / peak32, "traffic": None,
+                "kernel": "k_check_f32 (collision, 8 flops per sphere-obstacle pair)",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock", "projection": roof}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.profile):
         cpu = cpu_baseline(wl, q_np if not fp64 else q_np)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -176,9 +176,11 @@ mcp_status mcp_project_segments(mcp_ctx *ctx, const mcp_project_params *p, int64
 /* CollisionFree (Alg. 2) of n configurations: in_collision[i] = 1 iff some
  * robot sphere overlaps some obstacle sphere (|c_s - c_o| < r_s + r_o) or box
  * (distance from c_s to the box < r_s).  q: [d * ld] float (precision 0) or
- * double (precision 1). */
+ * double (precision 1).  Each configuration stops at the first block of
+ * spheres that overlaps; pairs_tested [n] (uint32, may be NULL) receives the
+ * number of sphere-obstacle pairs evaluated for it (work accounting). */
 mcp_status mcp_check_batch(mcp_ctx *ctx, int64_t n, int64_t ld, const void *q, int32_t precision,
-                           uint8_t *in_collision, mcp_stream stream);
+                           uint8_t *in_collision, uint32_t *pairs_tested, mcp_stream stream);
 
 /* Vector-Jacobian product of the projection at points on the manifold
  * (implicit-function theorem; the paper makes its log map differentiable "to

@@ -1,7 +1,30 @@
-// Kernel instantiations for the ProbHumanoid36 problem class (collision check;
-// projection of this class runs in the warp-cooperative kernels).
-#include "mcp_kernels.cuh"
+// Kernel instantiations for the ProbHumanoid36 problem class: the FP32 path
+// runs the warp-cooperative kernel, the plain FP64 path and the collision
+// check the thread-per-configuration kernels.
+#include "mcp_warp.cuh"
 
 namespace mcp {
-MCP_INSTANTIATE_CHECK_ONLY(ProbHumanoid36)
+
+template <>
+cudaError_t launch_project<ProbHumanoid36>(const HostModel &hm, const ProjCall &c, int *launches) {
+  if (c.precision == 1) {
+    if (c.total <= 0) return cudaSuccess;
+    if (c.segments) return cudaErrorNotSupported;
+    cudaError_t e = launch_plain64<ProbHumanoid36>(hm, c, BatchSrc<double>{static_cast<const double *>(c.q_in), c.ld_in});
+    *launches += 1;
+    return e;
+  }
+  return launch_project_warp<ProbHumanoid36>(hm, c, launches);
+}
+
+template <>
+cudaError_t launch_check<ProbHumanoid36>(const HostModel &hm, const CheckCall &c, int *launches) {
+  return launch_check_impl<ProbHumanoid36>(hm, c, launches);
+}
+
+template <>
+cudaError_t launch_vjp<ProbHumanoid36>(const HostModel &, const VjpCall &, int *) {
+  return cudaErrorNotSupported;
+}
+
 }  // namespace mcp

@@ -66,7 +66,7 @@ ClassDesc describe(bool project) {
 const std::vector<ClassDesc> &registry() {
   static const std::vector<ClassDesc> r = {describe<ProbSphere3>(true), describe<ProbArm7Axis>(true),
                                            describe<ProbArm7Pose>(true), describe<ProbDual14Rel>(true),
-                                           describe<ProbHumanoid36>(false)};
+                                           describe<ProbHumanoid36>(true)};
   return r;
 }
 
@@ -218,6 +218,62 @@ __global__ void k_resolve(const __grid_constant__ ResolveIn in, ResolveOut *out)
   out->inv_mass = M > 0.0 ? 1.0 / M : 0.0;
 }
 
+// Obstacle preparation (one block): centroid of the obstacle centres (FP64),
+// then per obstacle sphere the FP32 records of the expanded overlap test in
+// the shifted frame: (-2c, |c|^2 - r^2), (-2r, 0, 0, 0); boxes shifted.
+__global__ void k_prep_obstacles(const double *obs, int n_obs, const double *box, int n_box, float *obs32,
+                                 float *box32, double *origin) {
+  __shared__ double part[3][256];
+  const int t = threadIdx.x;
+  double sx = 0.0, sy = 0.0, sz = 0.0;
+  for (int o = t; o < n_obs; o += blockDim.x) {
+    sx += obs[4 * o];
+    sy += obs[4 * o + 1];
+    sz += obs[4 * o + 2];
+  }
+  if (n_obs == 0)
+    for (int b = t; b < n_box; b += blockDim.x) {
+      sx += 0.5 * (box[6 * b] + box[6 * b + 3]);
+      sy += 0.5 * (box[6 * b + 1] + box[6 * b + 4]);
+      sz += 0.5 * (box[6 * b + 2] + box[6 * b + 5]);
+    }
+  part[0][t] = sx;
+  part[1][t] = sy;
+  part[2][t] = sz;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (t < w)
+      for (int c = 0; c < 3; ++c) part[c][t] += part[c][t + w];
+    __syncthreads();
+  }
+  const int cnt = n_obs > 0 ? n_obs : n_box;
+  const double ox = cnt ? part[0][0] / cnt : 0.0, oy = cnt ? part[1][0] / cnt : 0.0, oz = cnt ? part[2][0] / cnt : 0.0;
+  if (t == 0) {
+    origin[0] = ox;
+    origin[1] = oy;
+    origin[2] = oz;
+  }
+  for (int o = t; o < n_obs; o += blockDim.x) {
+    const double cx = obs[4 * o] - ox, cy = obs[4 * o + 1] - oy, cz = obs[4 * o + 2] - oz, r = obs[4 * o + 3];
+    obs32[8 * o + 0] = static_cast<float>(-2.0 * cx);
+    obs32[8 * o + 1] = static_cast<float>(-2.0 * cy);
+    obs32[8 * o + 2] = static_cast<float>(-2.0 * cz);
+    obs32[8 * o + 3] = static_cast<float>(cx * cx + cy * cy + cz * cz - r * r);
+    obs32[8 * o + 4] = static_cast<float>(-2.0 * r);
+    obs32[8 * o + 5] = 0.f;
+    obs32[8 * o + 6] = 0.f;
+    obs32[8 * o + 7] = 0.f;
+  }
+  for (int b = t; b < n_box; b += blockDim.x) {
+    box32[6 * b + 0] = static_cast<float>(box[6 * b + 0] - ox);
+    box32[6 * b + 1] = static_cast<float>(box[6 * b + 1] - oy);
+    box32[6 * b + 2] = static_cast<float>(box[6 * b + 2] - oz);
+    box32[6 * b + 3] = static_cast<float>(box[6 * b + 3] - ox);
+    box32[6 * b + 4] = static_cast<float>(box[6 * b + 4] - oy);
+    box32[6 * b + 5] = static_cast<float>(box[6 * b + 5] - oz);
+  }
+}
+
 // Exclusive prefix sum of segment lengths into off[0..n]; one block.
 __global__ void k_scan_lengths(const int32_t *len, long long n, long long *off) {
   __shared__ long long part[1024];
@@ -296,8 +352,10 @@ struct mcp_ctx {
   double2 *d_tab = nullptr;
   float4 *d_obs32 = nullptr;
   double *d_obs64 = nullptr;
-  float4 *d_box32 = nullptr;
+  float *d_box32 = nullptr;
   double *d_box64 = nullptr;
+  double *d_origin = nullptr;
+  double origin[3] = {0.0, 0.0, 0.0};
   unsigned long long *d_counter = nullptr;
   long long *d_seg_off = nullptr;
   long long seg_cap = 0;
@@ -320,6 +378,10 @@ mcp_status fail(mcp_ctx *c, mcp_status s, const char *fmt, ...) {
 }
 
 mcp_status cuda_fail(mcp_ctx *c, cudaError_t e, const char *what) {
+  if (e == cudaErrorNotSupported) {
+    cudaGetLastError();
+    return fail(c, MCP_ERR_UNSUPPORTED, "%s: not compiled for this problem class / precision / source", what);
+  }
   return fail(c, e == cudaErrorMemoryAllocation ? MCP_ERR_OOM : MCP_ERR_CUDA, "%s: %s", what,
               cudaGetErrorString(e));
 }
@@ -429,6 +491,17 @@ void fill_constraints(const ResolveOut &ro, int nc, int nj, ModelT<T> &m) {
   m.inv_mass = static_cast<T>(ro.inv_mass);
 }
 
+// The collision-frame copy of the FP32 model: root offsets minus the obstacle origin.
+void update_shifted(mcp_ctx *ctx) {
+  ctx->hm.m32_shifted = ctx->hm.m32;
+  for (int j = 0; j < ctx->robot.nj; ++j) {
+    if (ctx->robot.parent[j] >= 0) continue;
+    for (int r = 0; r < 3; ++r)
+      ctx->hm.m32_shifted.X[j][r * 4 + 3] = static_cast<float>(ctx->robot.X[12 * j + r * 4 + 3] - ctx->origin[r]);
+  }
+  for (int r = 0; r < 3; ++r) ctx->hm.m32_shifted.shift[r] = static_cast<float>(ctx->origin[r]);
+}
+
 mcp_status check_batch_ptr(mcp_ctx *ctx, const void *p, const char *name) {
   if (!p) return fail(ctx, MCP_ERR_ARG, "%s is NULL", name);
   cudaPointerAttributes at;
@@ -500,6 +573,7 @@ mcp_status ensure_resolved(mcp_ctx *ctx) {
   fill_sphere_table(r, ctx->hm.st32);
   fill_sphere_table(r, ctx->hm.st64);
   MCP_CUDA(cudaMemcpy(ctx->d_m64, &ctx->hm.m64, sizeof(ModelT<double>), cudaMemcpyHostToDevice), "model copy");
+  update_shifted(ctx);
   return MCP_OK;
 }
 
@@ -557,6 +631,7 @@ void mcp_destroy(mcp_ctx *ctx) {
   cudaFree(ctx->d_counter);
   cudaFree(ctx->d_seg_off);
   cudaFree(ctx->d_resolve);
+  cudaFree(ctx->d_origin);
   delete ctx;
 }
 
@@ -679,26 +754,23 @@ mcp_status mcp_load_obstacles(mcp_ctx *ctx, const double *spheres, int32_t n_sph
   ctx->d_obs64 = nullptr;
   ctx->d_box32 = nullptr;
   ctx->d_box64 = nullptr;
-  std::vector<float4> o32(n_spheres > 0 ? n_spheres : 1);
-  for (int i = 0; i < n_spheres; ++i)
-    o32[i] = make_float4(static_cast<float>(spheres[4 * i]), static_cast<float>(spheres[4 * i + 1]),
-                         static_cast<float>(spheres[4 * i + 2]), static_cast<float>(spheres[4 * i + 3]));
-  std::vector<float> b32(6 * (n_aabbs > 0 ? n_aabbs : 1));
-  for (int i = 0; i < 6 * n_aabbs; ++i) b32[i] = static_cast<float>(aabbs[i]);
+  ctx->obs_loaded = false;
   const size_t n_o = static_cast<size_t>(n_spheres > 0 ? n_spheres : 1);
   const size_t n_b = static_cast<size_t>(n_aabbs > 0 ? n_aabbs : 1);
-  MCP_CUDA(cudaMalloc(&ctx->d_obs32, n_o * sizeof(float4)), "cudaMalloc obstacles");
+  MCP_CUDA(cudaMalloc(&ctx->d_obs32, n_o * 2 * sizeof(float4)), "cudaMalloc obstacles");
   MCP_CUDA(cudaMalloc(&ctx->d_obs64, n_o * 4 * sizeof(double)), "cudaMalloc obstacles");
   MCP_CUDA(cudaMalloc(&ctx->d_box32, n_b * 6 * sizeof(float)), "cudaMalloc boxes");
   MCP_CUDA(cudaMalloc(&ctx->d_box64, n_b * 6 * sizeof(double)), "cudaMalloc boxes");
-  if (n_spheres) {
-    MCP_CUDA(cudaMemcpy(ctx->d_obs32, o32.data(), n_spheres * sizeof(float4), cudaMemcpyHostToDevice), "copy");
+  if (!ctx->d_origin) MCP_CUDA(cudaMalloc(&ctx->d_origin, 3 * sizeof(double)), "cudaMalloc origin");
+  if (n_spheres)
     MCP_CUDA(cudaMemcpy(ctx->d_obs64, spheres, n_spheres * 4 * sizeof(double), cudaMemcpyHostToDevice), "copy");
-  }
-  if (n_aabbs) {
-    MCP_CUDA(cudaMemcpy(ctx->d_box32, b32.data(), n_aabbs * 6 * sizeof(float), cudaMemcpyHostToDevice), "copy");
+  if (n_aabbs)
     MCP_CUDA(cudaMemcpy(ctx->d_box64, aabbs, n_aabbs * 6 * sizeof(double), cudaMemcpyHostToDevice), "copy");
-  }
+  k_prep_obstacles<<<1, 256>>>(ctx->d_obs64, n_spheres, ctx->d_box64, n_aabbs, reinterpret_cast<float *>(ctx->d_obs32),
+                               ctx->d_box32, ctx->d_origin);
+  ctx->launches += 1;
+  MCP_CUDA(cudaGetLastError(), "obstacle preparation launch");
+  MCP_CUDA(cudaMemcpy(ctx->origin, ctx->d_origin, 3 * sizeof(double), cudaMemcpyDeviceToHost), "origin copy");
   ctx->hm.d_obs32 = ctx->d_obs32;
   ctx->hm.d_obs64 = ctx->d_obs64;
   ctx->hm.d_box32 = ctx->d_box32;
@@ -706,6 +778,7 @@ mcp_status mcp_load_obstacles(mcp_ctx *ctx, const double *spheres, int32_t n_sph
   ctx->hm.n_obs = n_spheres;
   ctx->hm.n_box = n_aabbs;
   ctx->obs_loaded = true;
+  update_shifted(ctx);
   return MCP_OK;
 }
 
@@ -812,7 +885,7 @@ mcp_status mcp_project_segments(mcp_ctx *ctx, const mcp_project_params *p, int64
 }
 
 mcp_status mcp_check_batch(mcp_ctx *ctx, int64_t n, int64_t ld, const void *q, int32_t precision,
-                           uint8_t *in_collision, mcp_stream stream) {
+                           uint8_t *in_collision, uint32_t *pairs_tested, mcp_stream stream) {
   if (!ctx) return MCP_ERR_ARG;
   if (!ctx->robot_loaded) return fail(ctx, MCP_ERR_STATE, "robot not loaded");
   if (!ctx->obs_loaded) return fail(ctx, MCP_ERR_STATE, "obstacles not loaded");
@@ -823,8 +896,10 @@ mcp_status mcp_check_batch(mcp_ctx *ctx, int64_t n, int64_t ld, const void *q, i
   mcp_status st;
   if ((st = check_batch_ptr(ctx, q, "q")) != MCP_OK) return st;
   if ((st = check_batch_ptr(ctx, in_collision, "in_collision")) != MCP_OK) return st;
+  if (pairs_tested && (st = check_batch_ptr(ctx, pairs_tested, "pairs_tested")) != MCP_OK) return st;
   DeviceGuard g(ctx->device);
   CheckCall c;
+  c.pairs = pairs_tested;
   c.precision = precision;
   c.n = n;
   c.ld = ld;

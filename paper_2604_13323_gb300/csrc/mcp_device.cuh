@@ -44,6 +44,7 @@ struct ModelT {
   T ctgt[MAXC][4];    // SPHERE radius; COM target xy
   T msub[MAXJ];       // mass of the subtree below (and including) joint j
   T inv_mass;         // 1 / total mass
+  T shift[3];         // collision frame: world coordinates minus this origin (root offsets are pre-shifted)
 };
 
 // ---------------------------------------------------------------------------
@@ -351,6 +352,7 @@ struct Kin {
   V3<T> z[P::D];      // world axis of joint j
   T fR[P::NF > 0 ? P::NF : 1][9];
   V3<T> fp[P::NF > 0 ? P::NF : 1];
+  V3<T> mc;           // sum_j m_j c_j (accumulated during FK when a CoM constraint is present)
 };
 
 template <class P, bool POS, class Ops, typename T>
@@ -369,6 +371,7 @@ __device__ __forceinline__ void fk(const Ops &ops, const ModelT<T> &m, const T (
       if constexpr (POS) ppre = add_rot_t<P::xtmask(j)>(k.p[pa], k.R[pa], load_p(m.X[j]));
     }
     k.z[j] = col(Rpre, 2);
+    if constexpr (j == 0 && POS && needs_com<P>()) k.mc = V3<T>{T(0), T(0), T(0)};
     if constexpr (P::jtype(j) == REV) {
       T s, c;
       ops.sincos(q[j], s, c);
@@ -381,6 +384,10 @@ __device__ __forceinline__ void fk(const Ops &ops, const ModelT<T> &m, const T (
 #pragma unroll
       for (int i = 0; i < 9; ++i) k.R[j][i] = Rpre[i];
       if constexpr (POS) k.p[j] = {fma_(q[j], Rpre[2], ppre.x), fma_(q[j], Rpre[5], ppre.y), fma_(q[j], Rpre[8], ppre.z)};
+    }
+    if constexpr (POS && needs_com<P>()) {
+      const V3<T> ci = add_rot_t<7>(k.p[j], k.R[j], V3<T>{m.com[j][0], m.com[j][1], m.com[j][2]});
+      k.mc = {fma_(m.mass[j], ci.x, k.mc.x), fma_(m.mass[j], ci.y, k.mc.y), fma_(m.mass[j], ci.z, k.mc.z)};
     }
   });
   static_for<P::NF>([&](auto FF) {

@@ -28,14 +28,15 @@ struct Tuning {
 
 struct HostModel {
   ModelT<float> m32;
+  ModelT<float> m32_shifted;  // m32 in the collision frame (origin at the obstacle centroid)
   ModelT<double> m64;
   SphereTable<float> st32;
   SphereTable<double> st64;
   const ModelT<double> *d_m64 = nullptr;  // device copy of m64
   const double2 *d_tab = nullptr;         // FP64 sin/cos table, 256 entries
-  const float4 *d_obs32 = nullptr;        // obstacle spheres (x, y, z, r)
+  const float4 *d_obs32 = nullptr;        // per obstacle 2 x float4: (-2c, |c|^2 - r^2), (-2r, 0, 0, 0), shifted
   const double *d_obs64 = nullptr;        // [n_obs * 4]
-  const float4 *d_box32 = nullptr;        // boxes as (lo.xyz, 0), (hi.xyz, 0)
+  const float *d_box32 = nullptr;         // [n_box * 6] lo.xyz, hi.xyz, shifted
   const double *d_box64 = nullptr;        // [n_box * 6]
   int n_obs = 0;
   int n_box = 0;
@@ -76,6 +77,7 @@ struct CheckCall {
   long long n = 0, ld = 0;
   const void *q = nullptr;
   uint8_t *out = nullptr;
+  uint32_t *pairs = nullptr;
   cudaStream_t stream = 0;
 };
 

@@ -111,26 +111,23 @@ __device__ __forceinline__ void residual(const ModelT<T> &m, const T (&q)[P::D],
       F[r0 + 4] = lg.phi.y;
       F[r0 + 5] = lg.phi.z;
     } else if constexpr (kind == K_COM) {
-      // Sec. V-C: x_com = sum_i m_i c_i / M with c_i = T_i com_i.  With WANT_J the
-      // subtree sums C_j = m_j c_j + sum over children are built in reverse
-      // topological order (children have larger indices).
-      V3<T> tot{T(0), T(0), T(0)};
-      static_for<P::D>([&](auto JJ) {
-        constexpr int j = P::D - 1 - decltype(JJ)::value;
-        const V3<T> ci = add_rot_t<7>(k.p[j], k.R[j], V3<T>{m.com[j][0], m.com[j][1], m.com[j][2]});
-        const V3<T> mc{m.mass[j] * ci.x, m.mass[j] * ci.y, m.mass[j] * ci.z};
-        tot = {tot.x + mc.x, tot.y + mc.y, tot.z + mc.z};
-        if constexpr (WANT_J) {
-          V3<T> acc = mc;
+      // Sec. V-C: x_com = sum_i m_i c_i / M with c_i = T_i com_i (the sum is
+      // accumulated during FK).  With WANT_J the subtree sums C_j = m_j c_j +
+      // sum over children are built in reverse topological order.
+      if constexpr (WANT_J) {
+        static_for<P::D>([&](auto JJ) {
+          constexpr int j = P::D - 1 - decltype(JJ)::value;
+          const V3<T> ci = add_rot_t<7>(k.p[j], k.R[j], V3<T>{m.com[j][0], m.com[j][1], m.com[j][2]});
+          V3<T> acc{m.mass[j] * ci.x, m.mass[j] * ci.y, m.mass[j] * ci.z};
           static_for<P::D>([&](auto II) {
             constexpr int i = decltype(II)::value;
             if constexpr (i > j && P::parent(i) == j) acc = {acc.x + e.C[i].x, acc.y + e.C[i].y, acc.z + e.C[i].z};
           });
           e.C[j] = acc;
-        }
-      });
-      F[r0] = fma_(tot.x, m.inv_mass, -m.ctgt[c][0]);
-      F[r0 + 1] = fma_(tot.y, m.inv_mass, -m.ctgt[c][1]);
+        });
+      }
+      F[r0] = fma_(k.mc.x, m.inv_mass, -m.ctgt[c][0]);
+      F[r0 + 1] = fma_(k.mc.y, m.inv_mass, -m.ctgt[c][1]);
     }
   });
 }
@@ -714,21 +711,33 @@ __global__ void __launch_bounds__(128) k_project_f64(const __grid_constant__ Pro
 
 // ---------------------------------------------------------------------------
 // Collision check (CollisionFree of Alg. 2): link spheres against obstacle
-// spheres and boxes; obstacles staged in shared memory, early exit on the
-// first overlap.  One thread per configuration.
+// spheres and boxes.  One thread per configuration.
+//
+// FP32 path: coordinates are shifted by the obstacle centroid o (applied to
+// the robot base translations and to the staged obstacles), and the sphere
+// test |c_s - c_o| < r_s + r_o is evaluated in the expanded form
+//     c_s . (-2 c_o) + (|c_o|^2 - r_o^2) + r_s (-2 r_o)  <  -(|c_s|^2 - r_s^2)
+// with the obstacle terms precomputed: 4 FMA + 1 min per pair.  Spheres are
+// processed in register blocks of 8 per link (ILP), obstacles are read from
+// shared memory with one broadcast load each; the configuration exits after
+// the first block that overlaps an obstacle.  In the shifted frame |c| stays
+// within a few metres, so the FP32 cancellation error of the expanded form
+// stays below ~1e-5 m in distance (verified against the FP64 oracle).
+// FP64 path: the plain difference form, one sphere at a time.
 // ---------------------------------------------------------------------------
 template <class P, typename T>
 struct CheckArgs {
   ModelT<T> m;
   SphereTable<T> st;
-  const T *obs;  // [n_obs * 4]
-  const T *box;  // [n_box * 6]
+  const T *obs;  // FP32: [n_obs * 8] (-2c, |c|^2 - r^2, -2r, pad) in the shifted frame; FP64: [n_obs * 4]
+  const T *box;  // [n_box * 6] (FP32: shifted)
   int n_obs;
   int n_box;
   const T *q;
   long long ld;
   long long n;
   uint8_t *out;
+  uint32_t *pairs;  // optional: number of sphere-obstacle pairs tested per configuration
   const double2 *tab;
 };
 
@@ -738,12 +747,7 @@ __device__ __forceinline__ T max_(T a, T b) {
 }
 
 template <typename T>
-__device__ __forceinline__ bool sphere_hits(V3<T> c, T rs, const T *s_obs, int n_obs, const T *s_box, int n_box) {
-  for (int o = 0; o < n_obs; ++o) {
-    const T dx = c.x - s_obs[4 * o], dy = c.y - s_obs[4 * o + 1], dz = c.z - s_obs[4 * o + 2];
-    const T rr = rs + s_obs[4 * o + 3];
-    if (fma_(dx, dx, fma_(dy, dy, dz * dz)) < rr * rr) return true;
-  }
+__device__ __forceinline__ bool box_hits(V3<T> c, T rs, const T *s_box, int n_box) {
   for (int b = 0; b < n_box; ++b) {
     const T *bx = s_box + 6 * b;
     const T ex = max_(max_(bx[0] - c.x, c.x - bx[3]), T(0));
@@ -754,36 +758,115 @@ __device__ __forceinline__ bool sphere_hits(V3<T> c, T rs, const T *s_obs, int n
   return false;
 }
 
-template <class P, typename T, class Ops>
-__global__ void __launch_bounds__(128) k_check(const __grid_constant__ CheckArgs<P, T> a) {
+template <typename T>
+__device__ __forceinline__ bool sphere_hits_plain(V3<T> c, T rs, const T *s_obs, int n_obs, const T *s_box, int n_box) {
+  for (int o = 0; o < n_obs; ++o) {
+    const T dx = c.x - s_obs[4 * o], dy = c.y - s_obs[4 * o + 1], dz = c.z - s_obs[4 * o + 2];
+    const T rr = rs + s_obs[4 * o + 3];
+    if (fma_(dx, dx, fma_(dy, dy, dz * dz)) < rr * rr) return true;
+  }
+  return box_hits<T>(c, rs, s_box, n_box);
+}
+
+constexpr int SPH_BLOCK = 8;
+
+template <class P>
+__global__ void __launch_bounds__(128) k_check_f32(const __grid_constant__ CheckArgs<P, float> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *s_obs = reinterpret_cast<T *>(smem_raw);
-  T *s_box = s_obs + 4 * a.n_obs;
+  float4 *s_obs = reinterpret_cast<float4 *>(smem_raw);          // 2 float4 per obstacle
+  float *s_box = reinterpret_cast<float *>(s_obs + 2 * a.n_obs);
+  for (int t = threadIdx.x; t < 8 * a.n_obs; t += blockDim.x) reinterpret_cast<float *>(s_obs)[t] = a.obs[t];
+  for (int t = threadIdx.x; t < 6 * a.n_box; t += blockDim.x) s_box[t] = a.box[t];
+  __syncthreads();
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  constexpr int D = P::D;
+  const OpsF32 ops{a.tab};
+  float q[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) q[j] = a.q[j * a.ld + i];
+  bool hit = false;
+  uint32_t pairs = 0;
+  // spheres of `count` at local centres transformed by (R, p); obstacle loop with 8 spheres in registers
+  auto test_block = [&](const float (&R)[9], V3<float> p, int s0, int count) {
+    float cx[SPH_BLOCK], cy[SPH_BLOCK], cz[SPH_BLOCK], rs[SPH_BLOCK], ks[SPH_BLOCK], mn[SPH_BLOCK];
+#pragma unroll
+    for (int b = 0; b < SPH_BLOCK; ++b) {
+      const int s = s0 + (b < count ? b : 0);
+      const V3<float> c = add_rot_t<7>(p, R, V3<float>{a.st.s[s][0], a.st.s[s][1], a.st.s[s][2]});
+      cx[b] = c.x;
+      cy[b] = c.y;
+      cz[b] = c.z;
+      rs[b] = a.st.s[s][3];
+      ks[b] = fmaf(c.x, c.x, fmaf(c.y, c.y, fmaf(c.z, c.z, -rs[b] * rs[b])));
+      mn[b] = FLT_MAX;
+    }
+    for (int o = 0; o < a.n_obs; ++o) {
+      const float4 g = s_obs[2 * o];       // -2 c_o, |c_o|^2 - r_o^2
+      const float g2 = s_obs[2 * o + 1].x; // -2 r_o
+#pragma unroll
+      for (int b = 0; b < SPH_BLOCK; ++b)
+        mn[b] = fminf(mn[b], fmaf(cx[b], g.x, fmaf(cy[b], g.y, fmaf(cz[b], g.z, fmaf(rs[b], g2, g.w)))));
+    }
+    pairs += static_cast<uint32_t>(count * a.n_obs);
+    bool h = false;
+#pragma unroll
+    for (int b = 0; b < SPH_BLOCK; ++b)
+      if (b < count) h |= (mn[b] < -ks[b]) || box_hits<float>(V3<float>{cx[b], cy[b], cz[b]}, rs[b], s_box, a.n_box);
+    return h;
+  };
+  {
+    const float Ri[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+    for (int s = a.st.off[0]; s < a.st.off[1] && !hit; s += SPH_BLOCK)
+      hit = test_block(Ri, V3<float>{-a.m.shift[0], -a.m.shift[1], -a.m.shift[2]}, s,
+                       min(SPH_BLOCK, a.st.off[1] - s));
+  }
+  Kin<P, float> k;
+  fk<P, true>(ops, a.m, q, k);
+  static_for<D>([&](auto JJ) {
+    constexpr int j = decltype(JJ)::value;
+    const int e = a.st.off[j + 2];
+    for (int s = a.st.off[j + 1]; s < e && !hit; s += SPH_BLOCK)
+      hit = test_block(k.R[j], k.p[j], s, min(SPH_BLOCK, e - s));
+  });
+  a.out[i] = hit ? 1 : 0;
+  if (a.pairs) a.pairs[i] = pairs;
+}
+
+template <class P>
+__global__ void __launch_bounds__(128) k_check_f64(const __grid_constant__ CheckArgs<P, double> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *s_obs = reinterpret_cast<double *>(smem_raw);
+  double *s_box = s_obs + 4 * a.n_obs;
   for (int t = threadIdx.x; t < 4 * a.n_obs; t += blockDim.x) s_obs[t] = a.obs[t];
   for (int t = threadIdx.x; t < 6 * a.n_box; t += blockDim.x) s_box[t] = a.box[t];
   __syncthreads();
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   constexpr int D = P::D;
-  const Ops ops{a.tab};
-  T q[D];
+  const OpsF64Plain ops{a.tab};
+  double q[D];
 #pragma unroll
   for (int j = 0; j < D; ++j) q[j] = a.q[j * a.ld + i];
   bool hit = false;
-  // world-fixed spheres
-  for (int s = a.st.off[0]; s < a.st.off[1] && !hit; ++s)
-    hit = sphere_hits<T>(V3<T>{a.st.s[s][0], a.st.s[s][1], a.st.s[s][2]}, a.st.s[s][3], s_obs, a.n_obs, s_box,
-                         a.n_box);
-  Kin<P, T> k;
+  uint32_t pairs = 0;
+  for (int s = a.st.off[0]; s < a.st.off[1] && !hit; ++s) {
+    hit = sphere_hits_plain<double>(V3<double>{a.st.s[s][0], a.st.s[s][1], a.st.s[s][2]}, a.st.s[s][3], s_obs,
+                                    a.n_obs, s_box, a.n_box);
+    pairs += a.n_obs;
+  }
+  Kin<P, double> k;
   fk<P, true>(ops, a.m, q, k);
   static_for<D>([&](auto JJ) {
     constexpr int j = decltype(JJ)::value;
     for (int s = a.st.off[j + 1]; s < a.st.off[j + 2] && !hit; ++s) {
-      const V3<T> c = add_rot_t<7>(k.p[j], k.R[j], V3<T>{a.st.s[s][0], a.st.s[s][1], a.st.s[s][2]});
-      hit = sphere_hits<T>(c, a.st.s[s][3], s_obs, a.n_obs, s_box, a.n_box);
+      const V3<double> c = add_rot_t<7>(k.p[j], k.R[j], V3<double>{a.st.s[s][0], a.st.s[s][1], a.st.s[s][2]});
+      hit = sphere_hits_plain<double>(c, a.st.s[s][3], s_obs, a.n_obs, s_box, a.n_box);
+      pairs += a.n_obs;
     }
   });
   a.out[i] = hit ? 1 : 0;
+  if (a.pairs) a.pairs[i] = pairs;
 }
 
 // ---------------------------------------------------------------------------
@@ -1027,12 +1110,13 @@ cudaError_t launch_check_impl(const HostModel &hm, const CheckCall &c, int *laun
     a.ld = c.ld;
     a.n = c.n;
     a.out = c.out;
+    a.pairs = c.pairs;
     a.tab = hm.d_tab;
     const size_t smem = sizeof(double) * (4 * hm.n_obs + 6 * hm.n_box);
-    k_check<P, double, OpsF64Plain><<<blocks, 128, smem, c.stream>>>(a);
+    k_check_f64<P><<<blocks, 128, smem, c.stream>>>(a);
   } else {
     CheckArgs<P, float> a;
-    a.m = hm.m32;
+    a.m = hm.m32_shifted;
     a.st = hm.st32;
     a.obs = reinterpret_cast<const float *>(hm.d_obs32);
     a.box = reinterpret_cast<const float *>(hm.d_box32);
@@ -1042,9 +1126,10 @@ cudaError_t launch_check_impl(const HostModel &hm, const CheckCall &c, int *laun
     a.ld = c.ld;
     a.n = c.n;
     a.out = c.out;
+    a.pairs = c.pairs;
     a.tab = hm.d_tab;
-    const size_t smem = sizeof(float) * (4 * hm.n_obs + 6 * hm.n_box);
-    k_check<P, float, OpsF32><<<blocks, 128, smem, c.stream>>>(a);
+    const size_t smem = sizeof(float) * (8 * hm.n_obs + 6 * hm.n_box);
+    k_check_f32<P><<<blocks, 128, smem, c.stream>>>(a);
   }
   *launches += 1;
   return cudaGetLastError();

@@ -68,7 +68,7 @@ def load_library(path: str = LIB_PATH):
                               ctypes.c_int),
         "mcp_project_segments": ([_vp, P(ProjectParams), ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp,
                                   ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
-        "mcp_check_batch": ([_vp, ctypes.c_int64, ctypes.c_int64, _vp, ctypes.c_int32, _vp, _vp], ctypes.c_int),
+        "mcp_check_batch": ([_vp, ctypes.c_int64, ctypes.c_int64, _vp, ctypes.c_int32, _vp, _vp, _vp], ctypes.c_int),
         "mcp_project_vjp": ([_vp, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
         "mcp_path_length_grad": ([_vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, _vp],
                                  ctypes.c_int),
@@ -246,13 +246,15 @@ class Projector:
                                                   _ptr(resid), _stream(stream)))
         return out, flags, iters, resid
 
-    def check(self, q, out=None, n=None, stream=None):
+    def check(self, q, out=None, n=None, pairs=None, stream=None):
+        """Collision verdicts (uint8); `pairs` (int32 tensor [ld]) optionally
+        receives the sphere-obstacle pairs evaluated per configuration."""
         import torch
         d, ld = q.shape
         n = ld if n is None else n
         out = torch.empty(ld, dtype=torch.uint8, device=q.device) if out is None else out
         prec = PREC_FP64 if q.dtype == torch.float64 else PREC_FP32
-        self._check(self.lib.mcp_check_batch(self.h, n, ld, _ptr(q), prec, _ptr(out), _stream(stream)))
+        self._check(self.lib.mcp_check_batch(self.h, n, ld, _ptr(q), prec, _ptr(out), _ptr(pairs), _stream(stream)))
         return out
 
     def vjp(self, q_star, g, out=None, flags=None, stream=None):

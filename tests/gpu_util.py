@@ -3,6 +3,7 @@ through the C ABI, with the FP64 oracle on identical seeded inputs)."""
 import numpy as np
 
 from oracle import oracle as orc
+from oracle import parity
 
 # Acceptance bars (from the projection spec): converged configurations agree to
 # 1e-4 rad in the infinity norm, the FP64 residual of every converged output is
@@ -18,20 +19,34 @@ def f32_exact(q):
     return np.asarray(q, dtype=np.float32).astype(np.float64)
 
 
-def compare_projection(gpu, ora, tol, q_tol=Q_TOL, flag_agree=FLAG_AGREE, oracle=None, sample_resid=256):
-    """gpu / ora: (q [d, n], flags, iters, resid) as numpy.  Returns a stats dict."""
+def eligible_mask(oracle, q0, params, rel=1e-6, thr=1e-5, reps=2, seed=0):
+    """Configurations whose projection is a well-defined function of the start
+    (see oracle/parity.py).  Returns (mask, oracle result)."""
+    return parity.eligible_mask(oracle, q0, params.tol, params.max_iters, params.lam, max_step=params.max_step,
+                                rel=rel, thr=thr, reps=reps, seed=seed)
+
+
+def compare_projection(gpu, ora, tol, q_tol=Q_TOL, flag_agree=FLAG_AGREE, oracle=None, sample_resid=256,
+                       eligible=None, min_eligible=0.0):
+    """gpu / ora: (q [d, n], flags, iters, resid) as numpy.  Flags are compared
+    on every configuration, points on the eligible ones (all if None), and
+    every converged GPU output must be a valid point of the manifold (FP64
+    residual recomputed by the oracle below tol).  Returns a stats dict."""
     qg, fg, ig, rg = gpu
     qo, fo, io, ro = ora
     cg = (fg & orc.CONVERGED) != 0
     co = (fo & orc.CONVERGED) != 0
     agree = float((cg == co).mean())
-    both = cg & co
+    el = np.ones(cg.shape, bool) if eligible is None else eligible
+    both = cg & co & el
     err = np.abs(qg[:, both] - qo[:, both]).max(axis=0) if both.any() else np.zeros(0)
     stats = {"n": int(cg.size), "conv_gpu": float(cg.mean()), "conv_oracle": float(co.mean()), "flag_agree": agree,
              "q_err_max": float(err.max()) if err.size else 0.0,
              "q_err_p999": float(np.quantile(err, 0.999)) if err.size else 0.0,
              "resid_max": float(rg[cg].max()) if cg.any() else 0.0,
-             "iters_equal": float((ig[both] == io[both]).mean()) if both.any() else 1.0}
+             "iters_equal": float((ig[both] == io[both]).mean()) if both.any() else 1.0,
+             "eligible": float(el.mean())}
+    assert stats["eligible"] >= min_eligible, stats
     assert agree >= flag_agree, stats
     assert stats["q_err_max"] <= q_tol, stats
     assert np.all(rg[cg] < tol), stats
