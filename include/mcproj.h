@@ -207,6 +207,34 @@ mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sam
 /* Number of kernels this context has launched so far (for launch accounting). */
 int64_t mcp_launch_count(const mcp_ctx *ctx);
 
+/* Allocation-free segment projection.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory once
+ * they are running -- a real-time planning or control loop where a
+ * cudaMalloc would add unbounded latency (and synchronise the device), or a
+ * caller whose device memory is owned by another allocator or budget.
+ * mcp_project_segments allocates its segment-offset scratch on demand; this
+ * variant computes exactly the same result but keeps the work counter and the
+ * offsets in a fixed, file-scope device array of the library, so no call
+ * allocates or frees anything (no cudaMalloc, cudaFree, or allocating
+ * library routine).  Arguments, layouts and outputs are those of
+ * mcp_project_segments.
+ *   - n_seg may be at most MCP_NOALLOC_MAX_SEGMENTS; larger batches return
+ *     MCP_ERR_ARG with a message and enqueue nothing.
+ *   - The array is per device, about 512 KiB, and stays allocated on every
+ *     GPU that loads the library until the process exits.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture.
+ *   - Every call shares the array and it keeps the last call's contents: the
+ *     counter is cleared by each call, but calls that overlap on the GPU (on
+ *     different streams, or from several contexts on the same device) race
+ *     and must not be issued. */
+#define MCP_NOALLOC_MAX_SEGMENTS 65536
+mcp_status mcp_project_segments_noalloc(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_seg, int64_t ld_seg,
+                                        const void *start, const void *delta, const int32_t *len, int64_t total,
+                                        int64_t ld_out, void *q_out, uint8_t *flags, uint8_t *iters, double *resid,
+                                        mcp_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

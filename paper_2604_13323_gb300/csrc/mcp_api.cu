@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -881,6 +882,94 @@ mcp_status mcp_project_segments(mcp_ctx *ctx, const mcp_project_params *p, int64
   cudaError_t e = registry()[ctx->prob_class].project_fn(ctx->hm, c, &launches);
   ctx->launches += launches;
   if (e != cudaSuccess) return cuda_fail(ctx, e, "project_segments launch");
+  return MCP_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free segment projection (mcp_project_segments_noalloc).
+//
+// The scratch of the segment projection -- the persistent kernel's work
+// counter, then the exclusive prefix sums of the segment lengths -- lives in
+// this file-scope device array instead of memory allocated per context.  Every
+// GPU that loads the library holds it until the process exits; every call
+// shares it.  In host code `g_noalloc_scratch` is only a stand-in for the
+// symbol, not a device address: its address on each device is looked up once
+// with cudaGetSymbolAddress, with that device current, and that pointer is
+// what the kernels receive.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) long long g_noalloc_scratch[2 + MCP_NOALLOC_MAX_SEGMENTS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+long long *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on `device` (which must be current).
+cudaError_t noalloc_scratch(int device, long long **out) {
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[device] = static_cast<long long *>(p);
+  }
+  *out = g_noalloc_ptr[device];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" {
+
+mcp_status mcp_project_segments_noalloc(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_seg, int64_t ld_seg,
+                                        const void *start, const void *delta, const int32_t *len, int64_t total,
+                                        int64_t ld_out, void *q_out, uint8_t *flags, uint8_t *iters, double *resid,
+                                        mcp_stream stream) {
+  if (!ctx) return MCP_ERR_ARG;
+  mcp_status st = validate_params(ctx, p);
+  if (st != MCP_OK) return st;
+  if (n_seg < 0 || ld_seg < n_seg) return fail(ctx, MCP_ERR_ARG, "need 0 <= n_seg <= ld_seg");
+  if (n_seg > MCP_NOALLOC_MAX_SEGMENTS)
+    return fail(ctx, MCP_ERR_ARG,
+                "n_seg = %lld exceeds the allocation-free limit of %d segments; split the batch or use "
+                "mcp_project_segments",
+                (long long)n_seg, MCP_NOALLOC_MAX_SEGMENTS);
+  if (total < 0 || ld_out < total) return fail(ctx, MCP_ERR_ARG, "need 0 <= total <= ld_out");
+  if (n_seg == 0 || total == 0) return MCP_OK;
+  const char *names[7] = {"start", "delta", "len", "q_out", "flags", "iters", "resid"};
+  const void *ptrs[7] = {start, delta, len, q_out, flags, iters, resid};
+  for (int i = 0; i < 7; ++i)
+    if ((st = check_batch_ptr(ctx, ptrs[i], names[i])) != MCP_OK) return st;
+  DeviceGuard g(ctx->device);
+  long long *scratch = nullptr;
+  MCP_CUDA(noalloc_scratch(ctx->device, &scratch), "cudaGetSymbolAddress of the allocation-free scratch");
+  unsigned long long *counter = reinterpret_cast<unsigned long long *>(scratch);
+  long long *offsets = scratch + 1;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  k_scan_lengths<<<1, 1024, 0, s>>>(len, n_seg, offsets);  // writes offsets[0 .. n_seg]
+  ctx->launches += 1;
+  MCP_CUDA(cudaGetLastError(), "segment scan launch");
+  ProjCall c;
+  fill_call(ctx, p, c, s);
+  c.counter = counter;  // cleared on the stream by the projection launcher before its kernel
+  c.segments = true;
+  c.start = start;
+  c.delta = delta;
+  c.ld_seg = ld_seg;
+  c.seg_off = offsets;
+  c.n_seg = static_cast<int>(n_seg);
+  c.total = total;
+  c.q_out = q_out;
+  c.ld_out = ld_out;
+  c.flags = flags;
+  c.iters = iters;
+  c.resid = resid;
+  int launches = 0;
+  cudaError_t e = registry()[ctx->prob_class].project_fn(ctx->hm, c, &launches);
+  ctx->launches += launches;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "project_segments_noalloc launch");
   return MCP_OK;
 }
 

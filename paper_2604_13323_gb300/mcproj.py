@@ -73,6 +73,8 @@ def load_library(path: str = LIB_PATH):
         "mcp_path_length_grad": ([_vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, _vp],
                                  ctypes.c_int),
         "mcp_autotune": ([_vp, P(ProjectParams), ctypes.c_int64, _vp], ctypes.c_int),
+        "mcp_project_segments_noalloc": ([_vp, P(ProjectParams), ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp,
+                                          ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -84,7 +86,8 @@ def load_library(path: str = LIB_PATH):
 
 EXPORTED = ("mcp_create", "mcp_destroy", "mcp_last_error", "mcp_launch_count", "mcp_load_robot",
             "mcp_load_constraints", "mcp_load_obstacles", "mcp_get_constraint", "mcp_project_batch",
-            "mcp_project_segments", "mcp_check_batch", "mcp_project_vjp", "mcp_path_length_grad", "mcp_autotune")
+            "mcp_project_segments", "mcp_check_batch", "mcp_project_vjp", "mcp_path_length_grad", "mcp_autotune",
+            "mcp_project_segments_noalloc")
 
 
 class MCPError(RuntimeError):
