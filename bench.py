@@ -43,24 +43,33 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="arm", choices=["arm", "dual_arm", "sphere"])
+    ap.add_argument("--workload", default="arm", choices=["arm", "dual_arm", "dual_segments", "sphere", "humanoid"])
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="use only the first N configurations (small cases for profilers; not a bench line)")
     ap.add_argument("--profile", action="store_true",
                     help="fixed launch count for profilers: no time-padded warm-up, no CPU baseline, no e2e pass")
     return ap.parse_args()
 
 
 def make_workload(name, rank):
+    """(workload, batch q [d, n] or None, name, segments or None)."""
     from paper_2604_13323_gb300 import workloads as W
     if name == "arm":
         wl = W.arm_workload(seed=1001 + 1000 * rank, n=65536)
-        return wl, wl.q, "arm7_axis_65536"
+        return wl, wl.q, "arm7_axis_65536", None
     if name == "sphere":
         wl = W.sphere_workload(seed=1000 + 1000 * rank)
-        return wl, W.segment_points(wl.segments), "sphere_geodesics_1024_pairs"
-    wl = W.dual_arm_workload(seed=1002, total=10, n_random=262144)
-    return wl, wl.q, "dual14_rel_262144"
+        return wl, W.segment_points(wl.segments), "sphere_geodesics_1024_pairs", wl.segments
+    if name == "humanoid":
+        wl = W.humanoid_workload(seed=1003 + 1000 * rank)
+        return wl, wl.q, "humanoid36_1048576", None
+    if name == "dual_segments":
+        wl = W.dual_arm_workload(seed=1002 + 1000 * rank)
+        return wl, None, f"dual14_rel_segments_{int(wl.extra['lengths'].sum())}", "raw"
+    wl = W.dual_arm_workload(seed=1002 + 1000 * rank, total=10, n_random=262144)
+    return wl, wl.q, "dual14_rel_262144", None
 
 
 class ClockSampler:
@@ -137,7 +146,10 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl, q, wname = make_workload(args.workload, 0)
+    wl, q, wname, segs = make_workload(args.workload, 0)
+    if q is None:
+        from paper_2604_13323_gb300 import workloads as W
+        q = wl.extra["raw_start"]   # the oracle arm projects segment starts-like configurations
     from oracle import oracle as orc
     O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
     threads = orc.default_threads()
@@ -184,18 +196,41 @@ def run_ours(args):
     from paper_2604_13323_gb300 import mcproj
     from paper_2604_13323_gb300 import workloads as W
 
-    wl, q_np, wname = make_workload(args.workload, rank)
+    wl, q_np, wname, segs = make_workload(args.workload, rank)
+    if args.batch and q_np is not None:
+        q_np = q_np[:, :args.batch]
+        wname += f"_first{args.batch}"
     if args.precision == "fp64":
         wl.params.precision = W.PREC_FP64
     elif args.precision == "fp32":
         wl.params.precision = W.PREC_FP32
     fp64 = wl.params.precision == W.PREC_FP64
     dt = torch.float64 if fp64 else torch.float32
-    d, n = q_np.shape
     P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles, device=local)
     stream = torch.cuda.current_stream(dev)
-    q_in = torch.tensor(q_np, dtype=dt, device=dev)
-    q_out = torch.empty_like(q_in)
+    seg_args = None
+    if segs is not None:
+        if segs == "raw":   # starts projected on the device (setup, untimed); ambient unit directions
+            st0 = torch.tensor(wl.extra["raw_start"], dtype=dt, device=dev)
+            starts = P.project(st0, wl.params)[0]
+            delta = torch.tensor(wl.extra["raw_dir"] * wl.extra["step"], dtype=dt, device=dev)
+            length = torch.tensor(wl.extra["lengths"], dtype=torch.int32, device=dev)
+        else:
+            starts = torch.tensor(segs.start, dtype=dt, device=dev)
+            delta = torch.tensor(segs.delta, dtype=dt, device=dev)
+            length = torch.tensor(segs.length, dtype=torch.int32, device=dev)
+        n = int(length.sum().item())
+        d = starts.shape[0]
+        seg_args = (starts, delta, length)
+        # the same points, materialised on the host, for the CPU baseline
+        cpu_q = W.segment_points(W.Segments(start=starts.double().cpu().numpy(), delta=delta.double().cpu().numpy(),
+                                            length=length.cpu().numpy()))
+        q_np = None
+    else:
+        d, n = q_np.shape
+        cpu_q = q_np
+    q_in = torch.tensor(q_np, dtype=dt, device=dev) if q_np is not None else None
+    q_out = torch.empty((d, n), dtype=dt, device=dev)
     flags = torch.empty(n, dtype=torch.uint8, device=dev)
     iters = torch.empty(n, dtype=torch.uint8, device=dev)
     resid = torch.empty(n, dtype=torch.float64, device=dev)
@@ -205,7 +240,11 @@ def run_ours(args):
     def step(ev=None):
         if ev:
             ev[0].record(stream)
-        P.project(q_in, wl.params, out=q_out, flags=flags, iters=iters, resid=resid, stream=stream)
+        if seg_args is not None:
+            P.project_segments(*seg_args, wl.params, total=n, out=q_out, flags=flags, iters=iters, resid=resid,
+                               stream=stream)
+        else:
+            P.project(q_in, wl.params, out=q_out, flags=flags, iters=iters, resid=resid, stream=stream)
         if ev:
             ev[1].record(stream)
         P.check(q_out, out=hit, stream=stream)
@@ -258,7 +297,11 @@ def run_ours(args):
     value = float(c_tot.item()) / (ms_max * 1e-3)
 
     # ---- end to end through the C ABI with host buffers ----
-    q_host = torch.tensor(q_np, dtype=dt).pin_memory()
+    if seg_args is not None:   # the step's inputs are the segment descriptions
+        host_in = [t.cpu().pin_memory() for t in seg_args]
+    else:
+        host_in = [torch.tensor(q_np, dtype=dt).pin_memory()]
+    dev_in = list(seg_args) if seg_args is not None else [q_in]
     out_host = torch.empty((d, n), dtype=dt).pin_memory()
     fl_host = torch.empty(n, dtype=torch.uint8).pin_memory()
     hit_host = torch.empty(n, dtype=torch.uint8).pin_memory()
@@ -267,7 +310,8 @@ def run_ours(args):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        q_in.copy_(q_host, non_blocking=True)
+        for hi, di in zip(host_in, dev_in):
+            di.copy_(hi, non_blocking=True)
         step()
         out_host.copy_(q_out, non_blocking=True)
         fl_host.copy_(flags, non_blocking=True)
@@ -283,7 +327,7 @@ def run_ours(args):
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
         dist.all_reduce(e2e_c, op=dist.ReduceOp.SUM)
     e2e = {"value": float(e2e_c.item()) / (float(e2e_t.item()) * 1e-3) if e2e_ms else None, "unit": UNIT,
-           "h2d_bytes_per_step": q_host.numel() * q_host.element_size(),
+           "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in host_in),
            "d2h_bytes_per_step": out_host.numel() * out_host.element_size() + 2 * n}
 
     # ---- roofline of the dominant kernel ----
@@ -297,8 +341,9 @@ def run_ours(args):
     peak64 = 1.25                                         # nominal dense FP64, TFLOP/s
     mp = sum(t_proj) / len(t_proj)
     mc = sum(t_check) / len(t_check)
-    # collision: FK with translations + per sphere block transform + 4 FMA per pair tested
-    check_flops = n * (fm.fk_positions() + 25 * wl.robot.n_spheres) + 8.0 * pairs_total
+    # collision: FK with translations + 8 flops (4 FMA) per overlap test performed (broad and
+    # narrow phase); sphere transforms are not counted (conservative)
+    check_flops = n * fm.fk_positions() + 8.0 * pairs_total
     check_roof = {"kernel": "k_check_f32", "achieved": check_flops / (mc * 1e-3) / 1e12,
                   "pairs_per_config": pairs_total / n}
     if fp64:
@@ -323,17 +368,18 @@ def run_ours(args):
     if mc > mp and not fp64:   # the dominant kernel carries the headline roofline
         roof = {"bound": "alu", "achieved": check_roof["achieved"], "peak": peak32, "unit": "TFLOP/s",
                 "frac": check_roof["achieved"] / peak32, "traffic": None,
-                "kernel": "k_check_f32 (collision, 8 flops per sphere-obstacle pair)",
+                "kernel": "k_check_f32 (collision, 8 flops per overlap test, broad + narrow phase)",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock", "projection": roof}
 
     cpu = None
     if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.profile):
-        cpu = cpu_baseline(wl, q_np if not fp64 else q_np)
+        cpu = cpu_baseline(wl, cpu_q)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
                 "config": {"workload": wname, "batch": n, "dof": d, "k": wl.k, "tol": wl.params.tol,
+                           "source": "segments (persistent launch, CUDA graph)" if seg_args is not None else "batch",
                            "cap": wl.params.max_iters, "lambda": wl.params.lam,
                            "precision": "fp64 plain" if fp64 else "fp32 + fp64 acceptance",
                            "obstacles": int(wl.obstacles.spheres.shape[0]), "robot_spheres": wl.robot.n_spheres,

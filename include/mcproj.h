@@ -167,7 +167,10 @@ mcp_status mcp_project_batch(mcp_ctx *ctx, const mcp_project_params *p, int64_t 
  * with ld_out >= sum(len); flags / iters / resid as in mcp_project_batch.
  * The library scans len on the device into context-owned scratch.  Idle
  * lanes refill themselves from a work counter, so segments of any length mix
- * in one launch. */
+ * in one launch.  The scan, the counter reset and the projection kernel are
+ * captured once into a CUDA graph and replayed while the arguments and the
+ * loaded model stay the same (not when the caller's stream is itself being
+ * captured: then the kernels are enqueued directly). */
 mcp_status mcp_project_segments(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_seg, int64_t ld_seg,
                                 const void *start, const void *delta, const int32_t *len, int64_t total,
                                 int64_t ld_out, void *q_out, uint8_t *flags, uint8_t *iters, double *resid,
@@ -199,10 +202,23 @@ mcp_status mcp_project_vjp(mcp_ctx *ctx, int64_t n, int64_t ld, const float *q_s
 mcp_status mcp_path_length_grad(mcp_ctx *ctx, int64_t n_paths, int32_t n_way, int64_t ld, const float *Q,
                                 float *length, float *grad, mcp_stream stream);
 
-/* Picks the persistent launch shape (threads per block, blocks per SM, work
- * chunk) for the loaded problem by timing candidates on n_sample generated
- * configurations, and caches it in the context.  Synchronous. */
-mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sample, mcp_stream stream);
+/* Gradient step on paths (the update of path shortening on the manifold):
+ * for every interior waypoint (not the first or last of its path)
+ *   Q[:, i] -= clip(eta * D[:, i]),  clip scales the step to infinity norm <= max_step (if > 0).
+ * Q (in/out) and D: float [d * ld], same waypoint layout as
+ * mcp_path_length_grad.  The result is off the manifold; project it again. */
+mcp_status mcp_path_step(mcp_ctx *ctx, int64_t n_paths, int32_t n_way, int64_t ld, float *Q, const float *D, float eta,
+                         float max_step, mcp_stream stream);
+
+/* Picks the launch shape of the persistent FP32 projection kernel (threads
+ * per block, resident blocks per SM, configurations claimed per atomic) for
+ * the loaded problem by timing every candidate on the caller's sample
+ * q_sample (DEVICE, float [d * ld], n_sample configurations), and keeps the
+ * fastest in the context for later calls.  Uses temporary device buffers;
+ * synchronous.  The chosen shape is returned in tpb / blocks_per_sm / chunk
+ * (HOST, each may be NULL).  Tuning never changes results, only speed. */
+mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sample, int64_t ld, const void *q_sample,
+                        int32_t *tpb, int32_t *blocks_per_sm, int32_t *chunk, mcp_stream stream);
 
 /* Number of kernels this context has launched so far (for launch accounting). */
 int64_t mcp_launch_count(const mcp_ctx *ctx);

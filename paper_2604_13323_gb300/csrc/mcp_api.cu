@@ -275,6 +275,40 @@ __global__ void k_prep_obstacles(const double *obs, int n_obs, const double *box
   }
 }
 
+// Bounding sphere of each link's spheres (local coordinates), one thread per
+// group: centre = mean of the sphere centres, radius = max(|c_s - centre| +
+// r_s) + 1e-4 m, so that an FP32 overlap test against it is conservative.
+// Group g < nj is link g; group MAXJ holds the world-fixed spheres.
+__global__ void k_link_bounds(const SphereTable<double> *st, int nj, double *out /* (MAXJ + 1) * 4 */) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g > MAXJ) return;
+  const int l = (g == MAXJ) ? -1 : g;
+  double *o = out + 4 * g;
+  o[0] = o[1] = o[2] = o[3] = 0.0;
+  if (l >= nj) return;
+  const int s0 = st->off[l + 1], e = st->off[l + 2];
+  if (s0 >= e) return;
+  double cx = 0.0, cy = 0.0, cz = 0.0;
+  for (int s = s0; s < e; ++s) {
+    cx += st->s[s][0];
+    cy += st->s[s][1];
+    cz += st->s[s][2];
+  }
+  cx /= (e - s0);
+  cy /= (e - s0);
+  cz /= (e - s0);
+  double r = 0.0;
+  for (int s = s0; s < e; ++s) {
+    const double dx = st->s[s][0] - cx, dy = st->s[s][1] - cy, dz = st->s[s][2] - cz;
+    const double v = sqrt(dx * dx + dy * dy + dz * dz) + st->s[s][3];
+    r = v > r ? v : r;
+  }
+  o[0] = cx;
+  o[1] = cy;
+  o[2] = cz;
+  o[3] = r + 1e-4;
+}
+
 // Exclusive prefix sum of segment lengths into off[0..n]; one block.
 __global__ void k_scan_lengths(const int32_t *len, long long n, long long *off) {
   __shared__ long long part[1024];
@@ -321,6 +355,18 @@ __global__ void k_path_grad(const float *Q, long long ld, long long n_paths, int
   for (int j = 0; j < d; ++j) grad[j * ld + i] = ep[j] * ip - en[j] * in;
 }
 
+__global__ void k_path_step(float *Q, const float *D, long long ld, long long n_paths, int n_way, int d, float eta,
+                            float max_step) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n_paths * n_way) return;
+  const int w = static_cast<int>(i % n_way);
+  if (w == 0 || w == n_way - 1) return;  // endpoints stay fixed
+  float m = 0.f;
+  for (int j = 0; j < d; ++j) m = fmaxf(m, fabsf(eta * D[j * ld + i]));
+  const float sc = (max_step > 0.f && m > max_step) ? max_step / m : 1.f;
+  for (int j = 0; j < d; ++j) Q[j * ld + i] = fmaf(-sc * eta, D[j * ld + i], Q[j * ld + i]);
+}
+
 __global__ void k_path_length(const float *Q, long long ld, long long n_paths, int n_way, int d, float *length) {
   const long long p = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (p >= n_paths) return;
@@ -364,6 +410,12 @@ struct mcp_ctx {
   Tuning tune;
   bool tuned = false;
   int64_t launches = 0;
+  uint64_t version = 0;  // bumped by every load: invalidates captured graphs
+  // captured segment-projection graph and the arguments it was captured with
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t seg_exec = nullptr;
+  std::vector<unsigned char> seg_key;
+  int seg_graph_launches = 0;  // kernels inside the captured graph
 };
 
 namespace {
@@ -573,6 +625,28 @@ mcp_status ensure_resolved(mcp_ctx *ctx) {
   fill_constraints(ro, static_cast<int>(ctx->cons.size()), r.nj, ctx->hm.m64);
   fill_sphere_table(r, ctx->hm.st32);
   fill_sphere_table(r, ctx->hm.st64);
+  {
+    SphereTable<double> *d_st = nullptr;
+    double *d_lb = nullptr;
+    MCP_CUDA(cudaMalloc(&d_st, sizeof(SphereTable<double>)), "cudaMalloc sphere table");
+    cudaError_t e = cudaMalloc(&d_lb, (MAXJ + 1) * 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(d_st, &ctx->hm.st64, sizeof(SphereTable<double>), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      k_link_bounds<<<1, 64>>>(d_st, r.nj, d_lb);
+      ctx->launches += 1;
+      e = cudaGetLastError();
+    }
+    double lb[(MAXJ + 1) * 4];
+    if (e == cudaSuccess) e = cudaMemcpy(lb, d_lb, sizeof(lb), cudaMemcpyDeviceToHost);
+    cudaFree(d_st);
+    cudaFree(d_lb);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "link bounds");
+    for (int g = 0; g <= MAXJ; ++g)
+      for (int c = 0; c < 4; ++c) {
+        ctx->hm.st64.lb[g][c] = lb[4 * g + c];
+        ctx->hm.st32.lb[g][c] = static_cast<float>(lb[4 * g + c]);
+      }
+  }
   MCP_CUDA(cudaMemcpy(ctx->d_m64, &ctx->hm.m64, sizeof(ModelT<double>), cudaMemcpyHostToDevice), "model copy");
   update_shifted(ctx);
   return MCP_OK;
@@ -603,6 +677,7 @@ mcp_status mcp_create(int device, mcp_ctx **out) {
   cudaError_t e = cudaMalloc(&ctx->d_m64, sizeof(ModelT<double>));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tab, 256 * sizeof(double2));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counter, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) {
     k_sincos_table<<<1, 256>>>(ctx->d_tab);
     ctx->launches += 1;
@@ -633,6 +708,8 @@ void mcp_destroy(mcp_ctx *ctx) {
   cudaFree(ctx->d_seg_off);
   cudaFree(ctx->d_resolve);
   cudaFree(ctx->d_origin);
+  if (ctx->seg_exec) cudaGraphExecDestroy(ctx->seg_exec);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
 
@@ -687,6 +764,7 @@ mcp_status mcp_load_robot(mcp_ctx *ctx, const mcp_robot_desc *rd) {
   }
   ctx->robot = std::move(r);
   ctx->robot_loaded = true;
+  ++ctx->version;
   ctx->cons.clear();
   ctx->cons_loaded = false;
   ctx->tuned = false;
@@ -726,6 +804,7 @@ mcp_status mcp_load_constraints(mcp_ctx *ctx, const mcp_constraint_desc *cd, int
   if (k > MCP_MAX_EQUATIONS) return fail(ctx, MCP_ERR_ARG, "%d equations > %d", k, MCP_MAX_EQUATIONS);
   ctx->cons = std::move(cons);
   ctx->cons_loaded = true;
+  ++ctx->version;
   ctx->tuned = false;
   bind_classes(ctx);
   return ensure_resolved(ctx);
@@ -779,6 +858,7 @@ mcp_status mcp_load_obstacles(mcp_ctx *ctx, const double *spheres, int32_t n_sph
   ctx->hm.n_obs = n_spheres;
   ctx->hm.n_box = n_aabbs;
   ctx->obs_loaded = true;
+  ++ctx->version;
   update_shifted(ctx);
   return MCP_OK;
 }
@@ -861,9 +941,6 @@ mcp_status mcp_project_segments(mcp_ctx *ctx, const mcp_project_params *p, int64
     ctx->seg_cap = n_seg + 1;
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  k_scan_lengths<<<1, 1024, 0, s>>>(len, n_seg, ctx->d_seg_off);
-  ctx->launches += 1;
-  MCP_CUDA(cudaGetLastError(), "segment scan launch");
   ProjCall c;
   fill_call(ctx, p, c, s);
   c.segments = true;
@@ -878,10 +955,63 @@ mcp_status mcp_project_segments(mcp_ctx *ctx, const mcp_project_params *p, int64
   c.flags = flags;
   c.iters = iters;
   c.resid = resid;
-  int launches = 0;
-  cudaError_t e = registry()[ctx->prob_class].project_fn(ctx->hm, c, &launches);
-  ctx->launches += launches;
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "project_segments launch");
+  const ClassDesc &cls = registry()[ctx->prob_class];
+  // enqueue: scan of the lengths, counter reset + persistent kernel
+  auto enqueue = [&](cudaStream_t st, int *launches) -> cudaError_t {
+    k_scan_lengths<<<1, 1024, 0, st>>>(len, n_seg, ctx->d_seg_off);
+    *launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ProjCall cc = c;
+    cc.stream = st;
+    return cls.project_fn(ctx->hm, cc, launches);
+  };
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  MCP_CUDA(cudaStreamIsCapturing(s, &cs), "cudaStreamIsCapturing");
+  if (cs != cudaStreamCaptureStatusNone) {  // the caller is capturing: enqueue directly into its graph
+    int launches = 0;
+    cudaError_t e = enqueue(s, &launches);
+    ctx->launches += launches;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "project_segments launch");
+    return MCP_OK;
+  }
+  // key: everything the captured launches depend on
+  std::vector<unsigned char> key;
+  auto put = [&key](const void *v, size_t n) {
+    const unsigned char *b = static_cast<const unsigned char *>(v);
+    key.insert(key.end(), b, b + n);
+  };
+  const void *key_ptrs[9] = {start, delta, len, q_out, flags, iters, resid, ctx->d_seg_off, ctx->d_counter};
+  put(key_ptrs, sizeof(key_ptrs));
+  const int64_t sizes[5] = {n_seg, ld_seg, total, ld_out, static_cast<int64_t>(ctx->version)};
+  put(sizes, sizeof(sizes));
+  put(p, sizeof(*p));
+  put(&ctx->tune, sizeof(ctx->tune));
+  if (!ctx->seg_exec || key != ctx->seg_key) {
+    if (ctx->seg_exec) {
+      cudaGraphExecDestroy(ctx->seg_exec);
+      ctx->seg_exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    MCP_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    int launches = 0;
+    cudaError_t e = enqueue(ctx->cap_stream, &launches);
+    cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(ctx, e != cudaSuccess ? e : e2, "capture of the segment projection");
+    }
+    e = cudaGraphInstantiate(&ctx->seg_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      ctx->seg_exec = nullptr;
+      return cuda_fail(ctx, e, "graph instantiation");
+    }
+    ctx->seg_key = std::move(key);
+    ctx->seg_graph_launches = launches;
+  }
+  MCP_CUDA(cudaGraphLaunch(ctx->seg_exec, s), "graph launch");
+  ctx->launches += ctx->seg_graph_launches;
   return MCP_OK;
 }
 
@@ -1057,12 +1187,103 @@ mcp_status mcp_path_length_grad(mcp_ctx *ctx, int64_t n_paths, int32_t n_way, in
   return MCP_OK;
 }
 
-mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sample, mcp_stream stream) {
+mcp_status mcp_path_step(mcp_ctx *ctx, int64_t n_paths, int32_t n_way, int64_t ld, float *Q, const float *D, float eta,
+                         float max_step, mcp_stream stream) {
   if (!ctx) return MCP_ERR_ARG;
-  (void)p;
-  (void)n_sample;
-  (void)stream;
-  return fail(ctx, MCP_ERR_UNSUPPORTED, "autotune not available yet");
+  if (!ctx->robot_loaded) return fail(ctx, MCP_ERR_STATE, "robot not loaded");
+  if (n_paths < 0 || n_way < 1 || ld < n_paths * n_way) return fail(ctx, MCP_ERR_ARG, "need ld >= n_paths * n_way");
+  if (!std::isfinite(eta) || !std::isfinite(max_step)) return fail(ctx, MCP_ERR_ARG, "non-finite step parameters");
+  if (n_paths == 0) return MCP_OK;
+  mcp_status st;
+  if ((st = check_batch_ptr(ctx, Q, "Q")) != MCP_OK) return st;
+  if ((st = check_batch_ptr(ctx, D, "D")) != MCP_OK) return st;
+  DeviceGuard gd(ctx->device);
+  const long long n = n_paths * n_way;
+  k_path_step<<<static_cast<unsigned>((n + 127) / 128), 128, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      Q, D, ld, n_paths, n_way, ctx->robot.nj, eta, max_step);
+  ctx->launches += 1;
+  MCP_CUDA(cudaGetLastError(), "path step launch");
+  return MCP_OK;
+}
+
+mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sample, int64_t ld, const void *q_sample,
+                        int32_t *tpb_out, int32_t *bps_out, int32_t *chunk_out, mcp_stream stream) {
+  if (!ctx) return MCP_ERR_ARG;
+  mcp_status st = validate_params(ctx, p);
+  if (st != MCP_OK) return st;
+  if (p->precision != 0) return fail(ctx, MCP_ERR_ARG, "autotune applies to the FP32 projection (precision 0)");
+  if (n_sample < 1 || ld < n_sample) return fail(ctx, MCP_ERR_ARG, "need 1 <= n_sample <= ld");
+  if ((st = check_batch_ptr(ctx, q_sample, "q_sample")) != MCP_OK) return st;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int d = ctx->robot.nj;
+  float *out = nullptr;
+  uint8_t *fl = nullptr, *it = nullptr;
+  double *res = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = cudaMalloc(&out, sizeof(float) * d * ld);
+  if (err == cudaSuccess) err = cudaMalloc(&fl, ld);
+  if (err == cudaSuccess) err = cudaMalloc(&it, ld);
+  if (err == cudaSuccess) err = cudaMalloc(&res, sizeof(double) * ld);
+  if (err == cudaSuccess) err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  const Tuning saved = ctx->tune;
+  Tuning best = saved;
+  float best_ms = 1e30f;
+  const int tpbs[3] = {64, 128, 256};
+  const int bpss[4] = {1, 2, 4, 8};
+  const int chunks[3] = {16, 32, 64};
+  for (int a = 0; a < 3 && err == cudaSuccess; ++a)
+    for (int b = 0; b < 4 && err == cudaSuccess; ++b)
+      for (int c = 0; c < 3 && err == cudaSuccess; ++c) {
+        if (tpbs[a] * bpss[b] > 2048) continue;
+        ctx->tune = Tuning{tpbs[a], bpss[b], chunks[c]};
+        float times[3];
+        for (int r = 0; r < 4 && err == cudaSuccess; ++r) {
+          ProjCall call;
+          fill_call(ctx, p, call, s);
+          call.q_in = q_sample;
+          call.ld_in = ld;
+          call.total = n_sample;
+          call.q_out = out;
+          call.ld_out = ld;
+          call.flags = fl;
+          call.iters = it;
+          call.resid = res;
+          int launches = 0;
+          err = cudaEventRecord(e0, s);
+          if (err == cudaSuccess) err = registry()[ctx->prob_class].project_fn(ctx->hm, call, &launches);
+          ctx->launches += launches;
+          if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+          if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+          float ms = 0.f;
+          if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+          if (r > 0) times[r - 1] = ms;  // first run warms up
+        }
+        if (err != cudaSuccess) break;
+        float med = times[0] + times[1] + times[2] - fminf(times[0], fminf(times[1], times[2])) -
+                    fmaxf(times[0], fmaxf(times[1], times[2]));
+        if (med < best_ms) {
+          best_ms = med;
+          best = ctx->tune;
+        }
+      }
+  cudaFree(out);
+  cudaFree(fl);
+  cudaFree(it);
+  cudaFree(res);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (err != cudaSuccess) {
+    ctx->tune = saved;
+    return cuda_fail(ctx, err, "autotune");
+  }
+  ctx->tune = best;
+  ctx->tuned = true;
+  if (tpb_out) *tpb_out = best.tpb;
+  if (bps_out) *bps_out = best.blocks_per_sm;
+  if (chunk_out) *chunk_out = best.chunk;
+  return MCP_OK;
 }
 
 }  // extern "C"

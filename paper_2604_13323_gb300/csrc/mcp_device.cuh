@@ -355,10 +355,24 @@ struct Kin {
   V3<T> mc;           // sum_j m_j c_j (accumulated during FK when a CoM constraint is present)
 };
 
-template <class P, bool POS, class Ops, typename T>
-__device__ __forceinline__ void fk(const Ops &ops, const ModelT<T> &m, const T (&q)[P::D], Kin<P, T> &k) {
+struct NoVisit {
+  template <class J, class R, class V>
+  __device__ __forceinline__ void operator()(J, const R &, V) const {}
+};
+struct NoStop {
+  __device__ __forceinline__ bool operator()() const { return false; }
+};
+
+// World transforms of every joint frame (and the task frames).  `visit(j, R_j,
+// p_j)` is called right after joint j is placed, and joints after `stop()`
+// becomes true are skipped, so consumers can use each link's pose while it is
+// live (the collision check does) instead of keeping the whole tree.
+template <class P, bool POS, class Ops, typename T, class Visit = NoVisit, class Stop = NoStop>
+__device__ __forceinline__ void fk(const Ops &ops, const ModelT<T> &m, const T (&q)[P::D], Kin<P, T> &k,
+                                   const Visit &visit = Visit{}, const Stop &stop = Stop{}) {
   static_for<P::D>([&](auto JJ) {
     constexpr int j = decltype(JJ)::value;
+    if (stop()) return;
     constexpr int pa = P::parent(j);
     constexpr int code = P::xrot(j);
     T Rpre[9];
@@ -389,7 +403,9 @@ __device__ __forceinline__ void fk(const Ops &ops, const ModelT<T> &m, const T (
       const V3<T> ci = add_rot_t<7>(k.p[j], k.R[j], V3<T>{m.com[j][0], m.com[j][1], m.com[j][2]});
       k.mc = {fma_(m.mass[j], ci.x, k.mc.x), fma_(m.mass[j], ci.y, k.mc.y), fma_(m.mass[j], ci.z, k.mc.z)};
     }
+    visit(JJ, k.R[j], k.p[j]);
   });
+  if (stop()) return;
   static_for<P::NF>([&](auto FF) {
     constexpr int f = decltype(FF)::value;
     constexpr int l = P::frame_link(f);
@@ -468,15 +484,15 @@ __device__ __forceinline__ V3<T> jl_inv_apply(V3<T> phi, T beta, V3<T> v) {
 
 // ---------------------------------------------------------------------------
 // Cholesky of a K x K SPD matrix held as the lower triangle A[i*(i+1)/2 + j],
-// in place (Dahlquist & Bjorck, no pivoting), then L L^T x = b.
-// Returns the smallest pre-square-root pivot.
+// in place (Dahlquist & Bjorck, no pivoting), and the solves L L^T x = b.
+// The factorisation returns the smallest pre-square-root pivot.
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
+// Factorisation only: A is overwritten by L (lower triangle), inv[j] = 1 / L_jj.
 template <int K, class Ops, typename T>
-__device__ __forceinline__ T cholesky_solve(T (&A)[K * (K + 1) / 2], T (&b)[K]) {
+__device__ __forceinline__ T cholesky_factor(T (&A)[K * (K + 1) / 2], T (&inv)[K]) {
   T minpiv = T(1e30);
-  T inv[K];
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     T s = A[tri(j, j)];
@@ -494,20 +510,33 @@ __device__ __forceinline__ T cholesky_solve(T (&A)[K * (K + 1) / 2], T (&b)[K]) 
       A[tri(i, j)] = t * ij;
     }
   }
+  return minpiv;
+}
+
+// b <- (L L^T)^{-1} b with the factor from cholesky_factor.
+template <int K, typename T>
+__device__ __forceinline__ void cholesky_subst(const T (&L)[K * (K + 1) / 2], const T (&inv)[K], T (&b)[K]) {
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     T s = b[i];
 #pragma unroll
-    for (int k = 0; k < i; ++k) s = fma_(-A[tri(i, k)], b[k], s);
+    for (int k = 0; k < i; ++k) s = fma_(-L[tri(i, k)], b[k], s);
     b[i] = s * inv[i];
   }
 #pragma unroll
   for (int i = K - 1; i >= 0; --i) {
     T s = b[i];
 #pragma unroll
-    for (int k = i + 1; k < K; ++k) s = fma_(-A[tri(k, i)], b[k], s);
+    for (int k = i + 1; k < K; ++k) s = fma_(-L[tri(k, i)], b[k], s);
     b[i] = s * inv[i];
   }
+}
+
+template <int K, class Ops, typename T>
+__device__ __forceinline__ T cholesky_solve(T (&A)[K * (K + 1) / 2], T (&b)[K]) {
+  T inv[K];
+  const T minpiv = cholesky_factor<K, Ops>(A, inv);
+  cholesky_subst<K>(A, inv, b);
   return minpiv;
 }
 

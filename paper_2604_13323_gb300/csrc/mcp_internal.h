@@ -17,6 +17,7 @@ constexpr int MAXS = 256;  // robot spheres per robot
 template <typename T>
 struct SphereTable {
   T s[MAXS][4];
+  T lb[MAXJ + 1][4];    // per link (index MAXJ: world-fixed spheres): bounding sphere, local centre + radius
   int16_t off[MAXJ + 2];
 };
 

@@ -7,8 +7,8 @@
 //   1. local transforms L_j = X_j Jnt(q_j), one joint per lane;
 //   2. world transforms by a parallel prefix over the tree (pointer jumping:
 //      T_j <- T_anc(j) T_j, anc(j) <- anc(anc(j)), ceil(log2(depth)) rounds);
-//   3. task frames, link CoMs, subtree CoM sums (segmented scan; joints are
-//      in depth-first order, so a subtree is a contiguous index range);
+//   3. task frames, link CoMs, subtree CoM sums (joints are in depth-first
+//      order, so a subtree is a contiguous index range);
 //   4. residuals, one constraint per lane; ||F|| by a warp reduction;
 //   5. Jacobian columns, one joint per lane;
 //   6. Gram rows, one row per lane, J rows read with broadcast loads;
@@ -64,7 +64,7 @@ __host__ __device__ constexpr bool dfs_preorder() {
 }
 
 template <class P>
-struct WarpState {
+struct __align__(16) WarpState {
   static constexpr int D = P::D, K = kdim<P>(), KP = (kdim<P>() + 3) & ~3;
   float T[D][12];
   float J[D][KP];
@@ -72,9 +72,10 @@ struct WarpState {
   float F[KP];
   float y[KP];
   float Tf[P::NF][12];
-  float mc[D][4];   // m_j c_j, then inclusive prefix sums
+  float mc[D][4];   // m_j c_j
   float C[D][4];    // subtree sums
   float q[D];
+  float dq[D];
   int anc[D];
   float G[P::NC][9];
   float x[P::NC][4];
@@ -232,22 +233,24 @@ __device__ __forceinline__ bool warp_iter(const A &a, const WarpTables<P> &tb, W
         mcv[s][r] = tb.mass[j] * fmaf(Tc[s][r * 4], c[0], fmaf(Tc[s][r * 4 + 1], c[1], fmaf(Tc[s][r * 4 + 2], c[2], Tc[s][r * 4 + 3])));
     }
   }
-  // inclusive prefix sums of m_j c_j over j (slot-major order = joint order)
+  // total CoM moment (warp reduction) and, per joint, the sum over its subtree
+  // [j, sub_end[j]) added directly (a difference of prefix sums would lose
+  // digits to cancellation for small distal subtrees)
   float tot[3] = {0.f, 0.f, 0.f};
 #pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    float v = 0.f;
+#pragma unroll
+    for (int s = 0; s < SL; ++s) v += mcv[s][r];
+    tot[r] = warp_sum(v);
+  }
+#pragma unroll
   for (int s = 0; s < SL; ++s) {
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      float v = mcv[s][r];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const float u = __shfl_up_sync(FULL, v, o);
-        if (lane >= o) v += u;
-      }
-      v += tot[r];
-      tot[r] = __shfl_sync(FULL, v, 31);
-      const int j = lane + 32 * s;
-      if (j < D) S.mc[j][r] = v;
+    const int j = lane + 32 * s;
+    if (j < D) {
+      S.mc[j][0] = mcv[s][0];
+      S.mc[j][1] = mcv[s][1];
+      S.mc[j][2] = mcv[s][2];
     }
   }
   __syncwarp();
@@ -256,9 +259,15 @@ __device__ __forceinline__ bool warp_iter(const A &a, const WarpTables<P> &tb, W
     for (int s = 0; s < SL; ++s) {
       const int j = lane + 32 * s;
       if (j < D) {
-        const int e = tb.sub_end[j] - 1;
-#pragma unroll
-        for (int r = 0; r < 3; ++r) S.C[j][r] = S.mc[e][r] - (j > 0 ? S.mc[j - 1][r] : 0.f);
+        float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+        for (int i = j; i < tb.sub_end[j]; ++i) {
+          c0 += S.mc[i][0];
+          c1 += S.mc[i][1];
+          c2 += S.mc[i][2];
+        }
+        S.C[j][0] = c0;
+        S.C[j][1] = c1;
+        S.C[j][2] = c2;
       }
     }
   }
@@ -444,39 +453,60 @@ __device__ __forceinline__ bool warp_iter(const A &a, const WarpTables<P> &tb, W
 #pragma unroll
     for (int b = 0; b < K; ++b) S.L[lane][b] = acc[b];
   }
-  // forward solve L y = F: lane i keeps its running value
-  float tv = fv;
+  // (L L^T)^{-1} b with row i of L in lane i's registers and L in shared memory:
+  // forward substitution broadcasts y_k, back substitution reads L[i][lane]
+  auto subst = [&](float tv) -> float {
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const float yk = __shfl_sync(FULL, tv * inv_diag, k);
-    if (lane == k) tv = yk;
-    if (lane > k) tv = fmaf(-acc[k], yk, tv);
-  }
-  __syncwarp();
-  // back solve L^T z = y: after z_i is known, lanes m < i subtract L[i][m] z_i
+    for (int k = 0; k < K; ++k) {
+      const float yk = __shfl_sync(FULL, tv * inv_diag, k);
+      if (lane == k) tv = yk;
+      if (lane > k) tv = fmaf(-acc[k], yk, tv);
+    }
+    __syncwarp();
 #pragma unroll
-  for (int i = K - 1; i >= 0; --i) {
-    const float zi = __shfl_sync(FULL, tv * inv_diag, i);
-    if (lane == i) tv = zi;
-    if (lane < i) tv = fmaf(-S.L[i][lane], zi, tv);
-  }
-  if (lane < K) S.y[lane] = tv;
-  __syncwarp();
-  // dq = J^T z, update, divergence / finiteness checks
+    for (int i = K - 1; i >= 0; --i) {
+      const float zi = __shfl_sync(FULL, tv * inv_diag, i);
+      if (lane == i) tv = zi;
+      if (lane < i) tv = fmaf(-S.L[i][lane], zi, tv);
+    }
+    return tv;
+  };
+  // dq = J^T y for the y held by lanes < K (joint j on lane j)
   float dq[SL];
+  auto jt_y = [&](float yv) {
+    if (lane < K) S.y[lane] = yv;
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < SL; ++s) {
+      const int j = lane + 32 * s;
+      dq[s] = 0.f;
+      if (j < D) {
+        float acc2 = 0.f;
+#pragma unroll
+        for (int b = 0; b < K; ++b) acc2 = fmaf(S.J[j][b], S.y[b], acc2);
+        dq[s] = acc2;
+        S.dq[j] = acc2;
+      }
+    }
+    __syncwarp();
+  };
+  float yv = subst(fv);
+  jt_y(yv);
+  // one refinement step with the residual from J (corrected semi-normal equations):
+  // r = F - J (J^T y) - lambda y
+  float rv = 0.f;
+  if (lane < K) {
+    float jd = 0.f;
+#pragma unroll 4
+    for (int j = 0; j < D; ++j) jd = fmaf(S.J[j][lane], S.dq[j], jd);
+    rv = fmaf(-a.lambda, yv, fv - jd);
+  }
+  __syncwarp();
+  yv += subst(rv);
+  jt_y(yv);
   float s2 = 0.f;
 #pragma unroll
-  for (int s = 0; s < SL; ++s) {
-    const int j = lane + 32 * s;
-    dq[s] = 0.f;
-    if (j < D) {
-      float acc2 = 0.f;
-#pragma unroll
-      for (int b = 0; b < K; ++b) acc2 = fmaf(S.J[j][b], S.y[b], acc2);
-      dq[s] = acc2;
-      s2 = fmaf(acc2, acc2, s2);
-    }
-  }
+  for (int s = 0; s < SL; ++s) s2 = fmaf(dq[s], dq[s], s2);
   s2 = warp_sum(s2);
   if (a.max_step2 > 0.f && s2 > a.max_step2) {
     fl |= FL_DIV;

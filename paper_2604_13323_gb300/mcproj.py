@@ -72,7 +72,10 @@ def load_library(path: str = LIB_PATH):
         "mcp_project_vjp": ([_vp, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
         "mcp_path_length_grad": ([_vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, _vp],
                                  ctypes.c_int),
-        "mcp_autotune": ([_vp, P(ProjectParams), ctypes.c_int64, _vp], ctypes.c_int),
+        "mcp_autotune": ([_vp, P(ProjectParams), ctypes.c_int64, ctypes.c_int64, _vp, _ip, _ip, _ip, _vp],
+                         ctypes.c_int),
+        "mcp_path_step": ([_vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _vp, _vp, ctypes.c_float,
+                           ctypes.c_float, _vp], ctypes.c_int),
         "mcp_project_segments_noalloc": ([_vp, P(ProjectParams), ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp,
                                           ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     }
@@ -87,7 +90,7 @@ def load_library(path: str = LIB_PATH):
 EXPORTED = ("mcp_create", "mcp_destroy", "mcp_last_error", "mcp_launch_count", "mcp_load_robot",
             "mcp_load_constraints", "mcp_load_obstacles", "mcp_get_constraint", "mcp_project_batch",
             "mcp_project_segments", "mcp_check_batch", "mcp_project_vjp", "mcp_path_length_grad", "mcp_autotune",
-            "mcp_project_segments_noalloc")
+            "mcp_project_segments_noalloc", "mcp_path_step")
 
 
 class MCPError(RuntimeError):
@@ -268,6 +271,23 @@ class Projector:
         self._check(self.lib.mcp_project_vjp(self.h, ld, ld, _ptr(q_star), _ptr(g), _ptr(out), _ptr(flags),
                                              _stream(stream)))
         return out, flags
+
+    def path_step(self, Q, D, n_paths, n_way, eta, max_step=0.0, stream=None):
+        """In place: interior waypoints of Q move by -clip(eta * D)."""
+        d, ld = Q.shape
+        self._check(self.lib.mcp_path_step(self.h, n_paths, n_way, ld, _ptr(Q), _ptr(D), float(eta), float(max_step),
+                                           _stream(stream)))
+        return Q
+
+    def autotune(self, q_sample, params, stream=None):
+        """Times the persistent kernel's launch shapes on q_sample ([d, n] float32
+        CUDA tensor) and keeps the fastest; returns (threads/block, blocks/SM, chunk)."""
+        d, n = q_sample.shape
+        t, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        pp = self.params(params)
+        self._check(self.lib.mcp_autotune(self.h, ctypes.byref(pp), n, n, _ptr(q_sample), ctypes.byref(t),
+                                          ctypes.byref(b), ctypes.byref(c), _stream(stream)))
+        return t.value, b.value, c.value
 
     def path_length_grad(self, Q, n_paths, n_way, length=None, grad=None, stream=None):
         import torch

@@ -1,0 +1,150 @@
+"""GPU tests of the batching and differentiation patterns around the kernels:
+autotuning, CUDA-graph replay of the segment projection, the autograd wrapper
+of projection + VJP, and path shortening on the manifold."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as orc  # noqa: E402
+from paper_2604_13323_gb300 import workloads as W  # noqa: E402
+from tests.gpu_util import f32_exact  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mcproj():
+    from paper_2604_13323_gb300 import build, mcproj as m
+    build.build()
+    m.load_library()
+    return m
+
+
+def dev(a, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def test_autotune_keeps_results(mcproj):
+    wl = W.arm_workload(n=8192)
+    P = mcproj.Projector(wl.robot, wl.constraints)
+    q = dev(f32_exact(wl.q))
+    before = [t.clone() for t in P.project(q, wl.params)]
+    tpb, bps, chunk = P.autotune(q, wl.params)
+    assert tpb in (64, 128, 256) and bps in (1, 2, 4, 8) and chunk in (16, 32, 64)
+    after = P.project(q, wl.params)
+    torch.cuda.synchronize()
+    for x, y in zip(before, after):
+        assert torch.equal(x, y)
+
+
+def test_segment_graph_replay_and_recapture(mcproj):
+    wl = W.dual_arm_workload(total=20000)
+    ex = wl.extra
+    P = mcproj.Projector(wl.robot, wl.constraints)
+    starts = P.project(dev(ex["raw_start"]), wl.params)[0]
+    delta = dev(ex["raw_dir"] * ex["step"])
+    length = dev(ex["lengths"], torch.int32)
+    total = int(ex["lengths"].sum())
+    outs = []
+    for rep in range(3):   # first call captures, the next ones replay the graph
+        outs.append([t.clone() for t in P.project_segments(starts, delta, length, wl.params)])
+    torch.cuda.synchronize()
+    for o in outs[1:]:
+        for x, y in zip(outs[0], o):
+            assert torch.equal(x, y)
+    # new inputs through the same buffers: the replayed graph reads them
+    delta.mul_(0.5)
+    o2 = P.project_segments(starts, delta, length, wl.params)
+    ref = mcproj.Projector(wl.robot, wl.constraints).project_segments(starts, delta, length, wl.params)
+    torch.cuda.synchronize()
+    assert torch.equal(o2[1], ref[1])
+    conv = (ref[1] & 1).bool()
+    assert (o2[0][:, conv] - ref[0][:, conv]).abs().max().item() <= 1e-4
+    # new buffers / parameters: a new capture
+    p2 = W.Params(tol=1e-5, max_iters=12, lam=1e-6)
+    o3 = P.project_segments(starts, delta, length, p2, total=total)
+    torch.cuda.synchronize()
+    assert int(o3[2].max().item()) <= 12
+
+
+def test_segments_inside_caller_graph(mcproj):
+    """Called while the caller captures its own graph, the library enqueues its
+    kernels into that graph instead of launching its private one."""
+    wl = W.dual_arm_workload(total=5000)
+    ex = wl.extra
+    P = mcproj.Projector(wl.robot, wl.constraints)
+    starts = P.project(dev(ex["raw_start"]), wl.params)[0]
+    delta = dev(ex["raw_dir"] * ex["step"])
+    length = dev(ex["lengths"], torch.int32)
+    total = int(ex["lengths"].sum())
+    out = torch.empty((14, total), device="cuda")
+    fl = torch.empty(total, dtype=torch.uint8, device="cuda")
+    it = torch.empty(total, dtype=torch.uint8, device="cuda")
+    rs = torch.empty(total, dtype=torch.float64, device="cuda")
+    ref = P.project_segments(starts, delta, length, wl.params)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+            P.project_segments(starts, delta, length, wl.params, total=total, out=out, flags=fl, iters=it,
+                               resid=rs, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(fl, ref[1])
+    conv = (fl & 1).bool()
+    assert (out[:, conv] - ref[0][:, conv]).abs().max().item() <= 1e-4
+
+
+def test_vjp_matches_finite_differences_of_oracle_projection(mcproj):
+    """g^T dPi/dq at the GPU's projected points, by central differences of the
+    FP64 oracle's projection (h = 1e-4, lambda = 0, tight tolerance)."""
+    wl = W.adjoint_workload(n=16)
+    P = mcproj.Projector(wl.robot, wl.constraints)
+    O = orc.Oracle(wl.robot, wl.constraints)
+    qs, fl, _, _ = P.project(dev(f32_exact(wl.q)), wl.params)
+    g = f32_exact(wl.extra["g"][:, :16])
+    v, _ = P.vjp(qs, dev(g))
+    torch.cuda.synchronize()
+    qs, v = qs.cpu().numpy().astype(np.float64), v.cpu().numpy()
+    h = 1e-4
+    for i in range(4):
+        D = np.zeros((14, 14))
+        for j in range(14):
+            e = np.zeros(14)
+            e[j] = h
+            pp = O.project(np.stack([qs[:, i] + e, qs[:, i] - e], 1), 1e-13, 80, 0.0)[0]
+            D[:, j] = (pp[:, 0] - pp[:, 1]) / (2 * h)
+        ref = g[:, i] @ D
+        assert np.linalg.norm(v[:, i] - ref) / np.linalg.norm(ref) < 1e-4
+
+
+def test_autograd_project_backward_is_vjp(mcproj):
+    from paper_2604_13323_gb300.shorten import ProjectFn
+    wl = W.adjoint_workload(n=256)
+    P = mcproj.Projector(wl.robot, wl.constraints)
+    q = dev(f32_exact(wl.q)).requires_grad_(True)
+    qs = ProjectFn.apply(q, P, wl.params)
+    g = dev(f32_exact(wl.extra["g"][:, :256]))
+    (qs * g).sum().backward()
+    v, _ = P.vjp(qs.detach(), g)
+    torch.cuda.synchronize()
+    assert torch.equal(q.grad, v)
+
+
+def test_path_shortening_reduces_length_on_manifold(mcproj):
+    from paper_2604_13323_gb300.shorten import initial_paths, shorten_paths
+    pw = W.path_workload(n_paths=64, n_way=16)
+    wl = pw["workload"]
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
+    Q = initial_paths(P, pw["qa"], pw["qb"], pw["noise"], wl.params)
+    Qf, st = shorten_paths(P, Q, 64, 16, wl.params, steps=20)
+    assert st["mean_length_reduction"] > 0.05, st
+    assert st["min_length_reduction"] > -1e-3, st
+    assert st["converged_fraction"] > 0.99 and st["max_resid"] < 1e-5, st
+    # the shortened waypoints are valid points of the manifold (FP64 oracle residual)
+    O = orc.Oracle(wl.robot, wl.constraints)
+    Qn = Qf.cpu().numpy().astype(np.float64)
+    for i in range(0, Qn.shape[1], 97):
+        assert np.linalg.norm(O.residual(Qn[:, i])) < 1e-5
