@@ -544,10 +544,63 @@ __device__ __forceinline__ double sqrt_refined(double v) {
   return fma(fma(-r0, r0, v), h, r0);
 }
 
-// Acceptance / finishing of one configuration that left the FP32 loop.  The
-// FP32 iterate is re-checked with the FP64 residual; if the FP32 test was too
-// optimistic, or the FP32 pivot was too small, the remaining steps are taken
-// in FP64 (rounded to the FP32 output).  Writes q, flags, iters and resid.
+// Remaining steps of one configuration in FP64 (rounded to the FP32 output):
+// taken when the FP32 residual test passed but the FP64 one did not, or when
+// the FP32 Cholesky pivot fell below the threshold.  Rare, so it lives out of
+// line (its registers and local arrays stay off the FP32 loop).  Updates q,
+// qd, it, fl; returns the final squared FP64 residual.
+template <class P, class A>
+__device__ __noinline__ double finish_f64(const A &a, float *q, double *qd, int *it_io, uint32_t *fl_io, double r2,
+                                          bool was_conv) {
+  constexpr int D = P::D;
+  const OpsF64Table ops{a.tab};
+  const ModelT<double> &m = *a.m64;
+  int it = *it_io;
+  uint32_t fl = *fl_io;
+  bool conv = r2 < a.tol2_64;
+  double qq[D];
+#pragma unroll 1
+  for (int j = 0; j < D; ++j) qq[j] = qd[j];
+  while (!conv && it < a.cap) {
+    double dq[D];
+    fl |= FL_RESOLVE;
+    if (!lm_step_f64<P>(ops, a.m64, qq, a.lambda64, dq)) {
+      fl |= FL_NONFINITE;
+      break;
+    }
+    double s2 = 0.0;
+#pragma unroll 1
+    for (int j = 0; j < D; ++j) s2 = fma(dq[j], dq[j], s2);
+    if (a.max_step2 > 0.f && s2 > static_cast<double>(a.max_step2)) {
+      fl |= FL_DIV;
+      break;
+    }
+#pragma unroll 1
+    for (int j = 0; j < D; ++j) {
+      q[j] = static_cast<float>(qq[j] - dq[j]);
+      qq[j] = static_cast<double>(q[j]);
+    }
+    ++it;
+    r2 = residual2_f64<P>(ops, m, qq);
+    if (!(r2 <= DBL_MAX)) {
+      fl |= FL_NONFINITE;
+      break;
+    }
+    conv = r2 < a.tol2_64;
+  }
+  if (conv) fl |= FL_CONV;
+  else if (!(fl & (FL_NONFINITE | FL_DIV))) fl |= FL_CAP | (was_conv ? FL_ACCEPT_FAIL : 0u);
+#pragma unroll 1
+  for (int j = 0; j < D; ++j) qd[j] = qq[j];
+  *it_io = it;
+  *fl_io = fl;
+  return r2;
+}
+
+// Acceptance of one configuration that left the FP32 loop: the FP32 iterate
+// is re-checked with the FP64 residual; if the FP32 test was too optimistic,
+// or the FP32 pivot was too small, finish_f64 takes the remaining steps.
+// Writes q (if changed), flags, iters and resid.
 template <class P, class A>
 __device__ __forceinline__ void accept_one(const A &a, long long item, int it, uint32_t fl) {
   constexpr int D = P::D;
@@ -561,45 +614,26 @@ __device__ __forceinline__ void accept_one(const A &a, long long item, int it, u
     qd[j] = static_cast<double>(q[j]);
   }
   double r2 = residual2_f64<P>(ops, m, qd);
-  bool changed = false;
   if (fl & (FL_INT_FP32CONV | FL_INT_NEEDS_F64)) {
     const bool was_conv = (fl & FL_INT_FP32CONV) != 0;
     fl &= ~(FL_INT_FP32CONV | FL_INT_NEEDS_F64);
-    bool conv = r2 < a.tol2_64;
-    while (!conv && it < a.cap) {
-      double dq[D];
-      fl |= FL_RESOLVE;
-      if (!lm_step_f64<P>(ops, a.m64, qd, a.lambda64, dq)) {
-        fl |= FL_NONFINITE;
-        break;
-      }
-      double s2 = 0.0;
-#pragma unroll
-      for (int j = 0; j < D; ++j) s2 = fma(dq[j], dq[j], s2);
-      if (a.max_step2 > 0.f && s2 > static_cast<double>(a.max_step2)) {
-        fl |= FL_DIV;
-        break;
-      }
+    if (r2 < a.tol2_64) {
+      fl |= FL_CONV;
+    } else {
+      float qf[D];
+      double qdd[D];
 #pragma unroll
       for (int j = 0; j < D; ++j) {
-        q[j] = static_cast<float>(qd[j] - dq[j]);
-        qd[j] = static_cast<double>(q[j]);
+        qf[j] = q[j];
+        qdd[j] = qd[j];
       }
-      changed = true;
-      ++it;
-      r2 = residual2_f64<P>(ops, m, qd);
-      if (!(r2 <= DBL_MAX)) {
-        fl |= FL_NONFINITE;
-        break;
-      }
-      conv = r2 < a.tol2_64;
-    }
-    if (conv) fl |= FL_CONV;
-    else if (!(fl & (FL_NONFINITE | FL_DIV))) fl |= FL_CAP | (was_conv ? FL_ACCEPT_FAIL : 0u);
-  }
-  if (changed) {
+      r2 = finish_f64<P>(a, qf, qdd, &it, &fl, r2, was_conv);
 #pragma unroll
-    for (int j = 0; j < D; ++j) a.q_out[j * a.ld_out + item] = q[j];
+      for (int j = 0; j < D; ++j) {
+        a.q_out[j * a.ld_out + item] = qf[j];
+        qd[j] = qdd[j];
+      }
+    }
   }
 #pragma unroll
   for (int j = 0; j < D; ++j)
@@ -620,8 +654,19 @@ __device__ __forceinline__ void accept_one(const A &a, long long item, int it, u
 // therefore never wait for the slowest configuration of their warp, and the
 // FP64 work runs in full warps, interleaved with other warps' FP32 work.
 // ---------------------------------------------------------------------------
+// Register budget of the persistent kernel: what the FP32 loop needs (the FP64
+// finishing path may spill; it is rare).  Sets the resident blocks per SM.
+template <class P>
+__host__ __device__ constexpr int reg_cap() {
+  return P::D <= 7 ? 128 : 168;
+}
+template <class P, int TPB>
+__host__ __device__ constexpr int min_blocks() {
+  return 65536 / (TPB * reg_cap<P>()) > 0 ? 65536 / (TPB * reg_cap<P>()) : 1;
+}
+
 template <class P, class Src, int TPB>
-__global__ void __launch_bounds__(TPB) k_project_f32(const __grid_constant__ ProjArgs<P, Src> a) {
+__global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(const __grid_constant__ ProjArgs<P, Src> a) {
   constexpr int D = P::D;
   constexpr int W = TPB / 32;
   __shared__ long long s_item[W][64];

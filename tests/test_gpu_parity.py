@@ -108,9 +108,14 @@ def test_arm_fp32_single_steps_all_configs(mcproj, steps):
     el = dev_max <= 1e-5 * (1.0 + step)
     same = ig == io
     assert same.mean() > 0.999
+    # a pivot below the threshold hands the step to the FP64 re-solve: a different
+    # code path through a nearly singular system (steps of hundreds of radians)
+    fp32 = (fg & mcproj.F_FP64_RESOLVE) == 0
+    assert (~fp32).mean() < 1e-3
     err = np.abs(qg - qo).max(axis=0)
     ok = err <= 1e-4 * (1.0 + step)
-    assert ok[same & el].all(), (np.flatnonzero(~ok & same & el)[:8], np.quantile(err[same & el], [0.5, 0.99, 1.0]))
+    sel = same & el & fp32
+    assert ok[sel].all(), (np.flatnonzero(~ok & sel)[:8], np.quantile(err[sel], [0.5, 0.99, 1.0]))
     # large first steps through nearly singular systems are common from uniform starts
     assert el.mean() > 0.6, el.mean()
 
