@@ -57,18 +57,18 @@ def make_workload(name, rank):
     """(workload, batch q [d, n] or None, name, segments or None)."""
     from paper_2604_13323_gb300 import workloads as W
     if name == "arm":
-        wl = W.arm_workload(seed=1001 + 1000 * rank, n=65536)
+        wl = W.arm_workload(n=65536, batch_seed=1001 + 1000 * rank)
         return wl, wl.q, "arm7_axis_65536", None
     if name == "sphere":
-        wl = W.sphere_workload(seed=1000 + 1000 * rank)
+        wl = W.sphere_workload(seed=1000 + 1000 * rank)   # the point robot has no geometry to keep
         return wl, W.segment_points(wl.segments), "sphere_geodesics_1024_pairs", wl.segments
     if name == "humanoid":
-        wl = W.humanoid_workload(seed=1003 + 1000 * rank)
+        wl = W.humanoid_workload(batch_seed=1003 + 1000 * rank)
         return wl, wl.q, "humanoid36_1048576", None
     if name == "dual_segments":
-        wl = W.dual_arm_workload(seed=1002 + 1000 * rank)
+        wl = W.dual_arm_workload(batch_seed=None if rank == 0 else 1002 + 1000 * rank)
         return wl, None, f"dual14_rel_segments_{int(wl.extra['lengths'].sum())}", "raw"
-    wl = W.dual_arm_workload(seed=1002 + 1000 * rank, total=10, n_random=262144)
+    wl = W.dual_arm_workload(total=10, n_random=262144, batch_seed=None if rank == 0 else 1002 + 1000 * rank)
     return wl, wl.q, "dual14_rel_262144", None
 
 
@@ -115,6 +115,20 @@ class ClockSampler:
         reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 3 + i and r[3 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.rows)}
+
+
+def aggregate_replicas(ms, converged, world, device):
+    """Whole-job numbers of independent replicas: the slowest rank's step time
+    and the sum of converged projections over ranks (the only cross-rank
+    exchange; the data path itself has no collective)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    c = torch.tensor([converged], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
 
 
 def cpu_baseline(wl, q, budget_s=10.0):
@@ -288,13 +302,8 @@ def run_ours(args):
     rs_np = resid.cpu().numpy()
     it_np = iters.cpu().numpy()
     conv = int((((fl_np & mcproj.F_CONVERGED) != 0) & (rs_np <= wl.params.tol)).sum())
-    t_tot = torch.tensor([ms], dtype=torch.float64, device=dev)
-    c_tot = torch.tensor([conv], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_tot, op=dist.ReduceOp.MAX)
-        dist.all_reduce(c_tot, op=dist.ReduceOp.SUM)
-    ms_max = float(t_tot.item())
-    value = float(c_tot.item()) / (ms_max * 1e-3)
+    ms_max, c_total = aggregate_replicas(ms, conv, world, dev)
+    value = c_total / (ms_max * 1e-3)
 
     # ---- end to end through the C ABI with host buffers ----
     if seg_args is not None:   # the step's inputs are the segment descriptions
@@ -321,12 +330,8 @@ def run_ours(args):
         if s >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
     conv_e2e = int(((fl_host.numpy() & mcproj.F_CONVERGED) != 0).sum())
-    e2e_t = torch.tensor([sum(e2e_ms) / max(1, len(e2e_ms))], dtype=torch.float64, device=dev)
-    e2e_c = torch.tensor([conv_e2e], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(e2e_c, op=dist.ReduceOp.SUM)
-    e2e = {"value": float(e2e_c.item()) / (float(e2e_t.item()) * 1e-3) if e2e_ms else None, "unit": UNIT,
+    e2e_ms_max, e2e_c = aggregate_replicas(sum(e2e_ms) / max(1, len(e2e_ms)), conv_e2e, world, dev)
+    e2e = {"value": e2e_c / (e2e_ms_max * 1e-3) if e2e_ms else None, "unit": UNIT,
            "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in host_in),
            "d2h_bytes_per_step": out_host.numel() * out_host.element_size() + 2 * n}
 

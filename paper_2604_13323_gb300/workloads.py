@@ -300,9 +300,10 @@ def segment_points(seg: Segments) -> np.ndarray:
     return out
 
 
-def arm_workload(seed: int = 1001, n: int = 65536, n_obstacles: int = 64) -> Workload:
-    """7-DoF DH arm, end-effector z-axis parallel to world z (2 equations)."""
-    rng = np.random.default_rng(seed)
+def arm_workload(seed: int = 1001, n: int = 65536, n_obstacles: int = 64, batch_seed: int | None = None) -> Workload:
+    """7-DoF DH arm, end-effector z-axis parallel to world z (2 equations).
+    `batch_seed` (default: seed) draws the start configurations only."""
+    rng = np.random.default_rng(seed if batch_seed is None else batch_seed)
     L = arm_link_lengths(seed + 2)
     robot = dh_arm_robot(L, rng=np.random.default_rng(seed + 3))
     q = rng.uniform(-2.8, 2.8, size=(7, n))
@@ -322,7 +323,8 @@ def dual_arm_robot(seed: int = 1002) -> Robot:
 
 
 def dual_arm_workload(seed: int = 1002, total: int = 262144, len_lo: int = 2, len_hi: int = 200,
-                      step: float = 0.05, n_obstacles: int = 128, n_random: int = 0) -> Workload:
+                      step: float = 0.05, n_obstacles: int = 128, n_random: int = 0,
+                      batch_seed: int | None = None) -> Workload:
     """Two 7-DoF arms 0.6 m apart; relative EE pose fixed (Eq. 2, 6 equations).
 
     The reference relative pose is the one the arms have at a seeded
@@ -336,6 +338,8 @@ def dual_arm_workload(seed: int = 1002, total: int = 262144, len_lo: int = 2, le
     rng = np.random.default_rng(seed)
     robot = dual_arm_robot(seed)
     q_ref = rng.uniform(-1.2, 1.2, size=14)
+    if batch_seed is not None:   # the robot and its reference stay; segments and batch are redrawn
+        rng = np.random.default_rng(batch_seed)
     lengths = []
     acc = 0
     while acc < total:
@@ -474,14 +478,15 @@ def humanoid_nominal(names) -> np.ndarray:
     return q
 
 
-def humanoid_workload(seed: int = 1003, n: int = 1048576, n_obstacles: int = 200) -> Workload:
+def humanoid_workload(seed: int = 1003, n: int = 1048576, n_obstacles: int = 200,
+                      batch_seed: int | None = None) -> Workload:
     """36-DoF tree; feet fixed in 6-D pose (2 x Eq. 1), hands in a fixed relative
     pose (Eq. 2), CoM xy at the support-polygon centre: 20 equations.  All
     references are taken at the nominal stance q_nom; the support-polygon
     centre is the midpoint of the two foot frames there."""
     robot, names = humanoid_robot(seed + 2)
     q_nom = humanoid_nominal(names)
-    rng = np.random.default_rng(seed)
+    rng = np.random.default_rng(seed if batch_seed is None else batch_seed)
     sigma = np.where(robot.type == PRISMATIC, 0.05, 0.3)
     q = q_nom[:, None] + sigma[:, None] * rng.standard_normal((robot.n_joints, n))
     cons = [Constraint(C_POSE, frame_a=0, q_ref=q_nom), Constraint(C_POSE, frame_a=1, q_ref=q_nom),
