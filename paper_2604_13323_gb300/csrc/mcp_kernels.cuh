@@ -904,7 +904,7 @@ __device__ __forceinline__ bool sphere_hits_plain(V3<T> c, T rs, const T *s_obs,
 constexpr int SPH_BLOCK = 8;
 
 // FP32 check with a per-link broad phase: the link's bounding sphere is
-// tested against chunks of 64 obstacles (same 4-FMA test); only the obstacles
+// tested against chunks of 32 obstacles (same 4-FMA test); only the obstacles
 // it overlaps are tested against the link's spheres.  The bound contains every
 // sphere of the link with a 1e-4 m margin, so no overlapping pair is skipped
 // and the verdict is that of the all-pairs test.  `pairs` counts every 4-FMA
@@ -938,14 +938,24 @@ __global__ void __launch_bounds__(128) k_check_f32(const __grid_constant__ Check
     const V3<float> bc = add_rot_t<7>(p, R, V3<float>{lb[0], lb[1], lb[2]});
     const float br = lb[3];
     const float kb = fmaf(bc.x, bc.x, fmaf(bc.y, bc.y, fmaf(bc.z, bc.z, -br * br)));
-    for (int o0 = 0; o0 < a.n_obs; o0 += 64) {
-      const int cnt = min(64, a.n_obs - o0);
-      unsigned long long cand = 0ull;
-      for (int t = 0; t < cnt; ++t) {
-        const float4 g = s_obs[2 * (o0 + t)];
-        const float g2 = s_obs[2 * (o0 + t) + 1].x;
-        const float v = fmaf(bc.x, g.x, fmaf(bc.y, g.y, fmaf(bc.z, g.z, fmaf(br, g2, g.w))));
-        if (v < -kb) cand |= 1ull << t;
+    for (int o0 = 0; o0 < a.n_obs; o0 += 32) {
+      const int cnt = min(32, a.n_obs - o0);
+      unsigned cand = 0u;
+      if (cnt == 32) {  // full chunk: unrolled, compile-time bit positions
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          const float4 g = s_obs[2 * (o0 + t)];
+          const float g2 = s_obs[2 * (o0 + t) + 1].x;
+          const float v = fmaf(bc.x, g.x, fmaf(bc.y, g.y, fmaf(bc.z, g.z, fmaf(br, g2, g.w))));
+          cand |= (v < -kb) ? (1u << t) : 0u;
+        }
+      } else {
+        for (int t = 0; t < cnt; ++t) {
+          const float4 g = s_obs[2 * (o0 + t)];
+          const float g2 = s_obs[2 * (o0 + t) + 1].x;
+          const float v = fmaf(bc.x, g.x, fmaf(bc.y, g.y, fmaf(bc.z, g.z, fmaf(br, g2, g.w))));
+          if (v < -kb) cand |= 1u << t;
+        }
       }
       tests += static_cast<uint32_t>(cnt);
       if (!cand) continue;
@@ -962,10 +972,10 @@ __global__ void __launch_bounds__(128) k_check_f32(const __grid_constant__ Check
           rs[b] = a.st.s[s][3];
           ks[b] = (b < count) ? fmaf(c.x, c.x, fmaf(c.y, c.y, fmaf(c.z, c.z, -rs[b] * rs[b]))) : FLT_MAX;  // pad: never a hit
         }
-        unsigned long long m = cand;
+        unsigned m = cand;
         while (m) {
-          const int t = __ffsll(static_cast<long long>(m)) - 1;
-          m &= m - 1ull;
+          const int t = __ffs(static_cast<int>(m)) - 1;
+          m &= m - 1u;
           const float4 g = s_obs[2 * (o0 + t)];
           const float g2 = s_obs[2 * (o0 + t) + 1].x;
           bool h = false;
