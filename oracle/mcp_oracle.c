@@ -13,6 +13,9 @@
  *   - constraint residuals: TSR pose error Eq. 1 (Sec. II), the bimanual
  *     relative-pose error Eq. 2 (Sec. V-B), the humanoid's stacked feet /
  *     hands / centre-of-mass constraints (Sec. V-C, Fig. 6), with B^w = 0;
+ *     the bounded TSR of Eq. 1 (distance outside the bounds B^w, Sec. II),
+ *     point-on-plane and point-on-line task constraints (Sec. III) and the
+ *     fixed distance of a closed linkage (Sec. V-C);
  *   - the SO(3) log map with a Taylor fallback of sinc near 0 (Sec. IV-A,
  *     "Tracing Compiler for Constraints");
  *   - ParallelProject and getDescentStep of Algorithm 2: d = F(q), stop when
@@ -46,7 +49,10 @@
 #define OR_MAXC 16
 
 enum { OR_REVOLUTE = 0, OR_PRISMATIC = 1 };
-enum { OR_SPHERE = 0, OR_AXIS_ALIGN = 1, OR_POSE = 2, OR_REL_POSE = 3, OR_COM_XY = 4 };
+enum {
+  OR_SPHERE = 0, OR_AXIS_ALIGN = 1, OR_POSE = 2, OR_REL_POSE = 3, OR_COM_XY = 4,
+  OR_PLANE = 5, OR_LINE = 6, OR_DIST = 7, OR_POSE_BOUNDED = 8
+};
 enum {
   OR_CONVERGED = 1, OR_CAP = 2, OR_DIVERGED = 4, OR_NONFINITE = 8, OR_OUT_OF_LIMITS = 64
 };
@@ -73,6 +79,7 @@ typedef struct {
   double P[12];
   double Q[12];
   double target[4];
+  double B[12];   /* POSE_BOUNDED: lower[6] then upper[6] of [t; log R] */
 } or_constraint;
 
 typedef struct {
@@ -284,6 +291,10 @@ static int cons_dim(int kind) {
     case OR_POSE: return 6;
     case OR_REL_POSE: return 6;
     case OR_COM_XY: return 2;
+    case OR_PLANE: return 1;
+    case OR_LINE: return 2;
+    case OR_DIST: return 1;
+    case OR_POSE_BOUNDED: return 6;
   }
   return 0;
 }
@@ -337,7 +348,8 @@ static int cons_eval(const or_robot *rb, const or_constraint *c, const double *q
       }
       return 2;
     }
-    case OR_POSE: {
+    case OR_POSE:
+    case OR_POSE_BOUNDED: {
       /* Eq. 1: T_err = (T_w^0)^{-1} T_s^0 (T_e^w)^{-1}, d = [t_err; log(R_err)] */
       double Ta[12], Pinv[12], Qinv[12], tmp[12], Terr[12], phi[3];
       frame_pose(rb, K, c->fa, Ta);
@@ -371,7 +383,67 @@ static int cons_eval(const or_robot *rb, const or_constraint *c, const double *q
           }
         }
       }
+      if (c->kind == OR_POSE_BOUNDED) {
+        /* bounded TSR: each component's distance outside [lower, upper];
+         * inside the bounds the residual and its derivative are zero */
+        for (int r = 0; r < 6; ++r) {
+          double lo = c->B[r], hi = c->B[6 + r];
+          if (F[r] < lo) F[r] -= lo;
+          else if (F[r] > hi) F[r] -= hi;
+          else {
+            F[r] = 0.0;
+            if (J)
+              for (int j = 0; j < d; ++j) J[(row0 + r) * d + j] = 0.0;
+          }
+        }
+      }
       return 6;
+    }
+    case OR_PLANE:
+    case OR_LINE: {
+      /* origin x of frame a on the xy-plane (PLANE: F = z of P^{-1} x) or on
+       * the z-axis (LINE: F = (x, y) of P^{-1} x) of the task frame P */
+      double Ta[12], Pinv[12], xl[3];
+      frame_pose(rb, K, c->fa, Ta);
+      double x[3] = {Ta[3], Ta[7], Ta[11]};
+      tf_inv(c->P, Pinv);
+      tf_point(Pinv, x, xl);
+      const int rows = c->kind == OR_PLANE ? 1 : 2;
+      if (c->kind == OR_PLANE) F[0] = xl[2];
+      else { F[0] = xl[0]; F[1] = xl[1]; }
+      if (J) {
+        int link = rb->frame_link[c->fa];
+        for (int j = 0; j < d; ++j) {
+          double v[3] = {0, 0, 0}, vt[3];
+          if (link >= 0 && is_ancestor(rb, j, link)) point_velocity(rb, K, j, x, v);
+          tf_rotate_t(c->P, v, vt);
+          if (c->kind == OR_PLANE) J[row0 * d + j] = vt[2];
+          else { J[row0 * d + j] = vt[0]; J[(row0 + 1) * d + j] = vt[1]; }
+        }
+      }
+      return rows;
+    }
+    case OR_DIST: {
+      /* closed linkage: F = |x_b - x_a| - L for the origins of frames a and b */
+      double Ta[12], Tb[12];
+      frame_pose(rb, K, c->fa, Ta);
+      frame_pose(rb, K, c->fb, Tb);
+      double xa[3] = {Ta[3], Ta[7], Ta[11]}, xb[3] = {Tb[3], Tb[7], Tb[11]};
+      double e[3] = {xb[0] - xa[0], xb[1] - xa[1], xb[2] - xa[2]};
+      double n = sqrt(dot3(e, e));
+      F[0] = n - c->target[0];
+      if (J) {
+        double u[3] = {e[0] / n, e[1] / n, e[2] / n};
+        int la = rb->frame_link[c->fa], lb = rb->frame_link[c->fb];
+        for (int j = 0; j < d; ++j) {
+          double va[3] = {0, 0, 0}, vb[3] = {0, 0, 0};
+          if (la >= 0 && is_ancestor(rb, j, la)) point_velocity(rb, K, j, xa, va);
+          if (lb >= 0 && is_ancestor(rb, j, lb)) point_velocity(rb, K, j, xb, vb);
+          double dv[3] = {vb[0] - va[0], vb[1] - va[1], vb[2] - va[2]};
+          J[row0 * d + j] = dot3(u, dv);
+        }
+      }
+      return 1;
     }
     case OR_REL_POSE: {
       /* Eq. 2: T_err = T_ref^{-1} (T_left^{-1} T_right), d = [t_err; log(R_err)] */
@@ -688,11 +760,24 @@ void or_so3_left_jac_inv(const double *phi, double *M) {
 void or_resolve_reference(const or_robot *rb, or_constraint *c, const double *q_ref) {
   or_kin K;
   fk(rb, q_ref, &K);
-  if (c->kind == OR_POSE) {
+  if (c->kind == OR_POSE || c->kind == OR_POSE_BOUNDED) {
     double Ta[12], Qinv[12];
     frame_pose(rb, &K, c->fa, Ta);
     tf_inv(c->Q, Qinv);
     tf_mul(Ta, Qinv, c->P);
+  } else if (c->kind == OR_PLANE || c->kind == OR_LINE) {
+    /* the plane / line keeps its orientation and passes through frame a */
+    double Ta[12];
+    frame_pose(rb, &K, c->fa, Ta);
+    c->P[3] = Ta[3];
+    c->P[7] = Ta[7];
+    c->P[11] = Ta[11];
+  } else if (c->kind == OR_DIST) {
+    double Ta[12], Tb[12];
+    frame_pose(rb, &K, c->fa, Ta);
+    frame_pose(rb, &K, c->fb, Tb);
+    double e[3] = {Tb[3] - Ta[3], Tb[7] - Ta[7], Tb[11] - Ta[11]};
+    c->target[0] = sqrt(dot3(e, e));
   } else if (c->kind == OR_REL_POSE) {
     double Ta[12], Tb[12], Tainv[12];
     frame_pose(rb, &K, c->fa, Ta);

@@ -27,7 +27,8 @@ _lib = None
 
 CONVERGED, CAP, DIVERGED, NONFINITE, OUT_OF_LIMITS = 1, 2, 4, 8, 64
 SPHERE, AXIS_ALIGN, POSE, REL_POSE, COM_XY = 0, 1, 2, 3, 4
-DIM = {SPHERE: 1, AXIS_ALIGN: 2, POSE: 6, REL_POSE: 6, COM_XY: 2}
+PLANE, LINE, DIST, POSE_BOUNDED = 5, 6, 7, 8
+DIM = {SPHERE: 1, AXIS_ALIGN: 2, POSE: 6, REL_POSE: 6, COM_XY: 2, PLANE: 1, LINE: 2, DIST: 1, POSE_BOUNDED: 6}
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
@@ -42,7 +43,8 @@ class _Robot(ctypes.Structure):
 
 class _Constraint(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("fa", ctypes.c_int32), ("fb", ctypes.c_int32), ("pad", ctypes.c_int32),
-                ("P", ctypes.c_double * 12), ("Q", ctypes.c_double * 12), ("target", ctypes.c_double * 4)]
+                ("P", ctypes.c_double * 12), ("Q", ctypes.c_double * 12), ("target", ctypes.c_double * 4),
+                ("B", ctypes.c_double * 12)]
 
 
 class _Params(ctypes.Structure):
@@ -143,6 +145,9 @@ class Oracle:
                 cc.Q[t] = float(c.Q[t])
             for t in range(3):
                 cc.target[t] = float(c.target[t])
+            B = getattr(c, "B", None)
+            for t in range(12):   # unbounded unless given
+                cc.B[t] = float(B[t]) if B is not None else (-np.inf if t < 6 else np.inf)
             if getattr(c, "q_ref", None) is not None:
                 lib.or_resolve_reference(ctypes.byref(r), ctypes.byref(cc), _ptr(_f64(c.q_ref)))
             self.k += DIM[int(c.kind)]
@@ -157,6 +162,10 @@ class Oracle:
     def constraint_values(self, i):
         c = self._cons[i]
         return np.array(c.P[:]), np.array(c.Q[:]), np.array(c.target[:3])
+
+    def bounds(self, i):
+        c = self._cons[i]
+        return np.array(c.B[:])
 
     # ---- single-configuration helpers ----
     def fk(self, q):

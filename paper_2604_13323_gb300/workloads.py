@@ -48,8 +48,13 @@ C_AXIS_ALIGN = 1  # frame z-axis parallel to world z    (k = 2)
 C_POSE = 2        # TSR pose error, Eq. 1, B^w = 0      (k = 6)
 C_REL_POSE = 3    # relative pose error, Eq. 2          (k = 6)
 C_COM_XY = 4      # centre-of-mass xy at a target point (k = 2)
+C_PLANE = 5       # frame origin on the xy-plane of P   (k = 1)
+C_LINE = 6        # frame origin on the z-axis of P     (k = 2)
+C_DIST = 7        # |x_b - x_a| = L, closed linkage     (k = 1)
+C_POSE_BOUNDED = 8  # TSR pose error outside bounds B^w (k = 6)
 
-CONSTRAINT_DIM = {C_SPHERE: 1, C_AXIS_ALIGN: 2, C_POSE: 6, C_REL_POSE: 6, C_COM_XY: 2}
+CONSTRAINT_DIM = {C_SPHERE: 1, C_AXIS_ALIGN: 2, C_POSE: 6, C_REL_POSE: 6, C_COM_XY: 2, C_PLANE: 1, C_LINE: 2,
+                  C_DIST: 1, C_POSE_BOUNDED: 6}
 
 # Precision selector of the projection entry point.
 PREC_FP32 = 0   # FP32 Newton with FP64 acceptance
@@ -111,11 +116,14 @@ class Constraint:
     kind    one of C_*
     frame_a / frame_b   task-frame indices (POSE: a; REL_POSE: a = left, b = right;
                         COM_XY reference: midpoint of a and b)
-    P       3x4: POSE -> T_w^0 (TSR frame in world); REL_POSE -> T_ref
-    Q       3x4: POSE -> T_e^w (end-effector offset in the TSR frame)
-    target  SPHERE -> (radius, -, -); COM_XY -> (cx, cy, -)
-    q_ref   if given, P (POSE, REL_POSE) or the CoM target (COM_XY) is derived
-            from the robot's pose at q_ref when the constraint is loaded
+    P       3x4: POSE, POSE_BOUNDED -> T_w^0 (TSR frame in world); REL_POSE -> T_ref;
+            PLANE / LINE -> task frame whose xy-plane / z-axis holds frame a's origin
+    Q       3x4: POSE, POSE_BOUNDED -> T_e^w (end-effector offset in the TSR frame)
+    target  SPHERE -> (radius, -, -); COM_XY -> (cx, cy, -); DIST -> (L, -, -)
+    B       POSE_BOUNDED: 12 bounds of [t; log R], lower[6] then upper[6]
+    q_ref   if given, P (POSE, POSE_BOUNDED, REL_POSE), the origin of P (PLANE,
+            LINE), L (DIST) or the CoM target (COM_XY) is derived from the
+            robot's pose at q_ref when the constraint is loaded
     """
     kind: int
     frame_a: int = -1
@@ -124,6 +132,7 @@ class Constraint:
     Q: np.ndarray = dataclasses.field(default_factory=lambda: IDENTITY12.copy())
     target: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(3))
     q_ref: np.ndarray | None = None
+    B: np.ndarray | None = None
 
     @property
     def dim(self) -> int:
@@ -138,6 +147,7 @@ class Params:
     max_step: float = 0.0       # <= 0: divergence exit disabled
     pivot_fp64: float = 1e-7    # FP32 Cholesky pivot below this -> FP64 re-solve
     precision: int = PREC_FP32
+    cyclic: bool = False        # one LM step per constraint in order (Sec. IV-C) instead of stacked
 
 
 @dataclasses.dataclass
@@ -315,6 +325,40 @@ def arm_workload(seed: int = 1001, n: int = 65536, n_obstacles: int = 64, batch_
                     obstacles=obst, params=Params(tol=1e-5, max_iters=30, lam=1e-6), q=q)
 
 
+def arm_task_workload(task: str, seed: int = 1007, n: int = 65536, n_obstacles: int = 64,
+                      batch_seed: int | None = None) -> Workload:
+    """The arm of `arm_workload` under a task constraint through its
+    end-effector pose at a seeded q_ref (so the manifold is not empty):
+
+    * ``tray``: the end effector on the horizontal plane through its q_ref
+      position and its z-axis vertical (PLANE + AXIS_ALIGN, 3 equations);
+    * ``peg``: the end effector on the vertical line through its q_ref
+      position and its z-axis vertical (LINE + AXIS_ALIGN, 4 equations);
+    * ``tsr``: a bounded TSR around the q_ref pose, +-5 cm in x and y,
+      +-2 cm in z, +-0.1 rad about x and y, +-0.6 rad about z (6 equations).
+
+    Starts are q_ref + N(0, 0.3^2) (configurations near a task, as the
+    extension steps of a planner produce)."""
+    rng = np.random.default_rng(seed)
+    q_ref = rng.uniform(-1.5, 1.5, 7)
+    base = arm_workload(n=1, n_obstacles=n_obstacles)
+    brng = np.random.default_rng(seed + 10 if batch_seed is None else batch_seed)
+    q = q_ref[:, None] + 0.3 * brng.standard_normal((7, n))
+    if task == "tray":
+        cons = [Constraint(C_PLANE, frame_a=0, q_ref=q_ref), Constraint(C_AXIS_ALIGN, frame_a=0)]
+    elif task == "peg":
+        cons = [Constraint(C_LINE, frame_a=0, q_ref=q_ref), Constraint(C_AXIS_ALIGN, frame_a=0)]
+    elif task == "tsr":
+        hi = np.array([0.05, 0.05, 0.02, 0.1, 0.1, 0.6])
+        cons = [Constraint(C_POSE_BOUNDED, frame_a=0, q_ref=q_ref, B=np.concatenate([-hi, hi]))]
+    else:
+        raise ValueError(task)
+    wl = Workload(name=f"arm_{task}", robot=base.robot, constraints=cons, obstacles=base.obstacles,
+                  params=Params(tol=1e-5, max_iters=30, lam=1e-6), q=q)
+    wl.extra["q_ref"] = q_ref
+    return wl
+
+
 def dual_arm_robot(seed: int = 1002) -> Robot:
     L = arm_link_lengths(1001 + 2)    # two copies of the arm workload's chain
     left = dh_arm_robot(L, base=(0.0, 0.3, 0.0), rng=np.random.default_rng(seed + 3))
@@ -360,6 +404,28 @@ def dual_arm_workload(seed: int = 1002, total: int = 262144, len_lo: int = 2, le
                     step=step, q_ref=q_ref)
     if n_random:
         wl.q = q_ref[:, None] + 0.3 * rng.standard_normal((14, n_random))
+    return wl
+
+
+def dual_rod_workload(seed: int = 1009, n: int = 65536, n_obstacles: int = 128, sigma: float = 0.3,
+                      batch_seed: int | None = None) -> Workload:
+    """The dual arm carrying a rigid rod on a table: the distance between the
+    two end effectors fixed (a closed linkage, DIST) and each end effector on
+    the horizontal plane through its position at a seeded q_ref (PLANE,
+    PLANE): 3 equations in 3 stacked constraints.  Starts q_ref + N(0, sigma^2)."""
+    rng = np.random.default_rng(seed)
+    robot = dual_arm_robot()
+    q_ref = rng.uniform(-1.2, 1.2, 14)
+    brng = rng if batch_seed is None else np.random.default_rng(batch_seed)
+    q = q_ref[:, None] + sigma * brng.standard_normal((14, n))
+    cons = [Constraint(C_DIST, frame_a=0, frame_b=1, q_ref=q_ref), Constraint(C_PLANE, frame_a=0, q_ref=q_ref),
+            Constraint(C_PLANE, frame_a=1, q_ref=q_ref)]
+    obst = Obstacles(spheres=_sphere_obstacles(np.random.default_rng(1002 + 1), n_obstacles,
+                                               (0.2, -1.05, 0.0), (1.7, 1.05, 1.5)),
+                     aabbs=np.zeros((0, 6)))
+    wl = Workload(name="dual_rod", robot=robot, constraints=cons, obstacles=obst,
+                  params=Params(tol=1e-5, max_iters=30, lam=1e-6, pivot_fp64=1e-7), q=q)
+    wl.extra["q_ref"] = q_ref
     return wl
 
 

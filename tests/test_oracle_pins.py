@@ -299,6 +299,15 @@ def test_references_from_q_ref_zero_the_residual():
     wl2 = W.dual_arm_workload(total=10)
     o2 = orc.Oracle(wl2.robot, wl2.constraints)
     np.testing.assert_allclose(o2.residual(wl2.extra["q_ref"]), 0.0, atol=1e-14)
+    wl3 = W.dual_rod_workload(n=1)
+    o3 = orc.Oracle(wl3.robot, wl3.constraints)
+    np.testing.assert_allclose(o3.residual(wl3.extra["q_ref"]), 0.0, atol=1e-14)
+    for task in ("tray", "peg", "tsr"):
+        wl4 = W.arm_task_workload(task, n=1)
+        o4 = orc.Oracle(wl4.robot, wl4.constraints)
+        # the plane / line / TSR pass through the end effector at q_ref (the axis
+        # constraint of tray and peg is not satisfied there)
+        np.testing.assert_allclose(o4.residual(wl4.extra["q_ref"])[:wl4.constraints[0].dim], 0.0, atol=1e-14)
 
 
 def test_axis_align_residual_is_ee_z_axis():
@@ -351,6 +360,14 @@ def _cases():
     yield "humanoid", wl.robot, wl.constraints
     wl2 = W.dual_arm_workload(total=10)
     yield "dual", wl2.robot, wl2.constraints
+    yield "plane", tree, [W.Constraint(W.C_PLANE, frame_a=1, P=P)]
+    yield "line", tree, [W.Constraint(W.C_LINE, frame_a=2, P=P)]
+    yield "dist", tree, [W.Constraint(W.C_DIST, frame_a=0, frame_b=2, target=np.array([0.3, 0, 0]))]
+    # bounds: some components pinned to zero (always active), some wide (always
+    # inactive), so that no finite difference straddles a bound
+    lo = np.array([0.0, -50.0, 0.0, -50.0, 0.0, 0.0])
+    yield "tsr", tree, [W.Constraint(W.C_POSE_BOUNDED, frame_a=1, P=P, Q=Q, B=np.concatenate([lo, -lo]))]
+    yield "rod", W.dual_rod_workload(n=1).robot, W.dual_rod_workload(n=1).constraints
 
 
 @pytest.mark.parametrize("case", list(_cases()), ids=lambda c: c[0])
@@ -378,17 +395,22 @@ def test_jacobian_matches_finite_differences(case):
 # ---------------------------------------------------------------------------
 # Convergence invariant and cyclic/stacked agreement
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("name", ["arm", "dual", "humanoid"])
+@pytest.mark.parametrize("name", ["arm", "dual", "humanoid", "tray", "peg", "tsr", "rod", "rod_cyclic",
+                                  "tsr_cyclic"])
 def test_converged_configs_satisfy_tolerance(name):
     if name == "arm":
         wl = W.arm_workload(n=256)
     elif name == "dual":
         wl = W.dual_arm_workload(total=10, n_random=256)
+    elif name in ("tray", "peg", "tsr", "tsr_cyclic"):
+        wl = W.arm_task_workload(name.split("_")[0], n=256)
+    elif name in ("rod", "rod_cyclic"):
+        wl = W.dual_rod_workload(n=256)
     else:
         wl = W.humanoid_workload(n=128)
     o = orc.Oracle(wl.robot, wl.constraints)
     p = wl.params
-    out, flags, iters, resid = o.project(wl.q, p.tol, p.max_iters, p.lam)
+    out, flags, iters, resid = o.project(wl.q, p.tol, p.max_iters, p.lam, cyclic=name.endswith("cyclic"))
     conv = (flags & orc.CONVERGED) != 0
     assert conv.mean() > 0.8
     for i in np.flatnonzero(conv)[:64]:
@@ -581,3 +603,147 @@ def test_residual_values_match_independent_evaluation():
         np.testing.assert_allclose(F, expect, atol=1e-11)
         checked += 1
     assert checked > 30
+
+
+# ---------------------------------------------------------------------------
+# Task constraints beyond B^w = 0 (Sec. II bounded TSRs, Sec. III task
+# constraints, Sec. V-C closed linkages): closed forms on Cartesian points,
+# where one Newton step from any start is the Euclidean projection.
+# ---------------------------------------------------------------------------
+def _two_points():
+    a = cartesian_robot()
+    return W._merge_robots(a, cartesian_robot())
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_plane_and_line_one_step_are_orthogonal_projections(seed):
+    rng = np.random.default_rng(40 + seed)
+    R = W.random_rotation(rng)
+    c = rng.uniform(-1, 1, 3)
+    P = _rt(R, c)
+    n, dl = R[:, 2], R[:, 2]
+    rb = cartesian_robot()
+    p0 = rng.uniform(-1.5, 1.5, (3, 16))
+    op = orc.Oracle(rb, [W.Constraint(W.C_PLANE, frame_a=0, P=P)])
+    # the residual is the signed distance to the plane
+    np.testing.assert_allclose(op.residual(p0[:, 0]), [n @ (p0[:, 0] - c)], atol=1e-14)
+    out, fl, it, _ = op.project(p0, 1e-12, 1, 0.0)
+    expect = p0 - np.outer(n, n @ (p0 - c[:, None]))
+    np.testing.assert_allclose(out, expect, atol=1e-13)
+    ol = orc.Oracle(rb, [W.Constraint(W.C_LINE, frame_a=0, P=P)])
+    out, fl, it, _ = ol.project(p0, 1e-12, 1, 0.0)
+    expect = c[:, None] + np.outer(dl, dl @ (p0 - c[:, None]))
+    np.testing.assert_allclose(out, expect, atol=1e-13)
+    # the distance to the line is the norm of the residual
+    r = ol.residual(p0[:, 1])
+    np.testing.assert_allclose(np.linalg.norm(r), np.linalg.norm(np.cross(p0[:, 1] - c, dl)), atol=1e-14)
+
+
+def test_distance_constraint_one_step_moves_both_points_symmetrically():
+    """F = |b - a| - L with J = [-u^T, u^T]: the minimum-norm step moves a and b
+    by F/2 each along u = (b - a)/|b - a|, which lands exactly on |b - a| = L."""
+    rb = _two_points()
+    rng = np.random.default_rng(44)
+    o = orc.Oracle(rb, [W.Constraint(W.C_DIST, frame_a=0, frame_b=1, target=np.array([0.7, 0, 0]))])
+    q0 = rng.uniform(-1, 1, (6, 32))
+    out, fl, it, res = o.project(q0, 1e-12, 1, 0.0)
+    a, b = q0[:3], q0[3:]
+    e = b - a
+    nrm = np.linalg.norm(e, axis=0)
+    u = e / nrm
+    F = nrm - 0.7
+    np.testing.assert_allclose(out[:3], a + u * F / 2, atol=1e-14)
+    np.testing.assert_allclose(out[3:], b - u * F / 2, atol=1e-14)
+    np.testing.assert_allclose(np.linalg.norm(out[3:] - out[:3], axis=0), 0.7, atol=1e-14)
+
+
+def test_bounded_tsr_zero_bounds_is_the_pose_constraint():
+    tree = W.random_tree_robot(4, n_joints=10, n_frames=3)
+    rng = np.random.default_rng(45)
+    P = _rt(W.random_rotation(rng), rng.uniform(-1, 1, 3))
+    Q = _rt(W.random_rotation(rng), rng.uniform(-0.2, 0.2, 3))
+    a = orc.Oracle(tree, [W.Constraint(W.C_POSE, frame_a=1, P=P, Q=Q)])
+    b = orc.Oracle(tree, [W.Constraint(W.C_POSE_BOUNDED, frame_a=1, P=P, Q=Q, B=np.zeros(12))])
+    for _ in range(8):
+        q = rng.uniform(-1.5, 1.5, tree.n_joints)
+        Fa, Ja = a.residual_jacobian(q)
+        Fb, Jb = b.residual_jacobian(q)
+        np.testing.assert_array_equal(Fa, Fb)
+        np.testing.assert_array_equal(Ja, Jb)
+
+
+def test_bounded_tsr_projects_a_point_onto_its_box():
+    """Translation bounds on a Cartesian point: the TSR set is a box and the
+    step moves only the violated coordinates, onto the box faces (clamp)."""
+    rb = cartesian_robot()
+    rng = np.random.default_rng(46)
+    R = W.random_rotation(rng)
+    c = rng.uniform(-0.5, 0.5, 3)
+    half = np.array([0.2, 0.1, 0.3])
+    inf = np.full(3, np.inf)
+    B = np.concatenate([-half, -inf, half, inf])
+    o = orc.Oracle(rb, [W.Constraint(W.C_POSE_BOUNDED, frame_a=0, P=_rt(R, c), B=B)])
+    p0 = rng.uniform(-1.2, 1.2, (3, 64))
+    local = R.T @ (p0 - c[:, None])
+    # inactive rows carry lambda only: lambda = 1e-14 leaves the active step exact to ~1e-14
+    out, fl, it, _ = o.project(p0, 1e-12, 1, 1e-14)
+    expect = c[:, None] + R @ np.clip(local, -half[:, None], half[:, None])
+    np.testing.assert_allclose(out, expect, atol=1e-12)
+    inside = (np.abs(local) <= half[:, None]).all(axis=0)
+    assert inside.any() and (~inside).any()
+    np.testing.assert_array_equal(out[:, inside], p0[:, inside])
+
+
+def test_bounded_tsr_yaw_interval():
+    """One revolute joint about z with the TSR's yaw bounded to [-0.2, 0.3]: the
+    valid set is that interval and a start outside lands on its nearer end."""
+    rb = W.Robot(parent=np.array([-1], np.int32), type=np.zeros(1, np.int32), X=_rt(np.eye(3), 0)[None],
+                 lower=np.full(1, -3.0), upper=np.full(1, 3.0), mass=np.ones(1), com=np.zeros((1, 3)),
+                 sphere_link=np.zeros(0, np.int32), sphere=np.zeros((0, 4)), frame_link=np.array([0], np.int32),
+                 frame_X=_rt(np.eye(3), (0.4, 0, 0))[None])
+    B = np.array([-np.inf] * 5 + [-0.2] + [np.inf] * 5 + [0.3])
+    B[0:3], B[6:9] = -1.0, 1.0           # translation bounds wide enough for the 0.4 m offset
+    o = orc.Oracle(rb, [W.Constraint(W.C_POSE_BOUNDED, frame_a=0, B=B)])
+    qs = np.array([[-1.0, -0.5, -0.1, 0.0, 0.25, 0.6, 1.4]])
+    out, fl, it, _ = o.project(qs, 1e-12, 5, 1e-14)
+    expect = np.clip(qs, -0.2, 0.3)
+    np.testing.assert_allclose(out, expect, atol=1e-12)
+
+
+def test_cyclic_sweep_equals_stacked_step_on_decoupled_linear_constraints():
+    """Two planes, each on its own Cartesian point: J is block diagonal, so one
+    cyclic sweep (a step per constraint) and one stacked step coincide, and both
+    land on the closed-form projections."""
+    rb = _two_points()
+    rng = np.random.default_rng(47)
+    Pa = _rt(W.random_rotation(rng), rng.uniform(-1, 1, 3))
+    Pb = _rt(W.random_rotation(rng), rng.uniform(-1, 1, 3))
+    cons = [W.Constraint(W.C_PLANE, frame_a=0, P=Pa), W.Constraint(W.C_PLANE, frame_a=1, P=Pb)]
+    o = orc.Oracle(rb, cons)
+    q0 = rng.uniform(-1, 1, (6, 16))
+    s = o.project(q0, 1e-12, 1, 0.0, cyclic=False)[0]
+    c = o.project(q0, 1e-12, 1, 0.0, cyclic=True)[0]
+    np.testing.assert_allclose(s, c, atol=1e-14)
+    na, ca = Pa.reshape(3, 4)[:, 2], Pa.reshape(3, 4)[:, 3]
+    np.testing.assert_allclose(c[:3], q0[:3] - np.outer(na, na @ (q0[:3] - ca[:, None])), atol=1e-13)
+
+
+def test_cyclic_sweep_is_sequential_on_coupled_constraints():
+    """Two planes on the same point: a sweep projects onto plane a, then from
+    there onto plane b (alternating projections), which is not the stacked
+    step; iterated, it converges to the intersection line."""
+    rb = cartesian_robot()
+    rng = np.random.default_rng(48)
+    Pa = _rt(W.random_rotation(rng), rng.uniform(-1, 1, 3))
+    Pb = _rt(W.random_rotation(rng), rng.uniform(-1, 1, 3))
+    o = orc.Oracle(rb, [W.Constraint(W.C_PLANE, frame_a=0, P=Pa), W.Constraint(W.C_PLANE, frame_a=0, P=Pb)])
+    q0 = rng.uniform(-1, 1, (3, 8))
+    na, ca = Pa.reshape(3, 4)[:, 2], Pa.reshape(3, 4)[:, 3]
+    nb, cb = Pb.reshape(3, 4)[:, 2], Pb.reshape(3, 4)[:, 3]
+    x = q0 - np.outer(na, na @ (q0 - ca[:, None]))
+    x = x - np.outer(nb, nb @ (x - cb[:, None]))
+    np.testing.assert_allclose(o.project(q0, 1e-12, 1, 0.0, cyclic=True)[0], x, atol=1e-13)
+    out, fl, it, _ = o.project(q0, 1e-10, 500, 0.0, cyclic=True)
+    assert (fl & orc.CONVERGED).all()
+    np.testing.assert_allclose(na @ (out - ca[:, None]), 0.0, atol=1e-10)
+    np.testing.assert_allclose(nb @ (out - cb[:, None]), 0.0, atol=1e-10)
