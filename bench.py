@@ -43,7 +43,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="arm", choices=["arm", "dual_arm", "dual_segments", "sphere", "humanoid"])
+    ap.add_argument("--workload", default="arm", choices=["arm", "dual_arm", "dual_segments", "sphere", "humanoid",
+                                                          "arm_tray", "arm_peg", "arm_tsr", "dual_rod"])
+    ap.add_argument("--cyclic", action="store_true",
+                    help="cyclic getDescentStep (one LM step per constraint per sweep) instead of the stacked step")
+    ap.add_argument("--cap", type=int, default=0, help="iteration cap (default: the workload's)")
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=0,
@@ -65,6 +69,12 @@ def make_workload(name, rank):
     if name == "humanoid":
         wl = W.humanoid_workload(batch_seed=1003 + 1000 * rank)
         return wl, wl.q, "humanoid36_1048576", None
+    if name in ("arm_tray", "arm_peg", "arm_tsr"):
+        wl = W.arm_task_workload(name[4:], batch_seed=None if rank == 0 else 1007 + 1000 * rank)
+        return wl, wl.q, f"arm7_{name[4:]}_65536", None
+    if name == "dual_rod":
+        wl = W.dual_rod_workload(batch_seed=None if rank == 0 else 1009 + 1000 * rank)
+        return wl, wl.q, "dual14_rod_65536", None
     if name == "dual_segments":
         wl = W.dual_arm_workload(batch_seed=None if rank == 0 else 1002 + 1000 * rank)
         return wl, None, f"dual14_rel_segments_{int(wl.extra['lengths'].sum())}", "raw"
@@ -131,6 +141,17 @@ def aggregate_replicas(ms, converged, world, device):
     return float(t.item()), float(c.item())
 
 
+def apply_overrides(wl, name, args):
+    """--cyclic / --cap on the workload's parameters; the workload name says so."""
+    if args.cyclic:
+        wl.params.cyclic = True
+        name += "_cyclic"
+    if args.cap:
+        wl.params.max_iters = args.cap
+        name += f"_cap{args.cap}"
+    return name
+
+
 def cpu_baseline(wl, q, budget_s=10.0):
     """The FP64 oracle, as it stands, on the host cores: projection + check of
     contiguous chunks of the workload until ~budget_s of wall time."""
@@ -144,7 +165,8 @@ def cpu_baseline(wl, q, budget_s=10.0):
     off = 0
     while time.perf_counter() - t0 < budget_s:
         sl = q[:, off:off + chunk]
-        out, fl, _, r = O.project(sl, p.tol, p.max_iters, p.lam, max_step=p.max_step, threads=threads)
+        out, fl, _, r = O.project(sl, p.tol, p.max_iters, p.lam, max_step=p.max_step, cyclic=p.cyclic,
+                                  threads=threads)
         O.check(out, threads=threads)
         conv += int(((fl & orc.CONVERGED) != 0).sum())
         done += sl.shape[1]
@@ -161,6 +183,7 @@ def run_reference(args):
     if rank != 0:
         return
     wl, q, wname, segs = make_workload(args.workload, 0)
+    wname = apply_overrides(wl, wname, args)
     if q is None:
         from paper_2604_13323_gb300 import workloads as W
         q = wl.extra["raw_start"]   # the oracle arm projects segment starts-like configurations
@@ -173,7 +196,8 @@ def run_reference(args):
     for s in range(args.warmup + args.steps):
         sl = q[:, (s * sample) % q.shape[1]:][:, :sample]
         t0 = time.perf_counter()
-        out, fl, _, _ = O.project(sl, p.tol, p.max_iters, p.lam, max_step=p.max_step, threads=threads)
+        out, fl, _, _ = O.project(sl, p.tol, p.max_iters, p.lam, max_step=p.max_step, cyclic=p.cyclic,
+                                  threads=threads)
         O.check(out, threads=threads)
         dt = time.perf_counter() - t0
         if s >= args.warmup:
@@ -211,6 +235,7 @@ def run_ours(args):
     from paper_2604_13323_gb300 import workloads as W
 
     wl, q_np, wname, segs = make_workload(args.workload, rank)
+    wname = apply_overrides(wl, wname, args)
     if args.batch and q_np is not None:
         q_np = q_np[:, :args.batch]
         wname += f"_first{args.batch}"
@@ -336,7 +361,7 @@ def run_ours(args):
            "d2h_bytes_per_step": out_host.numel() * out_host.element_size() + 2 * n}
 
     # ---- roofline of the dominant kernel ----
-    fm = FL.FlopModel(wl.robot, wl.constraints)
+    fm = FL.FlopModel(wl.robot, wl.constraints, cyclic=bool(wl.params.cyclic))
     fp32, fp64f = fm.projection(it_np)
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
@@ -386,6 +411,7 @@ def run_ours(args):
                 "config": {"workload": wname, "batch": n, "dof": d, "k": wl.k, "tol": wl.params.tol,
                            "source": "segments (persistent launch, CUDA graph)" if seg_args is not None else "batch",
                            "cap": wl.params.max_iters, "lambda": wl.params.lam,
+                           "form": "cyclic" if wl.params.cyclic else "stacked",
                            "precision": "fp64 plain" if fp64 else "fp32 + fp64 acceptance",
                            "obstacles": int(wl.obstacles.spheres.shape[0]), "robot_spheres": wl.robot.n_spheres,
                            "l2": "flushed between timed steps (512 MB write)",

@@ -80,7 +80,14 @@ typedef enum {
                            P = T_w^0, Q = T_e^w, k = 6 */
   MCP_C_REL_POSE = 3,   /* Eq. 2: T_err = P^-1 (T_a^-1 T_b), F = [t_err; log(R_err)],
                            P = T_ref, a = left, b = right, k = 6 */
-  MCP_C_COM_XY = 4      /* Sec. V-C stability: F = x_com^xy - target[0:2], k = 2 */
+  MCP_C_COM_XY = 4,     /* Sec. V-C stability: F = x_com^xy - target[0:2], k = 2 */
+  MCP_C_PLANE = 5,      /* Sec. III task constraint: origin x of frame_a on the xy-plane of the
+                           task frame P: F = z of P^-1 x, k = 1 */
+  MCP_C_LINE = 6,       /* Sec. III task constraint: x on the z-axis of P: F = (x, y) of P^-1 x, k = 2 */
+  MCP_C_DIST = 7,       /* Sec. V-C closed linkage: F = |x_b - x_a| - target[0] for the origins of
+                           frame_a and frame_b, k = 1 */
+  MCP_C_POSE_BOUNDED = 8 /* Eq. 1 with bounds B^w (Sec. II TSR): e = [t_err; log(R_err)] as for POSE,
+                           F_i = e_i - clamp(e_i, B[i], B[6 + i]) (zero inside the bounds), k = 6 */
 } mcp_ckind;
 
 /* Robot: a tree of 1-DoF joints in topological order (parent[j] < j, -1 = world).
@@ -107,10 +114,15 @@ typedef struct {
 
 /* One constraint.  If q_ref != NULL (HOST, n_joints doubles) the reference is
  * taken from the robot at q_ref when loaded, in FP64 on the device:
- *   POSE:     P := T_a(q_ref) Q^-1          (T_err(q_ref) = I)
+ *   POSE, POSE_BOUNDED: P := T_a(q_ref) Q^-1          (T_err(q_ref) = I)
  *   REL_POSE: P := T_a(q_ref)^-1 T_b(q_ref)
+ *   PLANE, LINE: the translation of P := origin of frame a at q_ref (P keeps
+ *             its rotation: the plane / line passes through frame a)
+ *   DIST:     target[0] := |x_b(q_ref) - x_a(q_ref)|
  *   COM_XY:   target := xy midpoint of frames a and b at q_ref (the centre of
- *             the support polygon of two feet). */
+ *             the support polygon of two feet).
+ * B: POSE_BOUNDED only, lower[6] then upper[6] of [t; log R] (+-inf allowed;
+ * lower <= upper required); ignored by the other kinds. */
 typedef struct {
   int32_t kind;
   int32_t frame_a, frame_b;
@@ -118,6 +130,7 @@ typedef struct {
   double Q[12];
   double target[3];
   const double *q_ref;
+  double B[12];
 } mcp_constraint_desc;
 
 typedef struct {
@@ -127,6 +140,11 @@ typedef struct {
   double lambda;       /* LM damping */
   double max_step;     /* Alg. 2 MaxDistance; <= 0 disables the exit */
   double pivot_fp64;   /* FP32 Cholesky pivot below this -> the step is re-solved in FP64 */
+  int32_t cyclic;      /* 0: stacked F, one LM step per iteration; 1: cyclic getDescentStep
+                          (Sec. IV-C): per iteration one LM step per constraint in stack order,
+                          each at the configuration the previous one produced; the stopping test
+                          and MaxDistance apply to the stacked F and to the whole sweep */
+  int32_t reserved;    /* 0 */
 } mcp_project_params;
 
 /* Context on CUDA device `device`. */

@@ -14,16 +14,16 @@ import numpy as np
 from . import oracle as orc
 
 
-def eligible_mask(o, q0, tol, max_iters, lam, max_step=0.0, rel=1e-6, thr=1e-5, reps=2, seed=0):
+def eligible_mask(o, q0, tol, max_iters, lam, max_step=0.0, rel=1e-6, thr=1e-5, reps=2, seed=0, cyclic=False):
     """(mask, oracle result): mask[i] is True when `reps` random relative
     perturbations of size `rel` of start i move the oracle's result by <= thr
     and do not change its convergence flag."""
     rng = np.random.default_rng(seed)
-    base = o.project(q0, tol, max_iters, lam, max_step=max_step)
+    base = o.project(q0, tol, max_iters, lam, max_step=max_step, cyclic=cyclic)
     dev_max = np.zeros(q0.shape[1])
     for _ in range(reps):
         q1 = q0 * (1.0 + rel * rng.choice([-1.0, 1.0], size=q0.shape))
-        other = o.project(q1, tol, max_iters, lam, max_step=max_step)
+        other = o.project(q1, tol, max_iters, lam, max_step=max_step, cyclic=cyclic)
         dev_max = np.maximum(dev_max, np.abs(base[0] - other[0]).max(axis=0))
         dev_max[(base[1] & orc.CONVERGED) != (other[1] & orc.CONVERGED)] = np.inf
     return dev_max <= thr, base

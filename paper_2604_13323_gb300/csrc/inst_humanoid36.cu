@@ -10,7 +10,8 @@ cudaError_t launch_project<ProbHumanoid36>(const HostModel &hm, const ProjCall &
   if (c.precision == 1) {
     if (c.total <= 0) return cudaSuccess;
     if (c.segments) return cudaErrorNotSupported;
-    cudaError_t e = launch_plain64<ProbHumanoid36>(hm, c, BatchSrc<double>{static_cast<const double *>(c.q_in), c.ld_in});
+    cudaError_t e =
+        launch_plain64_any<ProbHumanoid36>(hm, c, BatchSrc<double>{static_cast<const double *>(c.q_in), c.ld_in});
     *launches += 1;
     return e;
   }

@@ -65,9 +65,10 @@ ClassDesc describe(bool project) {
 }
 
 const std::vector<ClassDesc> &registry() {
-  static const std::vector<ClassDesc> r = {describe<ProbSphere3>(true), describe<ProbArm7Axis>(true),
-                                           describe<ProbArm7Pose>(true), describe<ProbDual14Rel>(true),
-                                           describe<ProbHumanoid36>(true)};
+  static const std::vector<ClassDesc> r = {
+      describe<ProbSphere3>(true),   describe<ProbArm7Axis>(true),  describe<ProbArm7Pose>(true),
+      describe<ProbArm7Tray>(true),  describe<ProbArm7Peg>(true),   describe<ProbArm7Tsr>(true),
+      describe<ProbDual14Rel>(true), describe<ProbDual14Rod>(true), describe<ProbHumanoid36>(true)};
   return r;
 }
 
@@ -101,7 +102,7 @@ struct RobotHost {
 
 struct ConsHost {
   int kind, fa, fb;
-  double P[12], Q[12], target[3];
+  double P[12], Q[12], target[3], B[12];
   bool has_ref;
   std::vector<double> q_ref;
 };
@@ -194,10 +195,18 @@ __global__ void k_resolve(const __grid_constant__ ResolveIn in, ResolveOut *out)
         }
       }
       const int a = in.fa[c], b = in.fb[c];
-      if (in.kind[c] == K_POSE) {
+      if (in.kind[c] == K_POSE || in.kind[c] == K_PBND) {
         double Qi[12];
         tf_inv64(in.Q[c], Qi);
         tf_mul64(Tf[a], Qi, out->P[c]);
+      } else if (in.kind[c] == K_PLANE || in.kind[c] == K_LINE) {
+        // the plane / line keeps its orientation and passes through frame a
+        out->P[c][3] = Tf[a][3];
+        out->P[c][7] = Tf[a][7];
+        out->P[c][11] = Tf[a][11];
+      } else if (in.kind[c] == K_DIST) {
+        const double dx = Tf[b][3] - Tf[a][3], dy = Tf[b][7] - Tf[a][7], dz = Tf[b][11] - Tf[a][11];
+        out->tgt[c][0] = sqrt(dx * dx + dy * dy + dz * dz);
       } else if (in.kind[c] == K_REL) {
         double Ai[12];
         tf_inv64(Tf[a], Ai);
@@ -478,8 +487,8 @@ bool cons_match(const ClassDesc &d, const std::vector<ConsHost> &c) {
   if (d.NC != static_cast<int>(c.size())) return false;
   for (int i = 0; i < d.NC; ++i) {
     if (d.ckind[i] != c[i].kind) return false;
-    const bool uses_a = c[i].kind == K_AXIS || c[i].kind == K_POSE || c[i].kind == K_REL;
-    const bool uses_b = c[i].kind == K_REL;
+    const bool uses_a = c[i].kind != K_SPHERE && c[i].kind != K_COM;
+    const bool uses_b = c[i].kind == K_REL || c[i].kind == K_DIST;
     if (uses_a && d.cfa[i] != c[i].fa) return false;
     if (uses_b && d.cfb[i] != c[i].fb) return false;
   }
@@ -532,11 +541,13 @@ void fill_robot_model(const RobotHost &r, ModelT<T> &m) {
 }
 
 template <typename T>
-void fill_constraints(const ResolveOut &ro, int nc, int nj, ModelT<T> &m) {
+void fill_constraints(const ResolveOut &ro, const std::vector<ConsHost> &cons, int nj, ModelT<T> &m) {
+  const int nc = static_cast<int>(cons.size());
   for (int c = 0; c < nc; ++c) {
     for (int i = 0; i < 12; ++i) {
       m.cPinv[c][i] = static_cast<T>(ro.Pinv[c][i]);
       m.cQinv[c][i] = static_cast<T>(ro.Qinv[c][i]);
+      m.cB[c][i] = static_cast<T>(cons[c].B[i]);
     }
     for (int i = 0; i < 3; ++i) m.ctgt[c][i] = static_cast<T>(ro.tgt[c][i]);
   }
@@ -621,8 +632,8 @@ mcp_status ensure_resolved(mcp_ctx *ctx) {
   }
   fill_robot_model(r, ctx->hm.m32);
   fill_robot_model(r, ctx->hm.m64);
-  fill_constraints(ro, static_cast<int>(ctx->cons.size()), r.nj, ctx->hm.m32);
-  fill_constraints(ro, static_cast<int>(ctx->cons.size()), r.nj, ctx->hm.m64);
+  fill_constraints(ro, ctx->cons, r.nj, ctx->hm.m32);
+  fill_constraints(ro, ctx->cons, r.nj, ctx->hm.m64);
   fill_sphere_table(r, ctx->hm.st32);
   fill_sphere_table(r, ctx->hm.st64);
   {
@@ -781,10 +792,10 @@ mcp_status mcp_load_constraints(mcp_ctx *ctx, const mcp_constraint_desc *cd, int
   int k = 0;
   for (int i = 0; i < n; ++i) {
     const mcp_constraint_desc &c = cd[i];
-    if (c.kind < MCP_C_SPHERE || c.kind > MCP_C_COM_XY) return fail(ctx, MCP_ERR_ARG, "constraint %d: kind %d", i, c.kind);
-    const bool uses_a = c.kind == MCP_C_AXIS_ALIGN || c.kind == MCP_C_POSE || c.kind == MCP_C_REL_POSE ||
-                        (c.kind == MCP_C_COM_XY && c.q_ref);
-    const bool uses_b = c.kind == MCP_C_REL_POSE || (c.kind == MCP_C_COM_XY && c.q_ref);
+    if (c.kind < MCP_C_SPHERE || c.kind > MCP_C_POSE_BOUNDED)
+      return fail(ctx, MCP_ERR_ARG, "constraint %d: kind %d", i, c.kind);
+    const bool uses_a = c.kind != MCP_C_SPHERE && (c.kind != MCP_C_COM_XY || c.q_ref);
+    const bool uses_b = c.kind == MCP_C_REL_POSE || c.kind == MCP_C_DIST || (c.kind == MCP_C_COM_XY && c.q_ref);
     if (uses_a && (c.frame_a < 0 || c.frame_a >= ctx->robot.nf))
       return fail(ctx, MCP_ERR_ARG, "constraint %d: frame_a %d out of range", i, c.frame_a);
     if (uses_b && (c.frame_b < 0 || c.frame_b >= ctx->robot.nf))
@@ -796,6 +807,11 @@ mcp_status mcp_load_constraints(mcp_ctx *ctx, const mcp_constraint_desc *cd, int
     std::memcpy(h.P, c.P, sizeof(h.P));
     std::memcpy(h.Q, c.Q, sizeof(h.Q));
     std::memcpy(h.target, c.target, sizeof(h.target));
+    std::memcpy(h.B, c.B, sizeof(h.B));
+    if (c.kind == MCP_C_POSE_BOUNDED)
+      for (int r = 0; r < 6; ++r)
+        if (!(c.B[r] <= c.B[6 + r]))
+          return fail(ctx, MCP_ERR_ARG, "constraint %d: bound %d has lower > upper or NaN", i, r);
     h.has_ref = c.q_ref != nullptr;
     if (h.has_ref) h.q_ref.assign(c.q_ref, c.q_ref + ctx->robot.nj);
     k += cdim(c.kind);
@@ -868,6 +884,7 @@ static mcp_status validate_params(mcp_ctx *ctx, const mcp_project_params *p) {
   if (!(p->tol > 0.0) || !std::isfinite(p->tol)) return fail(ctx, MCP_ERR_ARG, "tol must be positive");
   if (p->max_iters < 0 || p->max_iters > 255) return fail(ctx, MCP_ERR_ARG, "max_iters %d outside [0, 255]", p->max_iters);
   if (p->precision != 0 && p->precision != 1) return fail(ctx, MCP_ERR_ARG, "precision %d", p->precision);
+  if (p->cyclic != 0 && p->cyclic != 1) return fail(ctx, MCP_ERR_ARG, "cyclic %d", p->cyclic);
   if (!(p->lambda >= 0.0) || !std::isfinite(p->lambda)) return fail(ctx, MCP_ERR_ARG, "lambda must be >= 0");
   if (!std::isfinite(p->max_step) || !std::isfinite(p->pivot_fp64)) return fail(ctx, MCP_ERR_ARG, "non-finite parameter");
   if (!ctx->robot_loaded || !ctx->cons_loaded) return fail(ctx, MCP_ERR_STATE, "robot and constraints must be loaded");
@@ -883,6 +900,7 @@ static void fill_call(mcp_ctx *ctx, const mcp_project_params *p, ProjCall &c, cu
   c.lambda = p->lambda;
   c.max_step = p->max_step;
   c.pivot = p->pivot_fp64;
+  c.cyclic = p->cyclic != 0;
   c.counter = ctx->d_counter;
   c.tune = ctx->tune;
   c.stream = s;

@@ -25,7 +25,13 @@ constexpr int MAXC = 8;
 constexpr int MAXK = 24;
 
 enum : int { REV = 0, PRIS = 1 };
-enum : int { K_SPHERE = 0, K_AXIS = 1, K_POSE = 2, K_REL = 3, K_COM = 4 };
+enum : int {
+  K_SPHERE = 0, K_AXIS = 1, K_POSE = 2, K_REL = 3, K_COM = 4,
+  K_PLANE = 5,  // origin of frame a on the xy-plane of the task frame P
+  K_LINE = 6,   // origin of frame a on the z-axis of the task frame P
+  K_DIST = 7,   // |x_b - x_a| = L (closed linkage)
+  K_PBND = 8    // bounded TSR: Eq. 1 error outside the bounds B^w
+};
 enum : uint32_t {
   FL_CONV = 1, FL_CAP = 2, FL_DIV = 4, FL_NONFINITE = 8, FL_RESOLVE = 16, FL_ACCEPT_FAIL = 32, FL_LIMITS = 64
 };
@@ -41,7 +47,8 @@ struct ModelT {
   T upper[MAXJ];
   T cPinv[MAXC][12];  // POSE: (T_w^0)^-1; REL_POSE: T_ref^-1
   T cQinv[MAXC][12];  // POSE: (T_e^w)^-1
-  T ctgt[MAXC][4];    // SPHERE radius; COM target xy
+  T ctgt[MAXC][4];    // SPHERE radius; COM target xy; DIST length
+  T cB[MAXC][12];     // PBND: lower[6], upper[6] of [t; log R]
   T msub[MAXJ];       // mass of the subtree below (and including) joint j
   T inv_mass;         // 1 / total mass
   T shift[3];         // collision frame: world coordinates minus this origin (root offsets are pre-shifted)
@@ -291,8 +298,30 @@ __host__ __device__ constexpr bool is_anc(int j, int link) {
   return false;
 }
 __host__ __device__ constexpr int cdim(int kind) {
-  return kind == K_SPHERE ? 1 : kind == K_AXIS ? 2 : kind == K_POSE ? 6 : kind == K_REL ? 6 : 2;
+  return (kind == K_SPHERE || kind == K_PLANE || kind == K_DIST)             ? 1
+         : (kind == K_POSE || kind == K_REL || kind == K_PBND)               ? 6
+                                                                             : 2;  // AXIS, COM, LINE
 }
+// Model slot of constraint c: a sub-problem (one constraint of a stack, used
+// by the cyclic form) reads the slot of the constraint it stands for.
+template <class P, class = void>
+struct CBase {
+  static constexpr int value = 0;
+};
+template <class P>
+struct CBase<P, std::void_t<decltype(P::CBASE)>> {
+  static constexpr int value = P::CBASE;
+};
+// Constraint C of the stack P alone (same robot, one constraint): the unit of
+// one step of the cyclic getDescentStep (Sec. IV-C).
+template <class P, int C>
+struct Sub : P {
+  static constexpr int NC = 1;
+  static constexpr int CBASE = C;
+  __host__ __device__ static constexpr int ckind(int) { return P::ckind(C); }
+  __host__ __device__ static constexpr int cfa(int) { return P::cfa(C); }
+  __host__ __device__ static constexpr int cfb(int) { return P::cfb(C); }
+};
 template <class P>
 __host__ __device__ constexpr int roff(int c) {
   int r = 0;
@@ -306,7 +335,7 @@ __host__ __device__ constexpr int kdim() {
 template <class P>
 __host__ __device__ constexpr bool needs_pos() {  // any constraint uses translations
   for (int c = 0; c < P::NC; ++c)
-    if (P::ckind(c) == K_POSE || P::ckind(c) == K_REL || P::ckind(c) == K_COM) return true;
+    if (P::ckind(c) != K_SPHERE && P::ckind(c) != K_AXIS) return true;
   return false;
 }
 template <class P>
@@ -326,7 +355,8 @@ template <class P>
 __host__ __device__ constexpr int col_sign(int c, int j) {
   const int k = P::ckind(c);
   if (k == K_SPHERE || k == K_COM) return 1;
-  if (k == K_REL) return (is_anc<P>(j, P::frame_link(P::cfb(c))) ? 1 : 0) - (is_anc<P>(j, P::frame_link(P::cfa(c))) ? 1 : 0);
+  if (k == K_REL || k == K_DIST)
+    return (is_anc<P>(j, P::frame_link(P::cfb(c))) ? 1 : 0) - (is_anc<P>(j, P::frame_link(P::cfa(c))) ? 1 : 0);
   return is_anc<P>(j, P::frame_link(P::cfa(c))) ? 1 : 0;
 }
 // Structural nonzero of J[row][j].
@@ -338,7 +368,7 @@ __host__ __device__ constexpr bool jnz(int row, int j) {
   const int s = col_sign<P>(c, j);
   if (s == 0) return false;
   if (k == K_AXIS) return P::jtype(j) == REV;
-  if ((k == K_POSE || k == K_REL) && rr >= 3) return P::jtype(j) == REV;
+  if ((k == K_POSE || k == K_REL || k == K_PBND) && rr >= 3) return P::jtype(j) == REV;
   return true;
 }
 

@@ -51,6 +51,7 @@ struct ProjCall {
   double lambda = 0.0;
   double max_step = 0.0;
   double pivot = 1e-7;
+  bool cyclic = false;  // cyclic getDescentStep (one step per constraint per sweep)
   bool segments = false;
   // batch source
   const void *q_in = nullptr;

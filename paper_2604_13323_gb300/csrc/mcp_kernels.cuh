@@ -28,11 +28,12 @@ constexpr uint32_t FL_INT_NEEDS_F64 = 1u << 9;  // FP32 pivot below threshold: c
 // ---------------------------------------------------------------------------
 template <class P, typename T>
 struct Eval {
-  V3<T> x[P::NC];    // POSE: world origin of T_a Q^-1; REL: p_b
+  V3<T> x[P::NC];    // POSE, PBND: world origin of T_a Q^-1; REL: p_b
   T G[P::NC][9];     // world -> error-frame rotation (POSE: P^-1_R; REL: P^-1_R R_a^T)
   V3<T> phi[P::NC];  // log of the error rotation
   T beta[P::NC];     // Jl^-1 coefficient
-  V3<T> za[P::NC];   // AXIS: frame z axis
+  V3<T> za[P::NC];   // AXIS: frame z axis; DIST: unit vector from x_a to x_b
+  bool act[P::NC][6];  // PBND: component outside its bounds
   T inv_norm;        // SPHERE: 1 / |q|
   V3<T> C[P::D];     // COM: mass-weighted CoM sum over the subtree of joint j
 };
@@ -44,6 +45,7 @@ __device__ __forceinline__ void residual(const ModelT<T> &m, const T (&q)[P::D],
     constexpr int c = decltype(CC)::value;
     constexpr int kind = P::ckind(c);
     constexpr int r0 = roff<P>(c);
+    constexpr int cm = c + CBase<P>::value;  // model slot
     if constexpr (kind == K_SPHERE) {
       // F = |q| - r (configuration space)
       T n2 = T(0);
@@ -51,7 +53,7 @@ __device__ __forceinline__ void residual(const ModelT<T> &m, const T (&q)[P::D],
       for (int j = 0; j < P::D; ++j) n2 = fma_(q[j], q[j], n2);
       T inv = Ops::rsqrt_(n2);
       e.inv_norm = inv;
-      F[r0] = n2 * inv - m.ctgt[c][0];
+      F[r0] = n2 * inv - m.ctgt[cm][0];
     } else if constexpr (kind == K_AXIS) {
       // frame z axis parallel to world z: F = (z.x, z.y)
       constexpr int a = P::cfa(c);
@@ -59,19 +61,19 @@ __device__ __forceinline__ void residual(const ModelT<T> &m, const T (&q)[P::D],
       e.za[c] = za;
       F[r0] = za.x;
       F[r0 + 1] = za.y;
-    } else if constexpr (kind == K_POSE || kind == K_REL) {
+    } else if constexpr (kind == K_POSE || kind == K_REL || kind == K_PBND) {
       T Pr[9];
-      load_R(m.cPinv[c], Pr);
-      const V3<T> Pp = load_p(m.cPinv[c]);
+      load_R(m.cPinv[cm], Pr);
+      const V3<T> Pp = load_p(m.cPinv[cm]);
       T Rerr[9];
       V3<T> t;
-      if constexpr (kind == K_POSE) {
+      if constexpr (kind == K_POSE || kind == K_PBND) {
         // Eq. 1: T_err = (T_w^0)^-1 T_a (T_e^w)^-1
         constexpr int a = P::cfa(c);
         T Qr[9], RaQ[9];
-        load_R(m.cQinv[c], Qr);
+        load_R(m.cQinv[cm], Qr);
         mul33(k.fR[a], Qr, RaQ);
-        const V3<T> x = add_rot_t<7>(k.fp[a], k.fR[a], load_p(m.cQinv[c]));
+        const V3<T> x = add_rot_t<7>(k.fp[a], k.fR[a], load_p(m.cQinv[cm]));
         mul33(Pr, RaQ, Rerr);
         const V3<T> tx = mulv(Pr, x);
         t = {tx.x + Pp.x, tx.y + Pp.y, tx.z + Pp.z};
@@ -110,6 +112,36 @@ __device__ __forceinline__ void residual(const ModelT<T> &m, const T (&q)[P::D],
       F[r0 + 3] = lg.phi.x;
       F[r0 + 4] = lg.phi.y;
       F[r0 + 5] = lg.phi.z;
+      if constexpr (kind == K_PBND) {
+        // Eq. 1 with bounds B^w: each component's distance outside [lo, hi];
+        // inside, the residual and its row of J are zero
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+          const T lo = m.cB[cm][i], hi = m.cB[cm][6 + i], v = F[r0 + i];
+          const bool below = v < lo, above = v > hi;
+          F[r0 + i] = below ? v - lo : (above ? v - hi : T(0));
+          if constexpr (WANT_J) e.act[c][i] = below || above;
+        }
+      }
+    } else if constexpr (kind == K_PLANE || kind == K_LINE) {
+      // origin of frame a in the task frame P: PLANE F = z, LINE F = (x, y)
+      constexpr int a = P::cfa(c);
+      const T *Pi = m.cPinv[cm];
+      const V3<T> x = k.fp[a];
+      if constexpr (kind == K_PLANE) {
+        F[r0] = fma_(Pi[8], x.x, fma_(Pi[9], x.y, fma_(Pi[10], x.z, Pi[11])));
+      } else {
+        F[r0] = fma_(Pi[0], x.x, fma_(Pi[1], x.y, fma_(Pi[2], x.z, Pi[3])));
+        F[r0 + 1] = fma_(Pi[4], x.x, fma_(Pi[5], x.y, fma_(Pi[6], x.z, Pi[7])));
+      }
+    } else if constexpr (kind == K_DIST) {
+      // closed linkage: F = |x_b - x_a| - L
+      constexpr int a = P::cfa(c), b = P::cfb(c);
+      const V3<T> dv = sub(k.fp[b], k.fp[a]);
+      const T n2 = fma_(dv.x, dv.x, fma_(dv.y, dv.y, dv.z * dv.z));
+      const T inv = Ops::rsqrt_(n2);
+      F[r0] = n2 * inv - m.ctgt[cm][0];
+      if constexpr (WANT_J) e.za[c] = V3<T>{dv.x * inv, dv.y * inv, dv.z * inv};
     } else if constexpr (kind == K_COM) {
       // Sec. V-C: x_com = sum_i m_i c_i / M with c_i = T_i com_i (the sum is
       // accumulated during FK).  With WANT_J the subtree sums C_j = m_j c_j +
@@ -126,8 +158,8 @@ __device__ __forceinline__ void residual(const ModelT<T> &m, const T (&q)[P::D],
           e.C[j] = acc;
         });
       }
-      F[r0] = fma_(k.mc.x, m.inv_mass, -m.ctgt[c][0]);
-      F[r0 + 1] = fma_(k.mc.y, m.inv_mass, -m.ctgt[c][1]);
+      F[r0] = fma_(k.mc.x, m.inv_mass, -m.ctgt[cm][0]);
+      F[r0 + 1] = fma_(k.mc.y, m.inv_mass, -m.ctgt[cm][1]);
     }
   });
 }
@@ -141,6 +173,7 @@ __device__ __forceinline__ void jacobian(const ModelT<T> &m, const T (&q)[P::D],
     constexpr int c = decltype(CC)::value;
     constexpr int kind = P::ckind(c);
     constexpr int r0 = roff<P>(c);
+    constexpr int cm = c + CBase<P>::value;
     static_for<P::D>([&](auto JJ) {
       constexpr int j = decltype(JJ)::value;
       constexpr int s = col_sign<P>(c, j);
@@ -154,20 +187,41 @@ __device__ __forceinline__ void jacobian(const ModelT<T> &m, const T (&q)[P::D],
             J[r0][j] = d.x;
             J[r0 + 1][j] = d.y;
           }
-        } else if constexpr (kind == K_POSE || kind == K_REL) {
+        } else if constexpr (kind == K_POSE || kind == K_REL || kind == K_PBND) {
           // translation rows: G (velocity of the error point); rotation rows: Jl^-1 G z_j.
           // REL: s = +1 for joints above b only, -1 above a only (Eq. 2, T_a^-1 T_b).
+          // PBND: rows of components inside their bounds are zero.
           const V3<T> v = rev ? cross(k.z[j], sub(e.x[c], k.p[j])) : k.z[j];
           const V3<T> vt = mulv(e.G[c], v);
-          J[r0][j] = s > 0 ? vt.x : -vt.x;
-          J[r0 + 1][j] = s > 0 ? vt.y : -vt.y;
-          J[r0 + 2][j] = s > 0 ? vt.z : -vt.z;
+          T row[6] = {s > 0 ? vt.x : -vt.x, s > 0 ? vt.y : -vt.y, s > 0 ? vt.z : -vt.z, T(0), T(0), T(0)};
           if constexpr (rev) {
             const V3<T> w = jl_inv_apply(e.phi[c], e.beta[c], mulv(e.G[c], k.z[j]));
-            J[r0 + 3][j] = s > 0 ? w.x : -w.x;
-            J[r0 + 4][j] = s > 0 ? w.y : -w.y;
-            J[r0 + 5][j] = s > 0 ? w.z : -w.z;
+            row[3] = s > 0 ? w.x : -w.x;
+            row[4] = s > 0 ? w.y : -w.y;
+            row[5] = s > 0 ? w.z : -w.z;
           }
+#pragma unroll
+          for (int i = 0; i < (rev ? 6 : 3); ++i) {
+            if constexpr (kind == K_PBND) J[r0 + i][j] = e.act[c][i] ? row[i] : T(0);
+            else J[r0 + i][j] = row[i];
+          }
+        } else if constexpr (kind == K_PLANE || kind == K_LINE) {
+          // rows of P^-1_R applied to the velocity of frame a's origin
+          constexpr int a = P::cfa(c);
+          const V3<T> v = rev ? cross(k.z[j], sub(k.fp[a], k.p[j])) : k.z[j];
+          const T *Pi = m.cPinv[cm];
+          if constexpr (kind == K_PLANE) {
+            J[r0][j] = fma_(Pi[8], v.x, fma_(Pi[9], v.y, Pi[10] * v.z));
+          } else {
+            J[r0][j] = fma_(Pi[0], v.x, fma_(Pi[1], v.y, Pi[2] * v.z));
+            J[r0 + 1][j] = fma_(Pi[4], v.x, fma_(Pi[5], v.y, Pi[6] * v.z));
+          }
+        } else if constexpr (kind == K_DIST) {
+          // u . (velocity of x_b) for joints above b only, -u . (velocity of x_a) above a only
+          constexpr int f = s > 0 ? P::cfb(c) : P::cfa(c);
+          const V3<T> v = rev ? cross(k.z[j], sub(k.fp[f], k.p[j])) : k.z[j];
+          const T d = fma_(e.za[c].x, v.x, fma_(e.za[c].y, v.y, e.za[c].z * v.z));
+          J[r0][j] = s > 0 ? d : -d;
         } else if constexpr (kind == K_COM) {
           // d x_com / d q_j = (1/M) z_j x (C_j - M_j o_j) (revolute), (M_j / M) z_j (prismatic)
           if constexpr (rev) {
@@ -380,6 +434,89 @@ __device__ __forceinline__ bool newton_iter_f32(const A &a, float (&q)[P::D], in
   return false;
 }
 
+// One FP32 LM step of the (sub-)problem S at q, applied in place: the unit of
+// the cyclic form.  Returns false (q untouched) if a Cholesky pivot falls below
+// the FP64 re-solve threshold.
+template <class S, class A>
+__device__ __forceinline__ bool substep_f32(const A &a, float (&q)[S::D]) {
+  constexpr int D = S::D, K = kdim<S>();
+  const OpsF32 ops{a.tab};
+  Kin<S, float> k;
+  if constexpr (needs_fk<S>()) fk<S, needs_pos<S>()>(ops, a.m, q, k);
+  float F[K];
+  Eval<S, float> e;
+  residual<S, OpsF32, float, true>(a.m, q, k, F, e);
+  float J[K][D];
+  jacobian<S>(a.m, q, k, e, J);
+  float Am[K * (K + 1) / 2], inv[K];
+  gram<S>(J, a.lambda, Am);
+  const float piv = cholesky_factor<K, OpsF32>(Am, inv);
+  if (!(piv >= a.pivot)) return false;
+  float y[K], dq[D];
+#pragma unroll
+  for (int i = 0; i < K; ++i) y[i] = F[i];
+  cholesky_subst<K>(Am, inv, y);
+  jt_mul<S>(J, y, dq);
+  refine_step<S>(J, F, a.lambda, Am, inv, y, dq);
+#pragma unroll
+  for (int j = 0; j < D; ++j) q[j] -= dq[j];
+  return true;
+}
+
+// One sweep of the cyclic getDescentStep (Sec. IV-C): the stopping test on the
+// stacked F, then one LM step per constraint in stack order, each at the
+// configuration the previous one produced.  MaxDistance applies to the whole
+// sweep; a pivot below the threshold hands the sweep, from its start, to FP64.
+template <class P, class A>
+__device__ __forceinline__ bool cyclic_iter_f32(const A &a, float (&q)[P::D], int &it, uint32_t &fl) {
+  constexpr int D = P::D, K = kdim<P>();
+  {
+    const OpsF32 ops{a.tab};
+    Kin<P, float> k;
+    if constexpr (needs_fk<P>()) fk<P, needs_pos<P>()>(ops, a.m, q, k);
+    float F[K];
+    Eval<P, float> e;
+    residual<P, OpsF32, float, false>(a.m, q, k, F, e);
+    float r2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < K; ++i) r2 = fmaf(F[i], F[i], r2);
+    if (!(r2 <= FLT_MAX)) {
+      fl |= FL_NONFINITE;
+      return true;
+    }
+    if (r2 < a.tol2) {
+      fl |= FL_INT_FP32CONV;
+      return true;
+    }
+    if (it >= a.cap) {
+      fl |= FL_CAP;
+      return true;
+    }
+  }
+  float q0[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) q0[j] = q[j];
+  bool ok = true;
+  static_for<P::NC>([&](auto CC) {
+    if (ok) ok = substep_f32<Sub<P, decltype(CC)::value>>(a, q);
+  });
+  float s2 = 0.f;
+#pragma unroll
+  for (int j = 0; j < D; ++j) s2 = fmaf(q[j] - q0[j], q[j] - q0[j], s2);
+  if (!ok || (a.max_step2 > 0.f && s2 > a.max_step2)) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) q[j] = q0[j];
+    fl |= ok ? FL_DIV : FL_INT_NEEDS_F64;
+    return true;
+  }
+  ++it;
+  if (!(s2 <= FLT_MAX)) {
+    fl |= FL_NONFINITE;
+    return true;
+  }
+  return false;
+}
+
 // ---------------------------------------------------------------------------
 // FP64 pieces used by the acceptance pass.
 // ---------------------------------------------------------------------------
@@ -549,7 +686,7 @@ __device__ __forceinline__ double sqrt_refined(double v) {
 // the FP32 Cholesky pivot fell below the threshold.  Rare, so it lives out of
 // line (its registers and local arrays stay off the FP32 loop).  Updates q,
 // qd, it, fl; returns the final squared FP64 residual.
-template <class P, class A>
+template <class P, bool CYC, class A>
 __device__ __noinline__ double finish_f64(const A &a, float *q, double *qd, int *it_io, uint32_t *fl_io, double r2,
                                           bool was_conv) {
   constexpr int D = P::D;
@@ -562,23 +699,63 @@ __device__ __noinline__ double finish_f64(const A &a, float *q, double *qd, int 
 #pragma unroll 1
   for (int j = 0; j < D; ++j) qq[j] = qd[j];
   while (!conv && it < a.cap) {
-    double dq[D];
     fl |= FL_RESOLVE;
-    if (!lm_step_f64<P>(ops, a.m64, qq, a.lambda64, dq)) {
-      fl |= FL_NONFINITE;
-      break;
-    }
-    double s2 = 0.0;
+    if constexpr (CYC) {
+      // one cyclic sweep in FP64 (each sub-step's result rounded to the FP32 output)
+      float q0[D];
 #pragma unroll 1
-    for (int j = 0; j < D; ++j) s2 = fma(dq[j], dq[j], s2);
-    if (a.max_step2 > 0.f && s2 > static_cast<double>(a.max_step2)) {
-      fl |= FL_DIV;
-      break;
-    }
+      for (int j = 0; j < D; ++j) q0[j] = q[j];
+      bool sing = false;
+      static_for<P::NC>([&](auto CC) {
+        if (sing) return;
+        double dq[D];
+        if (!lm_step_f64<Sub<P, decltype(CC)::value>>(ops, a.m64, qq, a.lambda64, dq)) {
+          sing = true;
+          return;
+        }
 #pragma unroll 1
-    for (int j = 0; j < D; ++j) {
-      q[j] = static_cast<float>(qq[j] - dq[j]);
-      qq[j] = static_cast<double>(q[j]);
+        for (int j = 0; j < D; ++j) {
+          q[j] = static_cast<float>(qq[j] - dq[j]);
+          qq[j] = static_cast<double>(q[j]);
+        }
+      });
+      if (sing) {
+        fl |= FL_NONFINITE;
+        break;
+      }
+      double s2 = 0.0;
+#pragma unroll 1
+      for (int j = 0; j < D; ++j) {
+        const double dj = qq[j] - static_cast<double>(q0[j]);
+        s2 = fma(dj, dj, s2);
+      }
+      if (a.max_step2 > 0.f && s2 > static_cast<double>(a.max_step2)) {
+#pragma unroll 1
+        for (int j = 0; j < D; ++j) {
+          q[j] = q0[j];
+          qq[j] = static_cast<double>(q0[j]);
+        }
+        fl |= FL_DIV;
+        break;
+      }
+    } else {
+      double dq[D];
+      if (!lm_step_f64<P>(ops, a.m64, qq, a.lambda64, dq)) {
+        fl |= FL_NONFINITE;
+        break;
+      }
+      double s2 = 0.0;
+#pragma unroll 1
+      for (int j = 0; j < D; ++j) s2 = fma(dq[j], dq[j], s2);
+      if (a.max_step2 > 0.f && s2 > static_cast<double>(a.max_step2)) {
+        fl |= FL_DIV;
+        break;
+      }
+#pragma unroll 1
+      for (int j = 0; j < D; ++j) {
+        q[j] = static_cast<float>(qq[j] - dq[j]);
+        qq[j] = static_cast<double>(q[j]);
+      }
     }
     ++it;
     r2 = residual2_f64<P>(ops, m, qq);
@@ -601,7 +778,7 @@ __device__ __noinline__ double finish_f64(const A &a, float *q, double *qd, int 
 // is re-checked with the FP64 residual; if the FP32 test was too optimistic,
 // or the FP32 pivot was too small, finish_f64 takes the remaining steps.
 // Writes q (if changed), flags, iters and resid.
-template <class P, class A>
+template <class P, bool CYC, class A>
 __device__ __forceinline__ void accept_one(const A &a, long long item, int it, uint32_t fl) {
   constexpr int D = P::D;
   const OpsF64Table ops{a.tab};
@@ -627,7 +804,7 @@ __device__ __forceinline__ void accept_one(const A &a, long long item, int it, u
         qf[j] = q[j];
         qdd[j] = qd[j];
       }
-      r2 = finish_f64<P>(a, qf, qdd, &it, &fl, r2, was_conv);
+      r2 = finish_f64<P, CYC>(a, qf, qdd, &it, &fl, r2, was_conv);
 #pragma unroll
       for (int j = 0; j < D; ++j) {
         a.q_out[j * a.ld_out + item] = qf[j];
@@ -658,14 +835,14 @@ __device__ __forceinline__ void accept_one(const A &a, long long item, int it, u
 // finishing path may spill; it is rare).  Sets the resident blocks per SM.
 template <class P>
 __host__ __device__ constexpr int reg_cap() {
-  return P::D <= 7 ? 128 : 168;
+  return (P::D <= 7 && kdim<P>() <= 2) ? 128 : 168;
 }
 template <class P, int TPB>
 __host__ __device__ constexpr int min_blocks() {
   return 65536 / (TPB * reg_cap<P>()) > 0 ? 65536 / (TPB * reg_cap<P>()) : 1;
 }
 
-template <class P, class Src, int TPB>
+template <class P, class Src, int TPB, bool CYC>
 __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(const __grid_constant__ ProjArgs<P, Src> a) {
   constexpr int D = P::D;
   constexpr int W = TPB / 32;
@@ -727,7 +904,10 @@ __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(con
     }
     // (2) one FP32 Newton iteration
     bool done = false;
-    if (act) done = newton_iter_f32<P>(a, q, it, fl);
+    if (act) {
+      if constexpr (CYC) done = cyclic_iter_f32<P>(a, q, it, fl);
+      else done = newton_iter_f32<P>(a, q, it, fl);
+    }
     // (3) park finished lanes
     const unsigned fin = __ballot_sync(FULL, done);
     if (fin != 0u) {
@@ -749,7 +929,7 @@ __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(con
       if (lane < take) {
         const int pos = pend - take + lane;
         const uint32_t meta = s_meta[wib][pos];
-        accept_one<P>(a, s_item[wib][pos], static_cast<int>(meta & 0xffu), meta >> 8);
+        accept_one<P, CYC>(a, s_item[wib][pos], static_cast<int>(meta & 0xffu), meta >> 8);
       }
       pend -= take;
       __syncwarp();
@@ -779,7 +959,28 @@ struct ProjArgs64 {
   double max_step2;
 };
 
-template <class P, class Src>
+// One plain FP64 LM step of the (sub-)problem S at q: dq = J^T (J J^T + lambda I)^-1 F.
+// Returns false if the system is singular.
+template <class S, class M>
+__device__ __forceinline__ bool step_f64(const M &m, const double (&q)[S::D], double lambda, double (&dq)[S::D]) {
+  constexpr int D = S::D, K = kdim<S>();
+  const OpsF64Plain ops{nullptr};
+  Kin<S, double> k;
+  if constexpr (needs_fk<S>()) fk<S, needs_pos<S>()>(ops, m, q, k);
+  double F[K];
+  Eval<S, double> e;
+  residual<S, OpsF64Plain, double, true>(m, q, k, F, e);
+  double J[K][D];
+  jacobian<S>(m, q, k, e, J);
+  double Am[K * (K + 1) / 2];
+  gram<S>(J, lambda, Am);
+  const double piv = cholesky_solve<K, OpsF64Plain>(Am, F);
+  if (!(piv > 0.0)) return false;
+  jt_mul<S>(J, F, dq);
+  return true;
+}
+
+template <class P, class Src, bool CYC>
 __global__ void __launch_bounds__(128) k_project_f64(const __grid_constant__ ProjArgs64<P, Src> a) {
   constexpr int D = P::D, K = kdim<P>();
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -795,7 +996,7 @@ __global__ void __launch_bounds__(128) k_project_f64(const __grid_constant__ Pro
     if constexpr (needs_fk<P>()) fk<P, needs_pos<P>()>(ops, a.m, q, k);
     double F[K];
     Eval<P, double> e;
-    residual<P, OpsF64Plain, double, true>(a.m, q, k, F, e);
+    residual<P, OpsF64Plain, double, !CYC>(a.m, q, k, F, e);
     r2 = 0.0;
 #pragma unroll
     for (int r = 0; r < K; ++r) r2 = fma(F[r], F[r], r2);
@@ -811,26 +1012,57 @@ __global__ void __launch_bounds__(128) k_project_f64(const __grid_constant__ Pro
       fl |= FL_CAP;
       break;
     }
-    double J[K][D];
-    jacobian<P>(a.m, q, k, e, J);
-    double Am[K * (K + 1) / 2];
-    gram<P>(J, a.lambda, Am);
-    const double piv = cholesky_solve<K, OpsF64Plain>(Am, F);
-    if (!(piv > 0.0)) {
-      fl |= FL_NONFINITE;
-      break;
-    }
-    double dq[D];
-    jt_mul<P>(J, F, dq);
-    double s2 = 0.0;
+    if constexpr (CYC) {
+      // cyclic getDescentStep (Sec. IV-C): one step per constraint, in order
+      double q0[D];
 #pragma unroll
-    for (int j = 0; j < D; ++j) s2 = fma(dq[j], dq[j], s2);
-    if (a.max_step2 > 0.0 && s2 > a.max_step2) {
-      fl |= FL_DIV;
-      break;
-    }
+      for (int j = 0; j < D; ++j) q0[j] = q[j];
+      bool sing = false;
+      static_for<P::NC>([&](auto CC) {
+        if (sing) return;
+        double dq[D];
+        if (!step_f64<Sub<P, decltype(CC)::value>>(a.m, q, a.lambda, dq)) {
+          sing = true;
+          return;
+        }
 #pragma unroll
-    for (int j = 0; j < D; ++j) q[j] -= dq[j];
+        for (int j = 0; j < D; ++j) q[j] -= dq[j];
+      });
+      if (sing) {
+        fl |= FL_NONFINITE;
+        break;
+      }
+      double s2 = 0.0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) s2 = fma(q[j] - q0[j], q[j] - q0[j], s2);
+      if (a.max_step2 > 0.0 && s2 > a.max_step2) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) q[j] = q0[j];
+        fl |= FL_DIV;
+        break;
+      }
+    } else {
+      double J[K][D];
+      jacobian<P>(a.m, q, k, e, J);
+      double Am[K * (K + 1) / 2];
+      gram<P>(J, a.lambda, Am);
+      const double piv = cholesky_solve<K, OpsF64Plain>(Am, F);
+      if (!(piv > 0.0)) {
+        fl |= FL_NONFINITE;
+        break;
+      }
+      double dq[D];
+      jt_mul<P>(J, F, dq);
+      double s2 = 0.0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) s2 = fma(dq[j], dq[j], s2);
+      if (a.max_step2 > 0.0 && s2 > a.max_step2) {
+        fl |= FL_DIV;
+        break;
+      }
+#pragma unroll
+      for (int j = 0; j < D; ++j) q[j] -= dq[j];
+    }
   }
 #pragma unroll
   for (int j = 0; j < D; ++j) {
@@ -1191,7 +1423,7 @@ __global__ void __launch_bounds__(128) k_vjp(const __grid_constant__ VjpArgs<P> 
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-template <class P, class Src, int TPB>
+template <class P, class Src, int TPB, bool CYC>
 cudaError_t launch_persistent(const HostModel &hm, const ProjCall &c, const Src &src) {
   ProjArgs<P, Src> a;
   a.m = hm.m32;
@@ -1218,11 +1450,11 @@ cudaError_t launch_persistent(const HostModel &hm, const ProjCall &c, const Src 
   const long long max_useful = (warps_needed + (TPB / 32) - 1) / (TPB / 32);
   if (blocks > max_useful) blocks = max_useful;
   if (blocks < 1) blocks = 1;
-  k_project_f32<P, Src, TPB><<<static_cast<unsigned>(blocks), TPB, 0, c.stream>>>(a);
+  k_project_f32<P, Src, TPB, CYC><<<static_cast<unsigned>(blocks), TPB, 0, c.stream>>>(a);
   return cudaGetLastError();
 }
 
-template <class P, class Src>
+template <class P, class Src, bool CYC = false>
 cudaError_t launch_plain64(const HostModel &hm, const ProjCall &c, const Src &src) {
   ProjArgs64<P, Src> a;
   a.m = hm.m64;
@@ -1238,8 +1470,17 @@ cudaError_t launch_plain64(const HostModel &hm, const ProjCall &c, const Src &sr
   a.lambda = c.lambda;
   a.max_step2 = c.max_step > 0 ? c.max_step * c.max_step : 0.0;
   const long long blocks = (c.total + 127) / 128;
-  k_project_f64<P, Src><<<static_cast<unsigned>(blocks), 128, 0, c.stream>>>(a);
+  k_project_f64<P, Src, CYC><<<static_cast<unsigned>(blocks), 128, 0, c.stream>>>(a);
   return cudaGetLastError();
+}
+
+// Plain FP64 launch, stacked or cyclic (one constraint: the two forms coincide).
+template <class P, class Src>
+cudaError_t launch_plain64_any(const HostModel &hm, const ProjCall &c, const Src &src) {
+  if constexpr (P::NC > 1) {
+    if (c.cyclic) return launch_plain64<P, Src, true>(hm, c, src);
+  }
+  return launch_plain64<P, Src, false>(hm, c, src);
 }
 
 template <class P>
@@ -1248,21 +1489,25 @@ cudaError_t launch_project_impl(const HostModel &hm, const ProjCall &c, int *lau
   cudaError_t err;
   if (c.precision == 1) {
     if (c.segments)
-      err = launch_plain64<P>(hm, c, SegSrc<double>{static_cast<const double *>(c.start),
-                                                    static_cast<const double *>(c.delta), c.ld_seg, c.seg_off,
-                                                    c.n_seg});
+      err = launch_plain64_any<P>(hm, c, SegSrc<double>{static_cast<const double *>(c.start),
+                                                        static_cast<const double *>(c.delta), c.ld_seg,
+                                                        c.seg_off, c.n_seg});
     else
-      err = launch_plain64<P>(hm, c, BatchSrc<double>{static_cast<const double *>(c.q_in), c.ld_in});
+      err = launch_plain64_any<P>(hm, c, BatchSrc<double>{static_cast<const double *>(c.q_in), c.ld_in});
     *launches += 1;
     return err;
   }
   err = cudaMemsetAsync(c.counter, 0, sizeof(unsigned long long), c.stream);
   if (err != cudaSuccess) return err;
   auto go = [&](auto src) -> cudaError_t {
+    using S = decltype(src);
+    if constexpr (P::NC > 1) {  // one constraint: the cyclic and stacked forms coincide
+      if (c.cyclic) return launch_persistent<P, S, 128, true>(hm, c, src);
+    }
     switch (c.tune.tpb) {
-      case 64: return launch_persistent<P, decltype(src), 64>(hm, c, src);
-      case 256: return launch_persistent<P, decltype(src), 256>(hm, c, src);
-      default: return launch_persistent<P, decltype(src), 128>(hm, c, src);
+      case 64: return launch_persistent<P, S, 64, false>(hm, c, src);
+      case 256: return launch_persistent<P, S, 256, false>(hm, c, src);
+      default: return launch_persistent<P, S, 128, false>(hm, c, src);
     }
   };
   if (c.segments)

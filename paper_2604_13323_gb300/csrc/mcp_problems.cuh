@@ -58,6 +58,23 @@ struct ProbArm7Pose : ProbArm7Axis {  // full 6-D end-effector TSR, Eq. 1 (k = 6
   __host__ __device__ static constexpr int ckind(int) { return K_POSE; }
 };
 
+// --- task constraints on the 7-DoF arm (Sec. III: a tool held level on a
+//     table, a peg inserted along a vertical line; Sec. II: a bounded TSR) ---
+struct ProbArm7Tray : ProbArm7Axis {  // EE on a plane + EE z vertical (k = 3, two constraints)
+  static constexpr const char *name = "arm7_tray";
+  static constexpr int NC = 2;
+  __host__ __device__ static constexpr int ckind(int c) { return c == 0 ? K_PLANE : K_AXIS; }
+};
+struct ProbArm7Peg : ProbArm7Axis {  // EE on a line + EE z vertical (k = 4, two constraints)
+  static constexpr const char *name = "arm7_peg";
+  static constexpr int NC = 2;
+  __host__ __device__ static constexpr int ckind(int c) { return c == 0 ? K_LINE : K_AXIS; }
+};
+struct ProbArm7Tsr : ProbArm7Axis {  // bounded TSR, Eq. 1 with B^w (k = 6)
+  static constexpr const char *name = "arm7_tsr";
+  __host__ __device__ static constexpr int ckind(int) { return K_PBND; }
+};
+
 // --- two copies of the 7-DoF chain, bases offset; relative EE pose (Eq. 2) ---
 struct ProbDual14Rel : ArmChain7 {
   static constexpr const char *name = "dual14_rel";
@@ -72,6 +89,16 @@ struct ProbDual14Rel : ArmChain7 {
   __host__ __device__ static constexpr int ckind(int) { return K_REL; }
   __host__ __device__ static constexpr int cfa(int) { return 0; }
   __host__ __device__ static constexpr int cfb(int) { return 1; }
+};
+
+// --- the dual arm carrying a rod on a table: fixed EE distance (closed
+//     linkage) and both EEs on a plane (k = 3, three constraints) ---
+struct ProbDual14Rod : ProbDual14Rel {
+  static constexpr const char *name = "dual14_rod";
+  static constexpr int NC = 3;
+  __host__ __device__ static constexpr int ckind(int c) { return c == 0 ? K_DIST : K_PLANE; }
+  __host__ __device__ static constexpr int cfa(int c) { return c == 2 ? 1 : 0; }
+  __host__ __device__ static constexpr int cfb(int c) { return c == 0 ? 1 : -1; }
 };
 
 // --- 36-DoF humanoid tree: base (3P + 3R), two 6-DoF legs, 2 + 2 torso/neck,

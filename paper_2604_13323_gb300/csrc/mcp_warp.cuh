@@ -76,6 +76,7 @@ struct __align__(16) WarpState {
   float C[D][4];    // subtree sums
   float q[D];
   float dq[D];
+  float q0[D];      // start of a cyclic sweep
   int anc[D];
   float G[P::NC][9];
   float x[P::NC][4];
@@ -125,9 +126,15 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Modes of warp_iter: one stacked iteration; only the stopping test on the
+// stacked F (the head of a cyclic sweep); or (MODE = c >= 0) the LM step of
+// constraint c alone, with the rows of the other constraints masked out of F
+// and J and given a unit diagonal, which decouples them exactly.
+constexpr int WI_STACKED = -2, WI_CHECK = -1;
+
 // One FP32 iteration on the warp's configuration.  Returns true when the
 // configuration leaves the FP32 loop (flags say why).
-template <class P, class A>
+template <class P, int MODE, class A>
 __device__ __forceinline__ bool warp_iter(const A &a, const WarpTables<P> &tb, WarpState<P> &S, int &it,
                                           uint32_t &fl) {
   constexpr int D = P::D, K = kdim<P>(), KP = WarpState<P>::KP;
@@ -276,9 +283,13 @@ __device__ __forceinline__ bool warp_iter(const A &a, const WarpTables<P> &tb, W
     constexpr int c = decltype(CC)::value;
     constexpr int kind = P::ckind(c);
     constexpr int r0 = roff<P>(c);
-    static_assert(kind != K_SPHERE, "configuration-space constraints use the thread kernels");
+    static_assert(kind == K_AXIS || kind == K_COM || kind == K_POSE || kind == K_REL,
+                  "the warp kernel implements the axis, CoM, pose and relative-pose constraints");
     if (lane == c) {
-      if constexpr (kind == K_AXIS) {
+      if constexpr (MODE >= 0 && c != MODE) {
+#pragma unroll
+        for (int r = 0; r < cdim(kind); ++r) S.F[r0 + r] = 0.f;
+      } else if constexpr (kind == K_AXIS) {
         constexpr int fa = P::cfa(c);
         S.za[c][0] = S.Tf[fa][2];
         S.za[c][1] = S.Tf[fa][6];
@@ -349,18 +360,21 @@ __device__ __forceinline__ bool warp_iter(const A &a, const WarpTables<P> &tb, W
   });
   __syncwarp();
   const float fv = lane < K ? S.F[lane] : 0.f;
-  const float r2 = warp_sum(fv * fv);
-  if (!(r2 <= FLT_MAX)) {
-    fl |= FL_NONFINITE;
-    return true;
-  }
-  if (r2 < a.tol2) {
-    fl |= FL_INT_FP32CONV;
-    return true;
-  }
-  if (it >= a.cap) {
-    fl |= FL_CAP;
-    return true;
+  if constexpr (MODE < 0) {
+    const float r2 = warp_sum(fv * fv);
+    if (!(r2 <= FLT_MAX)) {
+      fl |= FL_NONFINITE;
+      return true;
+    }
+    if (r2 < a.tol2) {
+      fl |= FL_INT_FP32CONV;
+      return true;
+    }
+    if (it >= a.cap) {
+      fl |= FL_CAP;
+      return true;
+    }
+    if constexpr (MODE == WI_CHECK) return false;
   }
   // 5. Jacobian columns, joint j on lane j
 #pragma unroll
@@ -375,7 +389,10 @@ __device__ __forceinline__ bool warp_iter(const A &a, const WarpTables<P> &tb, W
         constexpr int kind = P::ckind(c);
         constexpr int r0 = roff<P>(c);
         const float sg = tb.coef[c][j];
-        if constexpr (kind == K_AXIS) {
+        if constexpr (MODE >= 0 && c != MODE) {
+#pragma unroll
+          for (int r = 0; r < cdim(kind); ++r) S.J[j][r0 + r] = 0.f;
+        } else if constexpr (kind == K_AXIS) {
           const V3<float> d = cross(z, V3<float>{S.za[c][0], S.za[c][1], S.za[c][2]});
           S.J[j][r0] = rev ? sg * d.x : 0.f;
           S.J[j][r0 + 1] = rev ? sg * d.y : 0.f;
@@ -423,9 +440,14 @@ __device__ __forceinline__ bool warp_iter(const A &a, const WarpTables<P> &tb, W
       acc[4 * b4 + 3] = fmaf(ja, v.w, acc[4 * b4 + 3]);
     }
   }
+  float diag = a.lambda;
+  if constexpr (MODE >= 0) {  // masked rows: unit diagonal, zero right-hand side
+    constexpr int lo = roff<P>(MODE), hi = roff<P>(MODE) + cdim(P::ckind(MODE));
+    if (lane < lo || lane >= hi) diag = 1.f;
+  }
 #pragma unroll
   for (int b = 0; b < K; ++b)
-    if (b == lane) acc[b] += a.lambda;
+    if (b == lane) acc[b] += diag;
   // 7. Cholesky, row `lane` in registers; column k exchanged through shared memory
   float minpiv = FLT_MAX;
   float inv_diag = 0.f;
@@ -504,6 +526,15 @@ __device__ __forceinline__ bool warp_iter(const A &a, const WarpTables<P> &tb, W
   __syncwarp();
   yv += subst(rv);
   jt_y(yv);
+  if constexpr (MODE >= 0) {  // a sub-step of a sweep: the sweep does the rest
+#pragma unroll
+    for (int s = 0; s < SL; ++s) {
+      const int j = lane + 32 * s;
+      if (j < D) S.q[j] -= dq[s];
+    }
+    __syncwarp();
+    return false;
+  }
   float s2 = 0.f;
 #pragma unroll
   for (int s = 0; s < SL; ++s) s2 = fmaf(dq[s], dq[s], s2);
@@ -526,7 +557,52 @@ __device__ __forceinline__ bool warp_iter(const A &a, const WarpTables<P> &tb, W
   return false;
 }
 
-template <class P, int W>
+// One sweep of the cyclic form (Sec. IV-C) on the warp's configuration: the
+// stopping test on the stacked F, then one masked LM step per constraint.
+// MaxDistance applies to the sweep; a small pivot returns the configuration,
+// at the start of its sweep, to the FP64 path.
+template <class P, class A>
+__device__ __forceinline__ bool warp_sweep(const A &a, const WarpTables<P> &tb, WarpState<P> &S, int &it,
+                                           uint32_t &fl) {
+  constexpr int D = P::D, SL = (D + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  if (warp_iter<P, WI_CHECK>(a, tb, S, it, fl)) return true;
+#pragma unroll
+  for (int s = 0; s < SL; ++s) {
+    const int j = lane + 32 * s;
+    if (j < D) S.q0[j] = S.q[j];
+  }
+  __syncwarp();
+  bool left = false;
+  static_for<P::NC>([&](auto CC) {
+    if (!left) left = warp_iter<P, decltype(CC)::value>(a, tb, S, it, fl);
+  });
+  float s2 = 0.f;
+#pragma unroll
+  for (int s = 0; s < SL; ++s) {
+    const int j = lane + 32 * s;
+    if (j < D) s2 = fmaf(S.q[j] - S.q0[j], S.q[j] - S.q0[j], s2);
+  }
+  s2 = warp_sum(s2);
+  if (left || (a.max_step2 > 0.f && s2 > a.max_step2)) {
+#pragma unroll
+    for (int s = 0; s < SL; ++s) {
+      const int j = lane + 32 * s;
+      if (j < D) S.q[j] = S.q0[j];
+    }
+    __syncwarp();
+    if (!left) fl |= FL_DIV;
+    return true;
+  }
+  ++it;
+  if (!(s2 <= FLT_MAX)) {
+    fl |= FL_NONFINITE;
+    return true;
+  }
+  return false;
+}
+
+template <class P, int W, bool CYC>
 __global__ void __launch_bounds__(W * 32) k_project_warp(const __grid_constant__ WarpArgs<P> a) {
   constexpr int D = P::D;
   constexpr int SL = (D + 31) / 32;
@@ -570,7 +646,12 @@ __global__ void __launch_bounds__(W * 32) k_project_warp(const __grid_constant__
       __syncwarp();
       int it = 0;
       uint32_t fl = 0;
-      while (!warp_iter<P>(a, tb, S, it, fl)) {
+      if constexpr (CYC) {
+        while (!warp_sweep<P>(a, tb, S, it, fl)) {
+        }
+      } else {
+        while (!warp_iter<P, WI_STACKED>(a, tb, S, it, fl)) {
+        }
       }
 #pragma unroll
       for (int s = 0; s < SL; ++s) {
@@ -588,7 +669,7 @@ __global__ void __launch_bounds__(W * 32) k_project_warp(const __grid_constant__
     if (pend == 32 || (drained && pend > 0)) {
       if (lane < pend) {
         const uint32_t meta = s_meta[wib][lane];
-        accept_one<P>(a, s_item[wib][lane], static_cast<int>(meta & 0xffu), meta >> 8);
+        accept_one<P, CYC>(a, s_item[wib][lane], static_cast<int>(meta & 0xffu), meta >> 8);
       }
       pend = 0;
       __syncwarp();
@@ -647,15 +728,19 @@ cudaError_t launch_project_warp(const HostModel &hm, const ProjCall &c, int *lau
   a.pivot = static_cast<float>(c.pivot);
   a.tol2_64 = c.tol * c.tol;
   a.lambda64 = c.lambda;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_project_warp<P, W>, W * 32, 0);
-  if (per_sm < 1) per_sm = 1;
-  long long blocks = static_cast<long long>(hm.sm_count) * per_sm;
-  const long long need = (c.total + a.chunk * W - 1) / (a.chunk * W);
-  if (blocks > need) blocks = need;
-  k_project_warp<P, W><<<static_cast<unsigned>(blocks), W * 32, 0, c.stream>>>(a);
-  *launches += 1;
-  return cudaGetLastError();
+  auto go = [&](auto kern) -> cudaError_t {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W * 32, 0);
+    if (per_sm < 1) per_sm = 1;
+    long long blocks = static_cast<long long>(hm.sm_count) * per_sm;
+    const long long need = (c.total + a.chunk * W - 1) / (a.chunk * W);
+    if (blocks > need) blocks = need;
+    kern<<<static_cast<unsigned>(blocks), W * 32, 0, c.stream>>>(a);
+    *launches += 1;
+    return cudaGetLastError();
+  };
+  if (c.cyclic && P::NC > 1) return go(k_project_warp<P, W, true>);
+  return go(k_project_warp<P, W, false>);
 }
 
 }  // namespace mcp

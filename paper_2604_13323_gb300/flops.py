@@ -13,7 +13,9 @@ FP64 table-driven: 24 flops).
 Per configuration:
     fp32 = iters * iteration + (evaluation only, for the final residual test)
     fp64 = acceptance (FK + residual in FP64), once
-with `iters` the number of Newton steps the configuration took.
+with `iters` the number of Newton steps the configuration took.  In the
+cyclic form (Sec. IV-C) an iteration is one sweep: the stopping test on the
+stacked F plus one full step (FK, residual, Jacobian, solve) per constraint.
 """
 from __future__ import annotations
 
@@ -45,7 +47,7 @@ def _ancestors(parent, link):
 
 
 class FlopModel:
-    def __init__(self, robot, constraints):
+    def __init__(self, robot, constraints, cyclic: bool = False):
         self.rb = robot
         self.cons = list(constraints)
         self.d = robot.n_joints
@@ -69,9 +71,13 @@ class FlopModel:
             chol += (K - j - 1) * (2 * j + 1)    # column below the pivot
         chol += 2 * sum(2 * i + 1 for i in range(K))   # forward + back substitution
         jty = 2 * int(nz.sum())
+        # the refinement step of the FP32 kernels is not part of the method and is not counted
         self.iteration = self._fk32 + self._res_j + 2 * K + self._jac + gram + chol + jty + 3 * self.d
         self.evaluation = self._fk32 + self._res + 2 * K
         self.acceptance = self._fk64 + self._res + 2 * K
+        if cyclic and len(self.cons) > 1:
+            self.iteration = self.evaluation + 3 * self.d + sum(
+                FlopModel(robot, [c]).iteration for c in self.cons)
 
     def _fk(self, sincos):
         rb = self.rb
@@ -101,8 +107,16 @@ class FlopModel:
         for c in self.cons:
             if c.kind == W.C_SPHERE:
                 total += 2 * self.d + 2
-            elif c.kind == W.C_POSE:
+            elif c.kind in (W.C_POSE, W.C_POSE_BOUNDED):
                 total += 2 * MUL33 + 18 + MULV + 3 + LOG_MAP + (BETA if with_j else 0)
+                if c.kind == W.C_POSE_BOUNDED:
+                    total += 6          # one subtraction per component outside its bounds
+            elif c.kind == W.C_PLANE:
+                total += 6
+            elif c.kind == W.C_LINE:
+                total += 12
+            elif c.kind == W.C_DIST:
+                total += 3 + 5 + 1 + (3 if with_j else 0)
             elif c.kind == W.C_REL_POSE:
                 total += 2 * MUL33 + 3 + MULV + 3 + LOG_MAP + (BETA if with_j else 0)
             elif c.kind == W.C_COM_XY:
@@ -125,6 +139,16 @@ class FlopModel:
             elif c.kind == W.C_COM_XY:
                 nz[r0:r0 + 2, :] = True
                 total += sum(17 if rb.type[j] == W.REVOLUTE else 3 for j in range(D))
+            elif c.kind in (W.C_PLANE, W.C_LINE, W.C_DIST):
+                la = _ancestors(rb.parent, rb.frame_link[c.frame_a])
+                lb = _ancestors(rb.parent, rb.frame_link[c.frame_b]) if c.kind == W.C_DIST else set()
+                for j in range(D):
+                    s = (j in lb) - (j in la) if c.kind == W.C_DIST else (1 if j in la else 0)
+                    if s == 0:
+                        continue
+                    rev = rb.type[j] == W.REVOLUTE
+                    nz[r0:r0 + kd, j] = True
+                    total += (12 if rev else 0) + 5 * kd   # point velocity + one dot product per row
             else:
                 la = _ancestors(rb.parent, rb.frame_link[c.frame_a])
                 lb = _ancestors(rb.parent, rb.frame_link[c.frame_b]) if c.kind == W.C_REL_POSE else set()

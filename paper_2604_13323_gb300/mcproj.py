@@ -17,6 +17,10 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmcproj.so")
 
 MCP_OK, MCP_ERR_ARG, MCP_ERR_STATE, MCP_ERR_CUDA, MCP_ERR_OOM, MCP_ERR_UNSUPPORTED = range(6)
 F_CONVERGED, F_CAP, F_DIVERGED, F_NONFINITE, F_FP64_RESOLVE, F_ACCEPT_FAIL, F_OUT_OF_LIMITS = 1, 2, 4, 8, 16, 32, 64
+# constraint kinds (mcp_ckind) and their equation counts
+C_SPHERE, C_AXIS_ALIGN, C_POSE, C_REL_POSE, C_COM_XY, C_PLANE, C_LINE, C_DIST, C_POSE_BOUNDED = range(9)
+C_DIM = {C_SPHERE: 1, C_AXIS_ALIGN: 2, C_POSE: 6, C_REL_POSE: 6, C_COM_XY: 2, C_PLANE: 1, C_LINE: 2, C_DIST: 1,
+         C_POSE_BOUNDED: 6}
 PREC_FP32, PREC_FP64 = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -33,12 +37,13 @@ class RobotDesc(ctypes.Structure):
 class ConstraintDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("frame_a", ctypes.c_int32), ("frame_b", ctypes.c_int32),
                 ("P", ctypes.c_double * 12), ("Q", ctypes.c_double * 12), ("target", ctypes.c_double * 3),
-                ("q_ref", _dp)]
+                ("q_ref", _dp), ("B", ctypes.c_double * 12)]
 
 
 class ProjectParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iters", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("lam", ctypes.c_double), ("max_step", ctypes.c_double), ("pivot_fp64", ctypes.c_double)]
+                ("lam", ctypes.c_double), ("max_step", ctypes.c_double), ("pivot_fp64", ctypes.c_double),
+                ("cyclic", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -194,7 +199,10 @@ class Projector:
                 arr[i].target[t] = float(c.target[t])
             if getattr(c, "q_ref", None) is not None:
                 arr[i].q_ref = self._arr(c.q_ref, np.float64).ctypes.data_as(_dp)
-            k += {0: 1, 1: 2, 2: 6, 3: 6, 4: 2}[int(c.kind)]
+            B = getattr(c, "B", None)
+            for t in range(12):   # unbounded unless given
+                arr[i].B[t] = float(B[t]) if B is not None else (-np.inf if t < 6 else np.inf)
+            k += C_DIM[int(c.kind)]
         self._check(self.lib.mcp_load_constraints(self.h, arr, n))
         self.k = k
 
@@ -219,7 +227,8 @@ class Projector:
     @staticmethod
     def params(p) -> ProjectParams:
         return ProjectParams(tol=p.tol, max_iters=p.max_iters, precision=p.precision, lam=p.lam,
-                             max_step=p.max_step, pivot_fp64=p.pivot_fp64)
+                             max_step=p.max_step, pivot_fp64=p.pivot_fp64,
+                             cyclic=int(bool(getattr(p, "cyclic", False))), reserved=0)
 
     # ---- batched entry points (torch CUDA tensors) ----
     def project(self, q, params, out=None, flags=None, iters=None, resid=None, n=None, stream=None):
