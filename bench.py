@@ -416,7 +416,11 @@ def run_ours(args):
                            "obstacles": int(wl.obstacles.spheres.shape[0]), "robot_spheres": wl.robot.n_spheres,
                            "l2": "flushed between timed steps (512 MB write)",
                            "parallelism": f"replicas x{world}", "converged_per_step": conv,
-                           "kernel_ms": kernel_ms, "mean_iters": float(it_np.mean())},
+                           "kernel_ms": kernel_ms, "mean_iters": float(it_np.mean()),
+                           "flag_fractions": {k: float(((fl_np & b) != 0).mean()) for k, b in
+                                              (("cap", mcproj.F_CAP), ("fp64_resolve", mcproj.F_FP64_RESOLVE),
+                                               ("accept_fail", mcproj.F_ACCEPT_FAIL),
+                                               ("nonfinite", mcproj.F_NONFINITE))}},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     P.close()

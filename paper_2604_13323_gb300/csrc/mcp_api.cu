@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <mutex>
 #include <new>
 #include <string>
@@ -129,10 +130,14 @@ struct ResolveOut {
 // Setup kernels (FP64, run once per load)
 // ---------------------------------------------------------------------------
 __global__ void k_sincos_table(double2 *tab) {
-  const int k = threadIdx.x;
-  if (k < 256) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < 256) {  // (sin, cos)(2 pi k / 256)
     double s, c;
     sincospi(static_cast<double>(k) / 128.0, &s, &c);
+    tab[k] = make_double2(s, c);
+  } else if (k < SPLIT_TAB_OFF + 1025) {  // (sin, cos)(m / 64), m = -512..512
+    double s, c;
+    sincos(static_cast<double>(k - SPLIT_TAB_OFF - 512) / 64.0, &s, &c);
     tab[k] = make_double2(s, c);
   }
 }
@@ -526,6 +531,22 @@ void fill_sphere_table(const RobotHost &r, SphereTable<T> &st) {
   for (int l = r.nj + 2; l < MAXJ + 2; ++l) st.off[l] = static_cast<int16_t>(n);
 }
 
+// Joint limits in precision T rounded outwards-in: lower up, upper down.  For a
+// value q exactly representable in T, q < lower_T iff q < lower and
+// q > upper_T iff q > upper, so limit flags of FP32 iterates need no FP64.
+template <typename T>
+T bound_up(double v) {
+  T t = static_cast<T>(v);
+  if (static_cast<double>(t) < v) t = std::nextafter(t, std::numeric_limits<T>::infinity());
+  return t;
+}
+template <typename T>
+T bound_down(double v) {
+  T t = static_cast<T>(v);
+  if (static_cast<double>(t) > v) t = std::nextafter(t, -std::numeric_limits<T>::infinity());
+  return t;
+}
+
 template <typename T>
 void fill_robot_model(const RobotHost &r, ModelT<T> &m) {
   std::memset(&m, 0, sizeof(m));
@@ -533,8 +554,8 @@ void fill_robot_model(const RobotHost &r, ModelT<T> &m) {
     for (int i = 0; i < 12; ++i) m.X[j][i] = static_cast<T>(r.X[12 * j + i]);
     m.mass[j] = static_cast<T>(r.mass[j]);
     for (int i = 0; i < 3; ++i) m.com[j][i] = static_cast<T>(r.com[3 * j + i]);
-    m.lower[j] = static_cast<T>(r.lower[j]);
-    m.upper[j] = static_cast<T>(r.upper[j]);
+    m.lower[j] = bound_up<T>(r.lower[j]);
+    m.upper[j] = bound_down<T>(r.upper[j]);
   }
   for (int f = 0; f < r.nf; ++f)
     for (int i = 0; i < 12; ++i) m.fX[f][i] = static_cast<T>(r.frame_X[12 * f + i]);
@@ -686,11 +707,11 @@ mcp_status mcp_create(int device, mcp_ctx **out) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   ctx->hm.sm_count = sms;
   cudaError_t e = cudaMalloc(&ctx->d_m64, sizeof(ModelT<double>));
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tab, 256 * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tab, (SPLIT_TAB_OFF + 1025) * sizeof(double2));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counter, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) {
-    k_sincos_table<<<1, 256>>>(ctx->d_tab);
+    k_sincos_table<<<(SPLIT_TAB_OFF + 1025 + 255) / 256, 256>>>(ctx->d_tab);
     ctx->launches += 1;
     e = cudaGetLastError();
   }

@@ -557,9 +557,15 @@ __device__ __forceinline__ V3<double> xrot_apply(const double *X, V3<double> v) 
 // enters F, so one vector is carried from the frame to the root,
 //   z = X_0 Rz(q_0) ... X_l Rz(q_l) Xf e_z,
 // at 4 FP64 operations per revolute joint (plus its sin/cos) instead of a
-// full rotation product.
+// full rotation product.  A revolute root joint whose axis is world z (X_0
+// without rotation) turns z about world z, which leaves z.x^2 + z.y^2 = |F|^2
+// unchanged: its rotation is skipped.
 template <class P>
-__device__ __forceinline__ double axis_residual2_f64(const OpsF64Table &ops, const ModelT<double> &m,
+__host__ __device__ constexpr bool norm_invariant_root(int j) {
+  return P::parent(j) < 0 && P::jtype(j) == REV && P::xrot(j) == XR_IDENTITY;
+}
+template <class P, class Ops>
+__device__ __forceinline__ double axis_residual2_f64(const Ops &ops, const ModelT<double> &m,
                                                      const double (&q)[P::D]) {
   double r2 = 0.0;
   static_for<P::NC>([&](auto CC) {
@@ -569,7 +575,9 @@ __device__ __forceinline__ double axis_residual2_f64(const OpsF64Table &ops, con
     V3<double> v = xrot_apply<P::frot(f)>(m.fX[f], V3<double>{0.0, 0.0, 1.0});
     static_for<chain_len<P>(l)>([&](auto KK) {
       constexpr int j = chain_at<P>(l, decltype(KK)::value);
-      if constexpr (P::jtype(j) == REV) {
+      if constexpr (norm_invariant_root<P>(j)) {
+        return;
+      } else if constexpr (P::jtype(j) == REV) {
         double sn, cs;
         ops.sincos(q[j], sn, cs);
         v = {fma(cs, v.x, -(sn * v.y)), fma(sn, v.x, cs * v.y), v.z};
@@ -581,8 +589,8 @@ __device__ __forceinline__ double axis_residual2_f64(const OpsF64Table &ops, con
   return r2;
 }
 
-template <class P>
-__device__ __forceinline__ double residual2_f64(const OpsF64Table &ops, const ModelT<double> &m,
+template <class P, class Ops>
+__device__ __forceinline__ double residual2_f64(const Ops &ops, const ModelT<double> &m,
                                                 const double (&q)[P::D]) {
   if constexpr (axis_only<P>()) return axis_residual2_f64<P>(ops, m, q);
   constexpr int K = kdim<P>();
@@ -590,7 +598,7 @@ __device__ __forceinline__ double residual2_f64(const OpsF64Table &ops, const Mo
   if constexpr (needs_fk<P>()) fk<P, needs_pos<P>()>(ops, m, q, k);
   double F[K];
   Eval<P, double> e;
-  residual<P, OpsF64Table, double, false>(m, q, k, F, e);
+  residual<P, Ops, double, false>(m, q, k, F, e);
   double r2 = 0.0;
 #pragma unroll
   for (int i = 0; i < K; ++i) r2 = fma(F[i], F[i], r2);
@@ -758,7 +766,7 @@ __device__ __noinline__ double finish_f64(const A &a, float *q, double *qd, int 
       }
     }
     ++it;
-    r2 = residual2_f64<P>(ops, m, qq);
+    r2 = residual2_f64<P>(OpsF64Split{a.tab}, m, qq);  // qq holds FP32 values
     if (!(r2 <= DBL_MAX)) {
       fl |= FL_NONFINITE;
       break;
@@ -781,7 +789,6 @@ __device__ __noinline__ double finish_f64(const A &a, float *q, double *qd, int 
 template <class P, bool CYC, class A>
 __device__ __forceinline__ void accept_one(const A &a, long long item, int it, uint32_t fl) {
   constexpr int D = P::D;
-  const OpsF64Table ops{a.tab};
   const ModelT<double> &m = *a.m64;
   float q[D];
   double qd[D];
@@ -790,7 +797,7 @@ __device__ __forceinline__ void accept_one(const A &a, long long item, int it, u
     q[j] = a.q_out[j * a.ld_out + item];
     qd[j] = static_cast<double>(q[j]);
   }
-  double r2 = residual2_f64<P>(ops, m, qd);
+  double r2 = residual2_f64<P>(OpsF64Split{a.tab}, m, qd);
   if (fl & (FL_INT_FP32CONV | FL_INT_NEEDS_F64)) {
     const bool was_conv = (fl & FL_INT_FP32CONV) != 0;
     fl &= ~(FL_INT_FP32CONV | FL_INT_NEEDS_F64);
@@ -808,13 +815,16 @@ __device__ __forceinline__ void accept_one(const A &a, long long item, int it, u
 #pragma unroll
       for (int j = 0; j < D; ++j) {
         a.q_out[j * a.ld_out + item] = qf[j];
-        qd[j] = qdd[j];
+        q[j] = qf[j];
       }
     }
   }
+  // limits in FP32: the FP32 copies of the bounds are rounded outwards
+  // (lower up, upper down), so for an FP32 value q the FP32 comparison equals
+  // the comparison with the FP64 bound
 #pragma unroll
   for (int j = 0; j < D; ++j)
-    if (qd[j] < m.lower[j] || qd[j] > m.upper[j]) fl |= FL_LIMITS;
+    if (q[j] < a.m.lower[j] || q[j] > a.m.upper[j]) fl |= FL_LIMITS;
   a.flags[item] = static_cast<uint8_t>(fl & 0xffu);
   a.iters[item] = static_cast<uint8_t>(it > 255 ? 255 : it);
   a.resid[item] = sqrt_refined(r2);

@@ -337,10 +337,17 @@ def arm_task_workload(task: str, seed: int = 1007, n: int = 65536, n_obstacles: 
     * ``tsr``: a bounded TSR around the q_ref pose, +-5 cm in x and y,
       +-2 cm in z, +-0.1 rad about x and y, +-0.6 rad about z (6 equations).
 
-    Starts are q_ref + N(0, 0.3^2) (configurations near a task, as the
-    extension steps of a planner produce)."""
+    For tray and peg, q_ref has q_2 = q_4 = 0 and q_5 = -(q_1 + q_3): with the
+    chain's alternating +-pi/2 twists, joints 1, 3 and 5 then turn about one
+    common horizontal axis by a total of zero, so the end effector's z-axis
+    is vertical at q_ref and q_ref lies on the manifold.  Starts are
+    q_ref + N(0, 0.3^2) (configurations near a task, as the extension steps
+    of a planner produce)."""
     rng = np.random.default_rng(seed)
     q_ref = rng.uniform(-1.5, 1.5, 7)
+    if task in ("tray", "peg"):
+        q_ref[2] = q_ref[4] = 0.0
+        q_ref[5] = -(q_ref[1] + q_ref[3])
     base = arm_workload(n=1, n_obstacles=n_obstacles)
     brng = np.random.default_rng(seed + 10 if batch_seed is None else batch_seed)
     q = q_ref[:, None] + 0.3 * brng.standard_normal((7, n))

@@ -42,8 +42,11 @@ def workload(name):
     return W.arm_task_workload(name, n=4099)
 
 
-@pytest.mark.parametrize("cyclic", [False, True], ids=["stacked", "cyclic"])
-@pytest.mark.parametrize("name", ["tray", "peg", "tsr", "rod"])
+CASES = [("tray", False), ("peg", False), ("tsr", False), ("rod", False), ("tray", True), ("tsr", True),
+         ("rod", True)]
+
+
+@pytest.mark.parametrize("name,cyclic", CASES, ids=[f"{n}-{'cyclic' if c else 'stacked'}" for n, c in CASES])
 def test_task_fp32_parity(mcproj, name, cyclic):
     wl = workload(name)
     if cyclic:
