@@ -290,6 +290,11 @@ def run_ours(args):
         if ev:
             ev[2].record(stream)
 
+    # launch shape: the library's autotuner over threads per block, resident
+    # blocks per SM and claim size, on this batch (setup, untimed)
+    tuning = None
+    if not fp64 and seg_args is None and args.workload != "humanoid":
+        tuning = dict(zip(("tpb", "blocks_per_sm", "chunk"), P.autotune(q_in, wl.params)))
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     sampler = ClockSampler(local)
     with sampler:
@@ -416,7 +421,7 @@ def run_ours(args):
                            "obstacles": int(wl.obstacles.spheres.shape[0]), "robot_spheres": wl.robot.n_spheres,
                            "l2": "flushed between timed steps (512 MB write)",
                            "parallelism": f"replicas x{world}", "converged_per_step": conv,
-                           "kernel_ms": kernel_ms, "mean_iters": float(it_np.mean()),
+                           "kernel_ms": kernel_ms, "mean_iters": float(it_np.mean()), "launch": tuning,
                            "flag_fractions": {k: float(((fl_np & b) != 0).mean()) for k, b in
                                               (("cap", mcproj.F_CAP), ("fp64_resolve", mcproj.F_FP64_RESOLVE),
                                                ("accept_fail", mcproj.F_ACCEPT_FAIL),

@@ -14,10 +14,14 @@ import numpy as np
 from . import oracle as orc
 
 
-def eligible_mask(o, q0, tol, max_iters, lam, max_step=0.0, rel=1e-6, thr=1e-5, reps=2, seed=0, cyclic=False):
+def eligible_mask(o, q0, tol, max_iters, lam, max_step=0.0, rel=1e-6, thr=1e-5, reps=2, seed=0, cyclic=False,
+                  stable_iters=False):
     """(mask, oracle result): mask[i] is True when `reps` random relative
     perturbations of size `rel` of start i move the oracle's result by <= thr
-    and do not change its convergence flag."""
+    and do not change its convergence flag (nor, with `stable_iters`, its
+    number of iterations: active-set changes of bounded constraints and slow
+    alternating projections can move the step at which ||F|| < tol is first
+    met while the point barely moves)."""
     rng = np.random.default_rng(seed)
     base = o.project(q0, tol, max_iters, lam, max_step=max_step, cyclic=cyclic)
     dev_max = np.zeros(q0.shape[1])
@@ -26,4 +30,6 @@ def eligible_mask(o, q0, tol, max_iters, lam, max_step=0.0, rel=1e-6, thr=1e-5, 
         other = o.project(q1, tol, max_iters, lam, max_step=max_step, cyclic=cyclic)
         dev_max = np.maximum(dev_max, np.abs(base[0] - other[0]).max(axis=0))
         dev_max[(base[1] & orc.CONVERGED) != (other[1] & orc.CONVERGED)] = np.inf
+        if stable_iters:
+            dev_max[base[2] != other[2]] = np.inf
     return dev_max <= thr, base

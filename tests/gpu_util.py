@@ -19,25 +19,33 @@ def f32_exact(q):
     return np.asarray(q, dtype=np.float32).astype(np.float64)
 
 
-def eligible_mask(oracle, q0, params, rel=1e-6, thr=1e-5, reps=2, seed=0):
+def eligible_mask(oracle, q0, params, rel=1e-6, thr=1e-5, reps=2, seed=0, stable_iters=False):
     """Configurations whose projection is a well-defined function of the start
     (see oracle/parity.py).  Returns (mask, oracle result)."""
     return parity.eligible_mask(oracle, q0, params.tol, params.max_iters, params.lam, max_step=params.max_step,
-                                rel=rel, thr=thr, reps=reps, seed=seed, cyclic=bool(getattr(params, "cyclic", False)))
+                                rel=rel, thr=thr, reps=reps, seed=seed, cyclic=bool(getattr(params, "cyclic", False)),
+                                stable_iters=stable_iters)
 
 
 def compare_projection(gpu, ora, tol, q_tol=Q_TOL, flag_agree=FLAG_AGREE, oracle=None, sample_resid=256,
-                       eligible=None, min_eligible=0.0):
+                       eligible=None, min_eligible=0.0, stable_only=False, overall_flag_agree=0.99):
     """gpu / ora: (q [d, n], flags, iters, resid) as numpy.  Flags are compared
     on every configuration, points on the eligible ones (all if None), and
     every converged GPU output must be a valid point of the manifold (FP64
-    residual recomputed by the oracle below tol).  Returns a stats dict."""
+    residual recomputed by the oracle below tol).  With `stable_only`, the
+    flag bar and the iteration-count comparison apply to the eligible
+    configurations (where the oracle's own flag and count survive a
+    perturbation of the start), and all configurations must still agree on
+    `overall_flag_agree` of the flags.  Returns a stats dict."""
     qg, fg, ig, rg = gpu
     qo, fo, io, ro = ora
     cg = (fg & orc.CONVERGED) != 0
     co = (fo & orc.CONVERGED) != 0
-    agree = float((cg == co).mean())
     el = np.ones(cg.shape, bool) if eligible is None else eligible
+    overall = float((cg == co).mean())
+    agree = float((cg == co)[el].mean()) if stable_only and el.any() else overall
+    if stable_only:
+        assert overall >= overall_flag_agree, overall
     # Same number of steps: the same sequence of Newton iterates, compared at
     # q_tol.  Steps differing by one: the ||F|| < tol decision was taken on
     # either side of the boundary in different precisions; the points then
@@ -57,7 +65,8 @@ def compare_projection(gpu, ora, tol, q_tol=Q_TOL, flag_agree=FLAG_AGREE, oracle
              "q_err_max": float(err.max()) if err.size else 0.0,
              "q_err_p999": float(np.quantile(err, 0.999)) if err.size else 0.0,
              "resid_max": float(rg[cg].max()) if cg.any() else 0.0,
-             "iters_equal": float(same_it[cg & co].mean()) if (cg & co).any() else 1.0,
+             "iters_equal": float(same_it[cg & co & (el if stable_only else True)].mean()) if (cg & co).any() else 1.0,
+             "flag_agree_all": overall,
              "off_by_one": int(off_by_one.sum()),
              "eligible": float(el.mean())}
     assert stats["eligible"] >= min_eligible, stats
