@@ -15,21 +15,30 @@ from . import oracle as orc
 
 
 def eligible_mask(o, q0, tol, max_iters, lam, max_step=0.0, rel=1e-6, thr=1e-5, reps=2, seed=0, cyclic=False,
-                  stable_iters=False):
+                  stable_iters=False, stats=None):
     """(mask, oracle result): mask[i] is True when `reps` random relative
     perturbations of size `rel` of start i move the oracle's result by <= thr
     and do not change its convergence flag (nor, with `stable_iters`, its
     number of iterations: active-set changes of bounded constraints and slow
     alternating projections can move the step at which ||F|| < tol is first
-    met while the point barely moves)."""
+    met while the point barely moves).  `stats` (a dict), if given, receives
+    how often the oracle disagrees with itself under those perturbations:
+    the fraction of flipped convergence flags and of changed step counts,
+    the scale of any other implementation's disagreement on the workload."""
     rng = np.random.default_rng(seed)
     base = o.project(q0, tol, max_iters, lam, max_step=max_step, cyclic=cyclic)
     dev_max = np.zeros(q0.shape[1])
+    flips = np.zeros(q0.shape[1], bool)
+    recount = np.zeros(q0.shape[1], bool)
     for _ in range(reps):
         q1 = q0 * (1.0 + rel * rng.choice([-1.0, 1.0], size=q0.shape))
         other = o.project(q1, tol, max_iters, lam, max_step=max_step, cyclic=cyclic)
         dev_max = np.maximum(dev_max, np.abs(base[0] - other[0]).max(axis=0))
-        dev_max[(base[1] & orc.CONVERGED) != (other[1] & orc.CONVERGED)] = np.inf
-        if stable_iters:
-            dev_max[base[2] != other[2]] = np.inf
+        flips |= (base[1] & orc.CONVERGED) != (other[1] & orc.CONVERGED)
+        recount |= base[2] != other[2]
+    dev_max[flips] = np.inf
+    if stable_iters:
+        dev_max[recount] = np.inf
+    if stats is not None:
+        stats.update(self_flip_rate=float(flips.mean()), self_recount_rate=float(recount.mean()))
     return dev_max <= thr, base

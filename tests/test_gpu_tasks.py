@@ -42,6 +42,14 @@ def run(P, q0, params, dtype=torch.float32, ld=None):
             r[:n].cpu().numpy())
 
 
+def self_consistent_bars(selfst):
+    """Overall flag agreement and step-count mismatch allowed on all starts:
+    twice what the FP64 oracle shows against itself under the perturbation,
+    and never looser than 99 % / 0.1 % where the oracle is self-consistent."""
+    return {"overall_flag_agree": 1.0 - max(0.01, 2.0 * selfst["self_flip_rate"]),
+            "max_recount": max(0.001, 2.0 * selfst["self_recount_rate"])}
+
+
 def workload(name):
     if name == "rod":
         return W.dual_rod_workload(n=4099)
@@ -65,9 +73,10 @@ def test_task_fp32_parity(mcproj, name, cyclic):
         np.testing.assert_allclose(P.constraint(i)[0], O.constraint_values(i)[0], atol=1e-14)
         np.testing.assert_allclose(P.constraint(i)[2], O.constraint_values(i)[2], atol=1e-14)
     gpu = run(P, q0, wl.params, ld=4128)
-    el, ora = eligible_mask(O, q0, wl.params, stable_iters=True)
+    selfst = {}
+    el, ora = eligible_mask(O, q0, wl.params, stable_iters=True, stats=selfst)
     st = compare_projection(gpu, ora, wl.params.tol, oracle=O, eligible=el, min_eligible=0.5, sample_resid=512,
-                            stable_only=True)
+                            stable_only=True, **self_consistent_bars(selfst))
     assert st["conv_oracle"] > 0.5, st
     if not cyclic:
         hit = P.check(torch.tensor(gpu[0], dtype=torch.float32, device="cuda")).cpu().numpy()
@@ -85,9 +94,10 @@ def test_task_fp64_plain_parity(mcproj, name, cyclic):
     O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
     P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
     gpu = run(P, wl.q, wl.params, dtype=torch.float64)
-    el, ora = eligible_mask(O, wl.q, wl.params, rel=1e-12, thr=1e-9, stable_iters=True)
+    selfst = {}
+    el, ora = eligible_mask(O, wl.q, wl.params, rel=1e-12, thr=1e-9, stable_iters=True, stats=selfst)
     st = compare_projection(gpu, ora, wl.params.tol, q_tol=1e-6, oracle=O, eligible=el, min_eligible=0.7,
-                            stable_only=True)
+                            stable_only=True, **self_consistent_bars(selfst))
     assert st["iters_equal"] > 0.999, st
 
 
