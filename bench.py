@@ -276,12 +276,21 @@ def run_ours(args):
     hit = torch.empty(n, dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def step(ev=None):
+    fused = seg_args is None   # a plain batch: projection and check in one call
+
+    def step(ev=None, separate=False):
         if ev:
             ev[0].record(stream)
         if seg_args is not None:
             P.project_segments(*seg_args, wl.params, total=n, out=q_out, flags=flags, iters=iters, resid=resid,
                                stream=stream)
+        elif fused and not separate:
+            P.project_check(q_in, wl.params, out=q_out, flags=flags, iters=iters, resid=resid, hit=hit,
+                            stream=stream)
+            if ev:
+                ev[1].record(stream)
+                ev[2].record(stream)
+            return
         else:
             P.project(q_in, wl.params, out=q_out, flags=flags, iters=iters, resid=resid, stream=stream)
         if ev:
@@ -318,6 +327,16 @@ def run_ours(args):
             step(evs[s])
         torch.cuda.synchronize()
     launches = P.launches - launches0
+    # the same step as two calls (projection, then check), for comparison only
+    sep_ms = None
+    if fused and not args.profile:
+        sev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        for s_ in range(args.steps):
+            flush.zero_()
+            step(sev[s_], separate=True)
+        torch.cuda.synchronize()
+        sep_ms = {"project": sum(e[0].elapsed_time(e[1]) for e in sev) / args.steps,
+                  "check": sum(e[1].elapsed_time(e[2]) for e in sev) / args.steps}
     if world > 1:
         dist.barrier()
     pairs = torch.zeros(n, dtype=torch.int32, device=dev)
@@ -374,37 +393,59 @@ def run_ours(args):
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak32 = sms * 128 * 2 * sm_max * 1e6 / 1e12        # FP32 FMA lanes x 2 flops x max clock
     peak64 = 1.25                                         # nominal dense FP64, TFLOP/s
-    mp = sum(t_proj) / len(t_proj)
-    mc = sum(t_check) / len(t_check)
+    # one fused kernel: FP32 batch problems of the thread-per-configuration kernels
+    one_kernel = fused and not fp64 and args.workload != "humanoid"
+    if fused and not one_kernel and sep_ms is not None:   # two launches: per-kernel times from the separate calls
+        mp, mc = sep_ms["project"], sep_ms["check"]
+    else:
+        mp = sum(t_proj) / len(t_proj)
+        mc = sum(t_check) / len(t_check)
     # collision: FK with translations + 8 flops (4 FMA) per overlap test performed (broad and
     # narrow phase); sphere transforms are not counted (conservative)
     check_flops = n * fm.fk_positions() + 8.0 * pairs_total
-    check_roof = {"kernel": "k_check_f32", "achieved": check_flops / (mc * 1e-3) / 1e12,
-                  "pairs_per_config": pairs_total / n}
-    if fp64:
-        flops_proj = fp32 + fp64f   # the plain kernel does all of it in FP64
-        ach = flops_proj / (mp * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": peak64, "unit": "TFLOP/s", "frac": ach / peak64,
-                "traffic": None, "kernel": "k_project_f64 (plain FP64)", "peak_source": "nominal FP64"}
-    else:
-        ach32 = fp32 / (mp * 1e-3) / 1e12
-        ach64 = fp64f / (mp * 1e-3) / 1e12
-        # both pipes: the time the FP32 and FP64 work need at their peaks bounds the kernel
-        t_min = max(fp32 / (peak32 * 1e12), fp64f / (peak64 * 1e12))
+    check_roof = {"kernel": "k_check_f32", "pairs_per_config": pairs_total / n}
+    peak_src = "152 SMs x 128 FP32 lanes x 2 x max SM clock"
+    if one_kernel:
+        t = mp * 1e-3
+        ach32 = (fp32 + check_flops) / t / 1e12
+        ach64 = fp64f / t / 1e12
+        t_min = max((fp32 + check_flops) / (peak32 * 1e12), fp64f / (peak64 * 1e12))
         roof = {"bound": "alu", "achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
-                "traffic": None, "kernel": "k_project_f32 (persistent, FP32 steps + FP64 acceptance)",
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
-                "fp64_achieved": ach64, "fp64_peak": peak64, "fp64_frac": ach64 / peak64,
-                "mixed_bound_frac": t_min / (mp * 1e-3),
-                "flops_per_config": {"fp32": fp32 / n, "fp64": fp64f / n}}
-    kernel_ms = {"project": mp, "check": mc}
-    roof["check"] = check_roof
-    roof["check"]["frac"] = check_roof["achieved"] / peak32
-    if mc > mp and not fp64:   # the dominant kernel carries the headline roofline
-        roof = {"bound": "alu", "achieved": check_roof["achieved"], "peak": peak32, "unit": "TFLOP/s",
-                "frac": check_roof["achieved"] / peak32, "traffic": None,
-                "kernel": "k_check_f32 (collision, 8 flops per overlap test, broad + narrow phase)",
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock", "projection": roof}
+                "traffic": None,
+                "kernel": "k_project_f32<CHK> (persistent: FP32 steps, FP64 acceptance, fused collision check)",
+                "peak_source": peak_src, "fp64_achieved": ach64, "fp64_peak": peak64, "fp64_frac": ach64 / peak64,
+                "mixed_bound_frac": t_min / t,
+                "flops_per_config": {"fp32_projection": fp32 / n, "fp32_check": check_flops / n, "fp64": fp64f / n},
+                "check": check_roof}
+        kernel_ms = {"project_check": mp}
+    else:
+        check_roof["achieved"] = check_flops / (mc * 1e-3) / 1e12
+        check_roof["frac"] = check_roof["achieved"] / peak32
+        if fp64:
+            flops_proj = fp32 + fp64f   # the plain kernel does all of it in FP64
+            ach = flops_proj / (mp * 1e-3) / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": peak64, "unit": "TFLOP/s", "frac": ach / peak64,
+                    "traffic": None, "kernel": "k_project_f64 (plain FP64)", "peak_source": "nominal FP64"}
+        else:
+            ach32 = fp32 / (mp * 1e-3) / 1e12
+            ach64 = fp64f / (mp * 1e-3) / 1e12
+            # both pipes: the time the FP32 and FP64 work need at their peaks bounds the kernel
+            t_min = max(fp32 / (peak32 * 1e12), fp64f / (peak64 * 1e12))
+            roof = {"bound": "alu", "achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
+                    "traffic": None, "kernel": "k_project_f32 (persistent, FP32 steps + FP64 acceptance)",
+                    "peak_source": peak_src,
+                    "fp64_achieved": ach64, "fp64_peak": peak64, "fp64_frac": ach64 / peak64,
+                    "mixed_bound_frac": t_min / (mp * 1e-3),
+                    "flops_per_config": {"fp32": fp32 / n, "fp64": fp64f / n}}
+        kernel_ms = {"project": mp, "check": mc}
+        roof["check"] = check_roof
+        if mc > mp and not fp64:   # the dominant kernel carries the headline roofline
+            roof = {"bound": "alu", "achieved": check_roof["achieved"], "peak": peak32, "unit": "TFLOP/s",
+                    "frac": check_roof["achieved"] / peak32, "traffic": None,
+                    "kernel": "k_check_f32 (collision, 8 flops per overlap test, broad + narrow phase)",
+                    "peak_source": peak_src, "projection": roof}
+    if sep_ms is not None:
+        kernel_ms["separate_calls"] = sep_ms
 
     cpu = None
     if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.profile):

@@ -176,6 +176,21 @@ mcp_status mcp_get_constraint(const mcp_ctx *ctx, int32_t i, double *P, double *
 mcp_status mcp_project_batch(mcp_ctx *ctx, const mcp_project_params *p, int64_t n, int64_t ld, const void *q_in,
                              void *q_out, uint8_t *flags, uint8_t *iters, double *resid, mcp_stream stream);
 
+/* Projection followed by the collision check of every returned configuration
+ * (Alg. 2: ParallelProject, then CollisionFree of each projected point), with
+ * the results of mcp_project_batch and then mcp_check_batch(q_out, precision
+ * p->precision).  For FP32 problems of the thread-per-configuration kernels the
+ * two run in one persistent launch: the check of each accepted output follows
+ * its FP64 acceptance in the same warp, so the ALU-bound check overlaps the
+ * FP64 acceptance of other warps; other paths launch the check after the
+ * projection.  Requires loaded obstacles.  in_collision [n] uint8 (DEVICE);
+ * pairs_tested [n] uint32 (DEVICE) or NULL: sphere-obstacle tests performed
+ * per configuration.  Errors as mcp_project_batch, plus MCP_ERR_STATE without
+ * obstacles. */
+mcp_status mcp_project_check_batch(mcp_ctx *ctx, const mcp_project_params *p, int64_t n, int64_t ld,
+                                   const void *q_in, void *q_out, uint8_t *flags, uint8_t *iters, double *resid,
+                                   uint8_t *in_collision, uint32_t *pairs_tested, mcp_stream stream);
+
 /* Projection of uneven interpolation segments in one persistent launch
  * (Alg. 2: n points interpolated between q_s and q_proj are projected in
  * parallel).  Point t of segment s is start[:, s] + t * delta[:, s],

@@ -13,9 +13,12 @@ cudaError_t launch_project<ProbHumanoid36>(const HostModel &hm, const ProjCall &
     cudaError_t e =
         launch_plain64_any<ProbHumanoid36>(hm, c, BatchSrc<double>{static_cast<const double *>(c.q_in), c.ld_in});
     *launches += 1;
+    if (e == cudaSuccess && c.fused_check) e = check_outputs<ProbHumanoid36>(hm, c, launches);
     return e;
   }
-  return launch_project_warp<ProbHumanoid36>(hm, c, launches);
+  cudaError_t e = launch_project_warp<ProbHumanoid36>(hm, c, launches);
+  if (e == cudaSuccess && c.fused_check) e = check_outputs<ProbHumanoid36>(hm, c, launches);
+  return e;
 }
 
 template <>

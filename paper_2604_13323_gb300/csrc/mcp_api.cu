@@ -410,6 +410,7 @@ struct mcp_ctx {
   int robot_class = -1;  // class whose robot part matches (collision check)
   int prob_class = -1;   // class whose robot and constraints match (projection, VJP)
   ModelT<double> *d_m64 = nullptr;
+  CheckData *d_chk = nullptr;
   double2 *d_tab = nullptr;
   float4 *d_obs32 = nullptr;
   double *d_obs64 = nullptr;
@@ -576,8 +577,9 @@ void fill_constraints(const ResolveOut &ro, const std::vector<ConsHost> &cons, i
   m.inv_mass = static_cast<T>(ro.inv_mass);
 }
 
-// The collision-frame copy of the FP32 model: root offsets minus the obstacle origin.
-void update_shifted(mcp_ctx *ctx) {
+// The collision-frame copy of the FP32 model: root offsets minus the obstacle
+// origin; also uploaded (with the sphere table) for the fused check.
+mcp_status update_shifted(mcp_ctx *ctx) {
   ctx->hm.m32_shifted = ctx->hm.m32;
   for (int j = 0; j < ctx->robot.nj; ++j) {
     if (ctx->robot.parent[j] >= 0) continue;
@@ -585,6 +587,19 @@ void update_shifted(mcp_ctx *ctx) {
       ctx->hm.m32_shifted.X[j][r * 4 + 3] = static_cast<float>(ctx->robot.X[12 * j + r * 4 + 3] - ctx->origin[r]);
   }
   for (int r = 0; r < 3; ++r) ctx->hm.m32_shifted.shift[r] = static_cast<float>(ctx->origin[r]);
+  if (!ctx->d_chk) {
+    cudaError_t e = cudaMalloc(&ctx->d_chk, sizeof(CheckData));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc check data");
+    ctx->hm.d_chk = ctx->d_chk;
+  }
+  CheckData *h = new (std::nothrow) CheckData;
+  if (!h) return fail(ctx, MCP_ERR_OOM, "host allocation failed");
+  h->m = ctx->hm.m32_shifted;
+  h->st = ctx->hm.st32;
+  cudaError_t e = cudaMemcpy(ctx->d_chk, h, sizeof(CheckData), cudaMemcpyHostToDevice);
+  delete h;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "check data copy");
+  return MCP_OK;
 }
 
 mcp_status check_batch_ptr(mcp_ctx *ctx, const void *p, const char *name) {
@@ -680,8 +695,7 @@ mcp_status ensure_resolved(mcp_ctx *ctx) {
       }
   }
   MCP_CUDA(cudaMemcpy(ctx->d_m64, &ctx->hm.m64, sizeof(ModelT<double>), cudaMemcpyHostToDevice), "model copy");
-  update_shifted(ctx);
-  return MCP_OK;
+  return update_shifted(ctx);
 }
 
 }  // namespace
@@ -731,6 +745,7 @@ void mcp_destroy(mcp_ctx *ctx) {
   DeviceGuard g(ctx->device);
   cudaDeviceSynchronize();
   cudaFree(ctx->d_m64);
+  cudaFree(ctx->d_chk);
   cudaFree(ctx->d_tab);
   cudaFree(ctx->d_obs32);
   cudaFree(ctx->d_obs64);
@@ -896,8 +911,7 @@ mcp_status mcp_load_obstacles(mcp_ctx *ctx, const double *spheres, int32_t n_sph
   ctx->hm.n_box = n_aabbs;
   ctx->obs_loaded = true;
   ++ctx->version;
-  update_shifted(ctx);
-  return MCP_OK;
+  return update_shifted(ctx);
 }
 
 static mcp_status validate_params(mcp_ctx *ctx, const mcp_project_params *p) {
@@ -953,6 +967,41 @@ mcp_status mcp_project_batch(mcp_ctx *ctx, const mcp_project_params *p, int64_t 
   cudaError_t e = registry()[ctx->prob_class].project_fn(ctx->hm, c, &launches);
   ctx->launches += launches;
   if (e != cudaSuccess) return cuda_fail(ctx, e, "project_batch launch");
+  return MCP_OK;
+}
+
+mcp_status mcp_project_check_batch(mcp_ctx *ctx, const mcp_project_params *p, int64_t n, int64_t ld,
+                                   const void *q_in, void *q_out, uint8_t *flags, uint8_t *iters, double *resid,
+                                   uint8_t *in_collision, uint32_t *pairs_tested, mcp_stream stream) {
+  if (!ctx) return MCP_ERR_ARG;
+  mcp_status st = validate_params(ctx, p);
+  if (st != MCP_OK) return st;
+  if (!ctx->obs_loaded) return fail(ctx, MCP_ERR_STATE, "obstacles must be loaded");
+  if (n < 0 || ld < n) return fail(ctx, MCP_ERR_ARG, "need 0 <= n <= ld (n = %lld, ld = %lld)", (long long)n, (long long)ld);
+  if (n == 0) return MCP_OK;
+  const char *names[6] = {"q_in", "q_out", "flags", "iters", "resid", "in_collision"};
+  const void *ptrs[6] = {q_in, q_out, flags, iters, resid, in_collision};
+  for (int i = 0; i < 6; ++i)
+    if ((st = check_batch_ptr(ctx, ptrs[i], names[i])) != MCP_OK) return st;
+  if (pairs_tested && (st = check_batch_ptr(ctx, pairs_tested, "pairs_tested")) != MCP_OK) return st;
+  DeviceGuard g(ctx->device);
+  ProjCall c;
+  fill_call(ctx, p, c, reinterpret_cast<cudaStream_t>(stream));
+  c.q_in = q_in;
+  c.ld_in = ld;
+  c.total = n;
+  c.q_out = q_out;
+  c.ld_out = ld;
+  c.flags = flags;
+  c.iters = iters;
+  c.resid = resid;
+  c.fused_check = true;
+  c.hit = in_collision;
+  c.pairs = pairs_tested;
+  int launches = 0;
+  cudaError_t e = registry()[ctx->prob_class].project_fn(ctx->hm, c, &launches);
+  ctx->launches += launches;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "project_check_batch launch");
   return MCP_OK;
 }
 

@@ -27,6 +27,13 @@ struct Tuning {
   int chunk = 32;         // configurations a warp claims per atomic
 };
 
+// What the collision check of the fused projection kernel reads from device
+// memory: the model in the collision frame and the robot's spheres.
+struct CheckData {
+  ModelT<float> m;
+  SphereTable<float> st;
+};
+
 struct HostModel {
   ModelT<float> m32;
   ModelT<float> m32_shifted;  // m32 in the collision frame (origin at the obstacle centroid)
@@ -39,6 +46,7 @@ struct HostModel {
   const double *d_obs64 = nullptr;        // [n_obs * 4]
   const float *d_box32 = nullptr;         // [n_box * 6] lo.xyz, hi.xyz, shifted
   const double *d_box64 = nullptr;        // [n_box * 6]
+  const CheckData *d_chk = nullptr;       // device copy of (m32_shifted, st32)
   int n_obs = 0;
   int n_box = 0;
   int sm_count = 1;
@@ -69,6 +77,10 @@ struct ProjCall {
   uint8_t *flags = nullptr;
   uint8_t *iters = nullptr;
   double *resid = nullptr;
+  // fused collision check of every output (project_check_batch)
+  bool fused_check = false;
+  uint8_t *hit = nullptr;
+  uint32_t *pairs = nullptr;
   unsigned long long *counter = nullptr;  // zeroed work counter (device)
   Tuning tune;
   cudaStream_t stream = 0;

@@ -350,6 +350,14 @@ struct ProjArgs {
   float pivot;
   double tol2_64;
   double lambda64;
+  // fused collision check of every output (CHK kernels only)
+  const CheckData *chk;
+  const float *obs;
+  const float *box;
+  int n_obs;
+  int n_box;
+  uint8_t *hit;
+  uint32_t *pairs;
 };
 
 // One step of iterative refinement of the LM solve with the residual formed
@@ -831,6 +839,226 @@ __device__ __forceinline__ void accept_one(const A &a, long long item, int it, u
 }
 
 // ---------------------------------------------------------------------------
+// Collision check (CollisionFree of Alg. 2): link spheres against obstacle
+// spheres and boxes.  One thread per configuration.
+//
+// FP32 path: coordinates are shifted by the obstacle centroid o (applied to
+// the robot base translations and to the staged obstacles), and the sphere
+// test |c_s - c_o| < r_s + r_o is evaluated in the expanded form
+//     c_s . (-2 c_o) + (|c_o|^2 - r_o^2) + r_s (-2 r_o)  <  -(|c_s|^2 - r_s^2)
+// with the obstacle terms precomputed: 4 FMA + 1 min per pair.  Spheres are
+// processed in register blocks of 8 per link (ILP), obstacles are read from
+// shared memory with one broadcast load each; the configuration exits after
+// the first block that overlaps an obstacle.  In the shifted frame |c| stays
+// within a few metres, so the FP32 cancellation error of the expanded form
+// stays below ~1e-5 m in distance (verified against the FP64 oracle).
+// FP64 path: the plain difference form, one sphere at a time.
+// ---------------------------------------------------------------------------
+template <class P, typename T>
+struct CheckArgs {
+  ModelT<T> m;
+  SphereTable<T> st;
+  const T *obs;  // FP32: [n_obs * 8] (-2c, |c|^2 - r^2, -2r, pad) in the shifted frame; FP64: [n_obs * 4]
+  const T *box;  // [n_box * 6] (FP32: shifted)
+  int n_obs;
+  int n_box;
+  const T *q;
+  long long ld;
+  long long n;
+  uint8_t *out;
+  uint32_t *pairs;  // optional: number of sphere-obstacle pairs tested per configuration
+  const double2 *tab;
+};
+
+template <typename T>
+__device__ __forceinline__ T max_(T a, T b) {
+  return a > b ? a : b;
+}
+
+template <typename T>
+__device__ __forceinline__ bool box_hits(V3<T> c, T rs, const T *s_box, int n_box) {
+  for (int b = 0; b < n_box; ++b) {
+    const T *bx = s_box + 6 * b;
+    const T ex = max_(max_(bx[0] - c.x, c.x - bx[3]), T(0));
+    const T ey = max_(max_(bx[1] - c.y, c.y - bx[4]), T(0));
+    const T ez = max_(max_(bx[2] - c.z, c.z - bx[5]), T(0));
+    if (fma_(ex, ex, fma_(ey, ey, ez * ez)) < rs * rs) return true;
+  }
+  return false;
+}
+
+template <typename T>
+__device__ __forceinline__ bool sphere_hits_plain(V3<T> c, T rs, const T *s_obs, int n_obs, const T *s_box, int n_box) {
+  for (int o = 0; o < n_obs; ++o) {
+    const T dx = c.x - s_obs[4 * o], dy = c.y - s_obs[4 * o + 1], dz = c.z - s_obs[4 * o + 2];
+    const T rr = rs + s_obs[4 * o + 3];
+    if (fma_(dx, dx, fma_(dy, dy, dz * dz)) < rr * rr) return true;
+  }
+  return box_hits<T>(c, rs, s_box, n_box);
+}
+
+constexpr int SPH_BLOCK = 8;
+
+// Collision verdict of one configuration q in the collision frame: model m
+// (root offsets shifted by the obstacle origin), spheres st, obstacle records
+// and boxes staged in shared memory.  `tests` counts the 4-FMA tests made.
+template <class P>
+__device__ __forceinline__ bool check_one_f32(const ModelT<float> &m, const SphereTable<float> &st,
+                                              const float4 *s_obs, int n_obs, const float *s_box, int n_box,
+                                              const double2 *tab, const float (&q)[P::D], uint32_t &tests) {
+  const OpsF32 ops{tab};
+  bool hit = false;
+  // spheres [s0, e) placed by (R, p), bounding sphere lb (local) of the group
+  auto group_hits = [&](const float (&R)[9], V3<float> p, int s0, int e, const float *lb) -> bool {
+    if (s0 >= e) return false;
+    if (n_box > 0) {
+      for (int s = s0; s < e; ++s) {
+        const V3<float> c = add_rot_t<7>(p, R, V3<float>{st.s[s][0], st.s[s][1], st.s[s][2]});
+        if (box_hits<float>(c, st.s[s][3], s_box, n_box)) return true;
+      }
+    }
+    const V3<float> bc = add_rot_t<7>(p, R, V3<float>{lb[0], lb[1], lb[2]});
+    const float br = lb[3];
+    const float kb = fmaf(bc.x, bc.x, fmaf(bc.y, bc.y, fmaf(bc.z, bc.z, -br * br)));
+    for (int o0 = 0; o0 < n_obs; o0 += 32) {
+      const int cnt = min(32, n_obs - o0);
+      unsigned cand = 0u;
+      if (cnt == 32) {  // full chunk: unrolled, compile-time bit positions
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          const float4 g = s_obs[2 * (o0 + t)];
+          const float g2 = s_obs[2 * (o0 + t) + 1].x;
+          const float v = fmaf(bc.x, g.x, fmaf(bc.y, g.y, fmaf(bc.z, g.z, fmaf(br, g2, g.w))));
+          cand |= (v < -kb) ? (1u << t) : 0u;
+        }
+      } else {
+        for (int t = 0; t < cnt; ++t) {
+          const float4 g = s_obs[2 * (o0 + t)];
+          const float g2 = s_obs[2 * (o0 + t) + 1].x;
+          const float v = fmaf(bc.x, g.x, fmaf(bc.y, g.y, fmaf(bc.z, g.z, fmaf(br, g2, g.w))));
+          if (v < -kb) cand |= 1u << t;
+        }
+      }
+      tests += static_cast<uint32_t>(cnt);
+      if (!cand) continue;
+      for (int sb = s0; sb < e; sb += SPH_BLOCK) {
+        const int count = min(SPH_BLOCK, e - sb);
+        float cx[SPH_BLOCK], cy[SPH_BLOCK], cz[SPH_BLOCK], rs[SPH_BLOCK], ks[SPH_BLOCK];
+#pragma unroll
+        for (int b = 0; b < SPH_BLOCK; ++b) {
+          const int s = sb + (b < count ? b : 0);
+          const V3<float> c = add_rot_t<7>(p, R, V3<float>{st.s[s][0], st.s[s][1], st.s[s][2]});
+          cx[b] = c.x;
+          cy[b] = c.y;
+          cz[b] = c.z;
+          rs[b] = st.s[s][3];
+          ks[b] = (b < count) ? fmaf(c.x, c.x, fmaf(c.y, c.y, fmaf(c.z, c.z, -rs[b] * rs[b]))) : FLT_MAX;  // pad: never a hit
+        }
+        unsigned msk = cand;
+        while (msk) {
+          const int t = __ffs(static_cast<int>(msk)) - 1;
+          msk &= msk - 1u;
+          const float4 g = s_obs[2 * (o0 + t)];
+          const float g2 = s_obs[2 * (o0 + t) + 1].x;
+          bool h = false;
+#pragma unroll
+          for (int b = 0; b < SPH_BLOCK; ++b)
+            h |= fmaf(cx[b], g.x, fmaf(cy[b], g.y, fmaf(cz[b], g.z, fmaf(rs[b], g2, g.w)))) < -ks[b];
+          tests += static_cast<uint32_t>(count);
+          if (h) return true;
+        }
+      }
+    }
+    return false;
+  };
+  {
+    const float Ri[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+    hit = group_hits(Ri, V3<float>{-m.shift[0], -m.shift[1], -m.shift[2]}, st.off[0], st.off[1], st.lb[MAXJ]);
+  }
+  Kin<P, float> k;
+  if (!hit)
+    fk<P, true>(
+        ops, m, q, k,
+        [&](auto JJ, const float (&R)[9], V3<float> p) {
+          constexpr int j = decltype(JJ)::value;
+          if (!hit) hit = group_hits(R, p, st.off[j + 1], st.off[j + 2], st.lb[j]);
+        },
+        [&]() { return hit; });
+  return hit;
+}
+
+// Stages the FP32 obstacle records and boxes of the collision frame in shared memory.
+__device__ __forceinline__ void stage_obstacles(const float *obs, int n_obs, const float *box, int n_box,
+                                                float4 *s_obs, float *s_box) {
+  for (int t = threadIdx.x; t < 8 * n_obs; t += blockDim.x) reinterpret_cast<float *>(s_obs)[t] = obs[t];
+  for (int t = threadIdx.x; t < 6 * n_box; t += blockDim.x) s_box[t] = box[t];
+}
+
+// FP32 check with a per-link broad phase: the link's bounding sphere is
+// tested against chunks of 32 obstacles (same 4-FMA test); only the obstacles
+// it overlaps are tested against the link's spheres.  The bound contains every
+// sphere of the link with a 1e-4 m margin, so no overlapping pair is skipped
+// and the verdict is that of the all-pairs test.  `pairs` counts every 4-FMA
+// test performed (broad and narrow).
+template <class P>
+__global__ void __launch_bounds__(128) k_check_f32(const __grid_constant__ CheckArgs<P, float> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4 *s_obs = reinterpret_cast<float4 *>(smem_raw);          // 2 float4 per obstacle
+  float *s_box = reinterpret_cast<float *>(s_obs + 2 * a.n_obs);
+  stage_obstacles(a.obs, a.n_obs, a.box, a.n_box, s_obs, s_box);
+  __syncthreads();
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  constexpr int D = P::D;
+  float q[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) q[j] = a.q[j * a.ld + i];
+  uint32_t tests = 0;
+  const bool hit = check_one_f32<P>(a.m, a.st, s_obs, a.n_obs, s_box, a.n_box, a.tab, q, tests);
+  a.out[i] = hit ? 1 : 0;
+  if (a.pairs) a.pairs[i] = tests;
+}
+
+template <class P>
+__global__ void __launch_bounds__(128) k_check_f64(const __grid_constant__ CheckArgs<P, double> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *s_obs = reinterpret_cast<double *>(smem_raw);
+  double *s_box = s_obs + 4 * a.n_obs;
+  for (int t = threadIdx.x; t < 4 * a.n_obs; t += blockDim.x) s_obs[t] = a.obs[t];
+  for (int t = threadIdx.x; t < 6 * a.n_box; t += blockDim.x) s_box[t] = a.box[t];
+  __syncthreads();
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  constexpr int D = P::D;
+  const OpsF64Plain ops{a.tab};
+  double q[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) q[j] = a.q[j * a.ld + i];
+  bool hit = false;
+  uint32_t pairs = 0;
+  for (int s = a.st.off[0]; s < a.st.off[1] && !hit; ++s) {
+    hit = sphere_hits_plain<double>(V3<double>{a.st.s[s][0], a.st.s[s][1], a.st.s[s][2]}, a.st.s[s][3], s_obs,
+                                    a.n_obs, s_box, a.n_box);
+    pairs += a.n_obs;
+  }
+  Kin<P, double> k;
+  if (!hit)
+    fk<P, true>(
+        ops, a.m, q, k,
+        [&](auto JJ, const double (&R)[9], V3<double> p) {
+          constexpr int j = decltype(JJ)::value;
+          for (int s = a.st.off[j + 1]; s < a.st.off[j + 2] && !hit; ++s) {
+            const V3<double> c = add_rot_t<7>(p, R, V3<double>{a.st.s[s][0], a.st.s[s][1], a.st.s[s][2]});
+            hit = sphere_hits_plain<double>(c, a.st.s[s][3], s_obs, a.n_obs, s_box, a.n_box);
+            pairs += a.n_obs;
+          }
+        },
+        [&]() { return hit; });
+  a.out[i] = hit ? 1 : 0;
+  if (a.pairs) a.pairs[i] = pairs;
+}
+
+// ---------------------------------------------------------------------------
 // Persistent projection kernel (FP32 steps, FP64 acceptance).
 //
 // Each warp keeps a local queue of work items claimed `chunk` at a time with
@@ -852,12 +1080,19 @@ __host__ __device__ constexpr int min_blocks() {
   return 65536 / (TPB * reg_cap<P>()) > 0 ? 65536 / (TPB * reg_cap<P>()) : 1;
 }
 
-template <class P, class Src, int TPB, bool CYC>
+template <class P, class Src, int TPB, bool CYC, bool CHK>
 __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(const __grid_constant__ ProjArgs<P, Src> a) {
   constexpr int D = P::D;
   constexpr int W = TPB / 32;
   __shared__ long long s_item[W][64];
   __shared__ uint32_t s_meta[W][64];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4 *s_obs = reinterpret_cast<float4 *>(smem_raw);
+  float *s_box = reinterpret_cast<float *>(s_obs + 2 * a.n_obs);
+  if constexpr (CHK) {  // obstacles of the fused check, staged once per block
+    stage_obstacles(a.obs, a.n_obs, a.box, a.n_box, s_obs, s_box);
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const long long total = a.src.clamp_total(a.total);
@@ -933,13 +1168,24 @@ __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(con
       __syncwarp();
     }
     const bool drained = !__any_sync(FULL, act) && qn >= qe && !more;
-    // (4) FP64 acceptance in full warps
+    // (4) FP64 acceptance in full warps (and, fused, the collision check of
+    // the accepted outputs: ALU work that overlaps other warps' FP64 passes)
     if (pend >= 32 || (drained && pend > 0)) {
       const int take = pend < 32 ? pend : 32;
       if (lane < take) {
         const int pos = pend - take + lane;
         const uint32_t meta = s_meta[wib][pos];
-        accept_one<P, CYC>(a, s_item[wib][pos], static_cast<int>(meta & 0xffu), meta >> 8);
+        const long long it_item = s_item[wib][pos];
+        accept_one<P, CYC>(a, it_item, static_cast<int>(meta & 0xffu), meta >> 8);
+        if constexpr (CHK) {
+          float qc[D];
+#pragma unroll
+          for (int j = 0; j < D; ++j) qc[j] = a.q_out[j * a.ld_out + it_item];
+          uint32_t tests = 0;
+          const bool h = check_one_f32<P>(a.chk->m, a.chk->st, s_obs, a.n_obs, s_box, a.n_box, a.tab, qc, tests);
+          a.hit[it_item] = h ? 1 : 0;
+          if (a.pairs) a.pairs[it_item] = tests;
+        }
       }
       pend -= take;
       __syncwarp();
@@ -1082,210 +1328,6 @@ __global__ void __launch_bounds__(128) k_project_f64(const __grid_constant__ Pro
   a.flags[i] = static_cast<uint8_t>(fl);
   a.iters[i] = static_cast<uint8_t>(it > 255 ? 255 : it);
   a.resid[i] = sqrt(r2);
-}
-
-// ---------------------------------------------------------------------------
-// Collision check (CollisionFree of Alg. 2): link spheres against obstacle
-// spheres and boxes.  One thread per configuration.
-//
-// FP32 path: coordinates are shifted by the obstacle centroid o (applied to
-// the robot base translations and to the staged obstacles), and the sphere
-// test |c_s - c_o| < r_s + r_o is evaluated in the expanded form
-//     c_s . (-2 c_o) + (|c_o|^2 - r_o^2) + r_s (-2 r_o)  <  -(|c_s|^2 - r_s^2)
-// with the obstacle terms precomputed: 4 FMA + 1 min per pair.  Spheres are
-// processed in register blocks of 8 per link (ILP), obstacles are read from
-// shared memory with one broadcast load each; the configuration exits after
-// the first block that overlaps an obstacle.  In the shifted frame |c| stays
-// within a few metres, so the FP32 cancellation error of the expanded form
-// stays below ~1e-5 m in distance (verified against the FP64 oracle).
-// FP64 path: the plain difference form, one sphere at a time.
-// ---------------------------------------------------------------------------
-template <class P, typename T>
-struct CheckArgs {
-  ModelT<T> m;
-  SphereTable<T> st;
-  const T *obs;  // FP32: [n_obs * 8] (-2c, |c|^2 - r^2, -2r, pad) in the shifted frame; FP64: [n_obs * 4]
-  const T *box;  // [n_box * 6] (FP32: shifted)
-  int n_obs;
-  int n_box;
-  const T *q;
-  long long ld;
-  long long n;
-  uint8_t *out;
-  uint32_t *pairs;  // optional: number of sphere-obstacle pairs tested per configuration
-  const double2 *tab;
-};
-
-template <typename T>
-__device__ __forceinline__ T max_(T a, T b) {
-  return a > b ? a : b;
-}
-
-template <typename T>
-__device__ __forceinline__ bool box_hits(V3<T> c, T rs, const T *s_box, int n_box) {
-  for (int b = 0; b < n_box; ++b) {
-    const T *bx = s_box + 6 * b;
-    const T ex = max_(max_(bx[0] - c.x, c.x - bx[3]), T(0));
-    const T ey = max_(max_(bx[1] - c.y, c.y - bx[4]), T(0));
-    const T ez = max_(max_(bx[2] - c.z, c.z - bx[5]), T(0));
-    if (fma_(ex, ex, fma_(ey, ey, ez * ez)) < rs * rs) return true;
-  }
-  return false;
-}
-
-template <typename T>
-__device__ __forceinline__ bool sphere_hits_plain(V3<T> c, T rs, const T *s_obs, int n_obs, const T *s_box, int n_box) {
-  for (int o = 0; o < n_obs; ++o) {
-    const T dx = c.x - s_obs[4 * o], dy = c.y - s_obs[4 * o + 1], dz = c.z - s_obs[4 * o + 2];
-    const T rr = rs + s_obs[4 * o + 3];
-    if (fma_(dx, dx, fma_(dy, dy, dz * dz)) < rr * rr) return true;
-  }
-  return box_hits<T>(c, rs, s_box, n_box);
-}
-
-constexpr int SPH_BLOCK = 8;
-
-// FP32 check with a per-link broad phase: the link's bounding sphere is
-// tested against chunks of 32 obstacles (same 4-FMA test); only the obstacles
-// it overlaps are tested against the link's spheres.  The bound contains every
-// sphere of the link with a 1e-4 m margin, so no overlapping pair is skipped
-// and the verdict is that of the all-pairs test.  `pairs` counts every 4-FMA
-// test performed (broad and narrow).
-template <class P>
-__global__ void __launch_bounds__(128) k_check_f32(const __grid_constant__ CheckArgs<P, float> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4 *s_obs = reinterpret_cast<float4 *>(smem_raw);          // 2 float4 per obstacle
-  float *s_box = reinterpret_cast<float *>(s_obs + 2 * a.n_obs);
-  for (int t = threadIdx.x; t < 8 * a.n_obs; t += blockDim.x) reinterpret_cast<float *>(s_obs)[t] = a.obs[t];
-  for (int t = threadIdx.x; t < 6 * a.n_box; t += blockDim.x) s_box[t] = a.box[t];
-  __syncthreads();
-  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  constexpr int D = P::D;
-  const OpsF32 ops{a.tab};
-  float q[D];
-#pragma unroll
-  for (int j = 0; j < D; ++j) q[j] = a.q[j * a.ld + i];
-  bool hit = false;
-  uint32_t tests = 0;
-  // spheres [s0, e) placed by (R, p), bounding sphere lb (local) of the group
-  auto group_hits = [&](const float (&R)[9], V3<float> p, int s0, int e, const float *lb) -> bool {
-    if (s0 >= e) return false;
-    if (a.n_box > 0) {
-      for (int s = s0; s < e; ++s) {
-        const V3<float> c = add_rot_t<7>(p, R, V3<float>{a.st.s[s][0], a.st.s[s][1], a.st.s[s][2]});
-        if (box_hits<float>(c, a.st.s[s][3], s_box, a.n_box)) return true;
-      }
-    }
-    const V3<float> bc = add_rot_t<7>(p, R, V3<float>{lb[0], lb[1], lb[2]});
-    const float br = lb[3];
-    const float kb = fmaf(bc.x, bc.x, fmaf(bc.y, bc.y, fmaf(bc.z, bc.z, -br * br)));
-    for (int o0 = 0; o0 < a.n_obs; o0 += 32) {
-      const int cnt = min(32, a.n_obs - o0);
-      unsigned cand = 0u;
-      if (cnt == 32) {  // full chunk: unrolled, compile-time bit positions
-#pragma unroll
-        for (int t = 0; t < 32; ++t) {
-          const float4 g = s_obs[2 * (o0 + t)];
-          const float g2 = s_obs[2 * (o0 + t) + 1].x;
-          const float v = fmaf(bc.x, g.x, fmaf(bc.y, g.y, fmaf(bc.z, g.z, fmaf(br, g2, g.w))));
-          cand |= (v < -kb) ? (1u << t) : 0u;
-        }
-      } else {
-        for (int t = 0; t < cnt; ++t) {
-          const float4 g = s_obs[2 * (o0 + t)];
-          const float g2 = s_obs[2 * (o0 + t) + 1].x;
-          const float v = fmaf(bc.x, g.x, fmaf(bc.y, g.y, fmaf(bc.z, g.z, fmaf(br, g2, g.w))));
-          if (v < -kb) cand |= 1u << t;
-        }
-      }
-      tests += static_cast<uint32_t>(cnt);
-      if (!cand) continue;
-      for (int sb = s0; sb < e; sb += SPH_BLOCK) {
-        const int count = min(SPH_BLOCK, e - sb);
-        float cx[SPH_BLOCK], cy[SPH_BLOCK], cz[SPH_BLOCK], rs[SPH_BLOCK], ks[SPH_BLOCK];
-#pragma unroll
-        for (int b = 0; b < SPH_BLOCK; ++b) {
-          const int s = sb + (b < count ? b : 0);
-          const V3<float> c = add_rot_t<7>(p, R, V3<float>{a.st.s[s][0], a.st.s[s][1], a.st.s[s][2]});
-          cx[b] = c.x;
-          cy[b] = c.y;
-          cz[b] = c.z;
-          rs[b] = a.st.s[s][3];
-          ks[b] = (b < count) ? fmaf(c.x, c.x, fmaf(c.y, c.y, fmaf(c.z, c.z, -rs[b] * rs[b]))) : FLT_MAX;  // pad: never a hit
-        }
-        unsigned m = cand;
-        while (m) {
-          const int t = __ffs(static_cast<int>(m)) - 1;
-          m &= m - 1u;
-          const float4 g = s_obs[2 * (o0 + t)];
-          const float g2 = s_obs[2 * (o0 + t) + 1].x;
-          bool h = false;
-#pragma unroll
-          for (int b = 0; b < SPH_BLOCK; ++b)
-            h |= fmaf(cx[b], g.x, fmaf(cy[b], g.y, fmaf(cz[b], g.z, fmaf(rs[b], g2, g.w)))) < -ks[b];
-          tests += static_cast<uint32_t>(count);
-          if (h) return true;
-        }
-      }
-    }
-    return false;
-  };
-  {
-    const float Ri[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
-    hit = group_hits(Ri, V3<float>{-a.m.shift[0], -a.m.shift[1], -a.m.shift[2]}, a.st.off[0], a.st.off[1],
-                     a.st.lb[MAXJ]);
-  }
-  Kin<P, float> k;
-  if (!hit)
-    fk<P, true>(
-        ops, a.m, q, k,
-        [&](auto JJ, const float (&R)[9], V3<float> p) {
-          constexpr int j = decltype(JJ)::value;
-          if (!hit) hit = group_hits(R, p, a.st.off[j + 1], a.st.off[j + 2], a.st.lb[j]);
-        },
-        [&]() { return hit; });
-  a.out[i] = hit ? 1 : 0;
-  if (a.pairs) a.pairs[i] = tests;
-}
-
-template <class P>
-__global__ void __launch_bounds__(128) k_check_f64(const __grid_constant__ CheckArgs<P, double> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double *s_obs = reinterpret_cast<double *>(smem_raw);
-  double *s_box = s_obs + 4 * a.n_obs;
-  for (int t = threadIdx.x; t < 4 * a.n_obs; t += blockDim.x) s_obs[t] = a.obs[t];
-  for (int t = threadIdx.x; t < 6 * a.n_box; t += blockDim.x) s_box[t] = a.box[t];
-  __syncthreads();
-  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  constexpr int D = P::D;
-  const OpsF64Plain ops{a.tab};
-  double q[D];
-#pragma unroll
-  for (int j = 0; j < D; ++j) q[j] = a.q[j * a.ld + i];
-  bool hit = false;
-  uint32_t pairs = 0;
-  for (int s = a.st.off[0]; s < a.st.off[1] && !hit; ++s) {
-    hit = sphere_hits_plain<double>(V3<double>{a.st.s[s][0], a.st.s[s][1], a.st.s[s][2]}, a.st.s[s][3], s_obs,
-                                    a.n_obs, s_box, a.n_box);
-    pairs += a.n_obs;
-  }
-  Kin<P, double> k;
-  if (!hit)
-    fk<P, true>(
-        ops, a.m, q, k,
-        [&](auto JJ, const double (&R)[9], V3<double> p) {
-          constexpr int j = decltype(JJ)::value;
-          for (int s = a.st.off[j + 1]; s < a.st.off[j + 2] && !hit; ++s) {
-            const V3<double> c = add_rot_t<7>(p, R, V3<double>{a.st.s[s][0], a.st.s[s][1], a.st.s[s][2]});
-            hit = sphere_hits_plain<double>(c, a.st.s[s][3], s_obs, a.n_obs, s_box, a.n_box);
-            pairs += a.n_obs;
-          }
-        },
-        [&]() { return hit; });
-  a.out[i] = hit ? 1 : 0;
-  if (a.pairs) a.pairs[i] = pairs;
 }
 
 // ---------------------------------------------------------------------------
@@ -1433,7 +1475,7 @@ __global__ void __launch_bounds__(128) k_vjp(const __grid_constant__ VjpArgs<P> 
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-template <class P, class Src, int TPB, bool CYC>
+template <class P, class Src, int TPB, bool CYC, bool CHK>
 cudaError_t launch_persistent(const HostModel &hm, const ProjCall &c, const Src &src) {
   ProjArgs<P, Src> a;
   a.m = hm.m32;
@@ -1455,12 +1497,20 @@ cudaError_t launch_persistent(const HostModel &hm, const ProjCall &c, const Src 
   a.pivot = static_cast<float>(c.pivot);
   a.tol2_64 = c.tol * c.tol;
   a.lambda64 = c.lambda;
+  a.chk = hm.d_chk;
+  a.obs = reinterpret_cast<const float *>(hm.d_obs32);
+  a.box = hm.d_box32;
+  a.n_obs = CHK ? hm.n_obs : 0;
+  a.n_box = CHK ? hm.n_box : 0;
+  a.hit = c.hit;
+  a.pairs = c.pairs;
+  const size_t smem = CHK ? sizeof(float) * (8 * hm.n_obs + 6 * hm.n_box) : 0;
   const long long warps_needed = (c.total + 31) / 32;
   long long blocks = static_cast<long long>(hm.sm_count) * c.tune.blocks_per_sm;
   const long long max_useful = (warps_needed + (TPB / 32) - 1) / (TPB / 32);
   if (blocks > max_useful) blocks = max_useful;
   if (blocks < 1) blocks = 1;
-  k_project_f32<P, Src, TPB, CYC><<<static_cast<unsigned>(blocks), TPB, 0, c.stream>>>(a);
+  k_project_f32<P, Src, TPB, CYC, CHK><<<static_cast<unsigned>(blocks), TPB, smem, c.stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -1494,6 +1544,24 @@ cudaError_t launch_plain64_any(const HostModel &hm, const ProjCall &c, const Src
 }
 
 template <class P>
+cudaError_t launch_check_impl(const HostModel &hm, const CheckCall &c, int *launches);
+
+// The collision check of a projection's outputs as a launch of its own (paths
+// without a fused kernel): same verdicts as check_batch on q_out.
+template <class P>
+cudaError_t check_outputs(const HostModel &hm, const ProjCall &c, int *launches) {
+  CheckCall cc;
+  cc.precision = c.precision;
+  cc.n = c.total;
+  cc.ld = c.ld_out;
+  cc.q = c.q_out;
+  cc.out = c.hit;
+  cc.pairs = c.pairs;
+  cc.stream = c.stream;
+  return launch_check_impl<P>(hm, cc, launches);
+}
+
+template <class P>
 cudaError_t launch_project_impl(const HostModel &hm, const ProjCall &c, int *launches) {
   if (c.total <= 0) return cudaSuccess;
   cudaError_t err;
@@ -1505,26 +1573,33 @@ cudaError_t launch_project_impl(const HostModel &hm, const ProjCall &c, int *lau
     else
       err = launch_plain64_any<P>(hm, c, BatchSrc<double>{static_cast<const double *>(c.q_in), c.ld_in});
     *launches += 1;
+    if (err == cudaSuccess && c.fused_check) err = check_outputs<P>(hm, c, launches);
     return err;
   }
   err = cudaMemsetAsync(c.counter, 0, sizeof(unsigned long long), c.stream);
   if (err != cudaSuccess) return err;
-  auto go = [&](auto src) -> cudaError_t {
+  auto go = [&](auto src, auto chk) -> cudaError_t {
     using S = decltype(src);
+    constexpr bool CHK = decltype(chk)::value;
     if constexpr (P::NC > 1) {  // one constraint: the cyclic and stacked forms coincide
-      if (c.cyclic) return launch_persistent<P, S, 128, true>(hm, c, src);
+      if (c.cyclic) return launch_persistent<P, S, 128, true, CHK>(hm, c, src);
     }
     switch (c.tune.tpb) {
-      case 64: return launch_persistent<P, S, 64, false>(hm, c, src);
-      case 256: return launch_persistent<P, S, 256, false>(hm, c, src);
-      default: return launch_persistent<P, S, 128, false>(hm, c, src);
+      case 64: return launch_persistent<P, S, 64, false, CHK>(hm, c, src);
+      case 256: return launch_persistent<P, S, 256, false, CHK>(hm, c, src);
+      default: return launch_persistent<P, S, 128, false, CHK>(hm, c, src);
     }
   };
-  if (c.segments)
+  if (c.segments) {
     err = go(SegSrc<float>{static_cast<const float *>(c.start), static_cast<const float *>(c.delta), c.ld_seg,
-                           c.seg_off, c.n_seg});
-  else
-    err = go(BatchSrc<float>{static_cast<const float *>(c.q_in), c.ld_in});
+                           c.seg_off, c.n_seg},
+             std::false_type{});
+    *launches += 1;
+    if (err == cudaSuccess && c.fused_check) err = check_outputs<P>(hm, c, launches);
+    return err;
+  }
+  const BatchSrc<float> src{static_cast<const float *>(c.q_in), c.ld_in};
+  err = c.fused_check ? go(src, std::true_type{}) : go(src, std::false_type{});
   *launches += 1;
   return err;
 }

@@ -71,6 +71,8 @@ def load_library(path: str = LIB_PATH):
         "mcp_get_constraint": ([_vp, ctypes.c_int32, _dp, _dp, _dp], ctypes.c_int),
         "mcp_project_batch": ([_vp, P(ProjectParams), ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp],
                               ctypes.c_int),
+        "mcp_project_check_batch": ([_vp, P(ProjectParams), ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
+                                     _vp, _vp, _vp], ctypes.c_int),
         "mcp_project_segments": ([_vp, P(ProjectParams), ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp,
                                   ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
         "mcp_check_batch": ([_vp, ctypes.c_int64, ctypes.c_int64, _vp, ctypes.c_int32, _vp, _vp, _vp], ctypes.c_int),
@@ -94,8 +96,8 @@ def load_library(path: str = LIB_PATH):
 
 EXPORTED = ("mcp_create", "mcp_destroy", "mcp_last_error", "mcp_launch_count", "mcp_load_robot",
             "mcp_load_constraints", "mcp_load_obstacles", "mcp_get_constraint", "mcp_project_batch",
-            "mcp_project_segments", "mcp_check_batch", "mcp_project_vjp", "mcp_path_length_grad", "mcp_autotune",
-            "mcp_project_segments_noalloc", "mcp_path_step")
+            "mcp_project_check_batch", "mcp_project_segments", "mcp_check_batch", "mcp_project_vjp",
+            "mcp_path_length_grad", "mcp_autotune", "mcp_project_segments_noalloc", "mcp_path_step")
 
 
 class MCPError(RuntimeError):
@@ -243,6 +245,24 @@ class Projector:
         self._check(self.lib.mcp_project_batch(self.h, ctypes.byref(pp), n, ld, _ptr(q), _ptr(out), _ptr(flags),
                                                _ptr(iters), _ptr(resid), _stream(stream)))
         return out, flags, iters, resid
+
+    def project_check(self, q, params, out=None, flags=None, iters=None, resid=None, hit=None, pairs=None, n=None,
+                      stream=None):
+        """Projection, then the collision verdict of every output (fused where
+        the kernels allow): (q*, flags, iters, resid, in_collision)."""
+        import torch
+        d, ld = q.shape
+        n = ld if n is None else n
+        out = torch.empty_like(q) if out is None else out
+        flags = torch.empty(ld, dtype=torch.uint8, device=q.device) if flags is None else flags
+        iters = torch.empty(ld, dtype=torch.uint8, device=q.device) if iters is None else iters
+        resid = torch.empty(ld, dtype=torch.float64, device=q.device) if resid is None else resid
+        hit = torch.empty(ld, dtype=torch.uint8, device=q.device) if hit is None else hit
+        pp = self.params(params)
+        self._check(self.lib.mcp_project_check_batch(self.h, ctypes.byref(pp), n, ld, _ptr(q), _ptr(out), _ptr(flags),
+                                                     _ptr(iters), _ptr(resid), _ptr(hit), _ptr(pairs),
+                                                     _stream(stream)))
+        return out, flags, iters, resid, hit
 
     def project_segments(self, start, delta, length, params, total=None, out=None, flags=None, iters=None,
                          resid=None, stream=None):

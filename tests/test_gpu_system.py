@@ -148,3 +148,36 @@ def test_path_shortening_reduces_length_on_manifold(mcproj):
     Qn = Qf.cpu().numpy().astype(np.float64)
     for i in range(0, Qn.shape[1], 97):
         assert np.linalg.norm(O.residual(Qn[:, i])) < 1e-5
+
+
+@pytest.mark.parametrize("name", ["arm", "dual", "tray", "tray_cyclic", "humanoid", "arm_fp64"])
+def test_project_check_equals_separate_calls(mcproj, name):
+    """mcp_project_check_batch (one persistent launch for the FP32 thread
+    kernels, two launches otherwise) returns what mcp_project_batch followed by
+    mcp_check_batch on its output returns, bit for bit."""
+    if name in ("arm", "arm_fp64"):
+        wl = W.arm_workload(n=8195)
+    elif name == "dual":
+        wl = W.dual_arm_workload(total=10, n_random=8195)
+    elif name.startswith("tray"):
+        wl = W.arm_task_workload("tray", n=8195)
+        wl.params.cyclic = name.endswith("cyclic")
+    else:
+        wl = W.humanoid_workload(n=2051)
+    dt = torch.float64 if name == "arm_fp64" else torch.float32
+    if name == "arm_fp64":
+        wl.params.precision = W.PREC_FP64
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
+    q = dev(f32_exact(wl.q), dt)
+    n = q.shape[1]
+    a = P.project(q, wl.params)
+    pa = torch.zeros(n, dtype=torch.int32, device="cuda")
+    ha = P.check(a[0], pairs=pa)
+    pb = torch.zeros(n, dtype=torch.int32, device="cuda")
+    b = P.project_check(q, wl.params, pairs=pb)
+    torch.cuda.synchronize()
+    for x, y in zip(a, b[:4]):
+        assert torch.equal(x, y)
+    assert torch.equal(ha, b[4])
+    assert torch.equal(pa, pb)
+    assert 0.05 < ha.float().mean().item() < 0.95
