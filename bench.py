@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--cyclic", action="store_true",
                     help="cyclic getDescentStep (one LM step per constraint per sweep) instead of the stacked step")
     ap.add_argument("--cap", type=int, default=0, help="iteration cap (default: the workload's)")
+    ap.add_argument("--launch", default="",
+                    help="tpb,blocks_per_sm,chunk,fuse_check instead of autotuning (profiler runs)")
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=0,
@@ -303,7 +305,12 @@ def run_ours(args):
     # blocks per SM and claim size, on this batch (setup, untimed)
     tuning = None
     if not fp64 and seg_args is None and args.workload != "humanoid":
-        tuning = dict(zip(("tpb", "blocks_per_sm", "chunk"), P.autotune(q_in, wl.params)))
+        if args.launch:   # a fixed shape (profiler runs reproduce the tuned one)
+            vals = [int(v) for v in args.launch.split(",")]
+            P.set_tuning(*vals)
+        else:
+            vals = P.autotune(q_in, wl.params)
+        tuning = dict(zip(("tpb", "blocks_per_sm", "chunk", "fuse_check"), vals))
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     sampler = ClockSampler(local)
     with sampler:
@@ -394,7 +401,7 @@ def run_ours(args):
     peak32 = sms * 128 * 2 * sm_max * 1e6 / 1e12        # FP32 FMA lanes x 2 flops x max clock
     peak64 = 1.25                                         # nominal dense FP64, TFLOP/s
     # one fused kernel: FP32 batch problems of the thread-per-configuration kernels
-    one_kernel = fused and not fp64 and args.workload != "humanoid"
+    one_kernel = fused and bool(tuning and tuning.get("fuse_check"))
     if fused and not one_kernel and sep_ms is not None:   # two launches: per-kernel times from the separate calls
         mp, mc = sep_ms["project"], sep_ms["check"]
     else:
@@ -412,7 +419,8 @@ def run_ours(args):
         t_min = max((fp32 + check_flops) / (peak32 * 1e12), fp64f / (peak64 * 1e12))
         roof = {"bound": "alu", "achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
                 "traffic": None,
-                "kernel": "k_project_f32<CHK> (persistent: FP32 steps, FP64 acceptance, fused collision check)",
+                "kernel": "k_project_f32 with the check fused (persistent: FP32 steps, FP64 acceptance, "
+                          "collision check)",
                 "peak_source": peak_src, "fp64_achieved": ach64, "fp64_peak": peak64, "fp64_frac": ach64 / peak64,
                 "mixed_bound_frac": t_min / t,
                 "flops_per_config": {"fp32_projection": fp32 / n, "fp32_check": check_flops / n, "fp64": fp64f / n},

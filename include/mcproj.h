@@ -180,10 +180,11 @@ mcp_status mcp_project_batch(mcp_ctx *ctx, const mcp_project_params *p, int64_t 
  * (Alg. 2: ParallelProject, then CollisionFree of each projected point), with
  * the results of mcp_project_batch and then mcp_check_batch(q_out, precision
  * p->precision).  For FP32 problems of the thread-per-configuration kernels the
- * two run in one persistent launch: the check of each accepted output follows
- * its FP64 acceptance in the same warp, so the ALU-bound check overlaps the
- * FP64 acceptance of other warps; other paths launch the check after the
- * projection.  Requires loaded obstacles.  in_collision [n] uint8 (DEVICE);
+ * two can run in one persistent launch (the check of each accepted output
+ * follows its FP64 acceptance in the same warp, so the ALU-bound check
+ * overlaps the FP64 acceptance of other warps); mcp_autotune or
+ * mcp_set_tuning decides, the default is a second launch.  Requires loaded
+ * obstacles.  in_collision [n] uint8 (DEVICE);
  * pairs_tested [n] uint32 (DEVICE) or NULL: sphere-obstacle tests performed
  * per configuration.  Errors as mcp_project_batch, plus MCP_ERR_STATE without
  * obstacles. */
@@ -243,15 +244,25 @@ mcp_status mcp_path_length_grad(mcp_ctx *ctx, int64_t n_paths, int32_t n_way, in
 mcp_status mcp_path_step(mcp_ctx *ctx, int64_t n_paths, int32_t n_way, int64_t ld, float *Q, const float *D, float eta,
                          float max_step, mcp_stream stream);
 
+/* Sets the launch shape of the persistent FP32 projection kernel directly
+ * (tpb in {64, 128, 256}, blocks_per_sm in 1..8 with tpb * blocks_per_sm <=
+ * 2048, chunk in 1..64, fuse_check 0 / 1), e.g. to reproduce a tuned shape.
+ * MCP_ERR_ARG outside those ranges. */
+mcp_status mcp_set_tuning(mcp_ctx *ctx, int32_t tpb, int32_t blocks_per_sm, int32_t chunk, int32_t fuse_check);
+
 /* Picks the launch shape of the persistent FP32 projection kernel (threads
  * per block, resident blocks per SM, configurations claimed per atomic) for
  * the loaded problem by timing every candidate on the caller's sample
  * q_sample (DEVICE, float [d * ld], n_sample configurations), and keeps the
- * fastest in the context for later calls.  Uses temporary device buffers;
- * synchronous.  The chosen shape is returned in tpb / blocks_per_sm / chunk
- * (HOST, each may be NULL).  Tuning never changes results, only speed. */
+ * fastest in the context for later calls.  With obstacles loaded it also
+ * times mcp_project_check_batch with the check inside the projection kernel
+ * against a second launch and keeps the faster.  Uses temporary device
+ * buffers; synchronous.  The choices are returned in tpb / blocks_per_sm /
+ * chunk / fuse_check (HOST, each may be NULL).  Tuning never changes results,
+ * only speed. */
 mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sample, int64_t ld, const void *q_sample,
-                        int32_t *tpb, int32_t *blocks_per_sm, int32_t *chunk, mcp_stream stream);
+                        int32_t *tpb, int32_t *blocks_per_sm, int32_t *chunk, int32_t *fuse_check,
+                        mcp_stream stream);
 
 /* Number of kernels this context has launched so far (for launch accounting). */
 int64_t mcp_launch_count(const mcp_ctx *ctx);

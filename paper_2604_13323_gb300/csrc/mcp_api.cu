@@ -970,6 +970,25 @@ mcp_status mcp_project_batch(mcp_ctx *ctx, const mcp_project_params *p, int64_t 
   return MCP_OK;
 }
 
+// Projection, then the check of its outputs: fused into the projection kernel
+// when the autotuner found that faster for this problem, else a second launch.
+static cudaError_t run_project_check(mcp_ctx *ctx, ProjCall c, int *launches) {
+  const ClassDesc &cd = registry()[ctx->prob_class];
+  c.fused_check = ctx->tune.fuse_check;
+  if (c.fused_check) return cd.project_fn(ctx->hm, c, launches);
+  cudaError_t e = cd.project_fn(ctx->hm, c, launches);
+  if (e != cudaSuccess) return e;
+  CheckCall k;
+  k.precision = c.precision;
+  k.n = c.total;
+  k.ld = c.ld_out;
+  k.q = c.q_out;
+  k.out = c.hit;
+  k.pairs = c.pairs;
+  k.stream = c.stream;
+  return cd.check_fn(ctx->hm, k, launches);
+}
+
 mcp_status mcp_project_check_batch(mcp_ctx *ctx, const mcp_project_params *p, int64_t n, int64_t ld,
                                    const void *q_in, void *q_out, uint8_t *flags, uint8_t *iters, double *resid,
                                    uint8_t *in_collision, uint32_t *pairs_tested, mcp_stream stream) {
@@ -995,11 +1014,10 @@ mcp_status mcp_project_check_batch(mcp_ctx *ctx, const mcp_project_params *p, in
   c.flags = flags;
   c.iters = iters;
   c.resid = resid;
-  c.fused_check = true;
   c.hit = in_collision;
   c.pairs = pairs_tested;
   int launches = 0;
-  cudaError_t e = registry()[ctx->prob_class].project_fn(ctx->hm, c, &launches);
+  cudaError_t e = run_project_check(ctx, c, &launches);
   ctx->launches += launches;
   if (e != cudaSuccess) return cuda_fail(ctx, e, "project_check_batch launch");
   return MCP_OK;
@@ -1294,8 +1312,20 @@ mcp_status mcp_path_step(mcp_ctx *ctx, int64_t n_paths, int32_t n_way, int64_t l
   return MCP_OK;
 }
 
+mcp_status mcp_set_tuning(mcp_ctx *ctx, int32_t tpb, int32_t blocks_per_sm, int32_t chunk, int32_t fuse_check) {
+  if (!ctx) return MCP_ERR_ARG;
+  if ((tpb != 64 && tpb != 128 && tpb != 256) || blocks_per_sm < 1 || blocks_per_sm > 8 ||
+      tpb * blocks_per_sm > 2048 || chunk < 1 || chunk > 64 || (fuse_check != 0 && fuse_check != 1))
+    return fail(ctx, MCP_ERR_ARG, "tuning (%d, %d, %d, %d) outside the supported shapes", tpb, blocks_per_sm, chunk,
+                fuse_check);
+  ctx->tune = Tuning{tpb, blocks_per_sm, chunk, fuse_check == 1};
+  ctx->tuned = true;
+  return MCP_OK;
+}
+
 mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sample, int64_t ld, const void *q_sample,
-                        int32_t *tpb_out, int32_t *bps_out, int32_t *chunk_out, mcp_stream stream) {
+                        int32_t *tpb_out, int32_t *bps_out, int32_t *chunk_out, int32_t *fuse_out,
+                        mcp_stream stream) {
   if (!ctx) return MCP_ERR_ARG;
   mcp_status st = validate_params(ctx, p);
   if (st != MCP_OK) return st;
@@ -1306,11 +1336,12 @@ mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sam
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int d = ctx->robot.nj;
   float *out = nullptr;
-  uint8_t *fl = nullptr, *it = nullptr;
+  uint8_t *fl = nullptr, *it = nullptr, *hit = nullptr;
   double *res = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t err = cudaMalloc(&out, sizeof(float) * d * ld);
   if (err == cudaSuccess) err = cudaMalloc(&fl, ld);
+  if (err == cudaSuccess) err = cudaMalloc(&hit, ld);
   if (err == cudaSuccess) err = cudaMalloc(&it, ld);
   if (err == cudaSuccess) err = cudaMalloc(&res, sizeof(double) * ld);
   if (err == cudaSuccess) err = cudaEventCreate(&e0);
@@ -1356,9 +1387,45 @@ mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sam
           best = ctx->tune;
         }
       }
+  // projection + check of the outputs: in one kernel, or as two launches
+  if (err == cudaSuccess && ctx->obs_loaded) {
+    float med[2] = {0.f, 0.f};
+    for (int f = 0; f < 2 && err == cudaSuccess; ++f) {
+      ctx->tune = best;
+      ctx->tune.fuse_check = f == 1;
+      float times[3];
+      for (int r = 0; r < 4 && err == cudaSuccess; ++r) {
+        ProjCall call;
+        fill_call(ctx, p, call, s);
+        call.q_in = q_sample;
+        call.ld_in = ld;
+        call.total = n_sample;
+        call.q_out = out;
+        call.ld_out = ld;
+        call.flags = fl;
+        call.iters = it;
+        call.resid = res;
+        call.hit = hit;
+        int launches = 0;
+        err = cudaEventRecord(e0, s);
+        if (err == cudaSuccess) err = run_project_check(ctx, call, &launches);
+        ctx->launches += launches;
+        if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) times[r - 1] = ms;
+      }
+      if (err == cudaSuccess)
+        med[f] = times[0] + times[1] + times[2] - fminf(times[0], fminf(times[1], times[2])) -
+                 fmaxf(times[0], fmaxf(times[1], times[2]));
+    }
+    best.fuse_check = err == cudaSuccess && med[1] < med[0];
+  }
   cudaFree(out);
   cudaFree(fl);
   cudaFree(it);
+  cudaFree(hit);
   cudaFree(res);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -1371,6 +1438,7 @@ mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sam
   if (tpb_out) *tpb_out = best.tpb;
   if (bps_out) *bps_out = best.blocks_per_sm;
   if (chunk_out) *chunk_out = best.chunk;
+  if (fuse_out) *fuse_out = best.fuse_check ? 1 : 0;
   return MCP_OK;
 }
 

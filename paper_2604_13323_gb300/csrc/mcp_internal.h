@@ -25,6 +25,7 @@ struct Tuning {
   int tpb = 128;          // threads per block of the persistent kernel
   int blocks_per_sm = 4;  // resident blocks per SM
   int chunk = 32;         // configurations a warp claims per atomic
+  bool fuse_check = false;  // project_check_batch: check inside the projection kernel (else a second launch)
 };
 
 // What the collision check of the fused projection kernel reads from device

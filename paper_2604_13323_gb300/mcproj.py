@@ -79,8 +79,9 @@ def load_library(path: str = LIB_PATH):
         "mcp_project_vjp": ([_vp, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
         "mcp_path_length_grad": ([_vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, _vp],
                                  ctypes.c_int),
-        "mcp_autotune": ([_vp, P(ProjectParams), ctypes.c_int64, ctypes.c_int64, _vp, _ip, _ip, _ip, _vp],
+        "mcp_autotune": ([_vp, P(ProjectParams), ctypes.c_int64, ctypes.c_int64, _vp, _ip, _ip, _ip, _ip, _vp],
                          ctypes.c_int),
+        "mcp_set_tuning": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
         "mcp_path_step": ([_vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _vp, _vp, ctypes.c_float,
                            ctypes.c_float, _vp], ctypes.c_int),
         "mcp_project_segments_noalloc": ([_vp, P(ProjectParams), ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp,
@@ -97,7 +98,8 @@ def load_library(path: str = LIB_PATH):
 EXPORTED = ("mcp_create", "mcp_destroy", "mcp_last_error", "mcp_launch_count", "mcp_load_robot",
             "mcp_load_constraints", "mcp_load_obstacles", "mcp_get_constraint", "mcp_project_batch",
             "mcp_project_check_batch", "mcp_project_segments", "mcp_check_batch", "mcp_project_vjp",
-            "mcp_path_length_grad", "mcp_autotune", "mcp_project_segments_noalloc", "mcp_path_step")
+            "mcp_path_length_grad", "mcp_autotune", "mcp_set_tuning", "mcp_project_segments_noalloc",
+            "mcp_path_step")
 
 
 class MCPError(RuntimeError):
@@ -310,13 +312,17 @@ class Projector:
 
     def autotune(self, q_sample, params, stream=None):
         """Times the persistent kernel's launch shapes on q_sample ([d, n] float32
-        CUDA tensor) and keeps the fastest; returns (threads/block, blocks/SM, chunk)."""
+        CUDA tensor) and keeps the fastest; returns (threads/block, blocks/SM,
+        chunk, fuse_check)."""
         d, n = q_sample.shape
-        t, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        t, b, c, f = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         pp = self.params(params)
         self._check(self.lib.mcp_autotune(self.h, ctypes.byref(pp), n, n, _ptr(q_sample), ctypes.byref(t),
-                                          ctypes.byref(b), ctypes.byref(c), _stream(stream)))
-        return t.value, b.value, c.value
+                                          ctypes.byref(b), ctypes.byref(c), ctypes.byref(f), _stream(stream)))
+        return t.value, b.value, c.value, f.value
+
+    def set_tuning(self, tpb, blocks_per_sm, chunk, fuse_check=0):
+        self._check(self.lib.mcp_set_tuning(self.h, int(tpb), int(blocks_per_sm), int(chunk), int(fuse_check)))
 
     def path_length_grad(self, Q, n_paths, n_way, length=None, grad=None, stream=None):
         import torch

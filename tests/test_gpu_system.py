@@ -30,8 +30,8 @@ def test_autotune_keeps_results(mcproj):
     P = mcproj.Projector(wl.robot, wl.constraints)
     q = dev(f32_exact(wl.q))
     before = [t.clone() for t in P.project(q, wl.params)]
-    tpb, bps, chunk = P.autotune(q, wl.params)
-    assert tpb in (64, 128, 256) and bps in (1, 2, 4, 8) and chunk in (16, 32, 64)
+    tpb, bps, chunk, fuse = P.autotune(q, wl.params)
+    assert tpb in (64, 128, 256) and bps in (1, 2, 4, 8) and chunk in (16, 32, 64) and fuse in (0, 1)
     after = P.project(q, wl.params)
     torch.cuda.synchronize()
     for x, y in zip(before, after):
@@ -173,11 +173,13 @@ def test_project_check_equals_separate_calls(mcproj, name):
     a = P.project(q, wl.params)
     pa = torch.zeros(n, dtype=torch.int32, device="cuda")
     ha = P.check(a[0], pairs=pa)
-    pb = torch.zeros(n, dtype=torch.int32, device="cuda")
-    b = P.project_check(q, wl.params, pairs=pb)
-    torch.cuda.synchronize()
-    for x, y in zip(a, b[:4]):
-        assert torch.equal(x, y)
-    assert torch.equal(ha, b[4])
-    assert torch.equal(pa, pb)
-    assert 0.05 < ha.float().mean().item() < 0.95
+    for fuse in (1, 0):
+        P.set_tuning(128, 4, 32, fuse)
+        pb = torch.zeros(n, dtype=torch.int32, device="cuda")
+        b = P.project_check(q, wl.params, pairs=pb)
+        torch.cuda.synchronize()
+        for x, y in zip(a, b[:4]):
+            assert torch.equal(x, y)
+        assert torch.equal(ha, b[4])
+        assert torch.equal(pa, pb)
+    assert 0.005 < ha.float().mean().item() < 0.995
