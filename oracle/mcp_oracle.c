@@ -28,6 +28,10 @@
  *     some robot sphere overlaps some obstacle sphere or box.
  *   - the projection's vector-Jacobian product at a point on the manifold:
  *     v = g - J^T (J J^T)^{-1} J g (the tangent-space projector).
+ *   - ParallelConstrainedExtend of Algorithm 2: steer, project particles
+ *     around q_steer (the earliest converged one wins), the 2 dist and r / n
+ *     early exits, interpolation between q_s and q_proj, recursive bisection
+ *     until the resolution is met, collision checks of every projected point.
  *
  * Conventions (shared with the input generators, not with the CUDA code):
  *   3x4 transforms are 12 doubles, row-major, column 3 = translation.
@@ -687,6 +691,137 @@ static int check_one(const or_robot *rb, const double *q, int n_obs, const doubl
   return hit;
 }
 
+
+/* ------------------------------------------------------------------------ */
+/* ParallelConstrainedExtend (Algorithm 2) for one extension.               */
+/* The particles and the interpolated points are projected one by one (each */
+/* with its own exit); the lockstep early exits of the algorithm become:    */
+/* the projection of the particles succeeds if some particle converges no   */
+/* later than the first step that exceeds MaxDistance (the convergence test */
+/* of an iteration precedes its step), and the winner is the particle that  */
+/* converged after the fewest steps (lowest index on ties).                 */
+/* ------------------------------------------------------------------------ */
+enum {
+  OR_EXT_OK = 0, OR_EXT_DEGENERATE = 1, OR_EXT_NO_PROJECTION = 2, OR_EXT_PROJ_COLLISION = 3, OR_EXT_TOO_FAR = 4,
+  OR_EXT_INTERP_FAIL = 5, OR_EXT_GAP = 6, OR_EXT_INTERP_COLLISION = 7, OR_EXT_RESOLUTION = 8
+};
+#define OR_EXT_MAXN 32
+#define OR_EXT_MAXPTS 128   /* points of the validated chain, both ends included */
+
+typedef struct {
+  double r;          /* extension range */
+  double delta;      /* resolution: consecutive validated points at most delta apart */
+  int32_t n;         /* particles = interpolated points (<= 32) */
+  int32_t max_depth; /* bisection levels after the first interpolation */
+} or_ext_params;
+
+static double dist2(int d, const double *a, const double *b) {
+  double s = 0.0;
+  for (int j = 0; j < d; ++j) s += (a[j] - b[j]) * (a[j] - b[j]);
+  return s;
+}
+
+typedef double or_pt[OR_MAXJ];
+
+static int extend_body(const or_robot *rb, const or_constraint *cons, int nc, const or_params *p,
+                       const or_ext_params *e, int n_obs, const double *obs, int n_box, const double *box,
+                       const double *qs, const double *qt, const double *eps, double *q_proj, int *n_points,
+                       int *winner, or_pt *chain, or_pt *next) {
+  const int d = rb->nj, n = e->n;
+  double v[OR_MAXJ], steer[OR_MAXJ], x[OR_MAXJ];
+  *n_points = 0;
+  *winner = -1;
+  for (int j = 0; j < d; ++j) q_proj[j] = qs[j];
+  double len = sqrt(dist2(d, qt, qs));
+  if (!(len > 0.0)) return OR_EXT_DEGENERATE;
+  double dist = len < e->r ? len : e->r;
+  for (int j = 0; j < d; ++j) {
+    v[j] = (qt[j] - qs[j]) / len;
+    steer[j] = qs[j] + dist * v[j];
+  }
+  /* particles around q_steer along v; the earliest converged one */
+  int best = -1, best_it = 1 << 30, first_div = 1 << 30;
+  double qp[OR_MAXJ];
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < d; ++j) x[j] = steer[j] + eps[i] * v[j];
+    int it = 0;
+    double res = 0.0;
+    int f = project_one(rb, cons, nc, p, x, &it, &res);
+    if ((f & OR_CONVERGED) && it < best_it) {
+      best = i;
+      best_it = it;
+      memcpy(qp, x, sizeof(double) * d);
+    }
+    if ((f & OR_DIVERGED) && it < first_div) first_div = it;
+  }
+  if (best < 0 || first_div < best_it) return OR_EXT_NO_PROJECTION;
+  *winner = best;
+  memcpy(q_proj, qp, sizeof(double) * d);
+  *n_points = 1;
+  if (check_one(rb, qp, n_obs, obs, n_box, box, NULL)) return OR_EXT_PROJ_COLLISION;
+  if (sqrt(dist2(d, qp, qs)) > 2.0 * dist) return OR_EXT_TOO_FAR;
+  /* n points between q_s and q_proj, projected; chain q_s, x_1 .. x_n, q_proj */
+  int m = 0;
+  memcpy(chain[m++], qs, sizeof(double) * d);
+  for (int k = 1; k <= n; ++k) {
+    double t = (double)k / (double)(n + 1);
+    for (int j = 0; j < d; ++j) x[j] = qs[j] + t * (qp[j] - qs[j]);
+    int it = 0;
+    double res = 0.0;
+    int f = project_one(rb, cons, nc, p, x, &it, &res);
+    if (!(f & OR_CONVERGED)) return OR_EXT_INTERP_FAIL;
+    memcpy(chain[m++], x, sizeof(double) * d);
+  }
+  memcpy(chain[m++], qp, sizeof(double) * d);
+  *n_points += n;
+  for (int k = 0; k + 1 < m; ++k)
+    if (sqrt(dist2(d, chain[k], chain[k + 1])) > e->r / n) return OR_EXT_GAP;
+  for (int k = 1; k + 1 < m; ++k)
+    if (check_one(rb, chain[k], n_obs, obs, n_box, box, NULL)) return OR_EXT_INTERP_COLLISION;
+  /* bisect every gap above the resolution, level by level: the midpoint's
+   * projection must converge, split the gap into two no longer than it, and
+   * be collision-free */
+  for (int level = 0;; ++level) {
+    int wide = 0;
+    for (int k = 0; k + 1 < m; ++k)
+      if (sqrt(dist2(d, chain[k], chain[k + 1])) > e->delta) ++wide;
+    if (wide == 0) break;
+    if (level >= e->max_depth || m + wide > OR_EXT_MAXPTS) return OR_EXT_RESOLUTION;
+    int m2 = 0;
+    for (int k = 0; k + 1 < m; ++k) {
+      memcpy(next[m2++], chain[k], sizeof(double) * d);
+      double g = sqrt(dist2(d, chain[k], chain[k + 1]));
+      if (g > e->delta) {
+        for (int j = 0; j < d; ++j) x[j] = 0.5 * (chain[k][j] + chain[k + 1][j]);
+        int it = 0;
+        double res = 0.0;
+        int f = project_one(rb, cons, nc, p, x, &it, &res);
+        if (!(f & OR_CONVERGED)) return OR_EXT_INTERP_FAIL;
+        if (sqrt(dist2(d, chain[k], x)) > g || sqrt(dist2(d, x, chain[k + 1])) > g) return OR_EXT_GAP;
+        if (check_one(rb, x, n_obs, obs, n_box, box, NULL)) return OR_EXT_INTERP_COLLISION;
+        memcpy(next[m2++], x, sizeof(double) * d);
+        *n_points += 1;
+      }
+    }
+    memcpy(next[m2++], chain[m - 1], sizeof(double) * d);
+    m = m2;
+    memcpy(chain, next, sizeof(or_pt) * m);
+  }
+  return OR_EXT_OK;
+}
+
+static int extend_one(const or_robot *rb, const or_constraint *cons, int nc, const or_params *p,
+                      const or_ext_params *e, int n_obs, const double *obs, int n_box, const double *box,
+                      const double *qs, const double *qt, const double *eps, double *q_proj, int *n_points,
+                      int *winner) {
+  or_pt *buf = (or_pt *)malloc(sizeof(or_pt) * 2 * OR_EXT_MAXPTS);
+  if (!buf) return OR_EXT_RESOLUTION;
+  int st = extend_body(rb, cons, nc, p, e, n_obs, obs, n_box, box, qs, qt, eps, q_proj, n_points, winner, buf,
+                       buf + OR_EXT_MAXPTS);
+  free(buf);
+  return st;
+}
+
 /* ------------------------------------------------------------------------ */
 /* VJP of the projection at a point on the manifold:                         */
 /*   v = g - J^T (J J^T)^{-1} J g.  Returns 0 if J J^T is singular.          */
@@ -812,6 +947,11 @@ typedef struct {
   /* vjp */
   const double *g;
   double *v;
+  /* extend */
+  const or_ext_params *ep;
+  const double *q_t, *eps;
+  int64_t ld_eps;
+  int32_t *n_points, *winner;
   int mode;
 } or_job;
 
@@ -833,6 +973,17 @@ static void *job_run(void *arg) {
       double m = 0.0;
       jb->hit[i] = (uint8_t)check_one(jb->rb, q, jb->n_obs, jb->obs, jb->n_box, jb->box, &m);
       if (jb->margin) jb->margin[i] = m;
+    } else if (jb->mode == 3) {
+      double qt[OR_MAXJ], eps[OR_EXT_MAXN], qp[OR_MAXJ];
+      for (int j = 0; j < d; ++j) qt[j] = jb->q_t[j * jb->ld + i];
+      for (int k = 0; k < jb->ep->n; ++k) eps[k] = jb->eps[k * jb->ld_eps + i];
+      int np = 0, w = -1;
+      int st = extend_one(jb->rb, jb->cons, jb->nc, jb->p, jb->ep, jb->n_obs, jb->obs, jb->n_box, jb->box, q, qt,
+                          eps, qp, &np, &w);
+      for (int j = 0; j < d; ++j) jb->q_out[j * jb->ld + i] = qp[j];
+      jb->flags[i] = (uint8_t)st;
+      jb->n_points[i] = np;
+      jb->winner[i] = w;
     } else {
       for (int j = 0; j < d; ++j) g[j] = jb->g[j * jb->ld + i];
       int ok = vjp_one(jb->rb, jb->cons, jb->nc, q, g, v);
@@ -893,4 +1044,20 @@ void or_vjp(const or_robot *rb, const or_constraint *cons, int nc, int64_t n, in
   jb.rb = rb; jb.cons = cons; jb.nc = nc; jb.ld = ld; jb.q_in = q; jb.g = g; jb.v = v; jb.flags = flags;
   jb.mode = 2;
   run_jobs(jb, n, nthreads);
+}
+
+/* ParallelConstrainedExtend of n_ext extensions (SoA): q_s, q_t [d * ld],
+ * eps [n * ld_eps] (particle offsets along the extension direction);
+ * outputs q_proj [d * ld], status [n_ext], n_points, winner. */
+void or_extend(const or_robot *rb, const or_constraint *cons, int nc, const or_params *p, const or_ext_params *ep,
+               int n_obs, const double *obs, int n_box, const double *box, int64_t n_ext, int64_t ld,
+               const double *q_s, const double *q_t, const double *eps, int64_t ld_eps, double *q_proj,
+               uint8_t *status, int32_t *n_points, int32_t *winner, int nthreads) {
+  or_job jb;
+  memset(&jb, 0, sizeof(jb));
+  jb.rb = rb; jb.cons = cons; jb.nc = nc; jb.p = p; jb.ld = ld; jb.ep = ep;
+  jb.n_obs = n_obs; jb.obs = obs; jb.n_box = n_box; jb.box = box;
+  jb.q_in = q_s; jb.q_t = q_t; jb.eps = eps; jb.ld_eps = ld_eps; jb.q_out = q_proj; jb.flags = status;
+  jb.n_points = n_points; jb.winner = winner; jb.mode = 3;
+  run_jobs(jb, n_ext, nthreads);
 }

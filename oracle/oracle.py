@@ -47,6 +47,16 @@ class _Constraint(ctypes.Structure):
                 ("B", ctypes.c_double * 12)]
 
 
+class _ExtParams(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_double), ("delta", ctypes.c_double), ("n", ctypes.c_int32),
+                ("max_depth", ctypes.c_int32)]
+
+
+# ParallelConstrainedExtend status codes (mcp_oracle.c)
+EXT_OK, EXT_DEGENERATE, EXT_NO_PROJECTION, EXT_PROJ_COLLISION, EXT_TOO_FAR, EXT_INTERP_FAIL, EXT_GAP, \
+    EXT_INTERP_COLLISION, EXT_RESOLUTION = range(9)
+
+
 class _Params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iters", ctypes.c_int32), ("cyclic", ctypes.c_int32),
                 ("lam", ctypes.c_double), ("alpha", ctypes.c_double), ("max_step", ctypes.c_double)]
@@ -84,6 +94,9 @@ def _load():
                                  _dp, _u8p, _dp, ctypes.c_int]
         lib.or_vjp.argtypes = [P(_Robot), P(_Constraint), ctypes.c_int, ctypes.c_int64, ctypes.c_int64, _dp, _dp,
                                _dp, _u8p, ctypes.c_int]
+        lib.or_extend.argtypes = [P(_Robot), P(_Constraint), ctypes.c_int, P(_Params), P(_ExtParams), ctypes.c_int,
+                                  _dp, ctypes.c_int, _dp, ctypes.c_int64, ctypes.c_int64, _dp, _dp, _dp,
+                                  ctypes.c_int64, _dp, _u8p, _ip, _ip, ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -217,6 +230,26 @@ class Oracle:
 
     def project_params(self, q, params, **kw):
         return self.project(q, params.tol, params.max_iters, params.lam, max_step=params.max_step, **kw)
+
+    def extend(self, q_s, q_t, eps, params, r, delta, max_depth=6, threads=None):
+        """ParallelConstrainedExtend (Alg. 2) of each column of q_s towards the
+        same column of q_t; eps [n, n_ext] are the particle offsets along the
+        extension direction.  Returns (q_proj, status, n_points, winner)."""
+        q_s, q_t, eps = _f64(q_s), _f64(q_t), _f64(eps)
+        d, m = q_s.shape
+        n = eps.shape[0]
+        q_proj = np.empty_like(q_s)
+        status = np.zeros(m, np.uint8)
+        n_points = np.zeros(m, np.int32)
+        winner = np.zeros(m, np.int32)
+        p = _Params(tol=params.tol, max_iters=params.max_iters, cyclic=int(bool(getattr(params, "cyclic", False))),
+                    lam=params.lam, alpha=1.0, max_step=params.max_step)
+        ep = _ExtParams(r=r, delta=delta, n=n, max_depth=max_depth)
+        _load().or_extend(ctypes.byref(self._robot), self._cons, self.nc, ctypes.byref(p), ctypes.byref(ep),
+                          self._obs.shape[0], _ptr(self._obs), self._box.shape[0], _ptr(self._box), m, m,
+                          _ptr(q_s), _ptr(q_t), _ptr(eps), m, _ptr(q_proj), _ptr(status, _u8p), _ptr(n_points, _ip),
+                          _ptr(winner, _ip), threads or default_threads())
+        return q_proj, status, n_points, winner
 
     def check(self, q, threads=None):
         q = _f64(q)

@@ -436,6 +436,32 @@ def dual_rod_workload(seed: int = 1009, n: int = 65536, n_obstacles: int = 128, 
     return wl
 
 
+def extend_workload(seed: int = 1010, n_ext: int = 4096, n: int = 8, r: float = 0.3, delta: float = 0.02,
+                    sigma: float = 0.05, n_obstacles: int = 32, batch_seed: int | None = None) -> Workload:
+    """Batched ParallelConstrainedExtend (Alg. 2) on the dual-arm closed chain
+    of `dual_arm_workload` (relative end-effector pose fixed at its q_ref):
+    n_ext extensions, each from a start on the manifold towards a random
+    target, with n particles and n interpolated points, range r, resolution
+    delta and particle offsets eps ~ N(0, sigma^2) along the extension
+    direction (the random numbers of Alg. 2, drawn here and passed to both
+    sides).  `extra['raw_start']` holds q_ref + N(0, 0.2^2) starts that are
+    projected before use; targets are q_ref + U(-1, 1)^14.  MaxDistance 1.0;
+    obstacles: spheres 1 .. n_obstacles of the dual-arm scene (its first
+    sphere sits where the right arm is at q_ref, which would put most starts
+    in collision)."""
+    base = dual_arm_workload(total=10)
+    q_ref = base.extra["q_ref"]
+    rng = np.random.default_rng(seed if batch_seed is None else batch_seed)
+    raw_start = q_ref[:, None] + 0.2 * rng.standard_normal((14, n_ext))
+    target = q_ref[:, None] + rng.uniform(-1.0, 1.0, size=(14, n_ext))
+    eps = sigma * rng.standard_normal((n, n_ext))
+    obst = Obstacles(spheres=base.obstacles.spheres[1:1 + n_obstacles].copy(), aabbs=np.zeros((0, 6)))
+    wl = Workload(name="extend", robot=base.robot, constraints=base.constraints, obstacles=obst,
+                  params=Params(tol=1e-5, max_iters=30, lam=1e-6, pivot_fp64=1e-7, max_step=1.0))
+    wl.extra.update(raw_start=raw_start, target=target, eps=eps, r=r, delta=delta, n=n, q_ref=q_ref)
+    return wl
+
+
 def make_segments(start: np.ndarray, direction: np.ndarray, lengths: np.ndarray, step: float) -> Segments:
     """Segments from (projected) starts and (unit) directions."""
     return Segments(start=np.ascontiguousarray(start, dtype=np.float64),

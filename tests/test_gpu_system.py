@@ -182,4 +182,3 @@ def test_project_check_equals_separate_calls(mcproj, name):
             assert torch.equal(x, y)
         assert torch.equal(ha, b[4])
         assert torch.equal(pa, pb)
-    assert 0.005 < ha.float().mean().item() < 0.995

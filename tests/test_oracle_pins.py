@@ -747,3 +747,95 @@ def test_cyclic_sweep_is_sequential_on_coupled_constraints():
     assert (fl & orc.CONVERGED).all()
     np.testing.assert_allclose(na @ (out - ca[:, None]), 0.0, atol=1e-10)
     np.testing.assert_allclose(nb @ (out - cb[:, None]), 0.0, atol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# ParallelConstrainedExtend (Algorithm 2) on the unit sphere: with lambda = 0
+# one Newton step on ||q|| - 1 is the radial projection q / ||q||, so every
+# particle converges after one step (the lowest index wins), each projected
+# point is a normalised chord point, and a bisection midpoint is the exact
+# angular bisector of its gap.
+# ---------------------------------------------------------------------------
+def _sphere_extend_setup(n=8):
+    wl = W.sphere_workload(n_pairs=2)
+    rb = wl.robot
+    cons = wl.constraints
+    p = W.Params(tol=1e-12, max_iters=20, lam=0.0)
+    return rb, cons, p, n
+
+
+def _unit(v):
+    return v / np.linalg.norm(v)
+
+
+def _expected(qs, qp, n, r, delta):
+    """(status, points) from the geometry of the arc: the n interpolated
+    points sit at angles atan2(t sin th, (1 - t) + t cos th), t = k / (n + 1),
+    along the great circle from q_s to q_proj; a chord longer than r / n is a
+    GAP exit after 1 + n points; otherwise a gap of angle phi needs 2^L - 1
+    bisection midpoints, L the least level with 2 sin(phi / 2^(L + 1)) <= delta."""
+    ang = [0.0]
+    th = math.acos(np.clip(qs @ qp, -1, 1))
+    for k in range(1, n + 1):
+        t = k / (n + 1)
+        ang.append(math.atan2(t * math.sin(th), (1 - t) + t * math.cos(th)))
+    ang.append(th)
+    gaps = [b - a for a, b in zip(ang[:-1], ang[1:])]
+    if max(2 * math.sin(g / 2) for g in gaps) > r / n:
+        return orc.EXT_GAP, 1 + n
+    total = 1 + n
+    for phi in gaps:
+        L = 0
+        while 2 * math.sin(phi / 2 ** (L + 1)) > delta:
+            L += 1
+        total += 2 ** L - 1
+    return orc.EXT_OK, total
+
+
+def test_extend_on_sphere_closed_form():
+    rb, cons, p, n = _sphere_extend_setup()
+    o = orc.Oracle(rb, cons)
+    rng = np.random.default_rng(60)
+    m = 24
+    qs = np.stack([_unit(rng.standard_normal(3)) for _ in range(m)], 1)
+    qt = np.stack([_unit(rng.standard_normal(3)) for _ in range(m)], 1) * 1.3
+    eps = 0.03 * rng.standard_normal((n, m))
+    r, delta = 0.5, 0.03
+    qp, st, npts, win = o.extend(qs, qt, eps, p, r, delta)
+    seen = set()
+    for i in range(m):
+        v = qt[:, i] - qs[:, i]
+        dist = min(np.linalg.norm(v), r)
+        v = v / np.linalg.norm(v)
+        expect = _unit(qs[:, i] + (dist + eps[0, i]) * v)
+        assert win[i] == 0
+        np.testing.assert_allclose(qp[:, i], expect, atol=1e-14)
+        status, points = _expected(qs[:, i], expect, n, r, delta)
+        assert st[i] == status and npts[i] == points, (i, st[i], status, npts[i], points)
+        seen.add(int(st[i]))
+    assert seen == {orc.EXT_OK, orc.EXT_GAP}
+
+
+def test_extend_exits():
+    rb, cons, p, n = _sphere_extend_setup()
+    qs = np.array([[1.0], [0.0], [0.0]])
+    qt = np.array([[0.0], [1.0], [0.0]])
+    eps = np.zeros((n, 1))
+    # q_t = q_s
+    assert orc.Oracle(rb, cons).extend(qs, qs, eps, p, 0.5, 0.05)[1][0] == orc.EXT_DEGENERATE
+    # every particle's first step exceeds MaxDistance
+    p_div = W.Params(tol=1e-12, max_iters=20, lam=0.0, max_step=1e-6)
+    assert orc.Oracle(rb, cons).extend(qs, qt, eps, p_div, 0.5, 0.05)[1][0] == orc.EXT_NO_PROJECTION
+    # the winning particle lands more than 2 dist from q_s
+    far = np.full((n, 1), 1.5)
+    assert orc.Oracle(rb, cons).extend(qs, qt, far, p, 0.2, 0.05)[1][0] == orc.EXT_TOO_FAR
+    # an obstacle on q_proj, then one on the arc between q_s and q_proj
+    dist = 0.5
+    qproj = _unit(qs[:, 0] + dist * _unit(qt[:, 0] - qs[:, 0]))
+    hit = W.Obstacles(spheres=np.array([[*qproj, 0.01]]), aabbs=np.zeros((0, 6)))
+    assert orc.Oracle(rb, cons, hit).extend(qs, qt, eps, p, dist, 0.05)[1][0] == orc.EXT_PROJ_COLLISION
+    mid = _unit(qs[:, 0] + qproj)
+    hit2 = W.Obstacles(spheres=np.array([[*mid, 0.01]]), aabbs=np.zeros((0, 6)))
+    assert orc.Oracle(rb, cons, hit2).extend(qs, qt, eps, p, dist, 0.05)[1][0] == orc.EXT_INTERP_COLLISION
+    # no resolution within the depth cap
+    assert orc.Oracle(rb, cons).extend(qs, qt, eps, p, dist, 1e-4, max_depth=2)[1][0] == orc.EXT_RESOLUTION
