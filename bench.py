@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="arm", choices=["arm", "dual_arm", "dual_segments", "sphere", "humanoid",
-                                                          "arm_tray", "arm_peg", "arm_tsr", "dual_rod"])
+                                                          "arm_tray", "arm_peg", "arm_tsr", "dual_rod", "extend"])
     ap.add_argument("--cyclic", action="store_true",
                     help="cyclic getDescentStep (one LM step per constraint per sweep) instead of the stacked step")
     ap.add_argument("--cap", type=int, default=0, help="iteration cap (default: the workload's)")
@@ -184,6 +184,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.workload == "extend":
+        return run_reference_extend(args)
     wl, q, wname, segs = make_workload(args.workload, 0)
     wname = apply_overrides(wl, wname, args)
     if q is None:
@@ -214,6 +216,38 @@ def run_reference(args):
                        "cap": p.max_iters},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{sample} configurations per step, projection + collision check"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_extend(args):
+    """Reference arm of the extend workload: the oracle's Alg. 2 on the host
+    cores, 1024 extensions per step."""
+    from oracle import oracle as orc
+    from paper_2604_13323_gb300 import workloads as W
+    wl = W.extend_workload(n_ext=EXT_N)
+    ex, p = wl.extra, wl.params
+    O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
+    threads = orc.default_threads()
+    qs = O.project(ex["raw_start"], p.tol, p.max_iters, p.lam, threads=threads)[0]
+    sample = 1024
+    times, pts = [], []
+    for s in range(args.warmup + args.steps):
+        sl = slice((s * sample) % EXT_N, (s * sample) % EXT_N + sample)
+        t0 = time.perf_counter()
+        res = O.extend(qs[:, sl], ex["target"][:, sl], ex["eps"][:, sl], p, ex["r"], ex["delta"], threads=threads)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            pts.append(int(res[2].sum()))
+    total = sum(times)
+    value = sum(pts) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"dual14_rel_extend_{EXT_N}", "extensions_per_step": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{sample} extensions per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -482,10 +516,151 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+EXT_N = 16384   # extensions per step of the extend workload
+
+
+def run_extend(args):
+    """Batched ParallelConstrainedExtend (Alg. 2) on the dual arm: one step is
+    one call extending EXT_N starts towards their targets; the metric counts
+    the projected points that converged and passed validation (q_proj, the
+    interpolated points and the bisection midpoints)."""
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2604_13323_gb300 import build as B
+    B.build()
+    from paper_2604_13323_gb300 import flops as FL
+    from paper_2604_13323_gb300 import mcproj
+    from paper_2604_13323_gb300 import workloads as W
+
+    wl = W.extend_workload(n_ext=EXT_N, batch_seed=None if rank == 0 else 1010 + 1000 * rank)
+    ex, p = wl.extra, wl.params
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles, device=local)
+    stream = torch.cuda.current_stream(dev)
+    # starts on the manifold (setup, untimed)
+    q_s = P.project(torch.tensor(ex["raw_start"], dtype=torch.float32, device=dev), p)[0].contiguous()
+    q_t = torch.tensor(ex["target"], dtype=torch.float32, device=dev)
+    eps = torch.tensor(ex["eps"], dtype=torch.float32, device=dev)
+    outs = (torch.empty_like(q_s), torch.empty(EXT_N, dtype=torch.uint8, device=dev),
+            torch.empty(EXT_N, dtype=torch.int32, device=dev), torch.empty(EXT_N, dtype=torch.int32, device=dev))
+    steps = torch.empty(EXT_N, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        P.extend(q_s, q_t, eps, p, ex["r"], ex["delta"], steps=steps, out=outs, stream=stream)
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    with sampler:
+        t0 = time.perf_counter()
+        w = 0
+        while w < args.warmup or (not args.profile and time.perf_counter() - t0 < 1.5):
+            flush.zero_()
+            step()
+            w += 1
+            if w % 16 == 0:
+                torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        launches0 = P.launches
+        for s_ in range(args.steps):
+            flush.zero_()
+            evs[s_][0].record(stream)
+            step()
+            evs[s_][1].record(stream)
+        torch.cuda.synchronize()
+    launches = P.launches - launches0
+    ms = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
+    st = outs[1].cpu().numpy()
+    npts = outs[2].cpu().numpy()
+    total_steps = float(steps.double().sum().item())
+    pts = int(npts.sum())
+    ms_max, c_total = aggregate_replicas(ms, pts, world, dev)
+    value = c_total / (ms_max * 1e-3)
+    # end to end: the step's inputs from pinned host memory, outputs back
+    host_in = [t.cpu().pin_memory() for t in (q_s, q_t, eps)]
+    host_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs]
+    e2e_ms = []
+    for s_ in range(0 if args.profile else args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for hi, di in zip(host_in, (q_s, q_t, eps)):
+            di.copy_(hi, non_blocking=True)
+        step()
+        for ho, do in zip(host_out, outs):
+            ho.copy_(do, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if s_ >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e = None
+    if e2e_ms:
+        e_ms, e_c = aggregate_replicas(sum(e2e_ms) / len(e2e_ms), int(host_out[2].numpy().sum()), world, dev)
+        e2e = {"value": e_c / (e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in host_in),
+               "d2h_bytes_per_step": sum(t.numel() * t.element_size() for t in host_out)}
+    # roofline: Newton steps and evaluations of every projection the kernel ran
+    fm = FL.FlopModel(wl.robot, wl.constraints)
+    clk = sampler.summary()
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    props = torch.cuda.get_device_properties(dev)
+    peak32 = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    fp32 = total_steps * fm.iteration
+    ach = fp32 / (ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s", "frac": ach / peak32,
+            "traffic": None, "kernel": "k_extend (warp per extension: particles, interpolation, bisection)",
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
+            "counted": "FP32 Newton steps of all projections x the step's flops (evaluations, FP64 "
+                       "acceptance and collision checks not counted)",
+            "newton_steps_per_step": total_steps}
+    cpu = None
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.profile):
+        from oracle import oracle as orc
+        O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
+        qs_np = q_s.double().cpu().numpy()
+        t0 = time.perf_counter()
+        done = pts_c = 0
+        while time.perf_counter() - t0 < 10.0:
+            sl = slice(done % EXT_N, done % EXT_N + 1024)
+            res = O.extend(qs_np[:, sl], ex["target"][:, sl], ex["eps"][:, sl], p, ex["r"], ex["delta"])
+            pts_c += int(res[2].sum())
+            done += 1024
+        dt = time.perf_counter() - t0
+        cpu = {"value": pts_c / dt, "unit": UNIT, "cores": orc.default_threads(), "kind": "oracle",
+               "sample": f"{done} extensions (chunks of 1024 of the bench batch), FP64, {dt:.1f} s wall"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"dual14_rel_extend_{EXT_N}", "extensions": EXT_N, "n": ex["n"],
+                           "r": ex["r"], "delta": ex["delta"], "max_step": p.max_step, "tol": p.tol,
+                           "cap": p.max_iters, "l2": "flushed between timed steps (512 MB write)",
+                           "parallelism": f"replicas x{world}", "validated_points_per_step": pts,
+                           "extensions_per_s": EXT_N * world / (ms_max * 1e-3),
+                           "status_hist": np.bincount(st, minlength=9).tolist(),
+                           "kernel_ms": {"extend": ms}},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    P.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "extend":
+        run_extend(args)
     else:
         run_ours(args)
 

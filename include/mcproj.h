@@ -192,6 +192,49 @@ mcp_status mcp_project_check_batch(mcp_ctx *ctx, const mcp_project_params *p, in
                                    const void *q_in, void *q_out, uint8_t *flags, uint8_t *iters, double *resid,
                                    uint8_t *in_collision, uint32_t *pairs_tested, mcp_stream stream);
 
+/* ParallelConstrainedExtend (Algorithm 2), one call for n_ext extensions.
+ * Extension x starts at q_s[:, x] (on the manifold, collision-free by the
+ * caller's construction) towards q_t[:, x]: dist = min(|q_t - q_s|, r),
+ * v = (q_t - q_s) / |q_t - q_s|, q_steer = q_s + dist v; the n particles
+ * q_steer + eps[i, x] v (eps: the N(0, sigma^2) offsets of Alg. 2, drawn by
+ * the caller) are projected and the one that converged after the fewest steps
+ * (lowest index on ties) is q_proj, unless a particle's step exceeded
+ * MaxDistance (p->max_step) earlier.  q_proj must be collision-free and within
+ * 2 dist of q_s; n points interpolated between q_s and q_proj are projected,
+ * no two consecutive points of q_s, x_1 .. x_n, q_proj may be more than r / n
+ * apart and none may collide; then every gap above delta is bisected (the
+ * midpoint projected, its two gaps no longer than the gap, collision-free),
+ * level by level, until all gaps are at most delta (at most max_depth levels
+ * and 128 points).  Each particle and point is projected on its own (FP32
+ * steps, FP64 acceptance, p->tol / max_iters / lambda / pivot_fp64).
+ * DEVICE buffers: q_s, q_t, q_proj float [d * ld]; eps float [n * ld_eps];
+ * status [n_ext] uint8 (MCP_EXT_*); n_points [n_ext] int32: points projected
+ * and validated (q_proj, interpolated, midpoints) before the outcome;
+ * winner [n_ext] int32: the particle index (-1 if none); steps [n_ext]
+ * int32 or NULL: Newton steps taken by all projections of the extension
+ * (work accounting).  Requires
+ * obstacles; precision 0 and the stacked step only; MCP_ERR_UNSUPPORTED for
+ * problem classes without the extension kernel (the humanoid). */
+#define MCP_EXT_OK 0
+#define MCP_EXT_DEGENERATE 1         /* q_t == q_s */
+#define MCP_EXT_NO_PROJECTION 2      /* no particle converged before one diverged (or at the cap) */
+#define MCP_EXT_PROJ_COLLISION 3     /* q_proj in collision */
+#define MCP_EXT_TOO_FAR 4            /* |q_proj - q_s| > 2 dist */
+#define MCP_EXT_INTERP_FAIL 5        /* an interpolated point or midpoint did not converge */
+#define MCP_EXT_GAP 6                /* consecutive projected points too far apart */
+#define MCP_EXT_INTERP_COLLISION 7   /* an interpolated point or midpoint in collision */
+#define MCP_EXT_RESOLUTION 8         /* delta not reached within max_depth levels / 128 points */
+typedef struct {
+  double r;           /* extension range */
+  double delta;       /* resolution of the validated chain */
+  int32_t n;          /* particles = interpolated points, 1..32 */
+  int32_t max_depth;  /* bisection levels, 0..16 */
+} mcp_extend_params;
+mcp_status mcp_extend_batch(mcp_ctx *ctx, const mcp_project_params *p, const mcp_extend_params *e, int64_t n_ext,
+                            int64_t ld, const float *q_s, const float *q_t, const float *eps, int64_t ld_eps,
+                            float *q_proj, uint8_t *status, int32_t *n_points, int32_t *winner, int32_t *steps,
+                            mcp_stream stream);
+
 /* Projection of uneven interpolation segments in one persistent launch
  * (Alg. 2: n points interpolated between q_s and q_proj are projected in
  * parallel).  Point t of segment s is start[:, s] + t * delta[:, s],

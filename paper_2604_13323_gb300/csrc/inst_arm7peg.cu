@@ -3,4 +3,5 @@
 
 namespace mcp {
 MCP_INSTANTIATE(ProbArm7Peg)
+MCP_NO_EXTEND(ProbArm7Peg)
 }  // namespace mcp

@@ -3,4 +3,5 @@
 
 namespace mcp {
 MCP_INSTANTIATE(ProbArm7Pose)
+MCP_NO_EXTEND(ProbArm7Pose)
 }  // namespace mcp

@@ -3,4 +3,5 @@
 
 namespace mcp {
 MCP_INSTANTIATE(ProbArm7Tray)
+MCP_NO_EXTEND(ProbArm7Tray)
 }  // namespace mcp

@@ -3,4 +3,5 @@
 
 namespace mcp {
 MCP_INSTANTIATE(ProbArm7Tsr)
+MCP_NO_EXTEND(ProbArm7Tsr)
 }  // namespace mcp

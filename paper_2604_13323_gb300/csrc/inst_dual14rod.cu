@@ -3,4 +3,5 @@
 
 namespace mcp {
 MCP_INSTANTIATE(ProbDual14Rod)
+MCP_NO_EXTEND(ProbDual14Rod)
 }  // namespace mcp

@@ -31,4 +31,6 @@ cudaError_t launch_vjp<ProbHumanoid36>(const HostModel &, const VjpCall &, int *
   return cudaErrorNotSupported;
 }
 
+MCP_NO_EXTEND(ProbHumanoid36)
+
 }  // namespace mcp

@@ -33,6 +33,7 @@ struct ClassDesc {
   cudaError_t (*project_fn)(const HostModel &, const ProjCall &, int *);
   cudaError_t (*check_fn)(const HostModel &, const CheckCall &, int *);
   cudaError_t (*vjp_fn)(const HostModel &, const VjpCall &, int *);
+  cudaError_t (*extend_fn)(const HostModel &, const ExtCall &, int *);
 };
 
 template <class P>
@@ -62,6 +63,7 @@ ClassDesc describe(bool project) {
   d.project_fn = &launch_project<P>;
   d.check_fn = &launch_check<P>;
   d.vjp_fn = &launch_vjp<P>;
+  d.extend_fn = &launch_extend<P>;
   return d;
 }
 
@@ -1020,6 +1022,59 @@ mcp_status mcp_project_check_batch(mcp_ctx *ctx, const mcp_project_params *p, in
   cudaError_t e = run_project_check(ctx, c, &launches);
   ctx->launches += launches;
   if (e != cudaSuccess) return cuda_fail(ctx, e, "project_check_batch launch");
+  return MCP_OK;
+}
+
+mcp_status mcp_extend_batch(mcp_ctx *ctx, const mcp_project_params *p, const mcp_extend_params *e, int64_t n_ext,
+                            int64_t ld, const float *q_s, const float *q_t, const float *eps, int64_t ld_eps,
+                            float *q_proj, uint8_t *status, int32_t *n_points, int32_t *winner, int32_t *steps,
+                            mcp_stream stream) {
+  if (!ctx) return MCP_ERR_ARG;
+  mcp_status st = validate_params(ctx, p);
+  if (st != MCP_OK) return st;
+  if (!e) return fail(ctx, MCP_ERR_ARG, "extend params is NULL");
+  if (p->precision != 0) return fail(ctx, MCP_ERR_ARG, "the extension runs the FP32 path (precision 0)");
+  if (p->cyclic != 0) return fail(ctx, MCP_ERR_ARG, "the extension uses the stacked step");
+  if (!ctx->obs_loaded) return fail(ctx, MCP_ERR_STATE, "obstacles must be loaded");
+  if (e->n < 1 || e->n > 32) return fail(ctx, MCP_ERR_ARG, "n = %d outside [1, 32]", e->n);
+  if (!(e->r > 0.0) || !(e->delta > 0.0) || !std::isfinite(e->r) || !std::isfinite(e->delta))
+    return fail(ctx, MCP_ERR_ARG, "r and delta must be positive");
+  if (e->max_depth < 0 || e->max_depth > 16) return fail(ctx, MCP_ERR_ARG, "max_depth %d outside [0, 16]", e->max_depth);
+  if (n_ext < 0 || ld < n_ext || ld_eps < n_ext) return fail(ctx, MCP_ERR_ARG, "need 0 <= n_ext <= ld, ld_eps");
+  if (n_ext == 0) return MCP_OK;
+  const char *names[7] = {"q_s", "q_t", "eps", "q_proj", "status", "n_points", "winner"};
+  const void *ptrs[7] = {q_s, q_t, eps, q_proj, status, n_points, winner};
+  for (int i = 0; i < 7; ++i)
+    if ((st = check_batch_ptr(ctx, ptrs[i], names[i])) != MCP_OK) return st;
+  if (steps && (st = check_batch_ptr(ctx, steps, "steps")) != MCP_OK) return st;
+  DeviceGuard g(ctx->device);
+  ExtCall c;
+  c.tol = p->tol;
+  c.cap = p->max_iters;
+  c.lambda = p->lambda;
+  c.max_step = p->max_step;
+  c.pivot = p->pivot_fp64;
+  c.r = e->r;
+  c.delta = e->delta;
+  c.n = e->n;
+  c.max_depth = e->max_depth;
+  c.n_ext = n_ext;
+  c.ld = ld;
+  c.ld_eps = ld_eps;
+  c.q_s = q_s;
+  c.q_t = q_t;
+  c.eps = eps;
+  c.q_proj = q_proj;
+  c.status = status;
+  c.n_points = n_points;
+  c.winner = winner;
+  c.steps = steps;
+  c.counter = ctx->d_counter;
+  c.stream = reinterpret_cast<cudaStream_t>(stream);
+  int launches = 0;
+  cudaError_t err = registry()[ctx->prob_class].extend_fn(ctx->hm, c, &launches);
+  ctx->launches += launches;
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "extend_batch launch");
   return MCP_OK;
 }
 

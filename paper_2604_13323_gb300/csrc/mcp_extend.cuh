@@ -1,0 +1,368 @@
+// Batched ParallelConstrainedExtend (Algorithm 2): one warp per extension, its
+// lanes playing the paper's SIMD lanes.  Lanes hold the n particles around
+// q_steer, then the n points interpolated between q_s and q_proj, then the
+// bisection midpoints; every point is projected by the per-thread FP32 Newton
+// loop with FP64 acceptance and collision-checked against the obstacles in
+// shared memory, and the early exits of the algorithm are warp votes.
+//
+// The particles and points are projected each with its own exit.  The
+// lockstep exits of Alg. 2 then read: the particle projection succeeds if some
+// particle converges no later than the first step that exceeds MaxDistance
+// (the convergence test of an iteration precedes its step); the winner is the
+// particle that converged after the fewest steps, the lowest lane on ties.
+#pragma once
+
+#include "mcp_kernels.cuh"
+
+namespace mcp {
+
+constexpr int EXT_MAXPTS = 128;  // points of the validated chain, both ends included
+enum : int {
+  EXT_OK = 0, EXT_DEGENERATE = 1, EXT_NO_PROJECTION = 2, EXT_PROJ_COLLISION = 3, EXT_TOO_FAR = 4,
+  EXT_INTERP_FAIL = 5, EXT_GAP = 6, EXT_INTERP_COLLISION = 7, EXT_RESOLUTION = 8
+};
+
+template <class P>
+struct ExtArgs {
+  ModelT<float> m;
+  const ModelT<double> *__restrict__ m64;
+  const double2 *__restrict__ tab;
+  const CheckData *chk;
+  const float *obs;
+  const float *box;
+  int n_obs;
+  int n_box;
+  const float *q_s;
+  const float *q_t;
+  long long ld;
+  const float *eps;
+  long long ld_eps;
+  float *q_proj;
+  uint8_t *status;
+  int32_t *n_points;
+  int32_t *winner;
+  int32_t *steps;  // optional: Newton steps of all projections of the extension
+  long long n_ext;
+  unsigned long long *counter;
+  int n;
+  int max_depth;
+  float r;
+  float delta;
+  int cap;
+  float tol2;
+  float lambda;
+  float max_step2;
+  float pivot;
+  double tol2_64;
+  double lambda64;
+};
+
+// FP64 acceptance of one FP32 iterate held in registers (accept_one without
+// the global outputs).
+template <class P, class A>
+__device__ __forceinline__ void accept_regs(const A &a, float (&q)[P::D], int &it, uint32_t &fl) {
+  constexpr int D = P::D;
+  double qd[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) qd[j] = static_cast<double>(q[j]);
+  double r2 = residual2_f64<P>(OpsF64Split{a.tab}, *a.m64, qd);
+  if (fl & (FL_INT_FP32CONV | FL_INT_NEEDS_F64)) {
+    const bool was_conv = (fl & FL_INT_FP32CONV) != 0;
+    fl &= ~(FL_INT_FP32CONV | FL_INT_NEEDS_F64);
+    if (r2 < a.tol2_64) {
+      fl |= FL_CONV;
+    } else {
+      float qf[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) qf[j] = q[j];
+      finish_f64<P, false>(a, qf, qd, &it, &fl, r2, was_conv);
+#pragma unroll
+      for (int j = 0; j < D; ++j) q[j] = qf[j];
+    }
+  }
+}
+
+// Projects the point of every active lane (warp-convergent: all lanes call it).
+template <class P, class A>
+__device__ __forceinline__ void project_lanes(const A &a, float (&q)[P::D], bool active, int &it, uint32_t &fl) {
+  it = 0;
+  fl = 0;
+  bool done = !active;
+  while (__any_sync(FULL, !done)) {
+    if (!done) done = newton_iter_f32<P>(a, q, it, fl);
+  }
+  if (active) accept_regs<P>(a, q, it, fl);
+}
+
+template <int D>
+__device__ __forceinline__ float pt_dist(const float *x, const float *y) {
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < D; ++j) s = fmaf(x[j] - y[j], x[j] - y[j], s);
+  return sqrtf(s);
+}
+template <int D>
+__device__ __forceinline__ float pt_dist_r(const float *x, const float (&y)[D]) {
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < D; ++j) s = fmaf(x[j] - y[j], x[j] - y[j], s);
+  return sqrtf(s);
+}
+
+template <class P, int W>
+__global__ void __launch_bounds__(W * 32) k_extend(const __grid_constant__ ExtArgs<P> a) {
+  constexpr int D = P::D;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4 *s_obs = reinterpret_cast<float4 *>(smem_raw);
+  float *s_box = reinterpret_cast<float *>(s_obs + 2 * a.n_obs);
+  float *s_chain = s_box + 6 * a.n_box;
+  stage_obstacles(a.obs, a.n_obs, a.box, a.n_box, s_obs, s_box);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  float *chain = s_chain + static_cast<size_t>(wib) * 2 * EXT_MAXPTS * D;  // [EXT_MAXPTS][D]
+  float *next = chain + EXT_MAXPTS * D;
+  const CheckData &cd = *a.chk;
+  auto collides = [&](const float (&q)[D]) -> bool {
+    uint32_t t = 0;
+    return check_one_f32<P>(cd.m, cd.st, s_obs, a.n_obs, s_box, a.n_box, a.tab, q, t);
+  };
+  while (true) {
+    unsigned long long e = 0;
+    if (lane == 0) e = atomicAdd(a.counter, 1ull);
+    e = __shfl_sync(FULL, e, 0);
+    if (static_cast<long long>(e) >= a.n_ext) break;
+    const long long x = static_cast<long long>(e);
+    float qs[D], qt[D], qp[D], v[D], steer[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      qs[j] = a.q_s[j * a.ld + x];
+      qt[j] = a.q_t[j * a.ld + x];
+      qp[j] = qs[j];
+    }
+    int status = EXT_OK, npts = 0, win = -1;
+    int work = 0;  // this lane's Newton steps
+    float len2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < D; ++j) len2 = fmaf(qt[j] - qs[j], qt[j] - qs[j], len2);
+    const float len = sqrtf(len2);
+    const bool act = lane < a.n;
+    int it = 0;
+    uint32_t fl = 0;
+    if (!(len > 0.f)) {
+      status = EXT_DEGENERATE;
+    } else {
+      // steer and the particles around it along the extension direction
+      const float dist = fminf(len, a.r);
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        v[j] = (qt[j] - qs[j]) / len;
+        steer[j] = fmaf(dist, v[j], qs[j]);
+      }
+      float p[D];
+      const float ep = act ? a.eps[lane * a.ld_eps + x] : 0.f;
+#pragma unroll
+      for (int j = 0; j < D; ++j) p[j] = fmaf(ep, v[j], steer[j]);
+      project_lanes<P>(a, p, act, it, fl);
+      if (act) work += it;
+      constexpr unsigned BIG = 0xffffffffu;
+      const unsigned c = (act && (fl & FL_CONV)) ? static_cast<unsigned>(it) : BIG;
+      const unsigned dv = (act && (fl & FL_DIV)) ? static_cast<unsigned>(it) : BIG;
+      const unsigned minc = __reduce_min_sync(FULL, c), mindv = __reduce_min_sync(FULL, dv);
+      if (minc == BIG || mindv < minc) {
+        status = EXT_NO_PROJECTION;
+      } else {
+        win = __ffs(static_cast<int>(__ballot_sync(FULL, c == minc))) - 1;
+#pragma unroll
+        for (int j = 0; j < D; ++j) qp[j] = __shfl_sync(FULL, p[j], win);
+        npts = 1;
+        float d2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < D; ++j) d2 = fmaf(qp[j] - qs[j], qp[j] - qs[j], d2);
+        if (collides(qp)) {
+          status = EXT_PROJ_COLLISION;
+        } else if (sqrtf(d2) > 2.f * dist) {
+          status = EXT_TOO_FAR;
+        } else {
+          // n points between q_s and q_proj (lane k: t = (k + 1) / (n + 1))
+          const float tk = static_cast<float>(lane + 1) / static_cast<float>(a.n + 1);
+          float xq[D];
+#pragma unroll
+          for (int j = 0; j < D; ++j) xq[j] = fmaf(tk, qp[j] - qs[j], qs[j]);
+          project_lanes<P>(a, xq, act, it, fl);
+          if (act) work += it;
+          if (__any_sync(FULL, act && !(fl & FL_CONV))) {
+            status = EXT_INTERP_FAIL;
+          } else {
+            npts += a.n;
+            // the chain q_s, x_1 .. x_n, q_proj
+            if (lane == 0) {
+#pragma unroll
+              for (int j = 0; j < D; ++j) {
+                chain[j] = qs[j];
+                chain[(a.n + 1) * D + j] = qp[j];
+              }
+            }
+            if (act) {
+#pragma unroll
+              for (int j = 0; j < D; ++j) chain[(lane + 1) * D + j] = xq[j];
+            }
+            __syncwarp();
+            int m = a.n + 2;
+            bool gap = false;
+            for (int k0 = 0; k0 < m - 1; k0 += 32) {
+              const int k = k0 + lane;
+              const bool in = k < m - 1;
+              gap |= __any_sync(FULL, in && pt_dist<D>(chain + k * D, chain + (k + 1) * D) > a.r / a.n);
+            }
+            if (gap) {
+              status = EXT_GAP;
+            } else if (__any_sync(FULL, act && collides(xq))) {
+              status = EXT_INTERP_COLLISION;
+            } else {
+              // bisect every gap above the resolution, level by level
+              for (int level = 0;; ++level) {
+                int wide = 0;
+                for (int k0 = 0; k0 < m - 1; k0 += 32) {
+                  const int k = k0 + lane;
+                  const bool w = k < m - 1 && pt_dist<D>(chain + k * D, chain + (k + 1) * D) > a.delta;
+                  wide += __popc(__ballot_sync(FULL, w));
+                }
+                if (wide == 0) break;
+                if (level >= a.max_depth || m + wide > EXT_MAXPTS) {
+                  status = EXT_RESOLUTION;
+                  break;
+                }
+                int base_w = 0;
+                bool failed = false;
+                for (int k0 = 0; k0 < m - 1 && !failed; k0 += 32) {
+                  const int k = k0 + lane;
+                  const bool in = k < m - 1;
+                  const float g = in ? pt_dist<D>(chain + k * D, chain + (k + 1) * D) : 0.f;
+                  const bool w = in && g > a.delta;
+                  const unsigned bal = __ballot_sync(FULL, w);
+                  const int pos = k + base_w + __popc(bal & ((1u << lane) - 1u));
+                  float mq[D];
+#pragma unroll
+                  for (int j = 0; j < D; ++j) {
+                    const float lo = in ? chain[k * D + j] : 0.f;
+                    const float hi = in ? chain[(k + 1) * D + j] : 0.f;
+                    if (in) next[pos * D + j] = lo;
+                    mq[j] = 0.5f * (lo + hi);
+                  }
+                  project_lanes<P>(a, mq, w, it, fl);
+                  if (w) work += it;
+                  int code = 0;
+                  if (w) {
+                    if (!(fl & FL_CONV)) code = EXT_INTERP_FAIL;
+                    else if (pt_dist_r<D>(chain + k * D, mq) > g || pt_dist_r<D>(chain + (k + 1) * D, mq) > g)
+                      code = EXT_GAP;
+                    else if (collides(mq)) code = EXT_INTERP_COLLISION;
+                    if (code == 0) {
+#pragma unroll
+                      for (int j = 0; j < D; ++j) next[(pos + 1) * D + j] = mq[j];
+                    }
+                  }
+                  const unsigned fb = __ballot_sync(FULL, code != 0);
+                  if (fb) {
+                    const int fl_lane = __ffs(static_cast<int>(fb)) - 1;
+                    status = __shfl_sync(FULL, code, fl_lane);
+                    npts += base_w + __popc(bal & ((1u << fl_lane) - 1u));
+                    failed = true;
+                  }
+                  base_w += __popc(bal);
+                }
+                if (failed) break;
+                npts += wide;
+                if (lane == 0) {
+#pragma unroll
+                  for (int j = 0; j < D; ++j) next[(m - 1 + wide) * D + j] = chain[(m - 1) * D + j];
+                }
+                __syncwarp();
+                m += wide;
+                float *t = chain;
+                chain = next;
+                next = t;
+              }
+            }
+          }
+        }
+      }
+    }
+    const int work_all = __reduce_add_sync(FULL, work);
+    if (lane == 0) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) a.q_proj[j * a.ld + x] = qp[j];
+      a.status[x] = static_cast<uint8_t>(status);
+      a.n_points[x] = npts;
+      a.winner[x] = win;
+      if (a.steps) a.steps[x] = work_all;
+    }
+    __syncwarp();
+  }
+}
+
+template <class P>
+cudaError_t launch_extend_impl(const HostModel &hm, const ExtCall &c, int *launches) {
+  if (c.n_ext <= 0) return cudaSuccess;
+  constexpr int W = 2;
+  ExtArgs<P> a;
+  a.m = hm.m32;
+  a.m64 = hm.d_m64;
+  a.tab = hm.d_tab;
+  a.chk = hm.d_chk;
+  a.obs = reinterpret_cast<const float *>(hm.d_obs32);
+  a.box = hm.d_box32;
+  a.n_obs = hm.n_obs;
+  a.n_box = hm.n_box;
+  a.q_s = c.q_s;
+  a.q_t = c.q_t;
+  a.ld = c.ld;
+  a.eps = c.eps;
+  a.ld_eps = c.ld_eps;
+  a.q_proj = c.q_proj;
+  a.status = c.status;
+  a.n_points = c.n_points;
+  a.winner = c.winner;
+  a.steps = c.steps;
+  a.n_ext = c.n_ext;
+  a.counter = c.counter;
+  a.n = c.n;
+  a.max_depth = c.max_depth;
+  a.r = static_cast<float>(c.r);
+  a.delta = static_cast<float>(c.delta);
+  a.cap = c.cap;
+  a.tol2 = static_cast<float>(c.tol * c.tol);
+  a.lambda = static_cast<float>(c.lambda);
+  a.max_step2 = c.max_step > 0 ? static_cast<float>(c.max_step * c.max_step) : 0.f;
+  a.pivot = static_cast<float>(c.pivot);
+  a.tol2_64 = c.tol * c.tol;
+  a.lambda64 = c.lambda;
+  const size_t smem = sizeof(float) * (8 * hm.n_obs + 6 * hm.n_box) + sizeof(float) * W * 2 * EXT_MAXPTS * P::D;
+  cudaError_t err = cudaSuccess;
+  if (smem > 48 * 1024)
+    err = cudaFuncSetAttribute(k_extend<P, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (err != cudaSuccess) return err;
+  int per_sm = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_extend<P, W>, W * 32, smem);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long blocks = static_cast<long long>(hm.sm_count) * per_sm;
+  const long long need = (c.n_ext + W - 1) / W;
+  if (blocks > need) blocks = need;
+  err = cudaMemsetAsync(c.counter, 0, sizeof(unsigned long long), c.stream);
+  if (err != cudaSuccess) return err;
+  k_extend<P, W><<<static_cast<unsigned>(blocks), W * 32, smem, c.stream>>>(a);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace mcp
+
+#define MCP_INSTANTIATE_EXTEND(P)                                                                \
+  namespace mcp {                                                                                \
+  template <>                                                                                    \
+  cudaError_t launch_extend<P>(const HostModel &hm, const ExtCall &c, int *launches) {            \
+    return launch_extend_impl<P>(hm, c, launches);                                               \
+  }                                                                                              \
+  }

@@ -106,6 +106,27 @@ struct VjpCall {
   cudaStream_t stream = 0;
 };
 
+struct ExtCall {
+  double tol = 1e-5;
+  int cap = 30;
+  double lambda = 0.0;
+  double max_step = 0.0;
+  double pivot = 1e-7;
+  double r = 0.3, delta = 0.02;
+  int n = 8, max_depth = 6;
+  long long n_ext = 0, ld = 0, ld_eps = 0;
+  const float *q_s = nullptr;
+  const float *q_t = nullptr;
+  const float *eps = nullptr;
+  float *q_proj = nullptr;
+  uint8_t *status = nullptr;
+  int32_t *n_points = nullptr;
+  int32_t *winner = nullptr;
+  int32_t *steps = nullptr;
+  unsigned long long *counter = nullptr;
+  cudaStream_t stream = 0;
+};
+
 // Launchers, one explicit instantiation per problem class.  Each returns the
 // CUDA error of its launch and adds the number of kernels it launched.
 template <class P>
@@ -114,5 +135,7 @@ template <class P>
 cudaError_t launch_check(const HostModel &hm, const CheckCall &c, int *launches);
 template <class P>
 cudaError_t launch_vjp(const HostModel &hm, const VjpCall &c, int *launches);
+template <class P>
+cudaError_t launch_extend(const HostModel &hm, const ExtCall &c, int *launches);
 
 }  // namespace mcp

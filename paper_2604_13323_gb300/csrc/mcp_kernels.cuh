@@ -1665,6 +1665,12 @@ cudaError_t launch_vjp_impl(const HostModel &hm, const VjpCall &c, int *launches
   return cudaGetLastError();
 }
 
+#define MCP_NO_EXTEND(P)                                                                       \
+  template <>                                                                                  \
+  cudaError_t launch_extend<P>(const HostModel &, const ExtCall &, int *) {                     \
+    return cudaErrorNotSupported;                                                              \
+  }
+
 #define MCP_INSTANTIATE_CHECK_ONLY(P)                                                          \
   template <>                                                                                  \
   cudaError_t launch_project<P>(const HostModel &, const ProjCall &, int *) {                   \

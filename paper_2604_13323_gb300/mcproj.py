@@ -17,6 +17,9 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmcproj.so")
 
 MCP_OK, MCP_ERR_ARG, MCP_ERR_STATE, MCP_ERR_CUDA, MCP_ERR_OOM, MCP_ERR_UNSUPPORTED = range(6)
 F_CONVERGED, F_CAP, F_DIVERGED, F_NONFINITE, F_FP64_RESOLVE, F_ACCEPT_FAIL, F_OUT_OF_LIMITS = 1, 2, 4, 8, 16, 32, 64
+# ParallelConstrainedExtend outcomes (MCP_EXT_*)
+EXT_OK, EXT_DEGENERATE, EXT_NO_PROJECTION, EXT_PROJ_COLLISION, EXT_TOO_FAR, EXT_INTERP_FAIL, EXT_GAP, \
+    EXT_INTERP_COLLISION, EXT_RESOLUTION = range(9)
 # constraint kinds (mcp_ckind) and their equation counts
 C_SPHERE, C_AXIS_ALIGN, C_POSE, C_REL_POSE, C_COM_XY, C_PLANE, C_LINE, C_DIST, C_POSE_BOUNDED = range(9)
 C_DIM = {C_SPHERE: 1, C_AXIS_ALIGN: 2, C_POSE: 6, C_REL_POSE: 6, C_COM_XY: 2, C_PLANE: 1, C_LINE: 2, C_DIST: 1,
@@ -38,6 +41,11 @@ class ConstraintDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("frame_a", ctypes.c_int32), ("frame_b", ctypes.c_int32),
                 ("P", ctypes.c_double * 12), ("Q", ctypes.c_double * 12), ("target", ctypes.c_double * 3),
                 ("q_ref", _dp), ("B", ctypes.c_double * 12)]
+
+
+class ExtendParams(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_double), ("delta", ctypes.c_double), ("n", ctypes.c_int32),
+                ("max_depth", ctypes.c_int32)]
 
 
 class ProjectParams(ctypes.Structure):
@@ -82,6 +90,8 @@ def load_library(path: str = LIB_PATH):
         "mcp_autotune": ([_vp, P(ProjectParams), ctypes.c_int64, ctypes.c_int64, _vp, _ip, _ip, _ip, _ip, _vp],
                          ctypes.c_int),
         "mcp_set_tuning": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+        "mcp_extend_batch": ([_vp, P(ProjectParams), P(ExtendParams), ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp,
+                              ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
         "mcp_path_step": ([_vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _vp, _vp, ctypes.c_float,
                            ctypes.c_float, _vp], ctypes.c_int),
         "mcp_project_segments_noalloc": ([_vp, P(ProjectParams), ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp,
@@ -99,7 +109,7 @@ EXPORTED = ("mcp_create", "mcp_destroy", "mcp_last_error", "mcp_launch_count", "
             "mcp_load_constraints", "mcp_load_obstacles", "mcp_get_constraint", "mcp_project_batch",
             "mcp_project_check_batch", "mcp_project_segments", "mcp_check_batch", "mcp_project_vjp",
             "mcp_path_length_grad", "mcp_autotune", "mcp_set_tuning", "mcp_project_segments_noalloc",
-            "mcp_path_step")
+            "mcp_path_step", "mcp_extend_batch")
 
 
 class MCPError(RuntimeError):
@@ -265,6 +275,26 @@ class Projector:
                                                      _ptr(iters), _ptr(resid), _ptr(hit), _ptr(pairs),
                                                      _stream(stream)))
         return out, flags, iters, resid, hit
+
+    def extend(self, q_s, q_t, eps, params, r, delta, max_depth=6, steps=None, out=None, stream=None):
+        """ParallelConstrainedExtend (Alg. 2) of every column of q_s towards the
+        same column of q_t ([d, n_ext] float32 CUDA tensors); eps [n, n_ext] the
+        particle offsets; `steps` (int32 [n_ext]) optionally receives the Newton
+        steps of each extension.  Returns (q_proj, status, n_points, winner)."""
+        import torch
+        d, m = q_s.shape
+        n = eps.shape[0]
+        if out is None:
+            out = (torch.empty_like(q_s), torch.empty(m, dtype=torch.uint8, device=q_s.device),
+                   torch.empty(m, dtype=torch.int32, device=q_s.device),
+                   torch.empty(m, dtype=torch.int32, device=q_s.device))
+        q_proj, status, n_points, winner = out
+        pp = self.params(params)
+        ep = ExtendParams(r=r, delta=delta, n=n, max_depth=max_depth)
+        self._check(self.lib.mcp_extend_batch(self.h, ctypes.byref(pp), ctypes.byref(ep), m, m, _ptr(q_s), _ptr(q_t),
+                                              _ptr(eps), eps.shape[1], _ptr(q_proj), _ptr(status), _ptr(n_points),
+                                              _ptr(winner), _ptr(steps), _stream(stream)))
+        return q_proj, status, n_points, winner
 
     def project_segments(self, start, delta, length, params, total=None, out=None, flags=None, iters=None,
                          resid=None, stream=None):
