@@ -93,6 +93,8 @@ typedef struct {
   double lambda;
   double alpha;
   double max_step;    /* <= 0: divergence exit off */
+  int32_t outer;      /* 0: inner form J^T (J J^T + lambda I)^{-1} F; 1: outer (J^T J + lambda I)^{-1} J^T F */
+  int32_t pad;
 } or_params;
 
 /* ------------------------------------------------------------------------ */
@@ -552,7 +554,7 @@ static int cholesky(int n, const double *A, double *L) {
 
 /* Solve L L^T x = b. */
 static void chol_solve(int n, const double *L, const double *b, double *x) {
-  double y[OR_MAXK];
+  double y[OR_MAXK > OR_MAXJ ? OR_MAXK : OR_MAXJ];
   for (int i = 0; i < n; ++i) {
     double s = b[i];
     for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
@@ -583,6 +585,30 @@ static int lm_step(int k, int d, const double *J, const double *F, double lambda
     dq[j] = alpha * s;
   }
   return 1;
+}
+
+/* Outer form of the LM step (Alg. 2, the alternative of getDescentStep):
+ * dq = alpha (J^T J + lambda I)^{-1} J^T F, a d x d system.  0 if singular. */
+static int lm_step_outer(int k, int d, const double *J, const double *F, double lambda, double alpha, double *dq) {
+  double A[OR_MAXJ * OR_MAXJ], L[OR_MAXJ * OR_MAXJ], b[OR_MAXJ], z[OR_MAXJ];
+  for (int i = 0; i < d; ++i) {
+    for (int j = 0; j < d; ++j) {
+      double s = 0.0;
+      for (int a = 0; a < k; ++a) s += J[a * d + i] * J[a * d + j];
+      A[i * d + j] = s + (i == j ? lambda : 0.0);
+    }
+    double s = 0.0;
+    for (int a = 0; a < k; ++a) s += J[a * d + i] * F[a];
+    b[i] = s;
+  }
+  if (!cholesky(d, A, L)) return 0;
+  chol_solve(d, L, b, z);
+  for (int j = 0; j < d; ++j) dq[j] = alpha * z[j];
+  return 1;
+}
+
+static int descent(const or_params *p, int k, int d, const double *J, const double *F, double *dq) {
+  return p->outer ? lm_step_outer(k, d, J, F, p->lambda, p->alpha, dq) : lm_step(k, d, J, F, p->lambda, p->alpha, dq);
 }
 
 static double norm(int n, const double *v) {
@@ -619,14 +645,14 @@ static int project_one(const or_robot *rb, const or_constraint *cons, int nc, co
     memcpy(q0, q, d * sizeof(double));
     if (!p->cyclic) {
       eval_stack(rb, cons, 0, nc, q, F, J);
-      if (!lm_step(k, d, J, F, p->lambda, p->alpha, dq)) { flags |= OR_NONFINITE; break; }
+      if (!descent(p, k, d, J, F, dq)) { flags |= OR_NONFINITE; break; }
       for (int j = 0; j < d; ++j) q[j] -= dq[j];
     } else {
       /* getDescentStep: one LM step per constraint F_i, in order */
       int singular = 0;
       for (int i = 0; i < nc && !singular; ++i) {
         int ki = eval_stack(rb, cons, i, i + 1, q, F, J);
-        if (!lm_step(ki, d, J, F, p->lambda, p->alpha, dq)) { singular = 1; break; }
+        if (!descent(p, ki, d, J, F, dq)) { singular = 1; break; }
         for (int j = 0; j < d; ++j) q[j] -= dq[j];
       }
       if (singular) { flags |= OR_NONFINITE; break; }

@@ -59,7 +59,8 @@ EXT_OK, EXT_DEGENERATE, EXT_NO_PROJECTION, EXT_PROJ_COLLISION, EXT_TOO_FAR, EXT_
 
 class _Params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iters", ctypes.c_int32), ("cyclic", ctypes.c_int32),
-                ("lam", ctypes.c_double), ("alpha", ctypes.c_double), ("max_step", ctypes.c_double)]
+                ("lam", ctypes.c_double), ("alpha", ctypes.c_double), ("max_step", ctypes.c_double),
+                ("outer", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -214,7 +215,7 @@ class Oracle:
         return F[:self.k], J[:self.k]
 
     # ---- batched (SoA [d, n]) ----
-    def project(self, q, tol, max_iters, lam, max_step=0.0, alpha=1.0, cyclic=False, threads=None):
+    def project(self, q, tol, max_iters, lam, max_step=0.0, alpha=1.0, cyclic=False, outer=False, threads=None):
         q = _f64(q)
         d, n = q.shape
         out = np.empty_like(q)
@@ -222,13 +223,16 @@ class Oracle:
         iters = np.zeros(n, np.int32)
         resid = np.zeros(n)
         p = _Params(tol=tol, max_iters=max_iters, cyclic=int(bool(cyclic)), lam=lam, alpha=alpha,
-                    max_step=max_step)
+                    max_step=max_step, outer=int(bool(outer)))
         _load().or_project(ctypes.byref(self._robot), self._cons, self.nc, ctypes.byref(p), n, n, _ptr(q),
                            _ptr(out), _ptr(flags, _u8p), _ptr(iters, _ip), _ptr(resid),
                            threads or default_threads())
         return out, flags, iters, resid
 
     def project_params(self, q, params, **kw):
+        kw.setdefault("alpha", getattr(params, "alpha", 1.0))
+        kw.setdefault("outer", getattr(params, "outer", False))
+        kw.setdefault("cyclic", getattr(params, "cyclic", False))
         return self.project(q, params.tol, params.max_iters, params.lam, max_step=params.max_step, **kw)
 
     def extend(self, q_s, q_t, eps, params, r, delta, max_depth=6, threads=None):
@@ -243,7 +247,8 @@ class Oracle:
         n_points = np.zeros(m, np.int32)
         winner = np.zeros(m, np.int32)
         p = _Params(tol=params.tol, max_iters=params.max_iters, cyclic=int(bool(getattr(params, "cyclic", False))),
-                    lam=params.lam, alpha=1.0, max_step=params.max_step)
+                    lam=params.lam, alpha=getattr(params, "alpha", 1.0), max_step=params.max_step,
+                    outer=int(bool(getattr(params, "outer", False))))
         ep = _ExtParams(r=r, delta=delta, n=n, max_depth=max_depth)
         _load().or_extend(ctypes.byref(self._robot), self._cons, self.nc, ctypes.byref(p), ctypes.byref(ep),
                           self._obs.shape[0], _ptr(self._obs), self._box.shape[0], _ptr(self._box), m, m,

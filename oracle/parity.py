@@ -15,7 +15,7 @@ from . import oracle as orc
 
 
 def eligible_mask(o, q0, tol, max_iters, lam, max_step=0.0, rel=1e-6, thr=1e-5, reps=2, seed=0, cyclic=False,
-                  stable_iters=False, stats=None):
+                  stable_iters=False, stats=None, alpha=1.0, outer=False):
     """(mask, oracle result): mask[i] is True when `reps` random relative
     perturbations of size `rel` of start i move the oracle's result by <= thr
     and do not change its convergence flag (nor, with `stable_iters`, its
@@ -26,13 +26,14 @@ def eligible_mask(o, q0, tol, max_iters, lam, max_step=0.0, rel=1e-6, thr=1e-5, 
     the fraction of flipped convergence flags and of changed step counts,
     the scale of any other implementation's disagreement on the workload."""
     rng = np.random.default_rng(seed)
-    base = o.project(q0, tol, max_iters, lam, max_step=max_step, cyclic=cyclic)
+    kw = dict(max_step=max_step, cyclic=cyclic, alpha=alpha, outer=outer)
+    base = o.project(q0, tol, max_iters, lam, **kw)
     dev_max = np.zeros(q0.shape[1])
     flips = np.zeros(q0.shape[1], bool)
     recount = np.zeros(q0.shape[1], bool)
     for _ in range(reps):
         q1 = q0 * (1.0 + rel * rng.choice([-1.0, 1.0], size=q0.shape))
-        other = o.project(q1, tol, max_iters, lam, max_step=max_step, cyclic=cyclic)
+        other = o.project(q1, tol, max_iters, lam, **kw)
         dev_max = np.maximum(dev_max, np.abs(base[0] - other[0]).max(axis=0))
         flips |= (base[1] & orc.CONVERGED) != (other[1] & orc.CONVERGED)
         recount |= base[2] != other[2]

@@ -148,6 +148,8 @@ class Params:
     pivot_fp64: float = 1e-7    # FP32 Cholesky pivot below this -> FP64 re-solve
     precision: int = PREC_FP32
     cyclic: bool = False        # one LM step per constraint in order (Sec. IV-C) instead of stacked
+    alpha: float = 1.0          # step scale of getDescentStep
+    outer: bool = False         # outer form (J^T J + lambda I)^{-1} J^T F instead of the inner one
 
 
 @dataclasses.dataclass

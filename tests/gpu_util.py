@@ -24,7 +24,8 @@ def eligible_mask(oracle, q0, params, rel=1e-6, thr=1e-5, reps=2, seed=0, stable
     (see oracle/parity.py).  Returns (mask, oracle result)."""
     return parity.eligible_mask(oracle, q0, params.tol, params.max_iters, params.lam, max_step=params.max_step,
                                 rel=rel, thr=thr, reps=reps, seed=seed, cyclic=bool(getattr(params, "cyclic", False)),
-                                stable_iters=stable_iters, stats=stats)
+                                stable_iters=stable_iters, stats=stats, alpha=getattr(params, "alpha", 1.0),
+                                outer=bool(getattr(params, "outer", False)))
 
 
 def compare_projection(gpu, ora, tol, q_tol=Q_TOL, flag_agree=FLAG_AGREE, oracle=None, sample_resid=256,

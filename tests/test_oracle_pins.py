@@ -839,3 +839,61 @@ def test_extend_exits():
     assert orc.Oracle(rb, cons, hit2).extend(qs, qt, eps, p, dist, 0.05)[1][0] == orc.EXT_INTERP_COLLISION
     # no resolution within the depth cap
     assert orc.Oracle(rb, cons).extend(qs, qt, eps, p, dist, 1e-4, max_depth=2)[1][0] == orc.EXT_RESOLUTION
+
+
+# ---------------------------------------------------------------------------
+# Outer form of the LM step, (J^T J + lambda I)^{-1} J^T F (Alg. 2), and the
+# step scale alpha.
+# ---------------------------------------------------------------------------
+def test_outer_step_is_least_squares_step():
+    """With lambda = 0 and J of full column rank the outer step is the
+    least-squares solution of J dq = F (numpy's lstsq)."""
+    rb = cartesian_robot()
+    rng = np.random.default_rng(70)
+    cons = [W.Constraint(W.C_PLANE, frame_a=0, P=_rt(W.random_rotation(rng), rng.uniform(-1, 1, 3)))
+            for _ in range(4)]
+    o = orc.Oracle(rb, cons)
+    q0 = rng.uniform(-1, 1, (3, 8))
+    out = o.project(q0, 1e-13, 1, 0.0, outer=True)[0]
+    for i in range(8):
+        F, J = o.residual_jacobian(q0[:, i])
+        np.testing.assert_allclose(out[:, i], q0[:, i] - np.linalg.lstsq(J, F, rcond=None)[0], atol=1e-13)
+
+
+def test_outer_form_solves_consistent_overdetermined_system():
+    """Four planes through one point, a Cartesian point (k = 4 > d = 3): the
+    outer step lands on the common point in one step; the inner form's
+    4 x 4 J J^T is singular at lambda = 0."""
+    rb = cartesian_robot()
+    rng = np.random.default_rng(71)
+    c = rng.uniform(-0.5, 0.5, 3)
+    cons = [W.Constraint(W.C_PLANE, frame_a=0, P=_rt(W.random_rotation(rng), c)) for _ in range(4)]
+    o = orc.Oracle(rb, cons)
+    q0 = rng.uniform(-1, 1, (3, 8))
+    out, fl, it, _ = o.project(q0, 1e-10, 5, 0.0, outer=True)
+    assert (fl & orc.CONVERGED).all() and (it == 1).all()
+    np.testing.assert_allclose(out, np.repeat(c[:, None], 8, 1), atol=1e-12)
+    assert (o.project(q0, 1e-10, 5, 0.0, outer=False)[1] & orc.NONFINITE).all()
+
+
+def test_inner_and_outer_steps_agree_with_damping():
+    """J^T (J J^T + lambda I)^{-1} = (J^T J + lambda I)^{-1} J^T for lambda > 0:
+    one step of either form from the same start, on the 7-DoF arm."""
+    wl = W.arm_workload(n=32)
+    o = orc.Oracle(wl.robot, wl.constraints)
+    a = o.project(wl.q, 1e-13, 1, 1e-3, outer=False)[0]
+    b = o.project(wl.q, 1e-13, 1, 1e-3, outer=True)[0]
+    np.testing.assert_allclose(a, b, atol=1e-9)
+
+
+def test_step_scale_alpha():
+    """On the unit sphere one full Newton step is the radial projection; with
+    alpha the point moves that fraction of the way: q - alpha (|q| - 1) q / |q|."""
+    wl = W.sphere_workload(n_pairs=2)
+    o = orc.Oracle(wl.robot, wl.constraints)
+    rng = np.random.default_rng(72)
+    q0 = rng.uniform(-1.5, 1.5, (3, 16))
+    nq = np.linalg.norm(q0, axis=0)
+    for alpha in (0.5, 0.8):
+        out = o.project(q0, 1e-13, 1, 0.0, alpha=alpha)[0]
+        np.testing.assert_allclose(out, q0 - alpha * (nq - 1) * q0 / nq, atol=1e-14)
