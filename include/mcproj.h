@@ -144,7 +144,12 @@ typedef struct {
                           (Sec. IV-C): per iteration one LM step per constraint in stack order,
                           each at the configuration the previous one produced; the stopping test
                           and MaxDistance apply to the stacked F and to the whole sweep */
-  int32_t reserved;    /* 0 */
+  int32_t outer;       /* 0: inner form dq = J^T (J J^T + lambda I)^-1 F (a k x k system);
+                          1: outer form dq = (J^T J + lambda I)^-1 J^T F (d x d; Alg. 2 offers both;
+                          for k >= d, e.g. consistent redundant constraints, where J J^T is
+                          singular).  Stacked steps of problems with at most 14 joints, batch calls
+                          (project_batch, project_check_batch); else MCP_ERR_UNSUPPORTED */
+  double alpha;        /* step scale of Alg. 2: q <- q - alpha dq; 0 means 1; else in (0, 2] */
 } mcp_project_params;
 
 /* Context on CUDA device `device`. */

@@ -69,7 +69,8 @@ ClassDesc describe(bool project) {
 
 const std::vector<ClassDesc> &registry() {
   static const std::vector<ClassDesc> r = {
-      describe<ProbSphere3>(true),   describe<ProbArm7Axis>(true),  describe<ProbArm7Pose>(true),
+      describe<ProbSphere3>(true),   describe<ProbPoint3Planes4>(true), describe<ProbArm7Axis>(true),
+      describe<ProbArm7Pose>(true),
       describe<ProbArm7Tray>(true),  describe<ProbArm7Peg>(true),   describe<ProbArm7Tsr>(true),
       describe<ProbDual14Rel>(true), describe<ProbDual14Rod>(true), describe<ProbHumanoid36>(true)};
   return r;
@@ -922,6 +923,9 @@ static mcp_status validate_params(mcp_ctx *ctx, const mcp_project_params *p) {
   if (p->max_iters < 0 || p->max_iters > 255) return fail(ctx, MCP_ERR_ARG, "max_iters %d outside [0, 255]", p->max_iters);
   if (p->precision != 0 && p->precision != 1) return fail(ctx, MCP_ERR_ARG, "precision %d", p->precision);
   if (p->cyclic != 0 && p->cyclic != 1) return fail(ctx, MCP_ERR_ARG, "cyclic %d", p->cyclic);
+  if (p->outer != 0 && p->outer != 1) return fail(ctx, MCP_ERR_ARG, "outer %d", p->outer);
+  if (p->outer && p->cyclic) return fail(ctx, MCP_ERR_UNSUPPORTED, "the outer form takes stacked steps");
+  if (!(p->alpha >= 0.0 && p->alpha <= 2.0)) return fail(ctx, MCP_ERR_ARG, "alpha must be in (0, 2] (0 = 1)");
   if (!(p->lambda >= 0.0) || !std::isfinite(p->lambda)) return fail(ctx, MCP_ERR_ARG, "lambda must be >= 0");
   if (!std::isfinite(p->max_step) || !std::isfinite(p->pivot_fp64)) return fail(ctx, MCP_ERR_ARG, "non-finite parameter");
   if (!ctx->robot_loaded || !ctx->cons_loaded) return fail(ctx, MCP_ERR_STATE, "robot and constraints must be loaded");
@@ -938,6 +942,8 @@ static void fill_call(mcp_ctx *ctx, const mcp_project_params *p, ProjCall &c, cu
   c.max_step = p->max_step;
   c.pivot = p->pivot_fp64;
   c.cyclic = p->cyclic != 0;
+  c.outer = p->outer != 0;
+  c.alpha = p->alpha > 0.0 ? p->alpha : 1.0;
   c.counter = ctx->d_counter;
   c.tune = ctx->tune;
   c.stream = s;
@@ -976,7 +982,7 @@ mcp_status mcp_project_batch(mcp_ctx *ctx, const mcp_project_params *p, int64_t 
 // when the autotuner found that faster for this problem, else a second launch.
 static cudaError_t run_project_check(mcp_ctx *ctx, ProjCall c, int *launches) {
   const ClassDesc &cd = registry()[ctx->prob_class];
-  c.fused_check = ctx->tune.fuse_check;
+  c.fused_check = ctx->tune.fuse_check && !c.outer;
   if (c.fused_check) return cd.project_fn(ctx->hm, c, launches);
   cudaError_t e = cd.project_fn(ctx->hm, c, launches);
   if (e != cudaSuccess) return e;
@@ -1034,7 +1040,7 @@ mcp_status mcp_extend_batch(mcp_ctx *ctx, const mcp_project_params *p, const mcp
   if (st != MCP_OK) return st;
   if (!e) return fail(ctx, MCP_ERR_ARG, "extend params is NULL");
   if (p->precision != 0) return fail(ctx, MCP_ERR_ARG, "the extension runs the FP32 path (precision 0)");
-  if (p->cyclic != 0) return fail(ctx, MCP_ERR_ARG, "the extension uses the stacked step");
+  if (p->cyclic != 0 || p->outer != 0) return fail(ctx, MCP_ERR_ARG, "the extension uses the stacked inner step");
   if (!ctx->obs_loaded) return fail(ctx, MCP_ERR_STATE, "obstacles must be loaded");
   if (e->n < 1 || e->n > 32) return fail(ctx, MCP_ERR_ARG, "n = %d outside [1, 32]", e->n);
   if (!(e->r > 0.0) || !(e->delta > 0.0) || !std::isfinite(e->r) || !std::isfinite(e->delta))
@@ -1054,6 +1060,7 @@ mcp_status mcp_extend_batch(mcp_ctx *ctx, const mcp_project_params *p, const mcp
   c.lambda = p->lambda;
   c.max_step = p->max_step;
   c.pivot = p->pivot_fp64;
+  c.alpha = p->alpha > 0.0 ? p->alpha : 1.0;
   c.r = e->r;
   c.delta = e->delta;
   c.n = e->n;

@@ -55,6 +55,7 @@ struct ExtArgs {
   float pivot;
   double tol2_64;
   double lambda64;
+  float alpha;
 };
 
 // FP64 acceptance of one FP32 iterate held in registers (accept_one without
@@ -75,7 +76,7 @@ __device__ __forceinline__ void accept_regs(const A &a, float (&q)[P::D], int &i
       float qf[D];
 #pragma unroll
       for (int j = 0; j < D; ++j) qf[j] = q[j];
-      finish_f64<P, false>(a, qf, qd, &it, &fl, r2, was_conv);
+      finish_f64<P, FORM_STACKED>(a, qf, qd, &it, &fl, r2, was_conv);
 #pragma unroll
       for (int j = 0; j < D; ++j) q[j] = qf[j];
     }
@@ -338,6 +339,7 @@ cudaError_t launch_extend_impl(const HostModel &hm, const ExtCall &c, int *launc
   a.pivot = static_cast<float>(c.pivot);
   a.tol2_64 = c.tol * c.tol;
   a.lambda64 = c.lambda;
+  a.alpha = static_cast<float>(c.alpha);
   const size_t smem = sizeof(float) * (8 * hm.n_obs + 6 * hm.n_box) + sizeof(float) * W * 2 * EXT_MAXPTS * P::D;
   cudaError_t err = cudaSuccess;
   if (smem > 48 * 1024)

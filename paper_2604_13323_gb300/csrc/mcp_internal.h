@@ -61,6 +61,8 @@ struct ProjCall {
   double max_step = 0.0;
   double pivot = 1e-7;
   bool cyclic = false;  // cyclic getDescentStep (one step per constraint per sweep)
+  bool outer = false;   // outer form (J^T J + lambda I)^-1 J^T F
+  double alpha = 1.0;   // step scale
   bool segments = false;
   // batch source
   const void *q_in = nullptr;
@@ -112,6 +114,7 @@ struct ExtCall {
   double lambda = 0.0;
   double max_step = 0.0;
   double pivot = 1e-7;
+  double alpha = 1.0;
   double r = 0.3, delta = 0.02;
   int n = 8, max_depth = 6;
   long long n_ext = 0, ld = 0, ld_eps = 0;

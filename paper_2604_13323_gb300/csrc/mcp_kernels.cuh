@@ -23,6 +23,11 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t FL_INT_FP32CONV = 1u << 8;   // FP32 residual passed; FP64 check pending
 constexpr uint32_t FL_INT_NEEDS_F64 = 1u << 9;  // FP32 pivot below threshold: continue in FP64
 
+// Forms of getDescentStep (Alg. 2): the stacked inner step J^T (J J^T + lambda I)^-1 F,
+// one inner step per constraint in turn (cyclic), or the stacked outer step
+// (J^T J + lambda I)^-1 J^T F (a d x d system).
+enum : int { FORM_STACKED = 0, FORM_CYCLIC = 1, FORM_OUTER = 2 };
+
 // ---------------------------------------------------------------------------
 // Stacked residual F(q) and Jacobian J(q)
 // ---------------------------------------------------------------------------
@@ -287,6 +292,23 @@ __device__ __forceinline__ void j_mul(const T (&J)[kdim<P>()][P::D], const T (&g
   });
 }
 
+// A = J^T J + lambda I (lower triangle of the d x d matrix), structural zeros skipped.
+template <class P, typename T>
+__device__ __forceinline__ void gram_outer(const T (&J)[kdim<P>()][P::D], T lambda, T (&A)[P::D * (P::D + 1) / 2]) {
+  static_for<P::D>([&](auto II) {
+    constexpr int i = decltype(II)::value;
+    static_for<i + 1>([&](auto JJ) {
+      constexpr int j = decltype(JJ)::value;
+      T s = (i == j) ? lambda : T(0);
+      static_for<kdim<P>()>([&](auto AA) {
+        constexpr int a = decltype(AA)::value;
+        if constexpr (jnz<P>(a, i) && jnz<P>(a, j)) s = fma_(J[a][i], J[a][j], s);
+      });
+      A[tri(i, j)] = s;
+    });
+  });
+}
+
 // ---------------------------------------------------------------------------
 // Work items: a plain batch, or points on uneven segments.
 // ---------------------------------------------------------------------------
@@ -350,6 +372,7 @@ struct ProjArgs {
   float pivot;
   double tol2_64;
   double lambda64;
+  float alpha;  // step scale of getDescentStep
   // fused collision check of every output (CHK kernels only)
   const CheckData *chk;
   const float *obs;
@@ -386,7 +409,7 @@ __device__ __forceinline__ void refine_step(const T (&J)[kdim<P>()][P::D], const
 // FP32 iteration (one pass of the ParallelProject loop for one configuration).
 // Returns true when the configuration leaves the FP32 loop.
 // ---------------------------------------------------------------------------
-template <class P, class A>
+template <class P, class A, bool OUTER = false>
 __device__ __forceinline__ bool newton_iter_f32(const A &a, float (&q)[P::D], int &it, uint32_t &fl) {
   constexpr int D = P::D, K = kdim<P>();
   const OpsF32 ops{a.tab};
@@ -412,22 +435,49 @@ __device__ __forceinline__ bool newton_iter_f32(const A &a, float (&q)[P::D], in
   }
   float J[K][D];
   jacobian<P>(a.m, q, k, e, J);
-  float Am[K * (K + 1) / 2], inv[K];
-  gram<P>(J, a.lambda, Am);
-  const float piv = cholesky_factor<K, OpsF32>(Am, inv);
-  if (!(piv >= a.pivot)) {  // also catches NaN: finish this configuration in FP64
-    fl |= FL_INT_NEEDS_F64;
-    return true;
-  }
-  float y[K], dq[D];
+  float dq[D];
+  if constexpr (OUTER) {
+    // (J^T J + lambda I) dq = J^T F, one refinement with r = J^T (F - J dq) - lambda dq
+    float Am[D * (D + 1) / 2], inv[D];
+    gram_outer<P>(J, a.lambda, Am);
+    const float piv = cholesky_factor<D, OpsF32>(Am, inv);
+    if (!(piv >= a.pivot)) {
+      fl |= FL_INT_NEEDS_F64;
+      return true;
+    }
+    jt_mul<P>(J, F, dq);
+    cholesky_subst<D>(Am, inv, dq);
+    float u[K], r[D];
+    j_mul<P>(J, dq, u);
 #pragma unroll
-  for (int i = 0; i < K; ++i) y[i] = F[i];
-  cholesky_subst<K>(Am, inv, y);
-  jt_mul<P>(J, y, dq);
-  refine_step<P>(J, F, a.lambda, Am, inv, y, dq);
+    for (int i = 0; i < K; ++i) u[i] = F[i] - u[i];
+    jt_mul<P>(J, u, r);
+#pragma unroll
+    for (int j = 0; j < D; ++j) r[j] = fmaf(-a.lambda, dq[j], r[j]);
+    cholesky_subst<D>(Am, inv, r);
+#pragma unroll
+    for (int j = 0; j < D; ++j) dq[j] += r[j];
+  } else {
+    float Am[K * (K + 1) / 2], inv[K];
+    gram<P>(J, a.lambda, Am);
+    const float piv = cholesky_factor<K, OpsF32>(Am, inv);
+    if (!(piv >= a.pivot)) {  // also catches NaN: finish this configuration in FP64
+      fl |= FL_INT_NEEDS_F64;
+      return true;
+    }
+    float y[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) y[i] = F[i];
+    cholesky_subst<K>(Am, inv, y);
+    jt_mul<P>(J, y, dq);
+    refine_step<P>(J, F, a.lambda, Am, inv, y, dq);
+  }
   float s2 = 0.f;
 #pragma unroll
-  for (int j = 0; j < D; ++j) s2 = fmaf(dq[j], dq[j], s2);
+  for (int j = 0; j < D; ++j) {
+    dq[j] *= a.alpha;
+    s2 = fmaf(dq[j], dq[j], s2);
+  }
   if (a.max_step2 > 0.f && s2 > a.max_step2) {
     fl |= FL_DIV;
     return true;
@@ -467,7 +517,7 @@ __device__ __forceinline__ bool substep_f32(const A &a, float (&q)[S::D]) {
   jt_mul<S>(J, y, dq);
   refine_step<S>(J, F, a.lambda, Am, inv, y, dq);
 #pragma unroll
-  for (int j = 0; j < D; ++j) q[j] -= dq[j];
+  for (int j = 0; j < D; ++j) q[j] -= a.alpha * dq[j];
   return true;
 }
 
@@ -617,7 +667,7 @@ __device__ __forceinline__ double residual2_f64(const Ops &ops, const ModelT<dou
 // system).  J and the factorisation live in local memory (runtime-indexed
 // loops) so that this rare path does not raise the register budget of the
 // FP32 loop.  Returns false if the FP64 system is singular as well.
-template <class P>
+template <class P, bool OUTER = false>
 __device__ __noinline__ bool lm_step_f64(const OpsF64Table ops, const ModelT<double> *__restrict__ m,
                                          const double *q_in, double lambda, double *dq_out) {
   constexpr int D = P::D, K = kdim<P>();
@@ -635,6 +685,56 @@ __device__ __noinline__ bool lm_step_f64(const OpsF64Table ops, const ModelT<dou
 #pragma unroll 1
     for (int j = 0; j < D; ++j) J[a][j] = 0.0;
   jacobian<P>(*m, q, k, e, J);
+  if constexpr (OUTER) {
+    // (J^T J + lambda I) dq = J^T F
+    double L[D][D], b[D];
+#pragma unroll 1
+    for (int i = 0; i < D; ++i) {
+      double t = 0.0;
+#pragma unroll 1
+      for (int a = 0; a < K; ++a) t = fma(J[a][i], F[a], t);
+      b[i] = t;
+#pragma unroll 1
+      for (int j = 0; j <= i; ++j) {
+        double s = (i == j) ? lambda : 0.0;
+#pragma unroll 1
+        for (int a = 0; a < K; ++a) s = fma(J[a][i], J[a][j], s);
+        L[i][j] = s;
+      }
+    }
+#pragma unroll 1
+    for (int j = 0; j < D; ++j) {
+      double s = L[j][j];
+#pragma unroll 1
+      for (int t = 0; t < j; ++t) s = fma(-L[j][t], L[j][t], s);
+      if (!(s > 0.0)) return false;
+      L[j][j] = sqrt(s);
+#pragma unroll 1
+      for (int i = j + 1; i < D; ++i) {
+        double t2 = L[i][j];
+#pragma unroll 1
+        for (int t = 0; t < j; ++t) t2 = fma(-L[i][t], L[j][t], t2);
+        L[i][j] = t2 / L[j][j];
+      }
+    }
+#pragma unroll 1
+    for (int i = 0; i < D; ++i) {
+      double t = b[i];
+#pragma unroll 1
+      for (int u = 0; u < i; ++u) t = fma(-L[i][u], b[u], t);
+      b[i] = t / L[i][i];
+    }
+#pragma unroll 1
+    for (int i = D - 1; i >= 0; --i) {
+      double t = b[i];
+#pragma unroll 1
+      for (int u = i + 1; u < D; ++u) t = fma(-L[u][i], b[u], t);
+      b[i] = t / L[i][i];
+    }
+#pragma unroll 1
+    for (int j = 0; j < D; ++j) dq_out[j] = b[j];
+    return true;
+  } else {
   double L[K][K];
 #pragma unroll 1
   for (int a = 0; a < K; ++a) {
@@ -684,6 +784,7 @@ __device__ __noinline__ bool lm_step_f64(const OpsF64Table ops, const ModelT<dou
     dq_out[j] = s;
   }
   return true;
+  }
 }
 
 // Heron refinement of an FP32 square root: one Newton step in FP64 brings the
@@ -702,10 +803,12 @@ __device__ __forceinline__ double sqrt_refined(double v) {
 // the FP32 Cholesky pivot fell below the threshold.  Rare, so it lives out of
 // line (its registers and local arrays stay off the FP32 loop).  Updates q,
 // qd, it, fl; returns the final squared FP64 residual.
-template <class P, bool CYC, class A>
+template <class P, int FORM, class A>
 __device__ __noinline__ double finish_f64(const A &a, float *q, double *qd, int *it_io, uint32_t *fl_io, double r2,
                                           bool was_conv) {
   constexpr int D = P::D;
+  constexpr bool CYC = FORM == FORM_CYCLIC;
+  const double alpha = static_cast<double>(a.alpha);
   const OpsF64Table ops{a.tab};
   const ModelT<double> &m = *a.m64;
   int it = *it_io;
@@ -731,7 +834,7 @@ __device__ __noinline__ double finish_f64(const A &a, float *q, double *qd, int 
         }
 #pragma unroll 1
         for (int j = 0; j < D; ++j) {
-          q[j] = static_cast<float>(qq[j] - dq[j]);
+          q[j] = static_cast<float>(qq[j] - alpha * dq[j]);
           qq[j] = static_cast<double>(q[j]);
         }
       });
@@ -756,13 +859,16 @@ __device__ __noinline__ double finish_f64(const A &a, float *q, double *qd, int 
       }
     } else {
       double dq[D];
-      if (!lm_step_f64<P>(ops, a.m64, qq, a.lambda64, dq)) {
+      if (!lm_step_f64<P, FORM == FORM_OUTER>(ops, a.m64, qq, a.lambda64, dq)) {
         fl |= FL_NONFINITE;
         break;
       }
       double s2 = 0.0;
 #pragma unroll 1
-      for (int j = 0; j < D; ++j) s2 = fma(dq[j], dq[j], s2);
+      for (int j = 0; j < D; ++j) {
+        dq[j] *= alpha;
+        s2 = fma(dq[j], dq[j], s2);
+      }
       if (a.max_step2 > 0.f && s2 > static_cast<double>(a.max_step2)) {
         fl |= FL_DIV;
         break;
@@ -794,7 +900,7 @@ __device__ __noinline__ double finish_f64(const A &a, float *q, double *qd, int 
 // is re-checked with the FP64 residual; if the FP32 test was too optimistic,
 // or the FP32 pivot was too small, finish_f64 takes the remaining steps.
 // Writes q (if changed), flags, iters and resid.
-template <class P, bool CYC, class A>
+template <class P, int FORM, class A>
 __device__ __forceinline__ void accept_one(const A &a, long long item, int it, uint32_t fl) {
   constexpr int D = P::D;
   const ModelT<double> &m = *a.m64;
@@ -819,7 +925,7 @@ __device__ __forceinline__ void accept_one(const A &a, long long item, int it, u
         qf[j] = q[j];
         qdd[j] = qd[j];
       }
-      r2 = finish_f64<P, CYC>(a, qf, qdd, &it, &fl, r2, was_conv);
+      r2 = finish_f64<P, FORM>(a, qf, qdd, &it, &fl, r2, was_conv);
 #pragma unroll
       for (int j = 0; j < D; ++j) {
         a.q_out[j * a.ld_out + item] = qf[j];
@@ -1080,7 +1186,7 @@ __host__ __device__ constexpr int min_blocks() {
   return 65536 / (TPB * reg_cap<P>()) > 0 ? 65536 / (TPB * reg_cap<P>()) : 1;
 }
 
-template <class P, class Src, int TPB, bool CYC, bool CHK>
+template <class P, class Src, int TPB, int FORM, bool CHK>
 __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(const __grid_constant__ ProjArgs<P, Src> a) {
   constexpr int D = P::D;
   constexpr int W = TPB / 32;
@@ -1150,8 +1256,8 @@ __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(con
     // (2) one FP32 Newton iteration
     bool done = false;
     if (act) {
-      if constexpr (CYC) done = cyclic_iter_f32<P>(a, q, it, fl);
-      else done = newton_iter_f32<P>(a, q, it, fl);
+      if constexpr (FORM == FORM_CYCLIC) done = cyclic_iter_f32<P>(a, q, it, fl);
+      else done = newton_iter_f32<P, ProjArgs<P, Src>, FORM == FORM_OUTER>(a, q, it, fl);
     }
     // (3) park finished lanes
     const unsigned fin = __ballot_sync(FULL, done);
@@ -1176,7 +1282,7 @@ __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(con
         const int pos = pend - take + lane;
         const uint32_t meta = s_meta[wib][pos];
         const long long it_item = s_item[wib][pos];
-        accept_one<P, CYC>(a, it_item, static_cast<int>(meta & 0xffu), meta >> 8);
+        accept_one<P, FORM>(a, it_item, static_cast<int>(meta & 0xffu), meta >> 8);
         if constexpr (CHK) {
           float qc[D];
 #pragma unroll
@@ -1213,11 +1319,12 @@ struct ProjArgs64 {
   double tol2;
   double lambda;
   double max_step2;
+  double alpha;
 };
 
 // One plain FP64 LM step of the (sub-)problem S at q: dq = J^T (J J^T + lambda I)^-1 F.
 // Returns false if the system is singular.
-template <class S, class M>
+template <class S, class M, bool OUTER = false>
 __device__ __forceinline__ bool step_f64(const M &m, const double (&q)[S::D], double lambda, double (&dq)[S::D]) {
   constexpr int D = S::D, K = kdim<S>();
   const OpsF64Plain ops{nullptr};
@@ -1228,17 +1335,25 @@ __device__ __forceinline__ bool step_f64(const M &m, const double (&q)[S::D], do
   residual<S, OpsF64Plain, double, true>(m, q, k, F, e);
   double J[K][D];
   jacobian<S>(m, q, k, e, J);
-  double Am[K * (K + 1) / 2];
-  gram<S>(J, lambda, Am);
-  const double piv = cholesky_solve<K, OpsF64Plain>(Am, F);
-  if (!(piv > 0.0)) return false;
-  jt_mul<S>(J, F, dq);
-  return true;
+  if constexpr (OUTER) {
+    double Am[D * (D + 1) / 2];
+    gram_outer<S>(J, lambda, Am);
+    jt_mul<S>(J, F, dq);
+    return cholesky_solve<D, OpsF64Plain>(Am, dq) > 0.0;
+  } else {
+    double Am[K * (K + 1) / 2];
+    gram<S>(J, lambda, Am);
+    const double piv = cholesky_solve<K, OpsF64Plain>(Am, F);
+    if (!(piv > 0.0)) return false;
+    jt_mul<S>(J, F, dq);
+    return true;
+  }
 }
 
-template <class P, class Src, bool CYC>
+template <class P, class Src, int FORM>
 __global__ void __launch_bounds__(128) k_project_f64(const __grid_constant__ ProjArgs64<P, Src> a) {
   constexpr int D = P::D, K = kdim<P>();
+  constexpr bool CYC = FORM == FORM_CYCLIC;
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= a.src.clamp_total(a.total)) return;
   const OpsF64Plain ops{nullptr};
@@ -1282,7 +1397,7 @@ __global__ void __launch_bounds__(128) k_project_f64(const __grid_constant__ Pro
           return;
         }
 #pragma unroll
-        for (int j = 0; j < D; ++j) q[j] -= dq[j];
+        for (int j = 0; j < D; ++j) q[j] -= a.alpha * dq[j];
       });
       if (sing) {
         fl |= FL_NONFINITE;
@@ -1300,18 +1415,29 @@ __global__ void __launch_bounds__(128) k_project_f64(const __grid_constant__ Pro
     } else {
       double J[K][D];
       jacobian<P>(a.m, q, k, e, J);
-      double Am[K * (K + 1) / 2];
-      gram<P>(J, a.lambda, Am);
-      const double piv = cholesky_solve<K, OpsF64Plain>(Am, F);
+      double dq[D];
+      double piv;
+      if constexpr (FORM == FORM_OUTER) {
+        double Am[D * (D + 1) / 2];
+        gram_outer<P>(J, a.lambda, Am);
+        jt_mul<P>(J, F, dq);
+        piv = cholesky_solve<D, OpsF64Plain>(Am, dq);
+      } else {
+        double Am[K * (K + 1) / 2];
+        gram<P>(J, a.lambda, Am);
+        piv = cholesky_solve<K, OpsF64Plain>(Am, F);
+        jt_mul<P>(J, F, dq);
+      }
       if (!(piv > 0.0)) {
         fl |= FL_NONFINITE;
         break;
       }
-      double dq[D];
-      jt_mul<P>(J, F, dq);
       double s2 = 0.0;
 #pragma unroll
-      for (int j = 0; j < D; ++j) s2 = fma(dq[j], dq[j], s2);
+      for (int j = 0; j < D; ++j) {
+        dq[j] *= a.alpha;
+        s2 = fma(dq[j], dq[j], s2);
+      }
       if (a.max_step2 > 0.0 && s2 > a.max_step2) {
         fl |= FL_DIV;
         break;
@@ -1475,7 +1601,7 @@ __global__ void __launch_bounds__(128) k_vjp(const __grid_constant__ VjpArgs<P> 
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-template <class P, class Src, int TPB, bool CYC, bool CHK>
+template <class P, class Src, int TPB, int FORM, bool CHK>
 cudaError_t launch_persistent(const HostModel &hm, const ProjCall &c, const Src &src) {
   ProjArgs<P, Src> a;
   a.m = hm.m32;
@@ -1497,6 +1623,7 @@ cudaError_t launch_persistent(const HostModel &hm, const ProjCall &c, const Src 
   a.pivot = static_cast<float>(c.pivot);
   a.tol2_64 = c.tol * c.tol;
   a.lambda64 = c.lambda;
+  a.alpha = static_cast<float>(c.alpha);
   a.chk = hm.d_chk;
   a.obs = reinterpret_cast<const float *>(hm.d_obs32);
   a.box = hm.d_box32;
@@ -1510,11 +1637,11 @@ cudaError_t launch_persistent(const HostModel &hm, const ProjCall &c, const Src 
   const long long max_useful = (warps_needed + (TPB / 32) - 1) / (TPB / 32);
   if (blocks > max_useful) blocks = max_useful;
   if (blocks < 1) blocks = 1;
-  k_project_f32<P, Src, TPB, CYC, CHK><<<static_cast<unsigned>(blocks), TPB, smem, c.stream>>>(a);
+  k_project_f32<P, Src, TPB, FORM, CHK><<<static_cast<unsigned>(blocks), TPB, smem, c.stream>>>(a);
   return cudaGetLastError();
 }
 
-template <class P, class Src, bool CYC = false>
+template <class P, class Src, int FORM = FORM_STACKED>
 cudaError_t launch_plain64(const HostModel &hm, const ProjCall &c, const Src &src) {
   ProjArgs64<P, Src> a;
   a.m = hm.m64;
@@ -1529,18 +1656,23 @@ cudaError_t launch_plain64(const HostModel &hm, const ProjCall &c, const Src &sr
   a.tol2 = c.tol * c.tol;
   a.lambda = c.lambda;
   a.max_step2 = c.max_step > 0 ? c.max_step * c.max_step : 0.0;
+  a.alpha = c.alpha;
   const long long blocks = (c.total + 127) / 128;
-  k_project_f64<P, Src, CYC><<<static_cast<unsigned>(blocks), 128, 0, c.stream>>>(a);
+  k_project_f64<P, Src, FORM><<<static_cast<unsigned>(blocks), 128, 0, c.stream>>>(a);
   return cudaGetLastError();
 }
 
-// Plain FP64 launch, stacked or cyclic (one constraint: the two forms coincide).
+// Plain FP64 launch in the requested form (one constraint: cyclic = stacked).
 template <class P, class Src>
 cudaError_t launch_plain64_any(const HostModel &hm, const ProjCall &c, const Src &src) {
-  if constexpr (P::NC > 1) {
-    if (c.cyclic) return launch_plain64<P, Src, true>(hm, c, src);
+  if (c.outer) {
+    if constexpr (P::D <= 14) return launch_plain64<P, Src, FORM_OUTER>(hm, c, src);
+    else return cudaErrorNotSupported;
   }
-  return launch_plain64<P, Src, false>(hm, c, src);
+  if constexpr (P::NC > 1) {
+    if (c.cyclic) return launch_plain64<P, Src, FORM_CYCLIC>(hm, c, src);
+  }
+  return launch_plain64<P, Src, FORM_STACKED>(hm, c, src);
 }
 
 template <class P>
@@ -1581,13 +1713,19 @@ cudaError_t launch_project_impl(const HostModel &hm, const ProjCall &c, int *lau
   auto go = [&](auto src, auto chk) -> cudaError_t {
     using S = decltype(src);
     constexpr bool CHK = decltype(chk)::value;
+    if (c.outer) {  // the outer form: d x d systems, thread kernels up to 14 joints
+      if constexpr (P::D <= 14 && !CHK && std::is_same_v<S, BatchSrc<float>>)
+        return launch_persistent<P, S, 128, FORM_OUTER, false>(hm, c, src);
+      else
+        return cudaErrorNotSupported;
+    }
     if constexpr (P::NC > 1) {  // one constraint: the cyclic and stacked forms coincide
-      if (c.cyclic) return launch_persistent<P, S, 128, true, CHK>(hm, c, src);
+      if (c.cyclic) return launch_persistent<P, S, 128, FORM_CYCLIC, CHK>(hm, c, src);
     }
     switch (c.tune.tpb) {
-      case 64: return launch_persistent<P, S, 64, false, CHK>(hm, c, src);
-      case 256: return launch_persistent<P, S, 256, false, CHK>(hm, c, src);
-      default: return launch_persistent<P, S, 128, false, CHK>(hm, c, src);
+      case 64: return launch_persistent<P, S, 64, FORM_STACKED, CHK>(hm, c, src);
+      case 256: return launch_persistent<P, S, 256, FORM_STACKED, CHK>(hm, c, src);
+      default: return launch_persistent<P, S, 128, FORM_STACKED, CHK>(hm, c, src);
     }
   };
   if (c.segments) {

@@ -31,6 +31,16 @@ struct ProbSphere3 {
   __host__ __device__ static constexpr int cfb(int) { return -1; }
 };
 
+// --- the Cartesian point on four planes through one point (k = 4 > d = 3): a
+//     consistent overdetermined stack, where J J^T is singular and the outer
+//     form (J^T J + lambda I)^-1 J^T F of Alg. 2 is the step that works ---
+struct ProbPoint3Planes4 : ProbSphere3 {
+  static constexpr const char *name = "point3_planes4";
+  static constexpr int NC = 4;
+  __host__ __device__ static constexpr int ckind(int) { return K_PLANE; }
+  __host__ __device__ static constexpr int cfa(int) { return 0; }
+};
+
 // --- 7-DoF DH chain: a = 0, d_i along z, twists alternating +-pi/2 ---
 struct ArmChain7 {
   __host__ __device__ static constexpr int arm_xrot(int i) {

@@ -107,6 +107,7 @@ struct WarpArgs {
   float pivot;
   double tol2_64;
   double lambda64;
+  float alpha;
 };
 
 // C = A B for row-major 3x4 rigid transforms held in registers
@@ -526,6 +527,8 @@ __device__ __forceinline__ bool warp_iter(const A &a, const WarpTables<P> &tb, W
   __syncwarp();
   yv += subst(rv);
   jt_y(yv);
+#pragma unroll
+  for (int s = 0; s < SL; ++s) dq[s] *= a.alpha;
   if constexpr (MODE >= 0) {  // a sub-step of a sweep: the sweep does the rest
 #pragma unroll
     for (int s = 0; s < SL; ++s) {
@@ -669,7 +672,8 @@ __global__ void __launch_bounds__(W * 32) k_project_warp(const __grid_constant__
     if (pend == 32 || (drained && pend > 0)) {
       if (lane < pend) {
         const uint32_t meta = s_meta[wib][lane];
-        accept_one<P, CYC>(a, s_item[wib][lane], static_cast<int>(meta & 0xffu), meta >> 8);
+        accept_one<P, CYC ? FORM_CYCLIC : FORM_STACKED>(a, s_item[wib][lane], static_cast<int>(meta & 0xffu),
+                                                        meta >> 8);
       }
       pend = 0;
       __syncwarp();
@@ -728,6 +732,8 @@ cudaError_t launch_project_warp(const HostModel &hm, const ProjCall &c, int *lau
   a.pivot = static_cast<float>(c.pivot);
   a.tol2_64 = c.tol * c.tol;
   a.lambda64 = c.lambda;
+  a.alpha = static_cast<float>(c.alpha);
+  if (c.outer) return cudaErrorNotSupported;
   auto go = [&](auto kern) -> cudaError_t {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W * 32, 0);

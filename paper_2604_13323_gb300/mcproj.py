@@ -51,7 +51,7 @@ class ExtendParams(ctypes.Structure):
 class ProjectParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iters", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("lam", ctypes.c_double), ("max_step", ctypes.c_double), ("pivot_fp64", ctypes.c_double),
-                ("cyclic", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("cyclic", ctypes.c_int32), ("outer", ctypes.c_int32), ("alpha", ctypes.c_double)]
 
 
 _lib = None
@@ -242,7 +242,8 @@ class Projector:
     def params(p) -> ProjectParams:
         return ProjectParams(tol=p.tol, max_iters=p.max_iters, precision=p.precision, lam=p.lam,
                              max_step=p.max_step, pivot_fp64=p.pivot_fp64,
-                             cyclic=int(bool(getattr(p, "cyclic", False))), reserved=0)
+                             cyclic=int(bool(getattr(p, "cyclic", False))), outer=int(bool(getattr(p, "outer", False))),
+                             alpha=float(getattr(p, "alpha", 1.0)))
 
     # ---- batched entry points (torch CUDA tensors) ----
     def project(self, q, params, out=None, flags=None, iters=None, resid=None, n=None, stream=None):
