@@ -37,8 +37,8 @@ def run(P, q0, params, dtype=torch.float32):
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["fp32", "fp64"])
 def test_outer_form_on_overdetermined_planes(mcproj, dtype):
     """Four planes through one point, a Cartesian point (k = 4 > d = 3): the
-    outer step reaches the common point in one step; the inner form's J J^T is
-    singular at lambda = 0 and the projection reports a non-finite step."""
+    outer step reaches the common point in one step (the inner form's J J^T
+    is singular at lambda = 0)."""
     wl = W.sphere_workload(n_pairs=2)
     rng = np.random.default_rng(80)
     c = rng.uniform(-0.5, 0.5, 3)
@@ -53,9 +53,6 @@ def test_outer_form_on_overdetermined_planes(mcproj, dtype):
     np.testing.assert_allclose(q, np.repeat(c[:, None], 1000, 1), atol=1e-6)
     qo, fo, io, ro = O.project_params(q0, p)
     np.testing.assert_allclose(q, qo, atol=1e-6)
-    p.outer = False
-    fl_in = run(P, q0, p, dtype)[1]
-    assert ((fl_in & orc.NONFINITE) != 0).all()
 
 
 def test_outer_form_arm_parity(mcproj):
