@@ -1120,7 +1120,10 @@ __global__ void __launch_bounds__(128) k_check_f32(const __grid_constant__ Check
 #pragma unroll
   for (int j = 0; j < D; ++j) q[j] = a.q[j * a.ld + i];
   uint32_t tests = 0;
-  const bool hit = check_one_f32<P>(a.m, a.st, s_obs, a.n_obs, s_box, a.n_box, a.tab, q, tests);
+  // a by-value copy lets the compiler read the model's compile-time-indexed
+  // entries straight from the parameter bank (a reference costs registers)
+  const ModelT<float> m = a.m;
+  const bool hit = check_one_f32<P>(m, a.st, s_obs, a.n_obs, s_box, a.n_box, a.tab, q, tests);
   a.out[i] = hit ? 1 : 0;
   if (a.pairs) a.pairs[i] = tests;
 }
