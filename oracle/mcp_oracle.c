@@ -55,7 +55,7 @@
 enum { OR_REVOLUTE = 0, OR_PRISMATIC = 1 };
 enum {
   OR_SPHERE = 0, OR_AXIS_ALIGN = 1, OR_POSE = 2, OR_REL_POSE = 3, OR_COM_XY = 4,
-  OR_PLANE = 5, OR_LINE = 6, OR_DIST = 7, OR_POSE_BOUNDED = 8
+  OR_PLANE = 5, OR_LINE = 6, OR_DIST = 7, OR_POSE_BOUNDED = 8, OR_COM_HULL = 9
 };
 enum {
   OR_CONVERGED = 1, OR_CAP = 2, OR_DIVERGED = 4, OR_NONFINITE = 8, OR_OUT_OF_LIMITS = 64
@@ -83,7 +83,8 @@ typedef struct {
   double P[12];
   double Q[12];
   double target[4];
-  double B[12];   /* POSE_BOUNDED: lower[6] then upper[6] of [t; log R] */
+  double B[12];   /* POSE_BOUNDED: lower[6] then upper[6] of [t; log R];
+                     COM_HULL: the support polygon's vertices x0 y0 x1 y1 ..., counter-clockwise */
 } or_constraint;
 
 typedef struct {
@@ -301,6 +302,7 @@ static int cons_dim(int kind) {
     case OR_LINE: return 2;
     case OR_DIST: return 1;
     case OR_POSE_BOUNDED: return 6;
+    case OR_COM_HULL: return 2;
   }
   return 0;
 }
@@ -316,6 +318,23 @@ static double com_world(const or_robot *rb, const or_kin *K, double x[3], double
   }
   for (int r = 0; r < 3; ++r) x[r] /= M;
   return M;
+}
+
+/* CoM xy Jacobian rows: d x_com / d q_j = (1/M) sum over links i below j of
+ * m_i * (velocity of c_i). */
+static void com_jacobian_xy(const or_robot *rb, const or_kin *K, double ci[][3], double M, double *J, int row0) {
+  const int d = rb->nj;
+  for (int j = 0; j < d; ++j) {
+    double acc[3] = {0, 0, 0};
+    for (int i = 0; i < d; ++i) {
+      if (!is_ancestor(rb, j, i)) continue;
+      double v[3];
+      point_velocity(rb, K, j, ci[i], v);
+      for (int r = 0; r < 3; ++r) acc[r] += rb->mass[i] * v[r];
+    }
+    J[row0 * d + j] = acc[0] / M;
+    J[(row0 + 1) * d + j] = acc[1] / M;
+  }
 }
 
 /* Residual of one constraint (and, if J != NULL, its Jacobian rows). */
@@ -499,18 +518,62 @@ static int cons_eval(const or_robot *rb, const or_constraint *c, const double *q
       double M = com_world(rb, K, x, ci);
       F[0] = x[0] - c->target[0];
       F[1] = x[1] - c->target[1];
-      if (J) {
-        /* d x_com / d q_j = (1/M) sum over links i below j of m_i * (velocity of c_i) */
-        for (int j = 0; j < d; ++j) {
-          double acc[3] = {0, 0, 0};
-          for (int i = 0; i < d; ++i) {
-            if (!is_ancestor(rb, j, i)) continue;
-            double v[3];
-            point_velocity(rb, K, j, ci[i], v);
-            for (int r = 0; r < 3; ++r) acc[r] += rb->mass[i] * v[r];
+      if (J) com_jacobian_xy(rb, K, ci, M, J, row0);
+      return 2;
+    }
+    case OR_COM_HULL: {
+      /* Sec. V-C stability constraint as printed: the CoM's xy distance to the
+       * support polygon, zero inside.  F = c - P(c), P the nearest point of the
+       * polygon (an edge's interior point or a vertex); dF/dq = n n^T J_com on
+       * an edge (n its normal), J_com at a vertex, 0 inside. */
+      double x[3], ci[OR_MAXJ][3];
+      double M = com_world(rb, K, x, ci);
+      const int nv = (int)c->target[0];
+      int inside = 1;
+      for (int e = 0; e < nv; ++e) {
+        const double *a = c->B + 2 * e, *b = c->B + 2 * ((e + 1) % nv);
+        double cr = (b[0] - a[0]) * (x[1] - a[1]) - (b[1] - a[1]) * (x[0] - a[0]);
+        if (cr < 0.0) inside = 0;
+      }
+      double px = x[0], py = x[1], nx = 0.0, ny = 0.0;
+      int on_edge = 0;
+      if (!inside) {
+        double best = INFINITY;
+        for (int e = 0; e < nv; ++e) {
+          const double *a = c->B + 2 * e, *b = c->B + 2 * ((e + 1) % nv);
+          double ex = b[0] - a[0], ey = b[1] - a[1];
+          double t = ((x[0] - a[0]) * ex + (x[1] - a[1]) * ey) / (ex * ex + ey * ey);
+          int interior = t > 0.0 && t < 1.0;
+          if (t < 0.0) t = 0.0;
+          if (t > 1.0) t = 1.0;
+          double qx = a[0] + t * ex, qy = a[1] + t * ey;
+          double dd = (x[0] - qx) * (x[0] - qx) + (x[1] - qy) * (x[1] - qy);
+          if (dd < best) {
+            best = dd;
+            px = qx;
+            py = qy;
+            on_edge = interior;
+            double el = sqrt(ex * ex + ey * ey);
+            nx = ey / el;
+            ny = -ex / el;
           }
-          J[row0 * d + j] = acc[0] / M;
-          J[(row0 + 1) * d + j] = acc[1] / M;
+        }
+      }
+      F[0] = x[0] - px;
+      F[1] = x[1] - py;
+      if (J) {
+        com_jacobian_xy(rb, K, ci, M, J, row0);
+        for (int j = 0; j < d; ++j) {
+          double g0 = J[row0 * d + j], g1 = J[(row0 + 1) * d + j];
+          if (inside) {
+            g0 = g1 = 0.0;
+          } else if (on_edge) {
+            double s = nx * g0 + ny * g1;
+            g0 = nx * s;
+            g1 = ny * s;
+          }
+          J[row0 * d + j] = g0;
+          J[(row0 + 1) * d + j] = g1;
         }
       }
       return 2;
@@ -951,6 +1014,18 @@ void or_resolve_reference(const or_robot *rb, or_constraint *c, const double *q_
     frame_pose(rb, &K, c->fb, Tb);
     c->target[0] = 0.5 * (Ta[3] + Tb[3]);
     c->target[1] = 0.5 * (Ta[7] + Tb[7]);
+  } else if (c->kind == OR_COM_HULL) {
+    /* the support polygon: the xy box around frames a and b grown by the
+     * margin target[1], counter-clockwise */
+    double Ta[12], Tb[12];
+    frame_pose(rb, &K, c->fa, Ta);
+    frame_pose(rb, &K, c->fb, Tb);
+    double m = c->target[1];
+    double x0 = fmin(Ta[3], Tb[3]) - m, x1 = fmax(Ta[3], Tb[3]) + m;
+    double y0 = fmin(Ta[7], Tb[7]) - m, y1 = fmax(Ta[7], Tb[7]) + m;
+    double v[8] = {x0, y0, x1, y0, x1, y1, x0, y1};
+    memcpy(c->B, v, sizeof(v));
+    c->target[0] = 4.0;
   }
 }
 

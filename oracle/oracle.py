@@ -27,8 +27,9 @@ _lib = None
 
 CONVERGED, CAP, DIVERGED, NONFINITE, OUT_OF_LIMITS = 1, 2, 4, 8, 64
 SPHERE, AXIS_ALIGN, POSE, REL_POSE, COM_XY = 0, 1, 2, 3, 4
-PLANE, LINE, DIST, POSE_BOUNDED = 5, 6, 7, 8
-DIM = {SPHERE: 1, AXIS_ALIGN: 2, POSE: 6, REL_POSE: 6, COM_XY: 2, PLANE: 1, LINE: 2, DIST: 1, POSE_BOUNDED: 6}
+PLANE, LINE, DIST, POSE_BOUNDED, COM_HULL = 5, 6, 7, 8, 9
+DIM = {SPHERE: 1, AXIS_ALIGN: 2, POSE: 6, REL_POSE: 6, COM_XY: 2, PLANE: 1, LINE: 2, DIST: 1, POSE_BOUNDED: 6,
+       COM_HULL: 2}
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
@@ -162,6 +163,7 @@ class Oracle:
             B = getattr(c, "B", None)
             for t in range(12):   # unbounded unless given
                 cc.B[t] = float(B[t]) if B is not None else (-np.inf if t < 6 else np.inf)
+            cc.target[3] = 0.0
             if getattr(c, "q_ref", None) is not None:
                 lib.or_resolve_reference(ctypes.byref(r), ctypes.byref(cc), _ptr(_f64(c.q_ref)))
             self.k += DIM[int(c.kind)]

@@ -52,9 +52,10 @@ C_PLANE = 5       # frame origin on the xy-plane of P   (k = 1)
 C_LINE = 6        # frame origin on the z-axis of P     (k = 2)
 C_DIST = 7        # |x_b - x_a| = L, closed linkage     (k = 1)
 C_POSE_BOUNDED = 8  # TSR pose error outside bounds B^w (k = 6)
+C_COM_HULL = 9    # CoM xy distance to the support polygon, zero inside (k = 2)
 
 CONSTRAINT_DIM = {C_SPHERE: 1, C_AXIS_ALIGN: 2, C_POSE: 6, C_REL_POSE: 6, C_COM_XY: 2, C_PLANE: 1, C_LINE: 2,
-                  C_DIST: 1, C_POSE_BOUNDED: 6}
+                  C_DIST: 1, C_POSE_BOUNDED: 6, C_COM_HULL: 2}
 
 # Precision selector of the projection entry point.
 PREC_FP32 = 0   # FP32 Newton with FP64 acceptance
@@ -119,11 +120,15 @@ class Constraint:
     P       3x4: POSE, POSE_BOUNDED -> T_w^0 (TSR frame in world); REL_POSE -> T_ref;
             PLANE / LINE -> task frame whose xy-plane / z-axis holds frame a's origin
     Q       3x4: POSE, POSE_BOUNDED -> T_e^w (end-effector offset in the TSR frame)
-    target  SPHERE -> (radius, -, -); COM_XY -> (cx, cy, -); DIST -> (L, -, -)
-    B       POSE_BOUNDED: 12 bounds of [t; log R], lower[6] then upper[6]
+    target  SPHERE -> (radius, -, -); COM_XY -> (cx, cy, -); DIST -> (L, -, -);
+            COM_HULL -> (number of polygon vertices, margin, -)
+    B       POSE_BOUNDED: 12 bounds of [t; log R], lower[6] then upper[6];
+            COM_HULL: polygon vertices x0, y0, x1, y1, ... counter-clockwise (<= 6)
     q_ref   if given, P (POSE, POSE_BOUNDED, REL_POSE), the origin of P (PLANE,
-            LINE), L (DIST) or the CoM target (COM_XY) is derived from the
-            robot's pose at q_ref when the constraint is loaded
+            LINE), L (DIST), the CoM target (COM_XY) or the support polygon
+            (COM_HULL: the xy box around frames a and b grown by the margin)
+            is derived from the robot's pose at q_ref when the constraint is
+            loaded
     """
     kind: int
     frame_a: int = -1
@@ -580,11 +585,14 @@ def humanoid_nominal(names) -> np.ndarray:
 
 
 def humanoid_workload(seed: int = 1003, n: int = 1048576, n_obstacles: int = 200,
-                      batch_seed: int | None = None) -> Workload:
+                      batch_seed: int | None = None, hull: bool = False) -> Workload:
     """36-DoF tree; feet fixed in 6-D pose (2 x Eq. 1), hands in a fixed relative
     pose (Eq. 2), CoM xy at the support-polygon centre: 20 equations.  All
     references are taken at the nominal stance q_nom; the support-polygon
-    centre is the midpoint of the two foot frames there."""
+    centre is the midpoint of the two foot frames there.  With `hull`, the
+    CoM constraint is the distance to the support polygon instead (zero
+    inside), the polygon being the xy box around the feet at q_nom grown by
+    0.08 m."""
     robot, names = humanoid_robot(seed + 2)
     q_nom = humanoid_nominal(names)
     rng = np.random.default_rng(seed if batch_seed is None else batch_seed)
@@ -593,6 +601,8 @@ def humanoid_workload(seed: int = 1003, n: int = 1048576, n_obstacles: int = 200
     cons = [Constraint(C_POSE, frame_a=0, q_ref=q_nom), Constraint(C_POSE, frame_a=1, q_ref=q_nom),
             Constraint(C_REL_POSE, frame_a=2, frame_b=3, q_ref=q_nom),
             Constraint(C_COM_XY, frame_a=0, frame_b=1, q_ref=q_nom)]
+    if hull:
+        cons[3] = Constraint(C_COM_HULL, frame_a=0, frame_b=1, q_ref=q_nom, target=np.array([4.0, 0.08, 0.0]))
     orng = np.random.default_rng(seed + 1)
     sph = _sphere_obstacles(orng, n_obstacles, (0.5, -2.0, 0.0), (2.5, 2.0, 2.2), 0.05, 0.15)
     # a shelf in front of the robot: two side panels, three boards, a back panel

@@ -368,6 +368,8 @@ def _cases():
     lo = np.array([0.0, -50.0, 0.0, -50.0, 0.0, 0.0])
     yield "tsr", tree, [W.Constraint(W.C_POSE_BOUNDED, frame_a=1, P=P, Q=Q, B=np.concatenate([lo, -lo]))]
     yield "rod", W.dual_rod_workload(n=1).robot, W.dual_rod_workload(n=1).constraints
+    poly = np.array([-0.1, -0.1, 0.1, -0.1, 0.1, 0.1, -0.1, 0.1, 0, 0, 0, 0])
+    yield "hull", tree, [W.Constraint(W.C_COM_HULL, target=np.array([4.0, 0.0, 0.0]), B=poly)]
 
 
 @pytest.mark.parametrize("case", list(_cases()), ids=lambda c: c[0])
@@ -897,3 +899,51 @@ def test_step_scale_alpha():
     for alpha in (0.5, 0.8):
         out = o.project(q0, 1e-13, 1, 0.0, alpha=alpha)[0]
         np.testing.assert_allclose(out, q0 - alpha * (nq - 1) * q0 / nq, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# CoM support-hull constraint (Sec. V-C): the CoM's xy distance to a convex
+# polygon, zero inside.
+# ---------------------------------------------------------------------------
+def test_com_hull_residual_is_distance_to_polygon():
+    """planar 2-link with all mass at the tip: the CoM is the tip, so the
+    residual is the vector from the polygon's nearest point to the tip; checked
+    against a brute-force nearest point on a densely sampled boundary."""
+    rb = planar_2link(0.7, 0.5)
+    square = np.array([0.2, -0.3, 0.8, -0.3, 0.8, 0.3, 0.2, 0.3, 0, 0, 0, 0])
+    o = orc.Oracle(rb, [W.Constraint(W.C_COM_HULL, target=np.array([4.0, 0.0, 0.0]), B=square)])
+    V = square[:8].reshape(4, 2)
+    t = np.linspace(0, 1, 20001)[:, None]
+    boundary = np.concatenate([V[i] + t * (V[(i + 1) % 4] - V[i]) for i in range(4)])
+    rng = np.random.default_rng(90)
+    inside_seen = outside_seen = 0
+    for _ in range(60):
+        q = rng.uniform(-3, 3, 2)
+        tip = np.array([0.7 * math.cos(q[0]) + 0.5 * math.cos(q[0] + q[1]),
+                        0.7 * math.sin(q[0]) + 0.5 * math.sin(q[0] + q[1])])
+        F = o.residual(q)
+        inside = (0.2 <= tip[0] <= 0.8) and (-0.3 <= tip[1] <= 0.3)
+        if inside:
+            inside_seen += 1
+            np.testing.assert_array_equal(F, [0.0, 0.0])
+        else:
+            outside_seen += 1
+            near = boundary[np.argmin(np.linalg.norm(boundary - tip, axis=1))]
+            np.testing.assert_allclose(F, tip - near, atol=1e-4)
+    assert inside_seen > 3 and outside_seen > 20
+
+
+def test_com_hull_reference_box_and_humanoid_hull_projection():
+    wl = W.humanoid_workload(n=64, hull=True)
+    o = orc.Oracle(wl.robot, wl.constraints)
+    _, Tf = o.fk(wl.extra["q_nom"])
+    fa, fb = Tf[0].reshape(3, 4)[:, 3], Tf[1].reshape(3, 4)[:, 3]
+    lo, hi = np.minimum(fa, fb)[:2] - 0.08, np.maximum(fa, fb)[:2] + 0.08
+    B = o.bounds(3)
+    np.testing.assert_allclose(B[:8], [lo[0], lo[1], hi[0], lo[1], hi[0], hi[1], lo[0], hi[1]], atol=1e-14)
+    p = wl.params
+    out, fl, it, res = o.project(wl.q, p.tol, p.max_iters, p.lam)
+    conv = (fl & orc.CONVERGED) != 0
+    assert conv.mean() > 0.9
+    for i in np.flatnonzero(conv)[:16]:
+        assert np.linalg.norm(o.residual(out[:, i])) < p.tol
