@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="arm", choices=["arm", "dual_arm", "dual_segments", "sphere", "humanoid",
-                                                          "arm_tray", "arm_peg", "arm_tsr", "dual_rod", "extend"])
+                                                          "arm_tray", "arm_peg", "arm_tsr", "dual_rod", "extend",
+                                                          "humanoid_hull"])
     ap.add_argument("--cyclic", action="store_true",
                     help="cyclic getDescentStep (one LM step per constraint per sweep) instead of the stacked step")
     ap.add_argument("--cap", type=int, default=0, help="iteration cap (default: the workload's)")
@@ -71,6 +72,9 @@ def make_workload(name, rank):
     if name == "humanoid":
         wl = W.humanoid_workload(batch_seed=1003 + 1000 * rank)
         return wl, wl.q, "humanoid36_1048576", None
+    if name == "humanoid_hull":
+        wl = W.humanoid_workload(batch_seed=1003 + 1000 * rank, hull=True)
+        return wl, wl.q, "humanoid36_hull_1048576", None
     if name in ("arm_tray", "arm_peg", "arm_tsr"):
         wl = W.arm_task_workload(name[4:], batch_seed=None if rank == 0 else 1007 + 1000 * rank)
         return wl, wl.q, f"arm7_{name[4:]}_65536", None
@@ -338,7 +342,7 @@ def run_ours(args):
     # launch shape: the library's autotuner over threads per block, resident
     # blocks per SM and claim size, on this batch (setup, untimed)
     tuning = None
-    if not fp64 and args.workload != "humanoid":
+    if not fp64 and not args.workload.startswith("humanoid"):
         if args.launch:   # a fixed shape (profiler runs reproduce the tuned one)
             vals = [int(v) for v in args.launch.split(",")]
             P.set_tuning(*vals)

@@ -86,8 +86,11 @@ typedef enum {
   MCP_C_LINE = 6,       /* Sec. III task constraint: x on the z-axis of P: F = (x, y) of P^-1 x, k = 2 */
   MCP_C_DIST = 7,       /* Sec. V-C closed linkage: F = |x_b - x_a| - target[0] for the origins of
                            frame_a and frame_b, k = 1 */
-  MCP_C_POSE_BOUNDED = 8 /* Eq. 1 with bounds B^w (Sec. II TSR): e = [t_err; log(R_err)] as for POSE,
+  MCP_C_POSE_BOUNDED = 8, /* Eq. 1 with bounds B^w (Sec. II TSR): e = [t_err; log(R_err)] as for POSE,
                            F_i = e_i - clamp(e_i, B[i], B[6 + i]) (zero inside the bounds), k = 6 */
+  MCP_C_COM_HULL = 9    /* Sec. V-C stability as the distance to the support polygon: F = c - P(c)
+                           with c the CoM xy and P(c) the polygon's nearest point (zero inside); the
+                           polygon's target[0] = 3..6 vertices are B[0..], counter-clockwise, k = 2 */
 } mcp_ckind;
 
 /* Robot: a tree of 1-DoF joints in topological order (parent[j] < j, -1 = world).
@@ -121,8 +124,11 @@ typedef struct {
  *   DIST:     target[0] := |x_b(q_ref) - x_a(q_ref)|
  *   COM_XY:   target := xy midpoint of frames a and b at q_ref (the centre of
  *             the support polygon of two feet).
- * B: POSE_BOUNDED only, lower[6] then upper[6] of [t; log R] (+-inf allowed;
- * lower <= upper required); ignored by the other kinds. */
+ *   COM_HULL: the polygon := the xy box around frames a and b at q_ref grown
+ *             by the margin target[1] (4 vertices).
+ * B: POSE_BOUNDED: lower[6] then upper[6] of [t; log R] (+-inf allowed;
+ * lower <= upper required); COM_HULL: the polygon's vertices; ignored by the
+ * other kinds. */
 typedef struct {
   int32_t kind;
   int32_t frame_a, frame_b;
@@ -169,9 +175,9 @@ mcp_status mcp_load_constraints(mcp_ctx *ctx, const mcp_constraint_desc *cons, i
  * boxes [m * 6] (min xyz, max xyz); HOST memory, copied.  Synchronous. */
 mcp_status mcp_load_obstacles(mcp_ctx *ctx, const double *spheres, int32_t n_spheres, const double *aabbs,
                               int32_t n_aabbs);
-/* Returns the resolved constraint i (after q_ref handling): P, Q (12 each) and
- * target (3), into HOST buffers. */
-mcp_status mcp_get_constraint(const mcp_ctx *ctx, int32_t i, double *P, double *Q, double *target);
+/* Returns the resolved constraint i (after q_ref handling): P, Q (12 each),
+ * target (3) and B (12), into HOST buffers (each may be NULL). */
+mcp_status mcp_get_constraint(const mcp_ctx *ctx, int32_t i, double *P, double *Q, double *target, double *B);
 
 /* ParallelProject (Alg. 2) of n configurations.
  * q_in / q_out: [d * ld] float (precision 0) or double (precision 1); q_out may alias q_in.

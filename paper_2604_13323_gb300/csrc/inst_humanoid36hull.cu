@@ -1,0 +1,37 @@
+// Kernel instantiations for the ProbHumanoid36Hull problem class (CoM on the
+// support polygon): the FP32 path
+// runs the warp-cooperative kernel, the plain FP64 path and the collision
+// check the thread-per-configuration kernels.
+#include "mcp_warp.cuh"
+
+namespace mcp {
+
+template <>
+cudaError_t launch_project<ProbHumanoid36Hull>(const HostModel &hm, const ProjCall &c, int *launches) {
+  if (c.precision == 1) {
+    if (c.total <= 0) return cudaSuccess;
+    if (c.segments) return cudaErrorNotSupported;
+    cudaError_t e =
+        launch_plain64_any<ProbHumanoid36Hull>(hm, c, BatchSrc<double>{static_cast<const double *>(c.q_in), c.ld_in});
+    *launches += 1;
+    if (e == cudaSuccess && c.fused_check) e = check_outputs<ProbHumanoid36Hull>(hm, c, launches);
+    return e;
+  }
+  cudaError_t e = launch_project_warp<ProbHumanoid36Hull>(hm, c, launches);
+  if (e == cudaSuccess && c.fused_check) e = check_outputs<ProbHumanoid36Hull>(hm, c, launches);
+  return e;
+}
+
+template <>
+cudaError_t launch_check<ProbHumanoid36Hull>(const HostModel &hm, const CheckCall &c, int *launches) {
+  return launch_check_impl<ProbHumanoid36Hull>(hm, c, launches);
+}
+
+template <>
+cudaError_t launch_vjp<ProbHumanoid36Hull>(const HostModel &, const VjpCall &, int *) {
+  return cudaErrorNotSupported;
+}
+
+MCP_NO_EXTEND(ProbHumanoid36Hull)
+
+}  // namespace mcp

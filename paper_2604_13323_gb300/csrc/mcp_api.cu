@@ -72,7 +72,8 @@ const std::vector<ClassDesc> &registry() {
       describe<ProbSphere3>(true),   describe<ProbPoint3Planes4>(true), describe<ProbArm7Axis>(true),
       describe<ProbArm7Pose>(true),
       describe<ProbArm7Tray>(true),  describe<ProbArm7Peg>(true),   describe<ProbArm7Tsr>(true),
-      describe<ProbDual14Rel>(true), describe<ProbDual14Rod>(true), describe<ProbHumanoid36>(true)};
+      describe<ProbDual14Rel>(true), describe<ProbDual14Rod>(true), describe<ProbHumanoid36>(true),
+      describe<ProbHumanoid36Hull>(true)};
   return r;
 }
 
@@ -117,11 +118,11 @@ struct ResolveIn {
   int parent[MAXJ], type[MAXJ], flink[MAXF];
   double X[MAXJ][12], fX[MAXF][12], mass[MAXJ];
   int kind[MAXC], fa[MAXC], fb[MAXC], has_ref[MAXC];
-  double P[MAXC][12], Q[MAXC][12], tgt[MAXC][3];
+  double P[MAXC][12], Q[MAXC][12], tgt[MAXC][3], B[MAXC][12];
   double qref[MAXC][MAXJ];
 };
 struct ResolveOut {
-  double P[MAXC][12], Q[MAXC][12], tgt[MAXC][3];
+  double P[MAXC][12], Q[MAXC][12], tgt[MAXC][3], B[MAXC][12];
   double Pinv[MAXC][12], Qinv[MAXC][12];
   double msub[MAXJ];
   double inv_mass;
@@ -175,6 +176,7 @@ __global__ void k_resolve(const __grid_constant__ ResolveIn in, ResolveOut *out)
       out->Q[c][i] = in.Q[c][i];
     }
     for (int i = 0; i < 3; ++i) out->tgt[c][i] = in.tgt[c][i];
+    for (int i = 0; i < 12; ++i) out->B[c][i] = in.B[c][i];
     if (in.has_ref[c]) {
       for (int j = 0; j < in.nj; ++j) {
         double pre[12], M[12];
@@ -222,6 +224,14 @@ __global__ void k_resolve(const __grid_constant__ ResolveIn in, ResolveOut *out)
       } else if (in.kind[c] == K_COM) {
         out->tgt[c][0] = 0.5 * (Tf[a][3] + Tf[b][3]);
         out->tgt[c][1] = 0.5 * (Tf[a][7] + Tf[b][7]);
+      } else if (in.kind[c] == K_HULL) {
+        // the support polygon: the xy box around frames a and b grown by the margin tgt[1]
+        const double mg = in.tgt[c][1];
+        const double x0 = fmin(Tf[a][3], Tf[b][3]) - mg, x1 = fmax(Tf[a][3], Tf[b][3]) + mg;
+        const double y0 = fmin(Tf[a][7], Tf[b][7]) - mg, y1 = fmax(Tf[a][7], Tf[b][7]) + mg;
+        const double v[8] = {x0, y0, x1, y0, x1, y1, x0, y1};
+        for (int i = 0; i < 8; ++i) out->B[c][i] = v[i];
+        out->tgt[c][0] = 4.0;
       }
     }
     tf_inv64(out->P[c], out->Pinv[c]);
@@ -572,7 +582,7 @@ void fill_constraints(const ResolveOut &ro, const std::vector<ConsHost> &cons, i
     for (int i = 0; i < 12; ++i) {
       m.cPinv[c][i] = static_cast<T>(ro.Pinv[c][i]);
       m.cQinv[c][i] = static_cast<T>(ro.Qinv[c][i]);
-      m.cB[c][i] = static_cast<T>(cons[c].B[i]);
+      m.cB[c][i] = static_cast<T>(ro.B[c][i]);
     }
     for (int i = 0; i < 3; ++i) m.ctgt[c][i] = static_cast<T>(ro.tgt[c][i]);
   }
@@ -648,6 +658,7 @@ mcp_status ensure_resolved(mcp_ctx *ctx) {
       in->Q[c][i] = ch.Q[i];
     }
     for (int i = 0; i < 3; ++i) in->tgt[c][i] = ch.target[i];
+    for (int i = 0; i < 12; ++i) in->B[c][i] = ch.B[i];
     if (ch.has_ref)
       for (int j = 0; j < r.nj; ++j) in->qref[c][j] = ch.q_ref[j];
   }
@@ -668,6 +679,7 @@ mcp_status ensure_resolved(mcp_ctx *ctx) {
     std::memcpy(ctx->cons[c].P, ro.P[c], sizeof(ro.P[c]));
     std::memcpy(ctx->cons[c].Q, ro.Q[c], sizeof(ro.Q[c]));
     std::memcpy(ctx->cons[c].target, ro.tgt[c], sizeof(ro.tgt[c]));
+    std::memcpy(ctx->cons[c].B, ro.B[c], sizeof(ro.B[c]));
   }
   fill_robot_model(r, ctx->hm.m32);
   fill_robot_model(r, ctx->hm.m64);
@@ -831,10 +843,11 @@ mcp_status mcp_load_constraints(mcp_ctx *ctx, const mcp_constraint_desc *cd, int
   int k = 0;
   for (int i = 0; i < n; ++i) {
     const mcp_constraint_desc &c = cd[i];
-    if (c.kind < MCP_C_SPHERE || c.kind > MCP_C_POSE_BOUNDED)
+    if (c.kind < MCP_C_SPHERE || c.kind > MCP_C_COM_HULL)
       return fail(ctx, MCP_ERR_ARG, "constraint %d: kind %d", i, c.kind);
-    const bool uses_a = c.kind != MCP_C_SPHERE && (c.kind != MCP_C_COM_XY || c.q_ref);
-    const bool uses_b = c.kind == MCP_C_REL_POSE || c.kind == MCP_C_DIST || (c.kind == MCP_C_COM_XY && c.q_ref);
+    const bool com = c.kind == MCP_C_COM_XY || c.kind == MCP_C_COM_HULL;
+    const bool uses_a = c.kind != MCP_C_SPHERE && (!com || c.q_ref);
+    const bool uses_b = c.kind == MCP_C_REL_POSE || c.kind == MCP_C_DIST || (com && c.q_ref);
     if (uses_a && (c.frame_a < 0 || c.frame_a >= ctx->robot.nf))
       return fail(ctx, MCP_ERR_ARG, "constraint %d: frame_a %d out of range", i, c.frame_a);
     if (uses_b && (c.frame_b < 0 || c.frame_b >= ctx->robot.nf))
@@ -851,6 +864,8 @@ mcp_status mcp_load_constraints(mcp_ctx *ctx, const mcp_constraint_desc *cd, int
       for (int r = 0; r < 6; ++r)
         if (!(c.B[r] <= c.B[6 + r]))
           return fail(ctx, MCP_ERR_ARG, "constraint %d: bound %d has lower > upper or NaN", i, r);
+    if (c.kind == MCP_C_COM_HULL && !c.q_ref && !(c.target[0] >= 3.0 && c.target[0] <= 6.0))
+      return fail(ctx, MCP_ERR_ARG, "constraint %d: a support polygon has 3 to 6 vertices", i);
     h.has_ref = c.q_ref != nullptr;
     if (h.has_ref) h.q_ref.assign(c.q_ref, c.q_ref + ctx->robot.nj);
     k += cdim(c.kind);
@@ -865,11 +880,12 @@ mcp_status mcp_load_constraints(mcp_ctx *ctx, const mcp_constraint_desc *cd, int
   return ensure_resolved(ctx);
 }
 
-mcp_status mcp_get_constraint(const mcp_ctx *ctx, int32_t i, double *P, double *Q, double *target) {
+mcp_status mcp_get_constraint(const mcp_ctx *ctx, int32_t i, double *P, double *Q, double *target, double *B) {
   if (!ctx || i < 0 || i >= static_cast<int>(ctx->cons.size())) return MCP_ERR_ARG;
   if (P) std::memcpy(P, ctx->cons[i].P, 12 * sizeof(double));
   if (Q) std::memcpy(Q, ctx->cons[i].Q, 12 * sizeof(double));
   if (target) std::memcpy(target, ctx->cons[i].target, 3 * sizeof(double));
+  if (B) std::memcpy(B, ctx->cons[i].B, 12 * sizeof(double));
   return MCP_OK;
 }
 

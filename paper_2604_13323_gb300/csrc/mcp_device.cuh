@@ -30,7 +30,8 @@ enum : int {
   K_PLANE = 5,  // origin of frame a on the xy-plane of the task frame P
   K_LINE = 6,   // origin of frame a on the z-axis of the task frame P
   K_DIST = 7,   // |x_b - x_a| = L (closed linkage)
-  K_PBND = 8    // bounded TSR: Eq. 1 error outside the bounds B^w
+  K_PBND = 8,   // bounded TSR: Eq. 1 error outside the bounds B^w
+  K_HULL = 9    // CoM xy distance to the support polygon (zero inside)
 };
 enum : uint32_t {
   FL_CONV = 1, FL_CAP = 2, FL_DIV = 4, FL_NONFINITE = 8, FL_RESOLVE = 16, FL_ACCEPT_FAIL = 32, FL_LIMITS = 64
@@ -48,7 +49,7 @@ struct ModelT {
   T cPinv[MAXC][12];  // POSE: (T_w^0)^-1; REL_POSE: T_ref^-1
   T cQinv[MAXC][12];  // POSE: (T_e^w)^-1
   T ctgt[MAXC][4];    // SPHERE radius; COM target xy; DIST length
-  T cB[MAXC][12];     // PBND: lower[6], upper[6] of [t; log R]
+  T cB[MAXC][12];     // PBND: lower[6], upper[6] of [t; log R]; HULL: polygon x0 y0 x1 y1 ... (CCW)
   T msub[MAXJ];       // mass of the subtree below (and including) joint j
   T inv_mass;         // 1 / total mass
   T shift[3];         // collision frame: world coordinates minus this origin (root offsets are pre-shifted)
@@ -332,7 +333,7 @@ __host__ __device__ constexpr bool is_anc(int j, int link) {
 __host__ __device__ constexpr int cdim(int kind) {
   return (kind == K_SPHERE || kind == K_PLANE || kind == K_DIST)             ? 1
          : (kind == K_POSE || kind == K_REL || kind == K_PBND)               ? 6
-                                                                             : 2;  // AXIS, COM, LINE
+                                                                             : 2;  // AXIS, COM, LINE, HULL
 }
 // Model slot of constraint c: a sub-problem (one constraint of a stack, used
 // by the cyclic form) reads the slot of the constraint it stands for.
@@ -379,14 +380,14 @@ __host__ __device__ constexpr bool needs_fk() {
 template <class P>
 __host__ __device__ constexpr bool needs_com() {
   for (int c = 0; c < P::NC; ++c)
-    if (P::ckind(c) == K_COM) return true;
+    if (P::ckind(c) == K_COM || P::ckind(c) == K_HULL) return true;
   return false;
 }
 // Sign with which joint j enters row block of constraint c (0 = structurally zero).
 template <class P>
 __host__ __device__ constexpr int col_sign(int c, int j) {
   const int k = P::ckind(c);
-  if (k == K_SPHERE || k == K_COM) return 1;
+  if (k == K_SPHERE || k == K_COM || k == K_HULL) return 1;
   if (k == K_REL || k == K_DIST)
     return (is_anc<P>(j, P::frame_link(P::cfb(c))) ? 1 : 0) - (is_anc<P>(j, P::frame_link(P::cfa(c))) ? 1 : 0);
   return is_anc<P>(j, P::frame_link(P::cfa(c))) ? 1 : 0;
@@ -600,6 +601,48 @@ __device__ __forceinline__ T cholesky_solve(T (&A)[K * (K + 1) / 2], T (&b)[K]) 
   const T minpiv = cholesky_factor<K, Ops>(A, inv);
   cholesky_subst<K>(A, inv, b);
   return minpiv;
+}
+
+
+// Nearest point of a convex polygon (vertices v[2 nv], counter-clockwise) to
+// the point (x, y).  mode 0: inside (the point itself); 1: on an edge's
+// interior, (nx, ny) its outward unit normal; 2: at a vertex.  Ties between
+// edges go to the first.
+template <typename T>
+__device__ __forceinline__ int polygon_nearest(const T *v, int nv, T x, T y, T &px, T &py, T &nx, T &ny) {
+  bool inside = true;
+  for (int e = 0; e < nv; ++e) {
+    const int f = e + 1 < nv ? e + 1 : 0;
+    const T cr = (v[2 * f] - v[2 * e]) * (y - v[2 * e + 1]) - (v[2 * f + 1] - v[2 * e + 1]) * (x - v[2 * e]);
+    if (cr < T(0)) inside = false;
+  }
+  px = x;
+  py = y;
+  nx = ny = T(0);
+  if (inside) return 0;
+  int mode = 2;
+  T best = T(0);
+  bool first = true;
+  for (int e = 0; e < nv; ++e) {
+    const int f = e + 1 < nv ? e + 1 : 0;
+    const T ex = v[2 * f] - v[2 * e], ey = v[2 * f + 1] - v[2 * e + 1];
+    T t = ((x - v[2 * e]) * ex + (y - v[2 * e + 1]) * ey) / (ex * ex + ey * ey);
+    const bool interior = t > T(0) && t < T(1);
+    t = t < T(0) ? T(0) : (t > T(1) ? T(1) : t);
+    const T qx = v[2 * e] + t * ex, qy = v[2 * e + 1] + t * ey;
+    const T dd = (x - qx) * (x - qx) + (y - qy) * (y - qy);
+    if (first || dd < best) {
+      first = false;
+      best = dd;
+      px = qx;
+      py = qy;
+      mode = interior ? 1 : 2;
+      const T el = sqrt(ex * ex + ey * ey);
+      nx = ey / el;
+      ny = -ex / el;
+    }
+  }
+  return mode;
 }
 
 }  // namespace mcp

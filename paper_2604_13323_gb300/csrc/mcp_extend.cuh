@@ -83,9 +83,11 @@ __device__ __forceinline__ void accept_regs(const A &a, float (&q)[P::D], int &i
   }
 }
 
-// Projects the point of every active lane (warp-convergent: all lanes call it).
+// Projects the point of every active lane (warp-convergent: all lanes call
+// it).  Out of line: the extension calls it at three places and one copy keeps
+// the kernel within the instruction cache.
 template <class P, class A>
-__device__ __forceinline__ void project_lanes(const A &a, float (&q)[P::D], bool active, int &it, uint32_t &fl) {
+__device__ __noinline__ void project_lanes(const A &a, float (&q)[P::D], bool active, int &it, uint32_t &fl) {
   it = 0;
   fl = 0;
   bool done = !active;
@@ -93,6 +95,14 @@ __device__ __forceinline__ void project_lanes(const A &a, float (&q)[P::D], bool
     if (!done) done = newton_iter_f32<P>(a, q, it, fl);
   }
   if (active) accept_regs<P>(a, q, it, fl);
+}
+
+// Collision verdict of one lane's configuration, out of line (called at three places).
+template <class P>
+__device__ __noinline__ bool collides_lane(const CheckData *chk, const float4 *s_obs, int n_obs, const float *s_box,
+                                           int n_box, const double2 *tab, const float (&q)[P::D]) {
+  uint32_t t = 0;
+  return check_one_f32<P>(chk->m, chk->st, s_obs, n_obs, s_box, n_box, tab, q, t);
 }
 
 template <int D>
@@ -123,10 +133,8 @@ __global__ void __launch_bounds__(W * 32) k_extend(const __grid_constant__ ExtAr
   const int wib = threadIdx.x >> 5;
   float *chain = s_chain + static_cast<size_t>(wib) * 2 * EXT_MAXPTS * D;  // [EXT_MAXPTS][D]
   float *next = chain + EXT_MAXPTS * D;
-  const CheckData &cd = *a.chk;
   auto collides = [&](const float (&q)[D]) -> bool {
-    uint32_t t = 0;
-    return check_one_f32<P>(cd.m, cd.st, s_obs, a.n_obs, s_box, a.n_box, a.tab, q, t);
+    return collides_lane<P>(a.chk, s_obs, a.n_obs, s_box, a.n_box, a.tab, q);
   };
   while (true) {
     unsigned long long e = 0;

@@ -39,6 +39,8 @@ struct Eval {
   T beta[P::NC];     // Jl^-1 coefficient
   V3<T> za[P::NC];   // AXIS: frame z axis; DIST: unit vector from x_a to x_b
   bool act[P::NC][6];  // PBND: component outside its bounds
+  int hmode[P::NC];    // HULL: 0 inside, 1 nearest point on an edge, 2 at a vertex
+  T hn[P::NC][2];      // HULL: outward normal of that edge
   T inv_norm;        // SPHERE: 1 / |q|
   V3<T> C[P::D];     // COM: mass-weighted CoM sum over the subtree of joint j
 };
@@ -147,7 +149,7 @@ __device__ __forceinline__ void residual(const ModelT<T> &m, const T (&q)[P::D],
       const T inv = Ops::rsqrt_(n2);
       F[r0] = n2 * inv - m.ctgt[cm][0];
       if constexpr (WANT_J) e.za[c] = V3<T>{dv.x * inv, dv.y * inv, dv.z * inv};
-    } else if constexpr (kind == K_COM) {
+    } else if constexpr (kind == K_COM || kind == K_HULL) {
       // Sec. V-C: x_com = sum_i m_i c_i / M with c_i = T_i com_i (the sum is
       // accumulated during FK).  With WANT_J the subtree sums C_j = m_j c_j +
       // sum over children are built in reverse topological order.
@@ -163,8 +165,22 @@ __device__ __forceinline__ void residual(const ModelT<T> &m, const T (&q)[P::D],
           e.C[j] = acc;
         });
       }
-      F[r0] = fma_(k.mc.x, m.inv_mass, -m.ctgt[cm][0]);
-      F[r0 + 1] = fma_(k.mc.y, m.inv_mass, -m.ctgt[cm][1]);
+      if constexpr (kind == K_COM) {
+        F[r0] = fma_(k.mc.x, m.inv_mass, -m.ctgt[cm][0]);
+        F[r0 + 1] = fma_(k.mc.y, m.inv_mass, -m.ctgt[cm][1]);
+      } else {
+        // distance to the support polygon: F = c - nearest point (zero inside)
+        const T cx = k.mc.x * m.inv_mass, cy = k.mc.y * m.inv_mass;
+        T px, py, nx, ny;
+        const int mode = polygon_nearest<T>(m.cB[cm], static_cast<int>(m.ctgt[cm][0]), cx, cy, px, py, nx, ny);
+        F[r0] = cx - px;
+        F[r0 + 1] = cy - py;
+        if constexpr (WANT_J) {
+          e.hmode[c] = mode;
+          e.hn[c][0] = nx;
+          e.hn[c][1] = ny;
+        }
+      }
     }
   });
 }
@@ -227,19 +243,31 @@ __device__ __forceinline__ void jacobian(const ModelT<T> &m, const T (&q)[P::D],
           const V3<T> v = rev ? cross(k.z[j], sub(k.fp[f], k.p[j])) : k.z[j];
           const T d = fma_(e.za[c].x, v.x, fma_(e.za[c].y, v.y, e.za[c].z * v.z));
           J[r0][j] = s > 0 ? d : -d;
-        } else if constexpr (kind == K_COM) {
+        } else if constexpr (kind == K_COM || kind == K_HULL) {
           // d x_com / d q_j = (1/M) z_j x (C_j - M_j o_j) (revolute), (M_j / M) z_j (prismatic)
+          T g0, g1;
           if constexpr (rev) {
             const T Mj = m.msub[j];
             const V3<T> r{fma_(-Mj, k.p[j].x, e.C[j].x), fma_(-Mj, k.p[j].y, e.C[j].y), fma_(-Mj, k.p[j].z, e.C[j].z)};
             const V3<T> d = cross(k.z[j], r);
-            J[r0][j] = d.x * m.inv_mass;
-            J[r0 + 1][j] = d.y * m.inv_mass;
+            g0 = d.x * m.inv_mass;
+            g1 = d.y * m.inv_mass;
           } else {
             const T f = m.msub[j] * m.inv_mass;
-            J[r0][j] = f * k.z[j].x;
-            J[r0 + 1][j] = f * k.z[j].y;
+            g0 = f * k.z[j].x;
+            g1 = f * k.z[j].y;
           }
+          if constexpr (kind == K_HULL) {  // inside: 0; on an edge: n n^T g; at a vertex: g
+            if (e.hmode[c] == 0) {
+              g0 = g1 = T(0);
+            } else if (e.hmode[c] == 1) {
+              const T sdot = fma_(e.hn[c][0], g0, e.hn[c][1] * g1);
+              g0 = e.hn[c][0] * sdot;
+              g1 = e.hn[c][1] * sdot;
+            }
+          }
+          J[r0][j] = g0;
+          J[r0 + 1][j] = g1;
         }
       }
     });
@@ -1005,6 +1033,86 @@ __device__ __forceinline__ bool sphere_hits_plain(V3<T> c, T rs, const T *s_obs,
 
 constexpr int SPH_BLOCK = 8;
 
+// A rotation by value (nine registers across a call).
+struct Rot9 {
+  float r[9];
+};
+
+// Spheres [s0, e) of one link placed by (R, p), with the link's bounding
+// sphere lb (local): the boxes, then the bounding sphere against chunks of 32
+// obstacles (broad phase), then the link's spheres in blocks of 8 against the
+// candidate obstacles (narrow phase).  One out-of-line copy serves every link
+// of every kernel (inlined per link, the unrolled broad phase made kernels
+// with many links instruction-cache bound).
+static __device__ __noinline__ bool link_hits_f32(const Rot9 Rr, V3<float> p, int s0, int e, const float *lb,
+                                           const SphereTable<float> &st, const float4 *s_obs, int n_obs,
+                                           const float *s_box, int n_box, uint32_t *tests_io) {
+  if (s0 >= e) return false;
+  const float(&R)[9] = Rr.r;
+  uint32_t tests = *tests_io;
+  bool hit = false;
+  if (n_box > 0) {
+    for (int s = s0; s < e && !hit; ++s) {
+      const V3<float> c = add_rot_t<7>(p, R, V3<float>{st.s[s][0], st.s[s][1], st.s[s][2]});
+      if (box_hits<float>(c, st.s[s][3], s_box, n_box)) hit = true;
+    }
+  }
+  const V3<float> bc = add_rot_t<7>(p, R, V3<float>{lb[0], lb[1], lb[2]});
+  const float br = lb[3];
+  const float kb = fmaf(bc.x, bc.x, fmaf(bc.y, bc.y, fmaf(bc.z, bc.z, -br * br)));
+  for (int o0 = 0; o0 < n_obs && !hit; o0 += 32) {
+    const int cnt = min(32, n_obs - o0);
+    unsigned cand = 0u;
+    if (cnt == 32) {  // full chunk: unrolled, compile-time bit positions
+#pragma unroll
+      for (int t = 0; t < 32; ++t) {
+        const float4 g = s_obs[2 * (o0 + t)];
+        const float g2 = s_obs[2 * (o0 + t) + 1].x;
+        const float v = fmaf(bc.x, g.x, fmaf(bc.y, g.y, fmaf(bc.z, g.z, fmaf(br, g2, g.w))));
+        cand |= (v < -kb) ? (1u << t) : 0u;
+      }
+    } else {
+      for (int t = 0; t < cnt; ++t) {
+        const float4 g = s_obs[2 * (o0 + t)];
+        const float g2 = s_obs[2 * (o0 + t) + 1].x;
+        const float v = fmaf(bc.x, g.x, fmaf(bc.y, g.y, fmaf(bc.z, g.z, fmaf(br, g2, g.w))));
+        if (v < -kb) cand |= 1u << t;
+      }
+    }
+    tests += static_cast<uint32_t>(cnt);
+    if (!cand) continue;
+    for (int sb = s0; sb < e && !hit; sb += SPH_BLOCK) {
+      const int count = min(SPH_BLOCK, e - sb);
+      float cx[SPH_BLOCK], cy[SPH_BLOCK], cz[SPH_BLOCK], rs[SPH_BLOCK], ks[SPH_BLOCK];
+#pragma unroll
+      for (int b = 0; b < SPH_BLOCK; ++b) {
+        const int s = sb + (b < count ? b : 0);
+        const V3<float> c = add_rot_t<7>(p, R, V3<float>{st.s[s][0], st.s[s][1], st.s[s][2]});
+        cx[b] = c.x;
+        cy[b] = c.y;
+        cz[b] = c.z;
+        rs[b] = st.s[s][3];
+        ks[b] = (b < count) ? fmaf(c.x, c.x, fmaf(c.y, c.y, fmaf(c.z, c.z, -rs[b] * rs[b]))) : FLT_MAX;  // pad: never a hit
+      }
+      unsigned msk = cand;
+      while (msk && !hit) {
+        const int t = __ffs(static_cast<int>(msk)) - 1;
+        msk &= msk - 1u;
+        const float4 g = s_obs[2 * (o0 + t)];
+        const float g2 = s_obs[2 * (o0 + t) + 1].x;
+        bool h = false;
+#pragma unroll
+        for (int b = 0; b < SPH_BLOCK; ++b)
+          h |= fmaf(cx[b], g.x, fmaf(cy[b], g.y, fmaf(cz[b], g.z, fmaf(rs[b], g2, g.w)))) < -ks[b];
+        tests += static_cast<uint32_t>(count);
+        hit = h;
+      }
+    }
+  }
+  *tests_io = tests;
+  return hit;
+}
+
 // Collision verdict of one configuration q in the collision frame: model m
 // (root offsets shifted by the obstacle origin), spheres st, obstacle records
 // and boxes staged in shared memory.  `tests` counts the 4-FMA tests made.
@@ -1014,72 +1122,10 @@ __device__ __forceinline__ bool check_one_f32(const ModelT<float> &m, const Sphe
                                               const double2 *tab, const float (&q)[P::D], uint32_t &tests) {
   const OpsF32 ops{tab};
   bool hit = false;
-  // spheres [s0, e) placed by (R, p), bounding sphere lb (local) of the group
-  auto group_hits = [&](const float (&R)[9], V3<float> p, int s0, int e, const float *lb) -> bool {
-    if (s0 >= e) return false;
-    if (n_box > 0) {
-      for (int s = s0; s < e; ++s) {
-        const V3<float> c = add_rot_t<7>(p, R, V3<float>{st.s[s][0], st.s[s][1], st.s[s][2]});
-        if (box_hits<float>(c, st.s[s][3], s_box, n_box)) return true;
-      }
-    }
-    const V3<float> bc = add_rot_t<7>(p, R, V3<float>{lb[0], lb[1], lb[2]});
-    const float br = lb[3];
-    const float kb = fmaf(bc.x, bc.x, fmaf(bc.y, bc.y, fmaf(bc.z, bc.z, -br * br)));
-    for (int o0 = 0; o0 < n_obs; o0 += 32) {
-      const int cnt = min(32, n_obs - o0);
-      unsigned cand = 0u;
-      if (cnt == 32) {  // full chunk: unrolled, compile-time bit positions
-#pragma unroll
-        for (int t = 0; t < 32; ++t) {
-          const float4 g = s_obs[2 * (o0 + t)];
-          const float g2 = s_obs[2 * (o0 + t) + 1].x;
-          const float v = fmaf(bc.x, g.x, fmaf(bc.y, g.y, fmaf(bc.z, g.z, fmaf(br, g2, g.w))));
-          cand |= (v < -kb) ? (1u << t) : 0u;
-        }
-      } else {
-        for (int t = 0; t < cnt; ++t) {
-          const float4 g = s_obs[2 * (o0 + t)];
-          const float g2 = s_obs[2 * (o0 + t) + 1].x;
-          const float v = fmaf(bc.x, g.x, fmaf(bc.y, g.y, fmaf(bc.z, g.z, fmaf(br, g2, g.w))));
-          if (v < -kb) cand |= 1u << t;
-        }
-      }
-      tests += static_cast<uint32_t>(cnt);
-      if (!cand) continue;
-      for (int sb = s0; sb < e; sb += SPH_BLOCK) {
-        const int count = min(SPH_BLOCK, e - sb);
-        float cx[SPH_BLOCK], cy[SPH_BLOCK], cz[SPH_BLOCK], rs[SPH_BLOCK], ks[SPH_BLOCK];
-#pragma unroll
-        for (int b = 0; b < SPH_BLOCK; ++b) {
-          const int s = sb + (b < count ? b : 0);
-          const V3<float> c = add_rot_t<7>(p, R, V3<float>{st.s[s][0], st.s[s][1], st.s[s][2]});
-          cx[b] = c.x;
-          cy[b] = c.y;
-          cz[b] = c.z;
-          rs[b] = st.s[s][3];
-          ks[b] = (b < count) ? fmaf(c.x, c.x, fmaf(c.y, c.y, fmaf(c.z, c.z, -rs[b] * rs[b]))) : FLT_MAX;  // pad: never a hit
-        }
-        unsigned msk = cand;
-        while (msk) {
-          const int t = __ffs(static_cast<int>(msk)) - 1;
-          msk &= msk - 1u;
-          const float4 g = s_obs[2 * (o0 + t)];
-          const float g2 = s_obs[2 * (o0 + t) + 1].x;
-          bool h = false;
-#pragma unroll
-          for (int b = 0; b < SPH_BLOCK; ++b)
-            h |= fmaf(cx[b], g.x, fmaf(cy[b], g.y, fmaf(cz[b], g.z, fmaf(rs[b], g2, g.w)))) < -ks[b];
-          tests += static_cast<uint32_t>(count);
-          if (h) return true;
-        }
-      }
-    }
-    return false;
-  };
   {
-    const float Ri[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
-    hit = group_hits(Ri, V3<float>{-m.shift[0], -m.shift[1], -m.shift[2]}, st.off[0], st.off[1], st.lb[MAXJ]);
+    const Rot9 Ri{{1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f}};
+    hit = link_hits_f32(Ri, V3<float>{-m.shift[0], -m.shift[1], -m.shift[2]}, st.off[0], st.off[1], st.lb[MAXJ], st,
+                        s_obs, n_obs, s_box, n_box, &tests);
   }
   Kin<P, float> k;
   if (!hit)
@@ -1087,7 +1133,12 @@ __device__ __forceinline__ bool check_one_f32(const ModelT<float> &m, const Sphe
         ops, m, q, k,
         [&](auto JJ, const float (&R)[9], V3<float> p) {
           constexpr int j = decltype(JJ)::value;
-          if (!hit) hit = group_hits(R, p, st.off[j + 1], st.off[j + 2], st.lb[j]);
+          if (!hit && st.off[j + 1] < st.off[j + 2]) {
+            Rot9 Rr;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) Rr.r[i] = R[i];
+            hit = link_hits_f32(Rr, p, st.off[j + 1], st.off[j + 2], st.lb[j], st, s_obs, n_obs, s_box, n_box, &tests);
+          }
         },
         [&]() { return hit; });
   return hit;

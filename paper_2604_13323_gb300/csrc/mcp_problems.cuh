@@ -152,4 +152,11 @@ struct ProbHumanoid36 {
   }
 };
 
+// --- the humanoid with the CoM constraint as the distance to the support
+//     polygon (zero inside) instead of equality to its centre ---
+struct ProbHumanoid36Hull : ProbHumanoid36 {
+  static constexpr const char *name = "humanoid36_hull";
+  __host__ __device__ static constexpr int ckind(int c) { return c == 3 ? K_HULL : ProbHumanoid36::ckind(c); }
+};
+
 }  // namespace mcp

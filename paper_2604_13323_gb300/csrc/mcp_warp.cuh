@@ -122,6 +122,8 @@ struct __align__(16) WarpState {
   float phi[P::NC][4];
   float beta[P::NC];
   float za[P::NC][4];
+  float hn[P::NC][2];  // support-hull constraint: normal of the nearest edge
+  int hmode[P::NC];    // 0 inside, 1 on an edge, 2 at a vertex
 };
 
 template <class P>
@@ -323,8 +325,8 @@ __device__ __forceinline__ bool warp_iter(const A &a, const WarpTables<P> &tb, W
     constexpr int c = decltype(CC)::value;
     constexpr int kind = P::ckind(c);
     constexpr int r0 = roff<P>(c);
-    static_assert(kind == K_AXIS || kind == K_COM || kind == K_POSE || kind == K_REL,
-                  "the warp kernel implements the axis, CoM, pose and relative-pose constraints");
+    static_assert(kind == K_AXIS || kind == K_COM || kind == K_HULL || kind == K_POSE || kind == K_REL,
+                  "the warp kernel implements the axis, CoM, CoM-hull, pose and relative-pose constraints");
     if (lane == c) {
       if constexpr (MODE >= 0 && c != MODE) {
 #pragma unroll
@@ -339,6 +341,14 @@ __device__ __forceinline__ bool warp_iter(const A &a, const WarpTables<P> &tb, W
       } else if constexpr (kind == K_COM) {
         S.F[r0] = fmaf(tot[0], m.inv_mass, -m.ctgt[c][0]);
         S.F[r0 + 1] = fmaf(tot[1], m.inv_mass, -m.ctgt[c][1]);
+      } else if constexpr (kind == K_HULL) {
+        const float cx = tot[0] * m.inv_mass, cy = tot[1] * m.inv_mass;
+        float px, py, nx, ny;
+        S.hmode[c] = polygon_nearest<float>(m.cB[c], static_cast<int>(m.ctgt[c][0]), cx, cy, px, py, nx, ny);
+        S.hn[c][0] = nx;
+        S.hn[c][1] = ny;
+        S.F[r0] = cx - px;
+        S.F[r0 + 1] = cy - py;
       } else {
         float Pr[9], Rerr[9], G[9];
         load_R(m.cPinv[c], Pr);
@@ -437,13 +447,25 @@ __device__ __forceinline__ bool warp_iter(const A &a, const WarpTables<P> &tb, W
           const V3<float> d = cross(z, V3<float>{S.za[c][0], S.za[c][1], S.za[c][2]});
           S.J[j][r0] = rev ? sg * d.x : 0.f;
           S.J[j][r0 + 1] = rev ? sg * d.y : 0.f;
-        } else if constexpr (kind == K_COM) {
+        } else if constexpr (kind == K_COM || kind == K_HULL) {
           const float Mj = tb.msub[j];
           const V3<float> r{fmaf(-Mj, o.x, S.C[j][0]), fmaf(-Mj, o.y, S.C[j][1]), fmaf(-Mj, o.z, S.C[j][2])};
           const V3<float> d = cross(z, r);
           const float fpr = Mj * m.inv_mass;
-          S.J[j][r0] = sg * (rev ? d.x * m.inv_mass : fpr * z.x);
-          S.J[j][r0 + 1] = sg * (rev ? d.y * m.inv_mass : fpr * z.y);
+          float g0 = sg * (rev ? d.x * m.inv_mass : fpr * z.x);
+          float g1 = sg * (rev ? d.y * m.inv_mass : fpr * z.y);
+          if constexpr (kind == K_HULL) {  // inside: 0; on an edge: n n^T g; at a vertex: g
+            const int hm = S.hmode[c];
+            if (hm == 0) {
+              g0 = g1 = 0.f;
+            } else if (hm == 1) {
+              const float sd = fmaf(S.hn[c][0], g0, S.hn[c][1] * g1);
+              g0 = S.hn[c][0] * sd;
+              g1 = S.hn[c][1] * sd;
+            }
+          }
+          S.J[j][r0] = g0;
+          S.J[j][r0 + 1] = g1;
         } else {
           float G[9];
 #pragma unroll

@@ -21,9 +21,9 @@ F_CONVERGED, F_CAP, F_DIVERGED, F_NONFINITE, F_FP64_RESOLVE, F_ACCEPT_FAIL, F_OU
 EXT_OK, EXT_DEGENERATE, EXT_NO_PROJECTION, EXT_PROJ_COLLISION, EXT_TOO_FAR, EXT_INTERP_FAIL, EXT_GAP, \
     EXT_INTERP_COLLISION, EXT_RESOLUTION = range(9)
 # constraint kinds (mcp_ckind) and their equation counts
-C_SPHERE, C_AXIS_ALIGN, C_POSE, C_REL_POSE, C_COM_XY, C_PLANE, C_LINE, C_DIST, C_POSE_BOUNDED = range(9)
+C_SPHERE, C_AXIS_ALIGN, C_POSE, C_REL_POSE, C_COM_XY, C_PLANE, C_LINE, C_DIST, C_POSE_BOUNDED, C_COM_HULL = range(10)
 C_DIM = {C_SPHERE: 1, C_AXIS_ALIGN: 2, C_POSE: 6, C_REL_POSE: 6, C_COM_XY: 2, C_PLANE: 1, C_LINE: 2, C_DIST: 1,
-         C_POSE_BOUNDED: 6}
+         C_POSE_BOUNDED: 6, C_COM_HULL: 2}
 PREC_FP32, PREC_FP64 = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -76,7 +76,7 @@ def load_library(path: str = LIB_PATH):
         "mcp_load_robot": ([_vp, P(RobotDesc)], ctypes.c_int),
         "mcp_load_constraints": ([_vp, P(ConstraintDesc), ctypes.c_int32], ctypes.c_int),
         "mcp_load_obstacles": ([_vp, _dp, ctypes.c_int32, _dp, ctypes.c_int32], ctypes.c_int),
-        "mcp_get_constraint": ([_vp, ctypes.c_int32, _dp, _dp, _dp], ctypes.c_int),
+        "mcp_get_constraint": ([_vp, ctypes.c_int32, _dp, _dp, _dp, _dp], ctypes.c_int),
         "mcp_project_batch": ([_vp, P(ProjectParams), ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp],
                               ctypes.c_int),
         "mcp_project_check_batch": ([_vp, P(ProjectParams), ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
@@ -231,8 +231,14 @@ class Projector:
         Q = np.zeros(12)
         t = np.zeros(3)
         self._check(self.lib.mcp_get_constraint(self.h, i, P.ctypes.data_as(_dp), Q.ctypes.data_as(_dp),
-                                                t.ctypes.data_as(_dp)))
+                                                t.ctypes.data_as(_dp), None))
         return P, Q, t
+
+    def constraint_bounds(self, i):
+        """B of constraint i (TSR bounds or support-polygon vertices) after q_ref handling."""
+        B = np.zeros(12)
+        self._check(self.lib.mcp_get_constraint(self.h, i, None, None, None, B.ctypes.data_as(_dp)))
+        return B
 
     @property
     def launches(self) -> int:

@@ -168,3 +168,32 @@ def test_bounded_tsr_rejects_inverted_bounds(mcproj):
     c.B[0], c.B[6] = 0.1, -0.1
     with pytest.raises(mcproj.MCPError):
         mcproj.Projector(wl.robot, [c])
+
+
+def test_humanoid_hull_fp32_parity(mcproj):
+    """The humanoid with the CoM on its support polygon (distance to the
+    polygon, zero inside) instead of at its centre: the warp kernel against
+    the oracle; the polygon is resolved alike on both sides."""
+    wl = W.humanoid_workload(n=4099, hull=True)
+    q0 = f32_exact(wl.q)
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
+    O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
+    np.testing.assert_allclose(P.constraint_bounds(3)[:8], O.bounds(3)[:8], atol=1e-13)
+    gpu = run(P, q0, wl.params, ld=4128)
+    selfst = {}
+    el, ora = eligible_mask(O, q0, wl.params, stable_iters=True, stats=selfst)
+    st = compare_projection(gpu, ora, wl.params.tol, oracle=O, eligible=el, min_eligible=0.5, sample_resid=512,
+                            stable_only=True, **self_consistent_bars(selfst))
+    assert st["conv_gpu"] > 0.95, st
+
+
+def test_humanoid_hull_fp64_plain_parity(mcproj):
+    wl = W.humanoid_workload(n=512, hull=True)
+    wl.params.precision = W.PREC_FP64
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
+    O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
+    gpu = run(P, wl.q, wl.params, dtype=torch.float64)
+    selfst = {}
+    el, ora = eligible_mask(O, wl.q, wl.params, rel=1e-12, thr=1e-9, stable_iters=True, stats=selfst)
+    compare_projection(gpu, ora, wl.params.tol, q_tol=1e-6, oracle=O, eligible=el, min_eligible=0.7,
+                       stable_only=True, **self_consistent_bars(selfst))
