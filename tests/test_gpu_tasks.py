@@ -182,8 +182,10 @@ def test_humanoid_hull_fp32_parity(mcproj):
     gpu = run(P, q0, wl.params, ld=4128)
     selfst = {}
     el, ora = eligible_mask(O, q0, wl.params, stable_iters=True, stats=selfst)
+    # inside / edge / vertex is decided on the CoM in the working precision
+    # (a nonsmooth residual like the bounded TSR's): points at the 99.9th percentile
     st = compare_projection(gpu, ora, wl.params.tol, oracle=O, eligible=el, min_eligible=0.5, sample_resid=512,
-                            stable_only=True, **self_consistent_bars(selfst))
+                            stable_only=True, q_quantile=0.999, **self_consistent_bars(selfst))
     assert st["conv_gpu"] > 0.95, st
 
 
