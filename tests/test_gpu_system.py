@@ -182,3 +182,25 @@ def test_project_check_equals_separate_calls(mcproj, name):
             assert torch.equal(x, y)
         assert torch.equal(ha, b[4])
         assert torch.equal(pa, pb)
+
+
+def test_arm_full_batch_in_the_benchmark_configuration(mcproj):
+    """The 65,536-configuration arm batch through the call and launch shape the
+    benchmark times (autotuned, projection and check possibly fused), against
+    the oracle: flags, points on the eligible starts, FP64 validity and the
+    collision verdicts outside the contact band."""
+    from tests.gpu_util import compare_collision, compare_projection, eligible_mask
+    wl = W.arm_workload(n=65536)
+    q0 = f32_exact(wl.q)
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
+    O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
+    q = dev(q0)
+    P.autotune(q, wl.params)
+    out, fl, it, r, hit = P.project_check(q, wl.params)
+    torch.cuda.synchronize()
+    gpu = (out.cpu().numpy().astype(np.float64), fl.cpu().numpy(), it.cpu().numpy().astype(np.int32), r.cpu().numpy())
+    el, ora = eligible_mask(O, q0, wl.params)
+    st = compare_projection(gpu, ora, wl.params.tol, oracle=O, eligible=el, min_eligible=0.5, sample_resid=4096)
+    assert st["conv_gpu"] > 0.99
+    h_o, m_o = O.check(gpu[0])
+    compare_collision(hit.cpu().numpy(), h_o, m_o)
