@@ -34,6 +34,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "converged projections/sec at ||F||<=1e-5 (batched FP32 vs plain FP64, 1 GB300)"
 UNIT = "projections/s"
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
+# dominant kernel, from one ncu capture of the kernel built from this source
+# (profiles/ gives the command and the full capture summary).  Keyed by
+# (workload, kernel); an entry is removed whenever its kernel changes.
+MEASURED_TRAFFIC = {
+    ("arm7_axis_65536", "k_project_f32+check"): 1955584,      # read 1.96 MB, write 0
+    ("dual14_rel_extend_16384", "k_extend"): 4159744 + 1251840,
+}
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 
 
@@ -457,7 +466,7 @@ def run_ours(args):
         ach64 = fp64f / t / 1e12
         t_min = max((fp32 + check_flops) / (peak32 * 1e12), fp64f / (peak64 * 1e12))
         roof = {"bound": "alu", "achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
-                "traffic": None,
+                "traffic": MEASURED_TRAFFIC.get((wname, "k_project_f32+check")),
                 "kernel": "k_project_f32 with the check fused (persistent: FP32 steps, FP64 acceptance, "
                           "collision check)",
                 "peak_source": peak_src, "fp64_achieved": ach64, "fp64_peak": peak64, "fp64_frac": ach64 / peak64,
@@ -622,7 +631,8 @@ def run_extend(args):
     fp32 = total_steps * fm.iteration
     ach = fp32 / (ms * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s", "frac": ach / peak32,
-            "traffic": None, "kernel": "k_extend (warp per extension: particles, interpolation, bisection)",
+            "traffic": MEASURED_TRAFFIC.get((f"dual14_rel_extend_{EXT_N}", "k_extend")),
+            "kernel": "k_extend (warp per extension: particles, interpolation, bisection)",
             "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
             "counted": "FP32 Newton steps of all projections x the step's flops (evaluations, FP64 "
                        "acceptance and collision checks not counted)",
