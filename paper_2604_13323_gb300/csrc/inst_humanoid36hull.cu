@@ -1,8 +1,8 @@
 // Kernel instantiations for the ProbHumanoid36Hull problem class (CoM on the
 // support polygon): the FP32 path
-// runs the warp-cooperative kernel, the plain FP64 path and the collision
+// runs the group-cooperative kernel (the cyclic form: the warp kernel), the plain FP64 path and the collision
 // check the thread-per-configuration kernels.
-#include "mcp_warp.cuh"
+#include "mcp_group.cuh"
 
 namespace mcp {
 
@@ -17,7 +17,10 @@ cudaError_t launch_project<ProbHumanoid36Hull>(const HostModel &hm, const ProjCa
     if (e == cudaSuccess && c.fused_check) e = check_outputs<ProbHumanoid36Hull>(hm, c, launches);
     return e;
   }
-  cudaError_t e = launch_project_warp<ProbHumanoid36Hull>(hm, c, launches);
+  // stacked form: four lanes per configuration; the cyclic form's masked
+  // sub-steps run on the warp-per-configuration kernel
+  cudaError_t e = c.cyclic ? launch_project_warp<ProbHumanoid36Hull>(hm, c, launches)
+                           : launch_project_group<ProbHumanoid36Hull>(hm, c, launches);
   if (e == cudaSuccess && c.fused_check) e = check_outputs<ProbHumanoid36Hull>(hm, c, launches);
   return e;
 }
