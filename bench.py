@@ -488,7 +488,12 @@ def run_ours(args):
             # both pipes: the time the FP32 and FP64 work need at their peaks bounds the kernel
             t_min = max(fp32 / (peak32 * 1e12), fp64f / (peak64 * 1e12))
             roof = {"bound": "alu", "achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
-                    "traffic": None, "kernel": "k_project_f32 (persistent, FP32 steps + FP64 acceptance)",
+                    "traffic": None,
+                    "kernel": ("k_project_group (four lanes per configuration: FP32 steps, FP64 acceptance)"
+                               if args.workload.startswith("humanoid") and not wl.params.cyclic else
+                               "k_project_warp (warp per configuration, cyclic sweeps)"
+                               if args.workload.startswith("humanoid") else
+                               "k_project_f32 (persistent, FP32 steps + FP64 acceptance)"),
                     "peak_source": peak_src,
                     "fp64_achieved": ach64, "fp64_peak": peak64, "fp64_frac": ach64 / peak64,
                     "mixed_bound_frac": t_min / (mp * 1e-3),
