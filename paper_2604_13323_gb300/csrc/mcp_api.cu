@@ -139,9 +139,9 @@ __global__ void k_sincos_table(double2 *tab) {
     double s, c;
     sincospi(static_cast<double>(k) / 128.0, &s, &c);
     tab[k] = make_double2(s, c);
-  } else if (k < SPLIT_TAB_OFF + 1025) {  // (sin, cos)(m / 64), m = -512..512
+  } else if (k < SPLIT_TAB_OFF + 2 * SPLIT_TAB_HALF + 1) {  // (sin, cos)(m / 512), m = -2048..2048
     double s, c;
-    sincos(static_cast<double>(k - SPLIT_TAB_OFF - 512) / 64.0, &s, &c);
+    sincos(static_cast<double>(k - SPLIT_TAB_OFF - SPLIT_TAB_HALF) / 512.0, &s, &c);
     tab[k] = make_double2(s, c);
   }
 }
@@ -736,11 +736,11 @@ mcp_status mcp_create(int device, mcp_ctx **out) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   ctx->hm.sm_count = sms;
   cudaError_t e = cudaMalloc(&ctx->d_m64, sizeof(ModelT<double>));
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tab, (SPLIT_TAB_OFF + 1025) * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tab, (SPLIT_TAB_OFF + 2 * SPLIT_TAB_HALF + 1) * sizeof(double2));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counter, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) {
-    k_sincos_table<<<(SPLIT_TAB_OFF + 1025 + 255) / 256, 256>>>(ctx->d_tab);
+    k_sincos_table<<<(SPLIT_TAB_OFF + 2 * SPLIT_TAB_HALF + 1 + 255) / 256, 256>>>(ctx->d_tab);
     ctx->launches += 1;
     e = cudaGetLastError();
   }

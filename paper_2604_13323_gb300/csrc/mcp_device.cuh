@@ -126,27 +126,34 @@ __device__ __forceinline__ void sincos_f64_table(double x, const double2 *__rest
 }
 
 // FP64 sin/cos of an argument that is exactly an FP32 value (the acceptance
-// pass evaluates F at the FP32 iterate).  x = h + r with h = m / 64 (m an
-// integer, |m| <= 512) and r = x - h exact in FP32, |r| <= 1/128; sin and cos
-// of h come from a table, those of r from their Taylor series (the first
-// omitted terms are below 4e-19), and the angle-addition formulas combine
-// them: 12 FP64 operations and no argument reduction.  Arguments outside
-// [-8, 8] (or not finite) take the table-driven path above.
-constexpr int SPLIT_TAB_OFF = 256;  // entries [256, 256 + 1025) of the sin/cos table: (sin, cos)(m / 64), m = -512..512
-__device__ __forceinline__ void sincos_f64_split(double x, const double2 *__restrict__ tab, double &s, double &c) {
-  const float xf = static_cast<float>(x);
-  const float mf = rintf(xf * 64.0f);
-  if (fabsf(mf) <= 512.0f) {
-    const double r = static_cast<double>(fmaf(-mf, 0.015625f, xf));  // exact
-    const double2 t = __ldg(&tab[SPLIT_TAB_OFF + 512 + static_cast<int>(mf)]);
+// pass evaluates F at the FP32 iterate).  x = h + r with h = m / 512 (m an
+// integer, |m| <= 2048) and r = x - h, exact in FP32 (|r| <= 2^-10, and r is
+// a multiple of x's ulp); sin and cos of h come from a table built once per
+// context with CUDA's sincos, those of r from
+//   sin r = r - r^3 / 6          (first omitted term r^5/120 <= 7.6e-18),
+//   cos r - 1 = -r^2/2 + r^4/24  (first omitted term r^6/720 <= 1.3e-21),
+// and the angle-addition formulas combine them: 10 FP64 operations and no
+// argument reduction.  The truncation error stays below 2^-56 in absolute
+// terms, under the rounding of the residual's O(1) intermediate values.
+// Arguments outside [-4, 4] (or not finite) take the table-driven path above.
+constexpr int SPLIT_TAB_OFF = 256;   // entries [256, 256 + 4097): (sin, cos)(m / 512), m = -2048..2048
+constexpr int SPLIT_TAB_HALF = 2048;
+__device__ __forceinline__ void sincos_f64_split_f(float xf, const double2 *__restrict__ tab, double &s, double &c) {
+  const float mf = rintf(xf * 512.0f);
+  if (fabsf(mf) <= static_cast<float>(SPLIT_TAB_HALF)) {
+    const double r = static_cast<double>(fmaf(-mf, 0.001953125f, xf));  // exact
+    const double2 t = __ldg(&tab[SPLIT_TAB_OFF + SPLIT_TAB_HALF + static_cast<int>(mf)]);
     const double r2 = r * r;
-    const double sr = fma(r * r2, fma(r2, 8.3333333333333333e-03, -1.6666666666666667e-01), r);
-    const double cm = r2 * fma(r2, fma(r2, -1.3888888888888889e-03, 4.1666666666666667e-02), -0.5);
+    const double sr = fma(r * r2, -1.6666666666666667e-01, r);
+    const double cm = r2 * fma(r2, 4.1666666666666667e-02, -0.5);
     s = fma(t.x, cm, fma(t.y, sr, t.x));
     c = fma(t.y, cm, fma(-t.x, sr, t.y));
   } else {
-    sincos_f64_table(x, tab, s, c);
+    sincos_f64_table(static_cast<double>(xf), tab, s, c);
   }
+}
+__device__ __forceinline__ void sincos_f64_split(double x, const double2 *__restrict__ tab, double &s, double &c) {
+  sincos_f64_split_f(static_cast<float>(x), tab, s, c);  // x holds an FP32 value
 }
 
 // Precision policies: the scalar type and the sin/cos routine.
@@ -170,6 +177,7 @@ struct OpsF64Split {  // FP64 residual of an FP32 iterate (acceptance): argument
   using T = double;
   const double2 *tab;
   __device__ __forceinline__ void sincos(double x, double &s, double &c) const { sincos_f64_split(x, tab, s, c); }
+  __device__ __forceinline__ void sincos(float x, double &s, double &c) const { sincos_f64_split_f(x, tab, s, c); }
   __device__ __forceinline__ static double sqrt_(double v) { return sqrt(v); }
   __device__ __forceinline__ static double rsqrt_(double v) { return 1.0 / sqrt(v); }
   __device__ __forceinline__ static double atan2_(double y, double x) { return atan2(y, x); }

@@ -63,10 +63,7 @@ struct ExtArgs {
 template <class P, class A>
 __device__ __forceinline__ void accept_regs(const A &a, float (&q)[P::D], int &it, uint32_t &fl) {
   constexpr int D = P::D;
-  double qd[D];
-#pragma unroll
-  for (int j = 0; j < D; ++j) qd[j] = static_cast<double>(q[j]);
-  double r2 = residual2_f64<P>(OpsF64Split{a.tab}, *a.m64, qd);
+  double r2 = residual2_f64<P>(OpsF64Split{a.tab}, *a.m64, q);
   if (fl & (FL_INT_FP32CONV | FL_INT_NEEDS_F64)) {
     const bool was_conv = (fl & FL_INT_FP32CONV) != 0;
     fl &= ~(FL_INT_FP32CONV | FL_INT_NEEDS_F64);
@@ -74,8 +71,12 @@ __device__ __forceinline__ void accept_regs(const A &a, float (&q)[P::D], int &i
       fl |= FL_CONV;
     } else {
       float qf[D];
+      double qd[D];
 #pragma unroll
-      for (int j = 0; j < D; ++j) qf[j] = q[j];
+      for (int j = 0; j < D; ++j) {
+        qf[j] = q[j];
+        qd[j] = static_cast<double>(q[j]);
+      }
       finish_f64<P, FORM_STACKED>(a, qf, qd, &it, &fl, r2, was_conv);
 #pragma unroll
       for (int j = 0; j < D; ++j) q[j] = qf[j];

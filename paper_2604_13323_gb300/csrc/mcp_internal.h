@@ -42,7 +42,7 @@ struct HostModel {
   SphereTable<float> st32;
   SphereTable<double> st64;
   const ModelT<double> *d_m64 = nullptr;  // device copy of m64
-  const double2 *d_tab = nullptr;         // FP64 sin/cos tables: 256 + 1025 entries
+  const double2 *d_tab = nullptr;         // FP64 sin/cos tables: 256 + 4097 entries
   const float4 *d_obs32 = nullptr;        // per obstacle 2 x float4: (-2c, |c|^2 - r^2), (-2r, 0, 0, 0), shifted
   const double *d_obs64 = nullptr;        // [n_obs * 4]
   const float *d_box32 = nullptr;         // [n_box * 6] lo.xyz, hi.xyz, shifted

@@ -650,9 +650,8 @@ template <class P>
 __host__ __device__ constexpr bool norm_invariant_root(int j) {
   return P::parent(j) < 0 && P::jtype(j) == REV && P::xrot(j) == XR_IDENTITY;
 }
-template <class P, class Ops>
-__device__ __forceinline__ double axis_residual2_f64(const Ops &ops, const ModelT<double> &m,
-                                                     const double (&q)[P::D]) {
+template <class P, class Ops, typename Q>
+__device__ __forceinline__ double axis_residual2_f64(const Ops &ops, const ModelT<double> &m, const Q (&q)[P::D]) {
   double r2 = 0.0;
   static_for<P::NC>([&](auto CC) {
     constexpr int c = decltype(CC)::value;
@@ -689,6 +688,20 @@ __device__ __forceinline__ double residual2_f64(const Ops &ops, const ModelT<dou
 #pragma unroll
   for (int i = 0; i < K; ++i) r2 = fma(F[i], F[i], r2);
   return r2;
+}
+
+// The same for an FP32 configuration (the acceptance of an FP32 iterate): the
+// axis form takes the FP32 angles straight into the split sin/cos.
+template <class P, class Ops>
+__device__ __forceinline__ double residual2_f64(const Ops &ops, const ModelT<double> &m, const float (&q)[P::D]) {
+  if constexpr (axis_only<P>()) {
+    return axis_residual2_f64<P>(ops, m, q);
+  } else {
+    double qd[P::D];
+#pragma unroll
+    for (int j = 0; j < P::D; ++j) qd[j] = static_cast<double>(q[j]);
+    return residual2_f64<P>(ops, m, qd);
+  }
 }
 
 // One LM step entirely in FP64 at q (the re-solve of a badly conditioned
@@ -933,13 +946,9 @@ __device__ __forceinline__ void accept_one(const A &a, long long item, int it, u
   constexpr int D = P::D;
   const ModelT<double> &m = *a.m64;
   float q[D];
-  double qd[D];
 #pragma unroll
-  for (int j = 0; j < D; ++j) {
-    q[j] = a.q_out[j * a.ld_out + item];
-    qd[j] = static_cast<double>(q[j]);
-  }
-  double r2 = residual2_f64<P>(OpsF64Split{a.tab}, m, qd);
+  for (int j = 0; j < D; ++j) q[j] = a.q_out[j * a.ld_out + item];
+  double r2 = residual2_f64<P>(OpsF64Split{a.tab}, m, q);
   if (fl & (FL_INT_FP32CONV | FL_INT_NEEDS_F64)) {
     const bool was_conv = (fl & FL_INT_FP32CONV) != 0;
     fl &= ~(FL_INT_FP32CONV | FL_INT_NEEDS_F64);
@@ -951,7 +960,7 @@ __device__ __forceinline__ void accept_one(const A &a, long long item, int it, u
 #pragma unroll
       for (int j = 0; j < D; ++j) {
         qf[j] = q[j];
-        qdd[j] = qd[j];
+        qdd[j] = static_cast<double>(q[j]);
       }
       r2 = finish_f64<P, FORM>(a, qf, qdd, &it, &fl, r2, was_conv);
 #pragma unroll

@@ -61,13 +61,19 @@ def compare_projection(gpu, ora, tol, q_tol=Q_TOL, flag_agree=FLAG_AGREE, oracle
     both = cg & co & el & same_it
     off_by_one = cg & co & el & (np.abs(ig.astype(np.int64) - io.astype(np.int64)) == 1)
     if oracle is not None:
+        viol = []
         for i in np.flatnonzero(off_by_one):
             # rows of inactive bounded constraints are zero (and so is their
             # residual): the step lives in the span of the nonzero rows
             sv = np.linalg.svd(oracle.residual_jacobian(qo[:, i])[1], compute_uv=False)
             smin = sv[sv > 1e-12 * max(sv.max(), 1e-300)].min() if (sv > 0).any() else 1.0
             e = np.abs(qg[:, i] - qo[:, i]).max()
-            assert e <= q_tol + 2.0 * tol / smin, (i, e, smin)
+            if e > q_tol + 2.0 * tol / smin:
+                viol.append((int(i), float(e), float(smin)))
+        # a nonsmooth residual (bounded TSR, support hull) can switch its active
+        # rows between the two iterates: there the bound holds at the quantile
+        allowed = 0 if q_quantile is None else int((1.0 - q_quantile) * cg.size)
+        assert len(viol) <= allowed, ("off-by-one points beyond the bound", viol[:5], len(viol), allowed)
     recount = int((cg & co & el & ~same_it & ~off_by_one).sum())
     assert recount <= max(1, int(max_recount * cg.size)), ("iteration counts differ", recount)
     err = np.abs(qg[:, both] - qo[:, both]).max(axis=0) if both.any() else np.zeros(0)
@@ -91,7 +97,8 @@ def compare_projection(gpu, ora, tol, q_tol=Q_TOL, flag_agree=FLAG_AGREE, oracle
         idx = np.flatnonzero(cg)[:: max(1, cg.sum() // sample_resid)]
         for i in idx:
             r = np.linalg.norm(oracle.residual(qg[:, i].astype(np.float64)))
-            assert abs(r - rg[i]) <= 1e-9 * max(1.0, r) + 1e-13, (i, r, rg[i])
+            # both sides evaluate the same FP32 configuration in FP64: rounding only
+            assert abs(r - rg[i]) <= 1e-12 * max(1.0, r), (i, r, rg[i])
             assert r < tol
     return stats
 
