@@ -504,10 +504,19 @@ __device__ __forceinline__ LogOut<Ops, T> so3_log(const T (&R)[9]) {
   T c = T(0.5) * (R[0] + R[4] + R[8] - T(1));
   T s2 = dot(w, w);
   T s = Ops::sqrt_(s2);
-  T th = Ops::atan2_(s, c);
-  o.theta = th;
   o.s = s;
   o.c = c;
+  if (c > T(0) && s < T(1e-3)) {
+    // small angle: theta = asin(s) = s f(s), f = 1 + s^2/6 + 3 s^4/40 (next
+    // term 5 s^6/112 < 1e-19), and phi = (theta / sin theta) w = f w: no atan2
+    // (the acceptance of a converged configuration always lands here)
+    T f = fma_(s2, fma_(s2, T(3.0 / 40.0), T(1.0 / 6.0)), T(1));
+    o.theta = f * s;
+    o.phi = {f * w.x, f * w.y, f * w.z};
+    return o;
+  }
+  T th = Ops::atan2_(s, c);
+  o.theta = th;
   if (th < T(1e-3)) {
     T f = fma_(th * th, T(1.0 / 6.0), T(1));
     o.phi = {f * w.x, f * w.y, f * w.z};
