@@ -59,9 +59,10 @@ struct ExtArgs {
 };
 
 // FP64 acceptance of one FP32 iterate held in registers (accept_one without
-// the global outputs).
+// the global outputs).  Out of line: it runs once per projection, and kept
+// apart from the Newton loop it does not dilute the loop's instruction stream.
 template <class P, class A>
-__device__ __forceinline__ void accept_regs(const A &a, float (&q)[P::D], int &it, uint32_t &fl) {
+__device__ __noinline__ void accept_regs(const A &a, float (&q)[P::D], int &it, uint32_t &fl) {
   constexpr int D = P::D;
   double r2 = residual2_f64<P>(OpsF64Split{a.tab}, *a.m64, q);
   if (fl & (FL_INT_FP32CONV | FL_INT_NEEDS_F64)) {
