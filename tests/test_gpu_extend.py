@@ -57,8 +57,12 @@ def test_extend_on_sphere_matches_oracle_and_geometry(mcproj):
     assert len(set(so.tolist())) >= 3   # several outcomes exercised
 
 
-def test_extend_dual_arm_parity(mcproj):
-    wl = W.extend_workload(n_ext=2048)
+@pytest.mark.parametrize("n,n_ext", [(8, 2048), (3, 1023), (12, 1021)])
+def test_extend_dual_arm_parity(mcproj, n, n_ext):
+    """n = 8 and n = 3 run four extensions per warp (groups of 8 lanes, the
+    latter with idle lanes in each group and a partial last claim); n = 12
+    runs one extension per warp."""
+    wl = W.extend_workload(n_ext=n_ext, n=n)
     ex = wl.extra
     p = wl.params
     O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
