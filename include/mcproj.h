@@ -308,10 +308,11 @@ mcp_status mcp_set_tuning(mcp_ctx *ctx, int32_t tpb, int32_t blocks_per_sm, int3
  * per block, resident blocks per SM, configurations claimed per atomic) for
  * the loaded problem by timing every candidate on the caller's sample
  * q_sample (DEVICE, float [d * ld], n_sample configurations), and keeps the
- * fastest in the context for later calls.  With obstacles loaded it also
- * times mcp_project_check_batch with the check inside the projection kernel
- * against a second launch and keeps the faster.  Uses temporary device
- * buffers; synchronous.  The choices are returned in tpb / blocks_per_sm /
+ * fastest in the context for later calls.  With obstacles loaded the timed
+ * step is mcp_project_check_batch, and every launch shape is timed with the
+ * check inside the projection kernel and as a second launch.  Each candidate
+ * is timed as the median of five bursts of four calls.  Uses temporary
+ * device buffers; synchronous.  The choices are returned in tpb / blocks_per_sm /
  * chunk / fuse_check (HOST, each may be NULL).  Tuning never changes results,
  * only speed. */
 mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sample, int64_t ld, const void *q_sample,

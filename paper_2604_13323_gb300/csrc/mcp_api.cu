@@ -1,6 +1,7 @@
 // C ABI of libmcproj.so (declared in include/mcproj.h): context, model
 // loading, binding of a loaded robot/constraint stack to a compiled problem
 // class, and the batched entry points.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1430,49 +1431,18 @@ mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sam
   const int tpbs[3] = {64, 128, 256};
   const int bpss[4] = {1, 2, 4, 8};
   const int chunks[3] = {16, 32, 64};
-  for (int a = 0; a < 3 && err == cudaSuccess; ++a)
-    for (int b = 0; b < 4 && err == cudaSuccess; ++b)
-      for (int c = 0; c < 3 && err == cudaSuccess; ++c) {
-        if (tpbs[a] * bpss[b] > 2048) continue;
-        ctx->tune = Tuning{tpbs[a], bpss[b], chunks[c]};
-        float times[3];
-        for (int r = 0; r < 4 && err == cudaSuccess; ++r) {
-          ProjCall call;
-          fill_call(ctx, p, call, s);
-          call.q_in = q_sample;
-          call.ld_in = ld;
-          call.total = n_sample;
-          call.q_out = out;
-          call.ld_out = ld;
-          call.flags = fl;
-          call.iters = it;
-          call.resid = res;
-          int launches = 0;
-          err = cudaEventRecord(e0, s);
-          if (err == cudaSuccess) err = registry()[ctx->prob_class].project_fn(ctx->hm, call, &launches);
-          ctx->launches += launches;
-          if (err == cudaSuccess) err = cudaEventRecord(e1, s);
-          if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-          float ms = 0.f;
-          if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-          if (r > 0) times[r - 1] = ms;  // first run warms up
-        }
-        if (err != cudaSuccess) break;
-        float med = times[0] + times[1] + times[2] - fminf(times[0], fminf(times[1], times[2])) -
-                    fmaxf(times[0], fmaxf(times[1], times[2]));
-        if (med < best_ms) {
-          best_ms = med;
-          best = ctx->tune;
-        }
-      }
-  // projection + check of the outputs: in one kernel, or as two launches
-  if (err == cudaSuccess && ctx->obs_loaded) {
-    float med[2] = {0.f, 0.f};
-    for (int f = 0; f < 2 && err == cudaSuccess; ++f) {
-      ctx->tune = best;
-      ctx->tune.fuse_check = f == 1;
-      float times[3];
-      for (int r = 0; r < 4 && err == cudaSuccess; ++r) {
+  // With obstacles loaded the step that matters is projection + check: every
+  // launch shape is timed both fused and as two launches.  Each candidate's
+  // time is the median of five bursts of four back-to-back calls (one
+  // warm-up burst first): single calls sit near the resolution of the events.
+  const int n_fuse = ctx->obs_loaded ? 2 : 1;
+  auto time_candidate = [&](float &med) -> cudaError_t {
+    constexpr int BURSTS = 6, CALLS = 4;
+    float times[BURSTS - 1];
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < BURSTS && e == cudaSuccess; ++r) {
+      e = cudaEventRecord(e0, s);
+      for (int k = 0; k < CALLS && e == cudaSuccess; ++k) {
         ProjCall call;
         fill_call(ctx, p, call, s);
         call.q_in = q_sample;
@@ -1483,23 +1453,40 @@ mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sam
         call.flags = fl;
         call.iters = it;
         call.resid = res;
-        call.hit = hit;
         int launches = 0;
-        err = cudaEventRecord(e0, s);
-        if (err == cudaSuccess) err = run_project_check(ctx, call, &launches);
+        if (ctx->obs_loaded) {
+          call.hit = hit;
+          e = run_project_check(ctx, call, &launches);
+        } else {
+          e = registry()[ctx->prob_class].project_fn(ctx->hm, call, &launches);
+        }
         ctx->launches += launches;
-        if (err == cudaSuccess) err = cudaEventRecord(e1, s);
-        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-        if (r > 0) times[r - 1] = ms;
       }
-      if (err == cudaSuccess)
-        med[f] = times[0] + times[1] + times[2] - fminf(times[0], fminf(times[1], times[2])) -
-                 fmaxf(times[0], fmaxf(times[1], times[2]));
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0) times[r - 1] = ms;
     }
-    best.fuse_check = err == cudaSuccess && med[1] < med[0];
-  }
+    if (e == cudaSuccess) {
+      std::sort(times, times + BURSTS - 1);
+      med = times[(BURSTS - 1) / 2];
+    }
+    return e;
+  };
+  for (int a = 0; a < 3 && err == cudaSuccess; ++a)
+    for (int b = 0; b < 4 && err == cudaSuccess; ++b)
+      for (int c = 0; c < 3 && err == cudaSuccess; ++c)
+        for (int f = 0; f < n_fuse && err == cudaSuccess; ++f) {
+          if (tpbs[a] * bpss[b] > 2048) continue;
+          ctx->tune = Tuning{tpbs[a], bpss[b], chunks[c], f == 1};
+          float med = 0.f;
+          err = time_candidate(med);
+          if (err == cudaSuccess && med < best_ms) {
+            best_ms = med;
+            best = ctx->tune;
+          }
+        }
   cudaFree(out);
   cudaFree(fl);
   cudaFree(it);
