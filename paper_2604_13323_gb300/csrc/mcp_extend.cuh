@@ -101,10 +101,10 @@ __device__ __noinline__ void project_lanes(const A &a, float (&q)[P::D], bool ac
 
 // Collision verdict of one lane's configuration, out of line (called at three places).
 template <class P>
-__device__ __noinline__ bool collides_lane(const CheckData *chk, const float4 *s_obs, int n_obs, const float *s_box,
+__device__ __noinline__ bool collides_lane(const CheckData *chk, const float4 *s_pair, int n_obs, const float *s_box,
                                            int n_box, const double2 *tab, const float (&q)[P::D]) {
   uint32_t t = 0;
-  return check_one_f32<P>(chk->m, chk->st, s_obs, n_obs, s_box, n_box, tab, q, t);
+  return check_one_f32<P>(chk->m, chk->st, s_pair, n_obs, s_box, n_box, tab, q, t);
 }
 
 template <int D>
@@ -126,17 +126,16 @@ template <class P, int W>
 __global__ void __launch_bounds__(W * 32) k_extend(const __grid_constant__ ExtArgs<P> a) {
   constexpr int D = P::D;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4 *s_obs = reinterpret_cast<float4 *>(smem_raw);
-  float *s_box = reinterpret_cast<float *>(s_obs + 2 * a.n_obs);
-  float *s_chain = s_box + 6 * a.n_box;
-  stage_obstacles(a.obs, a.n_obs, a.box, a.n_box, s_obs, s_box);
+  float4 *s_pair = reinterpret_cast<float4 *>(smem_raw);
+  const float *s_box = stage_obstacles(a.obs, a.n_obs, a.box, a.n_box, s_pair);
+  float *s_chain = reinterpret_cast<float *>(smem_raw + obs_smem_bytes(a.n_obs, a.n_box));
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   float *chain = s_chain + static_cast<size_t>(wib) * 2 * EXT_MAXPTS * D;  // [EXT_MAXPTS][D]
   float *next = chain + EXT_MAXPTS * D;
   auto collides = [&](const float (&q)[D]) -> bool {
-    return collides_lane<P>(a.chk, s_obs, a.n_obs, s_box, a.n_box, a.tab, q);
+    return collides_lane<P>(a.chk, s_pair, a.n_obs, s_box, a.n_box, a.tab, q);
   };
   while (true) {
     unsigned long long e = 0;
@@ -350,7 +349,7 @@ cudaError_t launch_extend_impl(const HostModel &hm, const ExtCall &c, int *launc
   a.tol2_64 = c.tol * c.tol;
   a.lambda64 = c.lambda;
   a.alpha = static_cast<float>(c.alpha);
-  const size_t smem = sizeof(float) * (8 * hm.n_obs + 6 * hm.n_box) + sizeof(float) * W * 2 * EXT_MAXPTS * P::D;
+  const size_t smem = obs_smem_bytes(hm.n_obs, hm.n_box) + sizeof(float) * W * 2 * EXT_MAXPTS * P::D;
   cudaError_t err = cudaSuccess;
   if (smem > 48 * 1024)
     err = cudaFuncSetAttribute(k_extend<P, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));

@@ -1047,15 +1047,37 @@ struct Rot9 {
   float r[9];
 };
 
+// Obstacle records in shared memory, two obstacles per 48-byte pair so that
+// the broad phase tests two obstacles per packed FP32x2 instruction:
+//   A = (gx0, gx1, gy0, gy1), B = (gz0, gz1, gw0, gw1), C = (g20, g21, 0, 0)
+// with g = -2 c, gw = |c|^2 - r^2, g2 = -2 r (the expanded overlap test
+// below).  An odd count is padded with a record that never overlaps.
+__host__ __device__ constexpr int obs_pairs(int n_obs) { return (n_obs + 1) / 2; }
+__host__ __device__ constexpr size_t obs_smem_bytes(int n_obs, int n_box) {
+  return sizeof(float) * (12 * static_cast<size_t>(obs_pairs(n_obs)) + 6 * static_cast<size_t>(n_box));
+}
+// Obstacle o's five values from its pair.
+struct ObsRec {
+  float gx, gy, gz, gw, g2;
+};
+__device__ __forceinline__ ObsRec obs_rec(const float4 *s_pair, int o) {
+  const float *f = reinterpret_cast<const float *>(s_pair + 3 * (o >> 1));
+  const int h = o & 1;
+  return ObsRec{f[h], f[2 + h], f[4 + h], f[6 + h], f[8 + h]};
+}
+
 // Spheres [s0, e) of one link placed by (R, p), with the link's bounding
 // sphere lb (local): the boxes, then the bounding sphere against chunks of 32
-// obstacles (broad phase), then the link's spheres in blocks of 8 against the
-// candidate obstacles (narrow phase).  One out-of-line copy serves every link
-// of every kernel (inlined per link, the unrolled broad phase made kernels
-// with many links instruction-cache bound).
+// obstacles (broad phase, two obstacles per FP32x2 instruction), then the
+// link's spheres in blocks of 8 against the candidate obstacles (narrow
+// phase, two spheres per instruction).  Every packed lane is an IEEE fma with
+// round-to-nearest, so each test is bit-identical to the scalar chain
+// fmaf(x, gx, fmaf(y, gy, fmaf(z, gz, fmaf(r, g2, gw)))).  One out-of-line
+// copy serves every link of every kernel (inlined per link, the unrolled
+// broad phase made kernels with many links instruction-cache bound).
 static __device__ __noinline__ bool link_hits_f32(const Rot9 Rr, V3<float> p, int s0, int e, const float *lb,
-                                           const SphereTable<float> &st, const float4 *s_obs, int n_obs,
-                                           const float *s_box, int n_box, uint32_t *tests_io) {
+                                                  const SphereTable<float> &st, const float4 *s_pair, int n_obs,
+                                                  const float *s_box, int n_box, uint32_t *tests_io) {
   if (s0 >= e) return false;
   const float(&R)[9] = Rr.r;
   uint32_t tests = *tests_io;
@@ -1069,50 +1091,63 @@ static __device__ __noinline__ bool link_hits_f32(const Rot9 Rr, V3<float> p, in
   const V3<float> bc = add_rot_t<7>(p, R, V3<float>{lb[0], lb[1], lb[2]});
   const float br = lb[3];
   const float kb = fmaf(bc.x, bc.x, fmaf(bc.y, bc.y, fmaf(bc.z, bc.z, -br * br)));
+  const float2 bx2 = make_float2(bc.x, bc.x), by2 = make_float2(bc.y, bc.y), bz2 = make_float2(bc.z, bc.z),
+               br2 = make_float2(br, br);
   for (int o0 = 0; o0 < n_obs && !hit; o0 += 32) {
     const int cnt = min(32, n_obs - o0);
+    const float4 *pr = s_pair + 3 * (o0 >> 1);
     unsigned cand = 0u;
+    auto pair_bits = [&](int pp) -> unsigned {
+      const float4 A = pr[3 * pp], B = pr[3 * pp + 1], C = pr[3 * pp + 2];
+      float2 v = __ffma2_rn(br2, make_float2(C.x, C.y), make_float2(B.z, B.w));
+      v = __ffma2_rn(bz2, make_float2(B.x, B.y), v);
+      v = __ffma2_rn(by2, make_float2(A.z, A.w), v);
+      v = __ffma2_rn(bx2, make_float2(A.x, A.y), v);
+      return (v.x < -kb ? 1u : 0u) | (v.y < -kb ? 2u : 0u);
+    };
     if (cnt == 32) {  // full chunk: unrolled, compile-time bit positions
 #pragma unroll
-      for (int t = 0; t < 32; ++t) {
-        const float4 g = s_obs[2 * (o0 + t)];
-        const float g2 = s_obs[2 * (o0 + t) + 1].x;
-        const float v = fmaf(bc.x, g.x, fmaf(bc.y, g.y, fmaf(bc.z, g.z, fmaf(br, g2, g.w))));
-        cand |= (v < -kb) ? (1u << t) : 0u;
-      }
-    } else {
-      for (int t = 0; t < cnt; ++t) {
-        const float4 g = s_obs[2 * (o0 + t)];
-        const float g2 = s_obs[2 * (o0 + t) + 1].x;
-        const float v = fmaf(bc.x, g.x, fmaf(bc.y, g.y, fmaf(bc.z, g.z, fmaf(br, g2, g.w))));
-        if (v < -kb) cand |= 1u << t;
-      }
+      for (int pp = 0; pp < 16; ++pp) cand |= pair_bits(pp) << (2 * pp);
+    } else {  // the padded record of an odd count never overlaps
+      for (int pp = 0; pp < obs_pairs(cnt); ++pp) cand |= pair_bits(pp) << (2 * pp);
     }
     tests += static_cast<uint32_t>(cnt);
     if (!cand) continue;
     for (int sb = s0; sb < e && !hit; sb += SPH_BLOCK) {
       const int count = min(SPH_BLOCK, e - sb);
-      float cx[SPH_BLOCK], cy[SPH_BLOCK], cz[SPH_BLOCK], rs[SPH_BLOCK], ks[SPH_BLOCK];
+      static_assert(SPH_BLOCK % 2 == 0, "spheres are tested in pairs");
+      float2 cx[SPH_BLOCK / 2], cy[SPH_BLOCK / 2], cz[SPH_BLOCK / 2], rs[SPH_BLOCK / 2], ks[SPH_BLOCK / 2];
 #pragma unroll
       for (int b = 0; b < SPH_BLOCK; ++b) {
         const int s = sb + (b < count ? b : 0);
         const V3<float> c = add_rot_t<7>(p, R, V3<float>{st.s[s][0], st.s[s][1], st.s[s][2]});
-        cx[b] = c.x;
-        cy[b] = c.y;
-        cz[b] = c.z;
-        rs[b] = st.s[s][3];
-        ks[b] = (b < count) ? fmaf(c.x, c.x, fmaf(c.y, c.y, fmaf(c.z, c.z, -rs[b] * rs[b]))) : FLT_MAX;  // pad: never a hit
+        const float r = st.s[s][3];
+        const float k = (b < count) ? fmaf(c.x, c.x, fmaf(c.y, c.y, fmaf(c.z, c.z, -r * r))) : FLT_MAX;  // pad: never a hit
+        float *dx = reinterpret_cast<float *>(&cx[b / 2]), *dy = reinterpret_cast<float *>(&cy[b / 2]),
+              *dz = reinterpret_cast<float *>(&cz[b / 2]), *dr = reinterpret_cast<float *>(&rs[b / 2]),
+              *dk = reinterpret_cast<float *>(&ks[b / 2]);
+        dx[b & 1] = c.x;
+        dy[b & 1] = c.y;
+        dz[b & 1] = c.z;
+        dr[b & 1] = r;
+        dk[b & 1] = k;
       }
       unsigned msk = cand;
       while (msk && !hit) {
         const int t = __ffs(static_cast<int>(msk)) - 1;
         msk &= msk - 1u;
-        const float4 g = s_obs[2 * (o0 + t)];
-        const float g2 = s_obs[2 * (o0 + t) + 1].x;
+        const ObsRec g = obs_rec(s_pair, o0 + t);
+        const float2 gx = make_float2(g.gx, g.gx), gy = make_float2(g.gy, g.gy), gz = make_float2(g.gz, g.gz),
+                     gw = make_float2(g.gw, g.gw), g2 = make_float2(g.g2, g.g2);
         bool h = false;
 #pragma unroll
-        for (int b = 0; b < SPH_BLOCK; ++b)
-          h |= fmaf(cx[b], g.x, fmaf(cy[b], g.y, fmaf(cz[b], g.z, fmaf(rs[b], g2, g.w)))) < -ks[b];
+        for (int b = 0; b < SPH_BLOCK / 2; ++b) {
+          float2 v = __ffma2_rn(rs[b], g2, gw);
+          v = __ffma2_rn(cz[b], gz, v);
+          v = __ffma2_rn(cy[b], gy, v);
+          v = __ffma2_rn(cx[b], gx, v);
+          h |= (v.x < -ks[b].x) | (v.y < -ks[b].y);
+        }
         tests += static_cast<uint32_t>(count);
         hit = h;
       }
@@ -1127,14 +1162,14 @@ static __device__ __noinline__ bool link_hits_f32(const Rot9 Rr, V3<float> p, in
 // and boxes staged in shared memory.  `tests` counts the 4-FMA tests made.
 template <class P>
 __device__ __forceinline__ bool check_one_f32(const ModelT<float> &m, const SphereTable<float> &st,
-                                              const float4 *s_obs, int n_obs, const float *s_box, int n_box,
+                                              const float4 *s_pair, int n_obs, const float *s_box, int n_box,
                                               const double2 *tab, const float (&q)[P::D], uint32_t &tests) {
   const OpsF32 ops{tab};
   bool hit = false;
   {
     const Rot9 Ri{{1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f}};
     hit = link_hits_f32(Ri, V3<float>{-m.shift[0], -m.shift[1], -m.shift[2]}, st.off[0], st.off[1], st.lb[MAXJ], st,
-                        s_obs, n_obs, s_box, n_box, &tests);
+                        s_pair, n_obs, s_box, n_box, &tests);
   }
   Kin<P, float> k;
   if (!hit)
@@ -1146,18 +1181,29 @@ __device__ __forceinline__ bool check_one_f32(const ModelT<float> &m, const Sphe
             Rot9 Rr;
 #pragma unroll
             for (int i = 0; i < 9; ++i) Rr.r[i] = R[i];
-            hit = link_hits_f32(Rr, p, st.off[j + 1], st.off[j + 2], st.lb[j], st, s_obs, n_obs, s_box, n_box, &tests);
+            hit = link_hits_f32(Rr, p, st.off[j + 1], st.off[j + 2], st.lb[j], st, s_pair, n_obs, s_box, n_box, &tests);
           }
         },
         [&]() { return hit; });
   return hit;
 }
 
-// Stages the FP32 obstacle records and boxes of the collision frame in shared memory.
-__device__ __forceinline__ void stage_obstacles(const float *obs, int n_obs, const float *box, int n_box,
-                                                float4 *s_obs, float *s_box) {
-  for (int t = threadIdx.x; t < 8 * n_obs; t += blockDim.x) reinterpret_cast<float *>(s_obs)[t] = obs[t];
+// Stages the FP32 obstacle records (in pairs, see obs_rec) and the boxes of
+// the collision frame in shared memory: s_pair holds obs_pairs(n_obs) x 3
+// float4, the boxes follow.  obs: [n_obs * 8] (gx, gy, gz, gw, g2, 0, 0, 0).
+__device__ __forceinline__ float *stage_obstacles(const float *obs, int n_obs, const float *box, int n_box,
+                                                  float4 *s_pair) {
+  const int np = obs_pairs(n_obs);
+  float *f = reinterpret_cast<float *>(s_pair);
+  for (int t = threadIdx.x; t < 12 * np; t += blockDim.x) {
+    const int pp = t / 12, c = t % 12, o = 2 * pp + (c & 1), field = c >> 1;  // gx gy gz gw g2 pad
+    float v = 0.f;
+    if (field < 5) v = o < n_obs ? obs[8 * o + field] : (field == 3 ? 1e30f : 0.f);  // padding: gw huge
+    f[t] = v;
+  }
+  float *s_box = f + 12 * np;
   for (int t = threadIdx.x; t < 6 * n_box; t += blockDim.x) s_box[t] = box[t];
+  return s_box;
 }
 
 // FP32 check with a per-link broad phase: the link's bounding sphere is
@@ -1169,9 +1215,8 @@ __device__ __forceinline__ void stage_obstacles(const float *obs, int n_obs, con
 template <class P>
 __global__ void __launch_bounds__(128) k_check_f32(const __grid_constant__ CheckArgs<P, float> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4 *s_obs = reinterpret_cast<float4 *>(smem_raw);          // 2 float4 per obstacle
-  float *s_box = reinterpret_cast<float *>(s_obs + 2 * a.n_obs);
-  stage_obstacles(a.obs, a.n_obs, a.box, a.n_box, s_obs, s_box);
+  float4 *s_pair = reinterpret_cast<float4 *>(smem_raw);  // 3 float4 per pair of obstacles
+  const float *s_box = stage_obstacles(a.obs, a.n_obs, a.box, a.n_box, s_pair);
   __syncthreads();
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
@@ -1183,7 +1228,7 @@ __global__ void __launch_bounds__(128) k_check_f32(const __grid_constant__ Check
   // a by-value copy lets the compiler read the model's compile-time-indexed
   // entries straight from the parameter bank (a reference costs registers)
   const ModelT<float> m = a.m;
-  const bool hit = check_one_f32<P>(m, a.st, s_obs, a.n_obs, s_box, a.n_box, a.tab, q, tests);
+  const bool hit = check_one_f32<P>(m, a.st, s_pair, a.n_obs, s_box, a.n_box, a.tab, q, tests);
   a.out[i] = hit ? 1 : 0;
   if (a.pairs) a.pairs[i] = tests;
 }
@@ -1256,10 +1301,10 @@ __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(con
   __shared__ long long s_item[W][64];
   __shared__ uint32_t s_meta[W][64];
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4 *s_obs = reinterpret_cast<float4 *>(smem_raw);
-  float *s_box = reinterpret_cast<float *>(s_obs + 2 * a.n_obs);
+  float4 *s_pair = reinterpret_cast<float4 *>(smem_raw);
+  const float *s_box = nullptr;
   if constexpr (CHK) {  // obstacles of the fused check, staged once per block
-    stage_obstacles(a.obs, a.n_obs, a.box, a.n_box, s_obs, s_box);
+    s_box = stage_obstacles(a.obs, a.n_obs, a.box, a.n_box, s_pair);
     __syncthreads();
   }
   const int lane = threadIdx.x & 31;
@@ -1351,7 +1396,7 @@ __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(con
 #pragma unroll
           for (int j = 0; j < D; ++j) qc[j] = a.q_out[j * a.ld_out + it_item];
           uint32_t tests = 0;
-          const bool h = check_one_f32<P>(a.chk->m, a.chk->st, s_obs, a.n_obs, s_box, a.n_box, a.tab, qc, tests);
+          const bool h = check_one_f32<P>(a.chk->m, a.chk->st, s_pair, a.n_obs, s_box, a.n_box, a.tab, qc, tests);
           a.hit[it_item] = h ? 1 : 0;
           if (a.pairs) a.pairs[it_item] = tests;
         }
@@ -1694,7 +1739,7 @@ cudaError_t launch_persistent(const HostModel &hm, const ProjCall &c, const Src 
   a.n_box = CHK ? hm.n_box : 0;
   a.hit = c.hit;
   a.pairs = c.pairs;
-  const size_t smem = CHK ? sizeof(float) * (8 * hm.n_obs + 6 * hm.n_box) : 0;
+  const size_t smem = CHK ? obs_smem_bytes(hm.n_obs, hm.n_box) : 0;
   const long long warps_needed = (c.total + 31) / 32;
   long long blocks = static_cast<long long>(hm.sm_count) * c.tune.blocks_per_sm;
   const long long max_useful = (warps_needed + (TPB / 32) - 1) / (TPB / 32);
@@ -1839,7 +1884,7 @@ cudaError_t launch_check_impl(const HostModel &hm, const CheckCall &c, int *laun
     a.out = c.out;
     a.pairs = c.pairs;
     a.tab = hm.d_tab;
-    const size_t smem = sizeof(float) * (8 * hm.n_obs + 6 * hm.n_box);
+    const size_t smem = obs_smem_bytes(hm.n_obs, hm.n_box);
     k_check_f32<P><<<blocks, 128, smem, c.stream>>>(a);
   }
   *launches += 1;
