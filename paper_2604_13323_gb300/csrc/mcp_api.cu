@@ -433,6 +433,7 @@ struct mcp_ctx {
   double *d_origin = nullptr;
   double origin[3] = {0.0, 0.0, 0.0};
   unsigned long long *d_counter = nullptr;
+  ScratchBuf ext_scratch;  // extend_batch: the validated chains
   long long *d_seg_off = nullptr;
   long long seg_cap = 0;
   ResolveOut *d_resolve = nullptr;
@@ -768,6 +769,7 @@ void mcp_destroy(mcp_ctx *ctx) {
   cudaFree(ctx->d_box32);
   cudaFree(ctx->d_box64);
   cudaFree(ctx->d_counter);
+  cudaFree(ctx->ext_scratch.ptr);
   cudaFree(ctx->d_seg_off);
   cudaFree(ctx->d_resolve);
   cudaFree(ctx->d_origin);
@@ -1094,6 +1096,7 @@ mcp_status mcp_extend_batch(mcp_ctx *ctx, const mcp_project_params *p, const mcp
   c.winner = winner;
   c.steps = steps;
   c.counter = ctx->d_counter;
+  c.scratch = &ctx->ext_scratch;
   c.stream = reinterpret_cast<cudaStream_t>(stream);
   int launches = 0;
   cudaError_t err = registry()[ctx->prob_class].extend_fn(ctx->hm, c, &launches);

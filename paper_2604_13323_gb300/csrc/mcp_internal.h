@@ -108,6 +108,12 @@ struct VjpCall {
   cudaStream_t stream = 0;
 };
 
+// Device scratch owned by a context and grown by the launcher that needs it.
+struct ScratchBuf {
+  float *ptr = nullptr;
+  size_t floats = 0;
+};
+
 struct ExtCall {
   double tol = 1e-5;
   int cap = 30;
@@ -127,6 +133,7 @@ struct ExtCall {
   int32_t *winner = nullptr;
   int32_t *steps = nullptr;
   unsigned long long *counter = nullptr;
+  ScratchBuf *scratch = nullptr;  // validated chains, one pair per resident group of lanes
   cudaStream_t stream = 0;
 };
 
