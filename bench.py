@@ -691,7 +691,7 @@ def run_extend(args):
     ach = fp32 / (ms * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s", "frac": ach / peak32,
             "traffic": MEASURED_TRAFFIC.get((f"dual14_rel_extend_{EXT_N}", "k_extend")),
-            "kernel": "k_extend (warp per extension: particles, interpolation, bisection)",
+            "kernel": "k_extend (8 lanes per extension, four per warp: particles, interpolation, bisection)",
             "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
             "counted": "FP32 Newton steps of all projections x the step's flops (evaluations, FP64 "
                        "acceptance and collision checks not counted)",
