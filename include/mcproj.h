@@ -225,7 +225,10 @@ mcp_status mcp_project_check_batch(mcp_ctx *ctx, const mcp_project_params *p, in
  * int32 or NULL: Newton steps taken by all projections of the extension
  * (work accounting).  Requires
  * obstacles; precision 0 and the stacked step only; MCP_ERR_UNSUPPORTED for
- * problem classes without the extension kernel (the humanoid). */
+ * problem classes without the extension kernel (the humanoid).  The first
+ * call (and a call that needs more resident groups) allocates the context's
+ * device scratch for the chains (2 x 128 points per resident group), which
+ * synchronises the device; later calls allocate nothing. */
 #define MCP_EXT_OK 0
 #define MCP_EXT_DEGENERATE 1         /* q_t == q_s */
 #define MCP_EXT_NO_PROJECTION 2      /* no particle converged before one diverged (or at the cap) */
