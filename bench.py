@@ -41,6 +41,7 @@ UNIT = "projections/s"
 # (workload, kernel); an entry is removed whenever its kernel changes.
 MEASURED_TRAFFIC = {
     ("arm7_axis_65536", "k_project_f32+check"): 2004480,      # read 2.00 MB, write 0
+    ("dual14_rel_extend_16384", "k_extend"): 3571456 + 1493504,
 }
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 
