@@ -167,29 +167,61 @@ def apply_overrides(wl, name, args):
     return name
 
 
-def cpu_baseline(wl, q, budget_s=10.0):
+def _parity_vs_gpu(O, q0, p, out, fl, it, hit, margin, gpu):
+    """The GPU's outputs for the first configurations of the batch against
+    the oracle's, as the parity tests compare them: flags over all of them;
+    points (where both converged after the same number of steps) and
+    collision verdicts (outside the 1e-5 m contact band) over the starts whose
+    oracle result is stable under +-1e-6 relative perturbations (elsewhere the
+    oracle disagrees with itself by as much)."""
+    from oracle import oracle as orc
+    from oracle import parity as par
+    n = q0.shape[1]
+    qg, fg, ig, hg = (a[..., :n] for a in gpu)
+    el, _ = par.eligible_mask(O, q0, p.tol, p.max_iters, p.lam, max_step=p.max_step, cyclic=p.cyclic)
+    cg, co = (fg & orc.CONVERGED) != 0, (fl & orc.CONVERGED) != 0
+    both = cg & co
+    same = both & (ig == it) & el
+    err = np.abs(qg[:, same].astype(np.float64) - out[:, same]).max(axis=0) if same.any() else np.zeros(1)
+    band = both & el & (margin >= 1e-5)
+    return {"configs": int(n), "eligible": float(el.mean()), "flag_agree": float((cg == co).mean()),
+            "flag_agree_eligible": float((cg == co)[el].mean()) if el.any() else 1.0,
+            "iters_equal_eligible": float(same.sum() / max(1, (both & el).sum())),
+            "q_err_max_eligible": float(err.max()), "q_err_p999_eligible": float(np.quantile(err, 0.999)),
+            "hit_agree_outside_band": float(((hg != 0) == (hit != 0))[band].mean()) if band.any() else 1.0}
+
+
+def cpu_baseline(wl, q, budget_s=10.0, gpu=None):
     """The FP64 oracle, as it stands, on the host cores: projection + check of
-    contiguous chunks of the workload until ~budget_s of wall time."""
+    contiguous chunks of the workload until ~budget_s of wall time.  With the
+    GPU's outputs of the same batch (`gpu`: q [d, n], flags, iters, hit), the
+    first chunk is also compared with them."""
     from oracle import oracle as orc
     O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
     threads = orc.default_threads()
     p = wl.params
     chunk = 4096
     done = conv = 0
+    parity = None
     t0 = time.perf_counter()
     off = 0
     while time.perf_counter() - t0 < budget_s:
         sl = q[:, off:off + chunk]
-        out, fl, _, r = O.project(sl, p.tol, p.max_iters, p.lam, max_step=p.max_step, cyclic=p.cyclic,
-                                  threads=threads)
-        O.check(out, threads=threads)
+        out, fl, it, r = O.project(sl, p.tol, p.max_iters, p.lam, max_step=p.max_step, cyclic=p.cyclic,
+                                   threads=threads)
+        hit, margin = O.check(out, threads=threads)
+        if gpu is not None and parity is None and off == 0:
+            parity = _parity_vs_gpu(O, sl, p, out, fl, it, hit, margin, gpu)
         conv += int(((fl & orc.CONVERGED) != 0).sum())
         done += sl.shape[1]
         off = (off + chunk) % q.shape[1]
     dt = time.perf_counter() - t0
-    return {"value": conv / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{done} configurations (contiguous chunks of {chunk} of the bench batch), "
-                      f"projection + collision check, FP64, {dt:.1f} s wall"}
+    res = {"value": conv / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{done} configurations (contiguous chunks of {chunk} of the bench batch), "
+                     f"projection + collision check, FP64, {dt:.1f} s wall"}
+    if parity is not None:
+        res["parity_vs_gpu"] = parity
+    return res
 
 
 def run_reference(args):
@@ -565,7 +597,13 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.profile):
-        cpu = cpu_baseline(wl, cpu_q)
+        if seg_args is None:   # the oracle starts from the FP32 values the GPU projected
+            q32 = np.asarray(cpu_q, dtype=np.float32).astype(np.float64)
+            gpu_out = (q_out[:, :4096].double().cpu().numpy(), flags[:4096].cpu().numpy(),
+                       iters[:4096].cpu().numpy(), hit[:4096].cpu().numpy())
+            cpu = cpu_baseline(wl, q32, gpu=gpu_out)
+        else:
+            cpu = cpu_baseline(wl, cpu_q)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
