@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="arm", choices=["arm", "dual_arm", "dual_segments", "sphere", "humanoid",
                                                           "arm_tray", "arm_peg", "arm_tsr", "dual_rod", "extend",
-                                                          "humanoid_hull"])
+                                                          "humanoid_hull", "vjp", "shorten"])
     ap.add_argument("--cyclic", action="store_true",
                     help="cyclic getDescentStep (one LM step per constraint per sweep) instead of the stacked step")
     ap.add_argument("--cap", type=int, default=0, help="iteration cap (default: the workload's)")
@@ -768,12 +768,203 @@ def run_extend(args):
         dist.destroy_process_group()
 
 
+VJP_N = 65536          # projected dual-arm configurations per VJP step
+PATHS, WAYPOINTS, SHORTEN_STEPS = 4096, 64, 100
+
+
+def run_adjoint(args):
+    """The adjoint of the projection on the dual-arm closed chain: `vjp`
+    times the VJP kernel v = g - J^T (J J^T)^{-1} J g on VJP_N projected
+    configurations with g ~ N(0, 1) (one step = one call); `shorten` times
+    gradient path shortening on the manifold (PATHS paths of WAYPOINTS
+    waypoints, SHORTEN_STEPS steps of project -> length -> backward through
+    the projection (VJP) -> clipped step; one bench step = one whole run) and
+    reports the mean length reduction and the largest FP64 residual."""
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2604_13323_gb300 import build as B
+    B.build()
+    from paper_2604_13323_gb300 import flops as FL
+    from paper_2604_13323_gb300 import mcproj
+    from paper_2604_13323_gb300 import shorten as SH
+    from paper_2604_13323_gb300 import workloads as W
+
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    vjp_mode = args.workload == "vjp"
+    extra = {}
+    if vjp_mode:
+        wl = W.dual_arm_workload(total=10, n_random=VJP_N, batch_seed=1011 + 1000 * rank)
+        p = wl.params
+        P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles, device=local)
+        q_star = P.project(torch.tensor(wl.q, dtype=torch.float32, device=dev), p)[0].contiguous()  # setup
+        g = torch.tensor(np.random.default_rng(1012 + 1000 * rank).standard_normal((14, VJP_N)),
+                         dtype=torch.float32, device=dev)
+        v = torch.empty_like(g)
+        vf = torch.empty(VJP_N, dtype=torch.uint8, device=dev)
+
+        def step():
+            P.vjp(q_star, g, out=v, flags=vf, stream=stream)
+        units_per_step = VJP_N
+        unit, metric = "VJPs/s", "vector-Jacobian products/sec at q* (dual-arm closed chain, 1 GB300)"
+        name = f"dual14_rel_vjp_{VJP_N}"
+    else:
+        pw = W.path_workload(n_paths=PATHS, n_way=WAYPOINTS)
+        wl = pw["workload"]
+        p = wl.params
+        P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles, device=local)
+        Q0 = SH.initial_paths(P, pw["qa"], pw["qb"], pw["noise"], p)   # setup
+        stats = {}
+
+        def step():   # the graph-captured descent (the autograd one computes the same, more slowly)
+            _, st = SH.shorten_paths_graph(P, Q0, PATHS, WAYPOINTS, p, SHORTEN_STEPS)
+            stats.update(st)
+        units_per_step = PATHS * WAYPOINTS * SHORTEN_STEPS
+        unit, metric = "waypoint-steps/s", "path-shortening waypoint steps/sec on the manifold (dual arm, 1 GB300)"
+        name = f"dual14_rel_shorten_{PATHS}x{WAYPOINTS}x{SHORTEN_STEPS}"
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    with sampler:
+        t0 = time.perf_counter()
+        w = 0
+        while w < args.warmup or (not args.profile and time.perf_counter() - t0 < 1.5):
+            flush.zero_()
+            step()
+            w += 1
+            if w % 16 == 0:
+                torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        launches0 = P.launches
+        for s_ in range(args.steps):
+            flush.zero_()
+            evs[s_][0].record(stream)
+            step()
+            evs[s_][1].record(stream)
+        torch.cuda.synchronize()
+    launches = P.launches - launches0
+    ms = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
+    ms_max, u_total = aggregate_replicas(ms, units_per_step, world, dev)
+    value = u_total / (ms_max * 1e-3)
+    fm = FL.FlopModel(wl.robot, wl.constraints)
+    clk = sampler.summary()
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak32 = torch.cuda.get_device_properties(dev).multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    if vjp_mode:
+        # one VJP evaluates F and J at q*, builds and factors J J^T, solves
+        # twice (with the refinement) and forms g - J^T y: counted as one LM step
+        ach = VJP_N * fm.iteration / (ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s", "frac": ach / peak32,
+                "traffic": None, "kernel": "k_vjp (thread per configuration, FP32 + FP64 re-solve below the pivot)",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                "counted": "one LM step's FP32 flops per VJP (FK, F, J, Gram, Cholesky, two solves, J^T y)"}
+        vfl = vf.cpu().numpy()
+        extra = {"vjp_flags_nonzero": float((vfl != 0).mean())}
+    else:
+        # one shortening step, its calls timed one by one (after the timed runs)
+        Qs = Q0.clone()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        Qv = Qs.detach().requires_grad_(True)
+        ev[0].record(stream)
+        out = P.project(Qv.detach(), p)[0]
+        ev[1].record(stream)
+        length, grad = P.path_length_grad(out, PATHS, WAYPOINTS)
+        ev[2].record(stream)
+        vv, _ = P.vjp(out, grad)
+        ev[3].record(stream)
+        P.path_step(out, vv, PATHS, WAYPOINTS, 0.1, 0.05)
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        parts = {k: ev[i].elapsed_time(ev[i + 1]) for i, k in
+                 enumerate(("project", "path_length_grad", "vjp", "path_step"))}
+        extra = {k: stats[k] for k in ("mean_length_reduction", "min_length_reduction", "max_resid",
+                                       "converged_fraction", "mean_length_before", "mean_length_after")}
+        extra["kernel_ms_one_step"] = parts
+        # the dominant call: the projection of the waypoints (FP32 steps of the
+        # shortened points, a few per step, counted from the final projection)
+        it = P.project(Qs, p)[2].cpu().numpy()
+        fp32, fp64f = fm.projection(it)
+        ach = fp32 / (parts["project"] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s", "frac": ach / peak32,
+                "traffic": None, "kernel": "k_project_f32 (the waypoints' re-projection in one shortening step)",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                "counted": "FP32 Newton-step and evaluation flops of the initial paths' projection"}
+    e2e = None
+    if vjp_mode and not args.profile:   # q* and g from pinned host memory, v back, one step at a time
+        hq, hg = q_star.cpu().pin_memory(), g.cpu().pin_memory()
+        hv = torch.empty(v.shape, dtype=v.dtype).pin_memory()
+        e_ms = []
+        for s_ in range(args.warmup + args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            q_star.copy_(hq, non_blocking=True)
+            g.copy_(hg, non_blocking=True)
+            step()
+            hv.copy_(v, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if s_ >= args.warmup:
+                e_ms.append(e0.elapsed_time(e1))
+        e_max, _ = aggregate_replicas(sum(e_ms) / len(e_ms), 0, world, dev)
+        e2e = {"value": units_per_step * world / (e_max * 1e-3), "unit": unit,
+               "h2d_bytes_per_step": 2 * hq.numel() * 4, "d2h_bytes_per_step": hv.numel() * 4}
+    cpu = None
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.profile) and vjp_mode:
+        from oracle import oracle as orc
+        O = orc.Oracle(wl.robot, wl.constraints)
+        qn = q_star.double().cpu().numpy()
+        gn = g.double().cpu().numpy()
+        vg = v.double().cpu().numpy()
+        t0 = time.perf_counter()
+        done = 0
+        rel = None
+        while time.perf_counter() - t0 < 10.0:
+            sl = slice(done % VJP_N, done % VJP_N + 4096)
+            vo, fo = O.vjp(qn[:, sl], gn[:, sl])
+            if rel is None:
+                ok = fo == 0
+                rel = float((np.abs(vg[:, sl][:, ok] - vo[:, ok]).max(axis=0) /
+                             np.maximum(np.abs(vo[:, ok]).max(axis=0), 1e-12)).max())
+            done += 4096
+        dt = time.perf_counter() - t0
+        cpu = {"value": done / dt, "unit": unit, "cores": orc.default_threads(), "kind": "oracle",
+               "sample": f"{done} VJPs (chunks of 4096 of the bench batch), FP64, {dt:.1f} s wall",
+               "parity_vs_gpu": {"configs": 4096, "max_rel_err": rel}}
+    if rank == 0:
+        line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": name, "l2": "flushed between timed steps (512 MB write)",
+                           "parallelism": f"replicas x{world}", **extra},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    P.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.impl == "reference" and args.workload in ("vjp", "shorten"):
+        if int(os.environ.get("RANK", "0")) == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle's VJP is timed in this workload's "
+                              "cpu_baseline leg; the oracle has no path-shortening driver"}))
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "extend":
         run_extend(args)
+    elif args.workload in ("vjp", "shorten"):
+        run_adjoint(args)
     else:
         run_ours(args)
 

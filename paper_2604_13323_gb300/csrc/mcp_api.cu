@@ -365,22 +365,30 @@ __global__ void k_scan_lengths(const int32_t *len, long long n, long long *off) 
 }
 
 // Path length and its gradient (thread per waypoint / per path).
+// One thread per waypoint: d/dq_i of |q_i - q_{i-1}| + |q_{i+1} - q_i|, in two
+// passes over the joints (the norms, then the output; the second pass re-reads
+// the same waypoints from L1) so that nothing is held in runtime-indexed arrays.
 __global__ void k_path_grad(const float *Q, long long ld, long long n_paths, int n_way, int d, float *grad) {
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n_paths * n_way) return;
   const int w = static_cast<int>(i % n_way);
-  float ep[MAXJ], en[MAXJ];
+  const bool has_p = w > 0, has_n = w + 1 < n_way;
   float np2 = 0.f, nn2 = 0.f;
   for (int j = 0; j < d; ++j) {
     const float qi = Q[j * ld + i];
-    ep[j] = (w > 0) ? qi - Q[j * ld + i - 1] : 0.f;
-    en[j] = (w + 1 < n_way) ? Q[j * ld + i + 1] - qi : 0.f;
-    np2 = fmaf(ep[j], ep[j], np2);
-    nn2 = fmaf(en[j], en[j], nn2);
+    const float ep = has_p ? qi - Q[j * ld + i - 1] : 0.f;
+    const float en = has_n ? Q[j * ld + i + 1] - qi : 0.f;
+    np2 = fmaf(ep, ep, np2);
+    nn2 = fmaf(en, en, nn2);
   }
   const float ip = np2 > 0.f ? rsqrtf(np2) : 0.f;
   const float in = nn2 > 0.f ? rsqrtf(nn2) : 0.f;
-  for (int j = 0; j < d; ++j) grad[j * ld + i] = ep[j] * ip - en[j] * in;
+  for (int j = 0; j < d; ++j) {
+    const float qi = Q[j * ld + i];
+    const float ep = has_p ? qi - Q[j * ld + i - 1] : 0.f;
+    const float en = has_n ? Q[j * ld + i + 1] - qi : 0.f;
+    grad[j * ld + i] = ep * ip - en * in;
+  }
 }
 
 __global__ void k_path_step(float *Q, const float *D, long long ld, long long n_paths, int n_way, int d, float eta,
@@ -395,11 +403,14 @@ __global__ void k_path_step(float *Q, const float *D, long long ld, long long n_
   for (int j = 0; j < d; ++j) Q[j * ld + i] = fmaf(-sc * eta, D[j * ld + i], Q[j * ld + i]);
 }
 
+// One warp per path: lane l sums the lengths of segments l, l + 32, ... and
+// the warp adds the partial sums in a fixed order (deterministic).
 __global__ void k_path_length(const float *Q, long long ld, long long n_paths, int n_way, int d, float *length) {
-  const long long p = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (p >= n_paths) return;
+  const long long p = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (p >= n_paths) return;  // whole warps leave together
   float L = 0.f;
-  for (int w = 0; w + 1 < n_way; ++w) {
+  for (int w = lane; w + 1 < n_way; w += 32) {
     const long long i = p * n_way + w;
     float n2 = 0.f;
     for (int j = 0; j < d; ++j) {
@@ -408,7 +419,9 @@ __global__ void k_path_length(const float *Q, long long ld, long long n_paths, i
     }
     L += sqrtf(n2);
   }
-  length[p] = L;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) L += __shfl_xor_sync(0xffffffffu, L, o);
+  if (lane == 0) length[p] = L;
 }
 
 // ---------------------------------------------------------------------------
@@ -1368,7 +1381,7 @@ mcp_status mcp_path_length_grad(mcp_ctx *ctx, int64_t n_paths, int32_t n_way, in
     MCP_CUDA(cudaGetLastError(), "path gradient launch");
   }
   if (length) {
-    k_path_length<<<static_cast<unsigned>((n_paths + 127) / 128), 128, 0, s>>>(Q, ld, n_paths, n_way, d, length);
+    k_path_length<<<static_cast<unsigned>((n_paths * 32 + 127) / 128), 128, 0, s>>>(Q, ld, n_paths, n_way, d, length);
     ctx->launches += 1;
     MCP_CUDA(cudaGetLastError(), "path length launch");
   }

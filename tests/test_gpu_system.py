@@ -150,6 +150,20 @@ def test_path_shortening_reduces_length_on_manifold(mcproj):
         assert np.linalg.norm(O.residual(Qn[:, i])) < 1e-5
 
 
+def test_graph_shortening_equals_autograd_shortening(mcproj):
+    """The graph-captured descent runs the same kernels in the same order as
+    the autograd one: identical waypoints and statistics."""
+    from paper_2604_13323_gb300.shorten import initial_paths, shorten_paths, shorten_paths_graph
+    pw = W.path_workload(n_paths=64, n_way=16)
+    wl = pw["workload"]
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
+    Q = initial_paths(P, pw["qa"], pw["qb"], pw["noise"], wl.params)
+    Qa, sa = shorten_paths(P, Q.clone(), 64, 16, wl.params, steps=12)
+    Qg, sg = shorten_paths_graph(P, Q.clone(), 64, 16, wl.params, steps=12)
+    assert torch.equal(Qa, Qg)
+    assert sa == sg
+
+
 @pytest.mark.parametrize("name", ["arm", "dual", "tray", "tray_cyclic", "humanoid", "arm_fp64"])
 def test_project_check_equals_separate_calls(mcproj, name):
     """mcp_project_check_batch (one persistent launch for the FP32 thread
