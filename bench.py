@@ -59,7 +59,8 @@ def parse():
                     help="cyclic getDescentStep (one LM step per constraint per sweep) instead of the stacked step")
     ap.add_argument("--cap", type=int, default=0, help="iteration cap (default: the workload's)")
     ap.add_argument("--launch", default="",
-                    help="tpb,blocks_per_sm,chunk,fuse_check instead of autotuning (profiler runs)")
+                    help="tpb,blocks_per_sm,chunk,fuse_check[,threads_per_config] instead of autotuning "
+                         "(profiler runs)")
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=0,
@@ -390,7 +391,7 @@ def run_ours(args):
         else:   # segments: tuned on a batch of their materialised points (the same persistent kernel)
             sample = q_in if seg_args is None else torch.tensor(cpu_q[:, :65536], dtype=dt, device=dev)
             vals = P.autotune(sample, wl.params)
-        tuning = dict(zip(("tpb", "blocks_per_sm", "chunk", "fuse_check"), vals))
+        tuning = dict(zip(("tpb", "blocks_per_sm", "chunk", "fuse_check", "threads_per_config"), vals))
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     sampler = ClockSampler(local)
     with sampler:
@@ -580,6 +581,8 @@ def run_ours(args):
                                if args.workload.startswith("humanoid") and not wl.params.cyclic else
                                "k_project_warp (warp per configuration, cyclic sweeps)"
                                if args.workload.startswith("humanoid") else
+                               "k_project_pair (persistent, one lane per arm: FP32 steps + FP64 acceptance)"
+                               if tuning and tuning.get("threads_per_config") == 2 else
                                "k_project_f32 (persistent, FP32 steps + FP64 acceptance)"),
                     "peak_source": peak_src,
                     "fp64_achieved": ach64, "fp64_peak": peak64, "fp64_frac": ach64 / peak64,

@@ -303,12 +303,18 @@ mcp_status mcp_path_step(mcp_ctx *ctx, int64_t n_paths, int32_t n_way, int64_t l
 
 /* Sets the launch shape of the persistent FP32 projection kernel directly
  * (tpb in {64, 128, 256}, blocks_per_sm in 1..8 with tpb * blocks_per_sm <=
- * 2048, chunk in 1..64, fuse_check 0 / 1), e.g. to reproduce a tuned shape.
- * MCP_ERR_ARG outside those ranges. */
-mcp_status mcp_set_tuning(mcp_ctx *ctx, int32_t tpb, int32_t blocks_per_sm, int32_t chunk, int32_t fuse_check);
+ * 2048, chunk in 1..64, fuse_check 0 / 1, threads_per_config 1 / 2), e.g. to
+ * reproduce a tuned shape.  threads_per_config = 2 runs the two-chain classes
+ * (the dual arm, Eq. 2) with one lane per chain; other classes ignore it; it
+ * has no fused check (the check is a second launch).  Results of the two
+ * kernels differ only by the rounding of the Gram sums.  MCP_ERR_ARG outside
+ * those ranges. */
+mcp_status mcp_set_tuning(mcp_ctx *ctx, int32_t tpb, int32_t blocks_per_sm, int32_t chunk, int32_t fuse_check,
+                          int32_t threads_per_config);
 
 /* Picks the launch shape of the persistent FP32 projection kernel (threads
- * per block, resident blocks per SM, configurations claimed per atomic) for
+ * per block, resident blocks per SM, configurations claimed per atomic, and
+ * threads per configuration where the class has a choice) for
  * the loaded problem by timing every candidate on the caller's sample
  * q_sample (DEVICE, float [d * ld], n_sample configurations), and keeps the
  * fastest in the context for later calls.  With obstacles loaded the timed
@@ -316,11 +322,12 @@ mcp_status mcp_set_tuning(mcp_ctx *ctx, int32_t tpb, int32_t blocks_per_sm, int3
  * check inside the projection kernel and as a second launch.  Each candidate
  * is timed as the median of five bursts of four calls.  Uses temporary
  * device buffers; synchronous.  The choices are returned in tpb / blocks_per_sm /
- * chunk / fuse_check (HOST, each may be NULL).  Tuning never changes results,
- * only speed. */
+ * chunk / fuse_check / threads_per_config (HOST, each may be NULL).  The
+ * launch shape never changes results; threads per configuration changes them
+ * by rounding only (see mcp_set_tuning). */
 mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sample, int64_t ld, const void *q_sample,
                         int32_t *tpb, int32_t *blocks_per_sm, int32_t *chunk, int32_t *fuse_check,
-                        mcp_stream stream);
+                        int32_t *threads_per_config, mcp_stream stream);
 
 /* Number of kernels this context has launched so far (for launch accounting). */
 int64_t mcp_launch_count(const mcp_ctx *ctx);

@@ -31,6 +31,7 @@ struct ClassDesc {
   int flink[MAXF], frot[MAXF], ftmask[MAXF];
   int ckind[MAXC], cfa[MAXC], cfb[MAXC];
   bool project;  // projection / VJP compiled for this class
+  bool pair;     // the FP32 projection also runs one lane per chain (threads per configuration 2)
   cudaError_t (*project_fn)(const HostModel &, const ProjCall &, int *);
   cudaError_t (*check_fn)(const HostModel &, const CheckCall &, int *);
   cudaError_t (*vjp_fn)(const HostModel &, const VjpCall &, int *);
@@ -61,6 +62,7 @@ ClassDesc describe(bool project) {
     d.cfb[c] = P::cfb(c);
   }
   d.project = project;
+  d.pair = has_pair_kernel<P>();
   d.project_fn = &launch_project<P>;
   d.check_fn = &launch_check<P>;
   d.vjp_fn = &launch_vjp<P>;
@@ -1407,20 +1409,22 @@ mcp_status mcp_path_step(mcp_ctx *ctx, int64_t n_paths, int32_t n_way, int64_t l
   return MCP_OK;
 }
 
-mcp_status mcp_set_tuning(mcp_ctx *ctx, int32_t tpb, int32_t blocks_per_sm, int32_t chunk, int32_t fuse_check) {
+mcp_status mcp_set_tuning(mcp_ctx *ctx, int32_t tpb, int32_t blocks_per_sm, int32_t chunk, int32_t fuse_check,
+                          int32_t threads_per_config) {
   if (!ctx) return MCP_ERR_ARG;
   if ((tpb != 64 && tpb != 128 && tpb != 256) || blocks_per_sm < 1 || blocks_per_sm > 8 ||
-      tpb * blocks_per_sm > 2048 || chunk < 1 || chunk > 64 || (fuse_check != 0 && fuse_check != 1))
-    return fail(ctx, MCP_ERR_ARG, "tuning (%d, %d, %d, %d) outside the supported shapes", tpb, blocks_per_sm, chunk,
-                fuse_check);
-  ctx->tune = Tuning{tpb, blocks_per_sm, chunk, fuse_check == 1};
+      tpb * blocks_per_sm > 2048 || chunk < 1 || chunk > 64 || (fuse_check != 0 && fuse_check != 1) ||
+      (threads_per_config != 1 && threads_per_config != 2))
+    return fail(ctx, MCP_ERR_ARG, "tuning (%d, %d, %d, %d, %d) outside the supported shapes", tpb, blocks_per_sm, chunk,
+                fuse_check, threads_per_config);
+  ctx->tune = Tuning{tpb, blocks_per_sm, chunk, fuse_check == 1, threads_per_config};
   ctx->tuned = true;
   return MCP_OK;
 }
 
 mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sample, int64_t ld, const void *q_sample,
                         int32_t *tpb_out, int32_t *bps_out, int32_t *chunk_out, int32_t *fuse_out,
-                        mcp_stream stream) {
+                        int32_t *tpc_out, mcp_stream stream) {
   if (!ctx) return MCP_ERR_ARG;
   mcp_status st = validate_params(ctx, p);
   if (st != MCP_OK) return st;
@@ -1452,6 +1456,9 @@ mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sam
   // time is the median of five bursts of four back-to-back calls (one
   // warm-up burst first): single calls sit near the resolution of the events.
   const int n_fuse = ctx->obs_loaded ? 2 : 1;
+  // threads per configuration: 1, and 2 where the class has a pair kernel
+  // (which has no fused check: its two-launch time is taken once)
+  const int n_tpc = registry()[ctx->prob_class].pair ? 2 : 1;
   auto time_candidate = [&](float &med) -> cudaError_t {
     constexpr int BURSTS = 6, CALLS = 4;
     float times[BURSTS - 1];
@@ -1493,16 +1500,17 @@ mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sam
   for (int a = 0; a < 3 && err == cudaSuccess; ++a)
     for (int b = 0; b < 4 && err == cudaSuccess; ++b)
       for (int c = 0; c < 3 && err == cudaSuccess; ++c)
-        for (int f = 0; f < n_fuse && err == cudaSuccess; ++f) {
-          if (tpbs[a] * bpss[b] > 2048) continue;
-          ctx->tune = Tuning{tpbs[a], bpss[b], chunks[c], f == 1};
-          float med = 0.f;
-          err = time_candidate(med);
-          if (err == cudaSuccess && med < best_ms) {
-            best_ms = med;
-            best = ctx->tune;
+        for (int f = 0; f < n_fuse && err == cudaSuccess; ++f)
+          for (int t = 1; t <= n_tpc && err == cudaSuccess; ++t) {
+            if (tpbs[a] * bpss[b] > 2048 || (t == 2 && f == 1)) continue;
+            ctx->tune = Tuning{tpbs[a], bpss[b], chunks[c], f == 1, t};
+            float med = 0.f;
+            err = time_candidate(med);
+            if (err == cudaSuccess && med < best_ms) {
+              best_ms = med;
+              best = ctx->tune;
+            }
           }
-        }
   cudaFree(out);
   cudaFree(fl);
   cudaFree(it);
@@ -1520,6 +1528,7 @@ mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sam
   if (bps_out) *bps_out = best.blocks_per_sm;
   if (chunk_out) *chunk_out = best.chunk;
   if (fuse_out) *fuse_out = best.fuse_check ? 1 : 0;
+  if (tpc_out) *tpc_out = best.tpc;
   return MCP_OK;
 }
 

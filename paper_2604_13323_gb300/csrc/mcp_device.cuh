@@ -434,12 +434,14 @@ struct NoStop {
   __device__ __forceinline__ bool operator()() const { return false; }
 };
 
-// World transforms of every joint frame (and the task frames).  `visit(j, R_j,
+// World transforms of every joint frame (and the task frames).  The model m
+// is a ModelT or any view with rows X[j] and fX[f] (and mass / com where a
+// CoM constraint needs them).  `visit(j, R_j,
 // p_j)` is called right after joint j is placed, and joints after `stop()`
 // becomes true are skipped, so consumers can use each link's pose while it is
 // live (the collision check does) instead of keeping the whole tree.
-template <class P, bool POS, class Ops, typename T, class Visit = NoVisit, class Stop = NoStop>
-__device__ __forceinline__ void fk(const Ops &ops, const ModelT<T> &m, const T (&q)[P::D], Kin<P, T> &k,
+template <class P, bool POS, class Ops, typename T, class Visit = NoVisit, class Stop = NoStop, class M = ModelT<T>>
+__device__ __forceinline__ void fk(const Ops &ops, const M &m, const T (&q)[P::D], Kin<P, T> &k,
                                    const Visit &visit = Visit{}, const Stop &stop = Stop{}) {
   static_for<P::D>([&](auto JJ) {
     constexpr int j = decltype(JJ)::value;

@@ -26,6 +26,7 @@ struct Tuning {
   int blocks_per_sm = 4;  // resident blocks per SM
   int chunk = 32;         // configurations a warp claims per atomic
   bool fuse_check = false;  // project_check_batch: check inside the projection kernel (else a second launch)
+  int tpc = 1;              // threads per configuration: 2 = one lane per chain (classes with a pair kernel)
 };
 
 // What the collision check of the fused projection kernel reads from device

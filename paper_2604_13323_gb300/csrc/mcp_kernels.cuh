@@ -22,6 +22,7 @@ constexpr unsigned FULL = 0xffffffffu;
 // internal flag bits (never written out)
 constexpr uint32_t FL_INT_FP32CONV = 1u << 8;   // FP32 residual passed; FP64 check pending
 constexpr uint32_t FL_INT_NEEDS_F64 = 1u << 9;  // FP32 pivot below threshold: continue in FP64
+constexpr uint32_t FL_INT_FORCE = 1u << 10;     // FP64 acceptance failed: one FP32 step before the next test
 
 // Forms of getDescentStep (Alg. 2): the stacked inner step J^T (J J^T + lambda I)^-1 F,
 // one inner step per constraint in turn (cyclic), or the stacked outer step
@@ -350,6 +351,12 @@ struct BatchSrc {
 #pragma unroll
     for (int j = 0; j < D; ++j) out[j] = q[j * ld + item];
   }
+  // joints j0 .. j0 + N - 1 only
+  template <int N>
+  __device__ __forceinline__ void load_part(long long item, int j0, T (&out)[N]) const {
+#pragma unroll
+    for (int j = 0; j < N; ++j) out[j] = q[(j0 + j) * ld + item];
+  }
 };
 
 template <typename T>
@@ -364,18 +371,27 @@ struct SegSrc {
     const long long dev_total = __ldg(&off[n]);
     return t < dev_total ? t : dev_total;
   }
-  template <int D>
-  __device__ __forceinline__ void load(long long item, T (&out)[D]) const {
-    // last segment s with off[s] <= item (segments of length 0 are skipped)
+  // last segment s with off[s] <= item (segments of length 0 are skipped)
+  __device__ __forceinline__ int segment_of(long long item) const {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (__ldg(&off[mid]) <= item) lo = mid;
       else hi = mid - 1;
     }
-    const T t = static_cast<T>(item - __ldg(&off[lo]));
+    return lo;
+  }
+  template <int D>
+  __device__ __forceinline__ void load(long long item, T (&out)[D]) const {
+    load_part<D>(item, 0, out);
+  }
+  // joints j0 .. j0 + N - 1 of the point
+  template <int N>
+  __device__ __forceinline__ void load_part(long long item, int j0, T (&out)[N]) const {
+    const int s = segment_of(item);
+    const T t = static_cast<T>(item - __ldg(&off[s]));
 #pragma unroll
-    for (int j = 0; j < D; ++j) out[j] = fma_(t, delta[j * ld + lo], start[j * ld + lo]);
+    for (int j = 0; j < N; ++j) out[j] = fma_(t, delta[(j0 + j) * ld + s], start[(j0 + j) * ld + s]);
   }
 };
 
@@ -453,7 +469,7 @@ __device__ __forceinline__ bool newton_iter_f32(const A &a, float (&q)[P::D], in
     fl |= FL_NONFINITE;
     return true;
   }
-  if (r2 < a.tol2) {
+  if (r2 < a.tol2 && !(fl & FL_INT_FORCE)) {
     fl |= FL_INT_FP32CONV;
     return true;
   }
@@ -513,6 +529,7 @@ __device__ __forceinline__ bool newton_iter_f32(const A &a, float (&q)[P::D], in
 #pragma unroll
   for (int j = 0; j < D; ++j) q[j] -= dq[j];
   ++it;
+  fl &= ~FL_INT_FORCE;
   if (!(s2 <= FLT_MAX)) {
     fl |= FL_NONFINITE;
     return true;
@@ -570,7 +587,7 @@ __device__ __forceinline__ bool cyclic_iter_f32(const A &a, float (&q)[P::D], in
       fl |= FL_NONFINITE;
       return true;
     }
-    if (r2 < a.tol2) {
+    if (r2 < a.tol2 && !(fl & FL_INT_FORCE)) {
       fl |= FL_INT_FP32CONV;
       return true;
     }
@@ -596,6 +613,7 @@ __device__ __forceinline__ bool cyclic_iter_f32(const A &a, float (&q)[P::D], in
     return true;
   }
   ++it;
+  fl &= ~FL_INT_FORCE;
   if (!(s2 <= FLT_MAX)) {
     fl |= FL_NONFINITE;
     return true;
@@ -938,17 +956,20 @@ __device__ __noinline__ double finish_f64(const A &a, float *q, double *qd, int 
 }
 
 // Acceptance of one configuration that left the FP32 loop: the FP32 iterate
-// is re-checked with the FP64 residual; if the FP32 test was too optimistic,
-// or the FP32 pivot was too small, finish_f64 takes the remaining steps.
+// is re-checked with the FP64 residual.  If the FP32 test was too optimistic
+// and steps remain, the configuration goes back to the FP32 loop for one more
+// step (retry allowed: returns true, nothing written); otherwise, or when the
+// FP32 pivot was too small, finish_f64 takes the remaining steps in FP64.
 // Writes q (if changed), flags, iters and resid.
 template <class P, int FORM, class A>
-__device__ __forceinline__ void accept_one(const A &a, long long item, int it, uint32_t fl) {
+__device__ __forceinline__ bool accept_one(const A &a, long long item, int it, uint32_t fl, bool retry_ok = false) {
   constexpr int D = P::D;
   const ModelT<double> &m = *a.m64;
   float q[D];
 #pragma unroll
   for (int j = 0; j < D; ++j) q[j] = a.q_out[j * a.ld_out + item];
   double r2 = residual2_f64<P>(OpsF64Split{a.tab}, m, q);
+  if (retry_ok && (fl & FL_INT_FP32CONV) && !(r2 < a.tol2_64) && r2 <= DBL_MAX && it < a.cap) return true;
   if (fl & (FL_INT_FP32CONV | FL_INT_NEEDS_F64)) {
     const bool was_conv = (fl & FL_INT_FP32CONV) != 0;
     fl &= ~(FL_INT_FP32CONV | FL_INT_NEEDS_F64);
@@ -979,6 +1000,7 @@ __device__ __forceinline__ void accept_one(const A &a, long long item, int it, u
   a.flags[item] = static_cast<uint8_t>(fl & 0xffu);
   a.iters[item] = static_cast<uint8_t>(it > 255 ? 255 : it);
   a.resid[item] = sqrt_refined(r2);
+  return false;
 }
 
 // ---------------------------------------------------------------------------
@@ -1294,12 +1316,18 @@ __host__ __device__ constexpr int min_blocks() {
   return 65536 / (TPB * reg_cap<P>()) > 0 ? 65536 / (TPB * reg_cap<P>()) : 1;
 }
 
+// Configurations a warp can hold for an FP32 retry after a failed FP64
+// acceptance (beyond this the acceptance finishes them in FP64 itself).
+constexpr int RETRY_CAP = 32;
+
 template <class P, class Src, int TPB, int FORM, bool CHK>
 __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(const __grid_constant__ ProjArgs<P, Src> a) {
   constexpr int D = P::D;
   constexpr int W = TPB / 32;
   __shared__ long long s_item[W][64];
   __shared__ uint32_t s_meta[W][64];
+  __shared__ long long s_ritem[W][RETRY_CAP];  // sent back to the FP32 loop by the acceptance
+  __shared__ uint32_t s_rmeta[W][RETRY_CAP];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4 *s_pair = reinterpret_cast<float4 *>(smem_raw);
   const float *s_box = nullptr;
@@ -1311,6 +1339,7 @@ __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(con
   const int wib = threadIdx.x >> 5;
   const long long total = a.src.clamp_total(a.total);
   int pend = 0;                   // warp-uniform count of pending configurations
+  int nret = 0;                   // warp-uniform count of configurations to retry in FP32
   long long qn = 0, qe = 0;       // warp-local queue [qn, qe)
   bool more = true;               // the global counter may still have work
   bool act = false;
@@ -1322,13 +1351,15 @@ __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(con
   for (int j = 0; j < D; ++j) q[j] = 0.f;
 
   while (true) {
-    // (1) refill
+    // (1) refill: configurations sent back by the acceptance first, then new work
     const unsigned idle = __ballot_sync(FULL, !act);
-    if (idle != 0u && (qn < qe || more)) {
-      const int need = __popc(idle);
+    if (idle != 0u && (nret > 0 || qn < qe || more)) {
+      const int n_idle = __popc(idle);
+      const int from_r = n_idle < nret ? n_idle : nret;
+      const int need = n_idle - from_r;
       const long long avail = qe - qn;
       long long b0 = 0, b1 = 0;
-      if (avail < need && more) {
+      if (need > 0 && avail < need && more) {
         unsigned long long b = 0;
         if (lane == 0) b = atomicAdd(a.counter, static_cast<unsigned long long>(a.chunk));
         b = __shfl_sync(FULL, b, 0);
@@ -1339,19 +1370,32 @@ __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(con
           b1 = b0 + a.chunk < total ? b0 + a.chunk : total;
         }
       }
-      const int rank = __popc(idle & ((1u << lane) - 1u));
+      const int rank_all = __popc(idle & ((1u << lane) - 1u));
       if (!act) {
-        long long cand = -1;
-        if (rank < avail) cand = qn + rank;
-        else if (rank - avail < b1 - b0) cand = b0 + (rank - avail);
-        if (cand >= 0) {
-          item = cand;
+        if (rank_all < from_r) {  // one more FP32 step from the parked iterate
+          const int pos = nret - 1 - rank_all;
+          item = s_ritem[wib][pos];
+          const uint32_t meta = s_rmeta[wib][pos];
+          it = static_cast<int>(meta & 0xffu);
+          fl = ((meta >> 8) & ~(FL_INT_FP32CONV | FL_INT_NEEDS_F64)) | FL_INT_FORCE;
           act = true;
-          it = 0;
-          fl = 0;
-          a.src.template load<D>(item, q);
+#pragma unroll
+          for (int j = 0; j < D; ++j) q[j] = a.q_out[j * a.ld_out + item];
+        } else {
+          const int rank = rank_all - from_r;
+          long long cand = -1;
+          if (rank < avail) cand = qn + rank;
+          else if (rank - avail < b1 - b0) cand = b0 + (rank - avail);
+          if (cand >= 0) {
+            item = cand;
+            act = true;
+            it = 0;
+            fl = 0;
+            a.src.template load<D>(item, q);
+          }
         }
       }
+      nret -= from_r;
       const long long used_old = need < avail ? need : avail;
       if (b1 > b0) {
         const long long rest = need - used_old;
@@ -1381,30 +1425,44 @@ __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(con
       pend += __popc(fin);
       __syncwarp();
     }
-    const bool drained = !__any_sync(FULL, act) && qn >= qe && !more;
+    const bool drained = !__any_sync(FULL, act) && qn >= qe && !more && nret == 0;
     // (4) FP64 acceptance in full warps (and, fused, the collision check of
     // the accepted outputs: ALU work that overlaps other warps' FP64 passes)
     if (pend >= 32 || (drained && pend > 0)) {
       const int take = pend < 32 ? pend : 32;
+      const bool room = nret + take <= RETRY_CAP;
+      bool retry = false;
+      long long it_item = 0;
+      uint32_t meta = 0;
       if (lane < take) {
         const int pos = pend - take + lane;
-        const uint32_t meta = s_meta[wib][pos];
-        const long long it_item = s_item[wib][pos];
-        accept_one<P, FORM>(a, it_item, static_cast<int>(meta & 0xffu), meta >> 8);
+        meta = s_meta[wib][pos];
+        it_item = s_item[wib][pos];
+        retry = accept_one<P, FORM>(a, it_item, static_cast<int>(meta & 0xffu), meta >> 8, room);
         if constexpr (CHK) {
-          float qc[D];
+          if (!retry) {
+            float qc[D];
 #pragma unroll
-          for (int j = 0; j < D; ++j) qc[j] = a.q_out[j * a.ld_out + it_item];
-          uint32_t tests = 0;
-          const bool h = check_one_f32<P>(a.chk->m, a.chk->st, s_pair, a.n_obs, s_box, a.n_box, a.tab, qc, tests);
-          a.hit[it_item] = h ? 1 : 0;
-          if (a.pairs) a.pairs[it_item] = tests;
+            for (int j = 0; j < D; ++j) qc[j] = a.q_out[j * a.ld_out + it_item];
+            uint32_t tests = 0;
+            const bool h = check_one_f32<P>(a.chk->m, a.chk->st, s_pair, a.n_obs, s_box, a.n_box, a.tab, qc, tests);
+            a.hit[it_item] = h ? 1 : 0;
+            if (a.pairs) a.pairs[it_item] = tests;
+          }
         }
       }
+      const unsigned rm = __ballot_sync(FULL, retry);
+      __syncwarp();
+      if (retry) {
+        const int rp = nret + __popc(rm & ((1u << lane) - 1u));
+        s_ritem[wib][rp] = it_item;
+        s_rmeta[wib][rp] = meta;
+      }
+      nret += __popc(rm);
       pend -= take;
       __syncwarp();
     }
-    if (drained && pend == 0) break;
+    if (drained && pend == 0 && nret == 0) break;
   }
 }
 

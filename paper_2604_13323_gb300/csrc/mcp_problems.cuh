@@ -159,4 +159,11 @@ struct ProbHumanoid36Hull : ProbHumanoid36 {
   __host__ __device__ static constexpr int ckind(int c) { return c == 3 ? K_HULL : ProbHumanoid36::ckind(c); }
 };
 
+// Classes whose FP32 projection also has a two-lanes-per-configuration
+// kernel (one lane per chain of a two-chain tree; the autotuner chooses).
+template <class P>
+__host__ __device__ constexpr bool has_pair_kernel() {
+  return std::is_same_v<P, ProbDual14Rel>;
+}
+
 }  // namespace mcp

@@ -87,9 +87,10 @@ def load_library(path: str = LIB_PATH):
         "mcp_project_vjp": ([_vp, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
         "mcp_path_length_grad": ([_vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, _vp],
                                  ctypes.c_int),
-        "mcp_autotune": ([_vp, P(ProjectParams), ctypes.c_int64, ctypes.c_int64, _vp, _ip, _ip, _ip, _ip, _vp],
+        "mcp_autotune": ([_vp, P(ProjectParams), ctypes.c_int64, ctypes.c_int64, _vp, _ip, _ip, _ip, _ip, _ip, _vp],
                          ctypes.c_int),
-        "mcp_set_tuning": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+        "mcp_set_tuning": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
+                           ctypes.c_int),
         "mcp_extend_batch": ([_vp, P(ProjectParams), P(ExtendParams), ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp,
                               ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
         "mcp_path_step": ([_vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _vp, _vp, ctypes.c_float,
@@ -350,16 +351,18 @@ class Projector:
     def autotune(self, q_sample, params, stream=None):
         """Times the persistent kernel's launch shapes on q_sample ([d, n] float32
         CUDA tensor) and keeps the fastest; returns (threads/block, blocks/SM,
-        chunk, fuse_check)."""
+        chunk, fuse_check, threads/configuration)."""
         d, n = q_sample.shape
-        t, b, c, f = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        t, b, c, f, k = (ctypes.c_int32() for _ in range(5))
         pp = self.params(params)
         self._check(self.lib.mcp_autotune(self.h, ctypes.byref(pp), n, n, _ptr(q_sample), ctypes.byref(t),
-                                          ctypes.byref(b), ctypes.byref(c), ctypes.byref(f), _stream(stream)))
-        return t.value, b.value, c.value, f.value
+                                          ctypes.byref(b), ctypes.byref(c), ctypes.byref(f), ctypes.byref(k),
+                                          _stream(stream)))
+        return t.value, b.value, c.value, f.value, k.value
 
-    def set_tuning(self, tpb, blocks_per_sm, chunk, fuse_check=0):
-        self._check(self.lib.mcp_set_tuning(self.h, int(tpb), int(blocks_per_sm), int(chunk), int(fuse_check)))
+    def set_tuning(self, tpb, blocks_per_sm, chunk, fuse_check=0, threads_per_config=1):
+        self._check(self.lib.mcp_set_tuning(self.h, int(tpb), int(blocks_per_sm), int(chunk), int(fuse_check),
+                                            int(threads_per_config)))
 
     def path_length_grad(self, Q, n_paths, n_way, length=None, grad=None, stream=None):
         import torch

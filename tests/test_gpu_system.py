@@ -30,8 +30,9 @@ def test_autotune_keeps_results(mcproj):
     P = mcproj.Projector(wl.robot, wl.constraints)
     q = dev(f32_exact(wl.q))
     before = [t.clone() for t in P.project(q, wl.params)]
-    tpb, bps, chunk, fuse = P.autotune(q, wl.params)
+    tpb, bps, chunk, fuse, tpc = P.autotune(q, wl.params)
     assert tpb in (64, 128, 256) and bps in (1, 2, 4, 8) and chunk in (16, 32, 64) and fuse in (0, 1)
+    assert tpc == 1  # the arm has one kernel shape per configuration
     after = P.project(q, wl.params)
     torch.cuda.synchronize()
     for x, y in zip(before, after):
