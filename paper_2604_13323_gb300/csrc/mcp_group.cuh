@@ -790,7 +790,7 @@ __device__ __forceinline__ bool grp_iter(const A &a, const GrpTables<P> &tb, con
     if (!(r2 <= FLT_MAX)) {
       fl |= FL_NONFINITE;
       done = true;
-    } else if (r2 < a.tol2) {
+    } else if (r2 < a.tol2 && !(fl & FL_INT_FORCE)) {
       fl |= FL_INT_FP32CONV;
       done = true;
     } else if (it >= a.cap) {
@@ -1089,6 +1089,7 @@ __device__ __forceinline__ bool grp_iter(const A &a, const GrpTables<P> &tb, con
   }
   if (go3) {
     ++it;
+    fl &= ~FL_INT_FORCE;
     if (!(s2 <= FLT_MAX)) {
       fl |= FL_NONFINITE;
       done = true;
@@ -1106,6 +1107,8 @@ __global__ void __launch_bounds__(W * 32) k_project_group(const __grid_constant_
   GrpState<P> *ws = reinterpret_cast<GrpState<P> *>(smem_raw + ((sizeof(GrpShared<P>) + 15) & ~size_t(15)));
   __shared__ long long s_item[W][40];  // parked configurations: < 32 + 8
   __shared__ uint32_t s_meta[W][40];
+  __shared__ long long s_ritem[W][RETRY_CAP];  // sent back to the FP32 loop by the acceptance
+  __shared__ uint32_t s_rmeta[W][RETRY_CAP];
   {
     static_assert(sizeof(GrpTables<P>) % 4 == 0 && sizeof(GroupPlan<P>) % 4 == 0, "word copies");
     const int *src = reinterpret_cast<const int *>(&a.t);
@@ -1128,15 +1131,19 @@ __global__ void __launch_bounds__(W * 32) k_project_group(const __grid_constant_
   int it = 0;
   uint32_t fl = 0;
   int pend = 0;
+  int nret = 0;  // warp-uniform count of configurations to retry in FP32
   const unsigned lead = 0x11111111u;  // lane 0 of every group
   while (true) {
-    // refill idle groups (decided by each group's lane 0, shared by the group)
+    // refill idle groups (decided by each group's lane 0, shared by the
+    // group): retries first, then new work
     const unsigned idle = __ballot_sync(FULL, !act) & lead;
-    if (idle != 0u && (qn < qe || more)) {
-      const int need = __popc(idle);
+    if (idle != 0u && (nret > 0 || qn < qe || more)) {
+      const int n_idle = __popc(idle);
+      const int from_r = n_idle < nret ? n_idle : nret;
+      const int need = n_idle - from_r;
       const long long avail = qe - qn;
       long long b0 = 0, b1 = 0;
-      if (avail < need && more) {
+      if (need > 0 && avail < need && more) {
         unsigned long long b = 0;
         if (lane == 0) b = atomicAdd(a.counter, static_cast<unsigned long long>(a.chunk));
         b = __shfl_sync(FULL, b, 0);
@@ -1147,19 +1154,31 @@ __global__ void __launch_bounds__(W * 32) k_project_group(const __grid_constant_
           b1 = b0 + a.chunk < a.total ? b0 + a.chunk : a.total;
         }
       }
-      const int rank = __popc(idle & ((1u << (grp * GG)) - 1u));
+      const int rank_all = __popc(idle & ((1u << (grp * GG)) - 1u));
       if (!act) {
-        long long cand = -1;
-        if (rank < avail) cand = qn + rank;
-        else if (rank - avail < b1 - b0) cand = b0 + (rank - avail);
-        if (cand >= 0) {
-          item = cand;
+        if (rank_all < from_r) {  // one more FP32 step from the parked iterate
+          const int pos = nret - 1 - rank_all;
+          item = s_ritem[wib][pos];
+          const uint32_t meta = s_rmeta[wib][pos];
+          it = static_cast<int>(meta & 0xffu);
+          fl = ((meta >> 8) & ~(FL_INT_FP32CONV | FL_INT_NEEDS_F64)) | FL_INT_FORCE;
           act = true;
-          it = 0;
-          fl = 0;
-          for (int j = g; j < D; j += GG) S.q[j] = a.src.q[j * a.src.ld + item];
+          for (int j = g; j < D; j += GG) S.q[j] = a.q_out[j * a.ld_out + item];
+        } else {
+          const int rank = rank_all - from_r;
+          long long cand = -1;
+          if (rank < avail) cand = qn + rank;
+          else if (rank - avail < b1 - b0) cand = b0 + (rank - avail);
+          if (cand >= 0) {
+            item = cand;
+            act = true;
+            it = 0;
+            fl = 0;
+            for (int j = g; j < D; j += GG) S.q[j] = a.src.q[j * a.src.ld + item];
+          }
         }
       }
+      nret -= from_r;
       const long long used_old = need < avail ? need : avail;
       if (b1 > b0) {
         const long long rest = need - used_old;
@@ -1186,19 +1205,33 @@ __global__ void __launch_bounds__(W * 32) k_project_group(const __grid_constant_
       pend += __popc(fin);
       __syncwarp();
     }
-    const bool drained = !__any_sync(FULL, act) && qn >= qe && !more;
-    // FP64 acceptance, one configuration per lane, 32 at a time
+    const bool drained = !__any_sync(FULL, act) && qn >= qe && !more && nret == 0;
+    // FP64 acceptance, one configuration per lane, 32 at a time; a failed
+    // acceptance with steps left goes back to the FP32 loop
     if (pend >= 32 || (drained && pend > 0)) {
       const int take = pend < 32 ? pend : 32;
+      const bool room = nret + take <= RETRY_CAP;
+      bool retry = false;
+      long long it_item = 0;
+      uint32_t meta = 0;
       if (lane < take) {
         const int pos = pend - take + lane;
-        const uint32_t meta = s_meta[wib][pos];
-        accept_one<P, FORM_STACKED>(a, s_item[wib][pos], static_cast<int>(meta & 0xffu), meta >> 8);
+        meta = s_meta[wib][pos];
+        it_item = s_item[wib][pos];
+        retry = accept_one<P, FORM_STACKED>(a, it_item, static_cast<int>(meta & 0xffu), meta >> 8, room);
       }
+      const unsigned rm = __ballot_sync(FULL, retry);
+      __syncwarp();
+      if (retry) {
+        const int rp = nret + __popc(rm & ((1u << lane) - 1u));
+        s_ritem[wib][rp] = it_item;
+        s_rmeta[wib][rp] = meta;
+      }
+      nret += __popc(rm);
       pend -= take;
       __syncwarp();
     }
-    if (drained && pend == 0) break;
+    if (drained && pend == 0 && nret == 0) break;
   }
 }
 
