@@ -63,10 +63,13 @@ struct ExtArgs {
 // FP64 acceptance of one FP32 iterate held in registers (accept_one without
 // the global outputs).  Out of line: it runs once per projection, and kept
 // apart from the Newton loop it does not dilute the loop's instruction stream.
+// Returns true (nothing changed) when the FP32 test was too optimistic and
+// steps remain: the caller takes one more FP32 step and asks again.
 template <class P, class A>
-__device__ __noinline__ void accept_regs(const A &a, float (&q)[P::D], int &it, uint32_t &fl) {
+__device__ __noinline__ bool accept_regs(const A &a, float (&q)[P::D], int &it, uint32_t &fl) {
   constexpr int D = P::D;
   double r2 = residual2_f64<P>(OpsF64Split{a.tab}, *a.m64, q);
+  if ((fl & FL_INT_FP32CONV) && !(r2 < a.tol2_64) && r2 <= DBL_MAX && it < a.cap) return true;
   if (fl & (FL_INT_FP32CONV | FL_INT_NEEDS_F64)) {
     const bool was_conv = (fl & FL_INT_FP32CONV) != 0;
     fl &= ~(FL_INT_FP32CONV | FL_INT_NEEDS_F64);
@@ -85,6 +88,7 @@ __device__ __noinline__ void accept_regs(const A &a, float (&q)[P::D], int &it, 
       for (int j = 0; j < D; ++j) q[j] = qf[j];
     }
   }
+  return false;
 }
 
 // Projects the point of every active lane (warp-convergent: all lanes call
@@ -95,10 +99,22 @@ __device__ __noinline__ void project_lanes(const A &a, float (&q)[P::D], bool ac
   it = 0;
   fl = 0;
   bool done = !active;
-  while (__any_sync(FULL, !done)) {
-    if (!done) done = newton_iter_f32<P>(a, q, it, fl);
+  bool final_ = !active;  // accepted (or inactive)
+  while (true) {
+    while (__any_sync(FULL, !done)) {
+      if (!done) done = newton_iter_f32<P>(a, q, it, fl);
+    }
+    bool again = false;
+    if (!final_) {
+      again = accept_regs<P>(a, q, it, fl);
+      final_ = !again;
+    }
+    if (!__any_sync(FULL, again)) break;
+    if (again) {  // one more FP32 step before the next test
+      fl = (fl & ~(FL_INT_FP32CONV | FL_INT_NEEDS_F64)) | FL_INT_FORCE;
+      done = false;
+    }
   }
-  if (active) accept_regs<P>(a, q, it, fl);
 }
 
 // Collision verdict of one lane's configuration, out of line (called at three places).
