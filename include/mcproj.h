@@ -305,10 +305,9 @@ mcp_status mcp_path_step(mcp_ctx *ctx, int64_t n_paths, int32_t n_way, int64_t l
  * (tpb in {64, 128, 256}, blocks_per_sm in 1..8 with tpb * blocks_per_sm <=
  * 2048, chunk in 1..64, fuse_check 0 / 1, threads_per_config 1 / 2), e.g. to
  * reproduce a tuned shape.  threads_per_config = 2 runs the two-chain classes
- * (the dual arm, Eq. 2) with one lane per chain; other classes ignore it; it
- * has no fused check (the check is a second launch).  Results of the two
- * kernels differ only by the rounding of the Gram sums.  MCP_ERR_ARG outside
- * those ranges. */
+ * (the dual arm, Eq. 2) with one lane per chain; other classes ignore it.
+ * Results of the two kernels differ only by the rounding of the Gram sums.
+ * MCP_ERR_ARG outside those ranges. */
 mcp_status mcp_set_tuning(mcp_ctx *ctx, int32_t tpb, int32_t blocks_per_sm, int32_t chunk, int32_t fuse_check,
                           int32_t threads_per_config);
 

@@ -14,14 +14,17 @@ cudaError_t launch_project<ProbDual14Rel>(const HostModel &hm, const ProjCall &c
   if (c.precision != 0 || c.tune.tpc != 2 || c.outer || c.total <= 0) return launch_project_impl<P>(hm, c, launches);
   cudaError_t err = cudaMemsetAsync(c.counter, 0, sizeof(unsigned long long), c.stream);
   if (err != cudaSuccess) return err;
-  if (c.segments)
-    err = launch_pair<P>(hm, c, SegSrc<float>{static_cast<const float *>(c.start), static_cast<const float *>(c.delta),
-                                              c.ld_seg, c.seg_off, c.n_seg});
-  else
-    err = launch_pair<P>(hm, c, BatchSrc<float>{static_cast<const float *>(c.q_in), c.ld_in});
+  if (c.segments) {
+    const SegSrc<float> src{static_cast<const float *>(c.start), static_cast<const float *>(c.delta), c.ld_seg,
+                            c.seg_off, c.n_seg};
+    err = c.fused_check ? launch_pair<P, SegSrc<float>, true>(hm, c, src)
+                        : launch_pair<P, SegSrc<float>, false>(hm, c, src);
+  } else {
+    const BatchSrc<float> src{static_cast<const float *>(c.q_in), c.ld_in};
+    err = c.fused_check ? launch_pair<P, BatchSrc<float>, true>(hm, c, src)
+                        : launch_pair<P, BatchSrc<float>, false>(hm, c, src);
+  }
   *launches += 1;
-  // the pair kernel has no fused check: the check of its outputs is a second launch
-  if (err == cudaSuccess && c.fused_check) err = check_outputs<P>(hm, c, launches);
   return err;
 }
 

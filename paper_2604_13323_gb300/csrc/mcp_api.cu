@@ -1457,7 +1457,6 @@ mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sam
   // warm-up burst first): single calls sit near the resolution of the events.
   const int n_fuse = ctx->obs_loaded ? 2 : 1;
   // threads per configuration: 1, and 2 where the class has a pair kernel
-  // (which has no fused check: its two-launch time is taken once)
   const int n_tpc = registry()[ctx->prob_class].pair ? 2 : 1;
   auto time_candidate = [&](float &med) -> cudaError_t {
     constexpr int BURSTS = 6, CALLS = 4;
@@ -1502,7 +1501,7 @@ mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sam
       for (int c = 0; c < 3 && err == cudaSuccess; ++c)
         for (int f = 0; f < n_fuse && err == cudaSuccess; ++f)
           for (int t = 1; t <= n_tpc && err == cudaSuccess; ++t) {
-            if (tpbs[a] * bpss[b] > 2048 || (t == 2 && f == 1)) continue;
+            if (tpbs[a] * bpss[b] > 2048) continue;
             ctx->tune = Tuning{tpbs[a], bpss[b], chunks[c], f == 1, t};
             float med = 0.f;
             err = time_candidate(med);

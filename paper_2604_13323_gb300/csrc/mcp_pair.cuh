@@ -217,7 +217,7 @@ __host__ __device__ constexpr int pair_min_blocks() {
 // The persistent loop of k_project_f32 with pairs as slots (16 per warp):
 // warp-local work queue, refill of idle pairs, parked configurations accepted
 // in FP64 32 at a time.
-template <class P, class Src, int TPB>
+template <class P, class Src, int TPB, bool CHK>
 __global__ void __launch_bounds__(TPB, (pair_min_blocks<TPB>())) k_project_pair(const __grid_constant__ ProjArgs<P, Src> a) {
   using C = typename PairOf<P>::C;
   constexpr int H = C::D;
@@ -227,6 +227,13 @@ __global__ void __launch_bounds__(TPB, (pair_min_blocks<TPB>())) k_project_pair(
   __shared__ uint32_t s_meta[W][64];
   __shared__ long long s_ritem[W][RETRY_CAP];
   __shared__ uint32_t s_rmeta[W][RETRY_CAP];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4 *s_pair = reinterpret_cast<float4 *>(smem_raw);
+  const float *s_box = nullptr;
+  if constexpr (CHK) {  // obstacles of the fused check, staged once per block
+    s_box = stage_obstacles(a.obs, a.n_obs, a.box, a.n_box, s_pair);
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int h = lane & 1;
@@ -333,6 +340,17 @@ __global__ void __launch_bounds__(TPB, (pair_min_blocks<TPB>())) k_project_pair(
         meta = s_meta[wib][pos];
         it_item = s_item[wib][pos];
         retry = accept_one<P, FORM_STACKED>(a, it_item, static_cast<int>(meta & 0xffu), meta >> 8, room);
+        if constexpr (CHK) {  // the collision check of the accepted output, one configuration per lane
+          if (!retry) {
+            float qc[P::D];
+#pragma unroll
+            for (int j = 0; j < P::D; ++j) qc[j] = a.q_out[j * a.ld_out + it_item];
+            uint32_t tests = 0;
+            const bool hit = check_one_f32<P>(a.chk->m, a.chk->st, s_pair, a.n_obs, s_box, a.n_box, a.tab, qc, tests);
+            a.hit[it_item] = hit ? 1 : 0;
+            if (a.pairs) a.pairs[it_item] = tests;
+          }
+        }
       }
       const unsigned rm = __ballot_sync(FULL, retry);
       __syncwarp();
@@ -349,7 +367,7 @@ __global__ void __launch_bounds__(TPB, (pair_min_blocks<TPB>())) k_project_pair(
   }
 }
 
-template <class P, class Src, int TPB>
+template <class P, class Src, int TPB, bool CHK>
 cudaError_t launch_pair_tpb(const HostModel &hm, const ProjCall &c, const Src &src) {
   ProjArgs<P, Src> a{};
   a.m = hm.m32;
@@ -372,21 +390,29 @@ cudaError_t launch_pair_tpb(const HostModel &hm, const ProjCall &c, const Src &s
   a.tol2_64 = c.tol * c.tol;
   a.lambda64 = c.lambda;
   a.alpha = static_cast<float>(c.alpha);
+  a.chk = hm.d_chk;
+  a.obs = reinterpret_cast<const float *>(hm.d_obs32);
+  a.box = hm.d_box32;
+  a.n_obs = CHK ? hm.n_obs : 0;
+  a.n_box = CHK ? hm.n_box : 0;
+  a.hit = c.hit;
+  a.pairs = c.pairs;
+  const size_t smem = CHK ? obs_smem_bytes(hm.n_obs, hm.n_box) : 0;
   const long long warps_needed = (2 * c.total + 31) / 32;
   long long blocks = static_cast<long long>(hm.sm_count) * c.tune.blocks_per_sm;
   const long long max_useful = (warps_needed + (TPB / 32) - 1) / (TPB / 32);
   if (blocks > max_useful) blocks = max_useful;
   if (blocks < 1) blocks = 1;
-  k_project_pair<P, Src, TPB><<<static_cast<unsigned>(blocks), TPB, 0, c.stream>>>(a);
+  k_project_pair<P, Src, TPB, CHK><<<static_cast<unsigned>(blocks), TPB, smem, c.stream>>>(a);
   return cudaGetLastError();
 }
 
-template <class P, class Src>
+template <class P, class Src, bool CHK>
 cudaError_t launch_pair(const HostModel &hm, const ProjCall &c, const Src &src) {
   switch (c.tune.tpb) {
-    case 64: return launch_pair_tpb<P, Src, 64>(hm, c, src);
-    case 256: return launch_pair_tpb<P, Src, 256>(hm, c, src);
-    default: return launch_pair_tpb<P, Src, 128>(hm, c, src);
+    case 64: return launch_pair_tpb<P, Src, 64, CHK>(hm, c, src);
+    case 256: return launch_pair_tpb<P, Src, 256, CHK>(hm, c, src);
+    default: return launch_pair_tpb<P, Src, 128, CHK>(hm, c, src);
   }
 }
 

@@ -10,7 +10,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import oracle as orc  # noqa: E402
 from paper_2604_13323_gb300 import workloads as W  # noqa: E402
-from tests.gpu_util import compare_projection, eligible_mask, f32_exact  # noqa: E402
+from tests.gpu_util import compare_collision, compare_projection, eligible_mask, f32_exact  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -172,4 +172,28 @@ def test_autotune_times_both_kernels(mcproj, dual):
     q = torch.tensor(f32_exact(dual.q), dtype=torch.float32, device="cuda")
     P = mcproj.Projector(dual.robot, dual.constraints)
     tpb, bps, chunk, fuse, tpc = P.autotune(q, dual.params)
-    assert tpc in (1, 2) and fuse in (0, 1) and not (tpc == 2 and fuse == 1)
+    assert tpc in (1, 2) and fuse in (0, 1)
+
+
+def test_pair_fused_check(mcproj):
+    """The collision check inside the pair kernel (one configuration per lane
+    after the acceptance) gives the verdicts and test counts of the check
+    kernel run on the same outputs, which match the oracle's verdicts."""
+    wl = W.dual_arm_workload(total=10, n_random=8192)
+    q0 = f32_exact(wl.q)
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
+    O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
+    q = torch.tensor(q0, dtype=torch.float32, device="cuda")
+    n = q.shape[1]
+    res = []
+    for fuse in (1, 0):
+        P.set_tuning(128, 4, 32, fuse, 2)
+        pairs = torch.zeros(n, dtype=torch.int32, device="cuda")
+        res.append((*P.project_check(q, wl.params, pairs=pairs), pairs))
+    torch.cuda.synchronize()
+    (out, fl, it, r, hit, pairs), (out2, fl2, it2, r2, hit2, pairs2) = res
+    for x, y in ((out, out2), (fl, fl2), (it, it2), (r, r2), (hit, hit2), (pairs, pairs2)):
+        assert torch.equal(x, y)
+    h_o, m_o = O.check(out.double().cpu().numpy())
+    st = compare_collision(hit.cpu().numpy(), h_o, m_o)
+    assert 0.0 < st["collide_frac"] < 1.0
