@@ -39,10 +39,7 @@ UNIT = "projections/s"
 # dominant kernel, from one ncu capture of the kernel built from this source
 # (profiles/ gives the command and the full capture summary).  Keyed by
 # (workload, kernel); an entry is removed whenever its kernel changes.
-MEASURED_TRAFFIC = {
-    ("arm7_axis_65536", "k_project_f32+check"): 2004480,      # read 2.00 MB, write 0
-    ("dual14_rel_extend_16384", "k_extend"): 3571456 + 1493504,
-}
+MEASURED_TRAFFIC = {}
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 
 
@@ -575,15 +572,16 @@ def run_ours(args):
             ach64 = fp64f / (mp * 1e-3) / 1e12
             # both pipes: the time the FP32 and FP64 work need at their peaks bounds the kernel
             t_min = max(fp32 / (peak32 * 1e12), fp64f / (peak64 * 1e12))
+            kshort = ("k_project_group" if args.workload.startswith("humanoid") and not wl.params.cyclic else
+                      "k_project_warp" if args.workload.startswith("humanoid") else
+                      "k_project_pair" if tuning and tuning.get("threads_per_config") == 2 else "k_project_f32")
             roof = {"bound": "alu", "achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
-                    "traffic": None,
-                    "kernel": ("k_project_group (four lanes per configuration: FP32 steps, FP64 acceptance)"
-                               if args.workload.startswith("humanoid") and not wl.params.cyclic else
-                               "k_project_warp (warp per configuration, cyclic sweeps)"
-                               if args.workload.startswith("humanoid") else
-                               "k_project_pair (persistent, one lane per arm: FP32 steps + FP64 acceptance)"
-                               if tuning and tuning.get("threads_per_config") == 2 else
-                               "k_project_f32 (persistent, FP32 steps + FP64 acceptance)"),
+                    "traffic": MEASURED_TRAFFIC.get((wname, kshort)),
+                    "kernel": kshort + {
+                        "k_project_group": " (four lanes per configuration: FP32 steps, FP64 acceptance)",
+                        "k_project_warp": " (warp per configuration, cyclic sweeps)",
+                        "k_project_pair": " (persistent, one lane per arm: FP32 steps + FP64 acceptance)",
+                        "k_project_f32": " (persistent, FP32 steps + FP64 acceptance)"}[kshort],
                     "peak_source": peak_src,
                     "fp64_achieved": ach64, "fp64_peak": peak64, "fp64_frac": ach64 / peak64,
                     "mixed_bound_frac": t_min / (mp * 1e-3),
