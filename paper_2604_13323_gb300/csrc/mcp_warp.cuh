@@ -416,7 +416,7 @@ __device__ __forceinline__ bool warp_iter(const A &a, const WarpTables<P> &tb, W
       fl |= FL_NONFINITE;
       return true;
     }
-    if (r2 < a.tol2) {
+    if (r2 < a.tol2 && !(fl & FL_INT_FORCE)) {
       fl |= FL_INT_FP32CONV;
       return true;
     }
@@ -625,6 +625,7 @@ __device__ __forceinline__ bool warp_iter(const A &a, const WarpTables<P> &tb, W
     if (j < D) S.q[j] -= dq[s];
   }
   ++it;
+  fl &= ~FL_INT_FORCE;
   __syncwarp();
   if (!(s2 <= FLT_MAX)) {
     fl |= FL_NONFINITE;
@@ -671,6 +672,7 @@ __device__ __forceinline__ bool warp_sweep(const A &a, const WarpTables<P> &tb, 
     return true;
   }
   ++it;
+  fl &= ~FL_INT_FORCE;
   if (!(s2 <= FLT_MAX)) {
     fl |= FL_NONFINITE;
     return true;
@@ -688,6 +690,8 @@ __global__ void __launch_bounds__(W * 32, 512 / (W * 32)) k_project_warp(const _
   __shared__ WarpState<P> ws[W];
   __shared__ long long s_item[W][32];
   __shared__ uint32_t s_meta[W][32];
+  __shared__ long long s_ritem[W][RETRY_CAP];  // sent back to the FP32 loop by the acceptance
+  __shared__ uint32_t s_rmeta[W][RETRY_CAP];
   {
     const int *src = reinterpret_cast<const int *>(&a.t);
     int *dst = reinterpret_cast<int *>(&tb);
@@ -700,9 +704,11 @@ __global__ void __launch_bounds__(W * 32, 512 / (W * 32)) k_project_warp(const _
   long long qn = 0, qe = 0;
   bool more = true;
   int pend = 0;
+  int nret = 0;  // configurations to retry in FP32 after a failed acceptance
   while (true) {
-    // claim the next configuration (chunks of `chunk` per atomic)
-    if (qn >= qe && more) {
+    // a configuration to retry first, else the next one (chunks of `chunk` per atomic)
+    const bool from_retry = nret > 0;
+    if (!from_retry && qn >= qe && more) {
       unsigned long long b = 0;
       if (lane == 0) b = atomicAdd(a.counter, static_cast<unsigned long long>(a.chunk));
       b = __shfl_sync(FULL, b, 0);
@@ -713,17 +719,31 @@ __global__ void __launch_bounds__(W * 32, 512 / (W * 32)) k_project_warp(const _
         qe = qn + a.chunk < a.total ? qn + a.chunk : a.total;
       }
     }
-    const bool have = qn < qe;
+    const bool have = from_retry || qn < qe;
     if (have) {
-      const long long item = qn++;
-#pragma unroll
-      for (int s = 0; s < SL; ++s) {
-        const int j = lane + 32 * s;
-        if (j < D) S.q[j] = a.src.q[j * a.src.ld + item];
-      }
-      __syncwarp();
+      long long item;
       int it = 0;
       uint32_t fl = 0;
+      if (from_retry) {  // one more FP32 step from the parked iterate
+        --nret;
+        item = s_ritem[wib][nret];
+        const uint32_t meta = s_rmeta[wib][nret];
+        it = static_cast<int>(meta & 0xffu);
+        fl = ((meta >> 8) & ~(FL_INT_FP32CONV | FL_INT_NEEDS_F64)) | FL_INT_FORCE;
+#pragma unroll
+        for (int s = 0; s < SL; ++s) {
+          const int j = lane + 32 * s;
+          if (j < D) S.q[j] = a.q_out[j * a.ld_out + item];
+        }
+      } else {
+        item = qn++;
+#pragma unroll
+        for (int s = 0; s < SL; ++s) {
+          const int j = lane + 32 * s;
+          if (j < D) S.q[j] = a.src.q[j * a.src.ld + item];
+        }
+      }
+      __syncwarp();
       if constexpr (CYC) {
         while (!warp_sweep<P>(a, tb, S, it, fl)) {
         }
@@ -743,17 +763,30 @@ __global__ void __launch_bounds__(W * 32, 512 / (W * 32)) k_project_warp(const _
       ++pend;
       __syncwarp();
     }
-    const bool drained = !have && !more;
+    const bool drained = !have && !more;  // (no retry pending either)
     if (pend == 32 || (drained && pend > 0)) {
+      const bool room = nret + pend <= RETRY_CAP;
+      bool retry = false;
+      long long it_item = 0;
+      uint32_t meta = 0;
       if (lane < pend) {
-        const uint32_t meta = s_meta[wib][lane];
-        accept_one<P, CYC ? FORM_CYCLIC : FORM_STACKED>(a, s_item[wib][lane], static_cast<int>(meta & 0xffu),
-                                                        meta >> 8);
+        meta = s_meta[wib][lane];
+        it_item = s_item[wib][lane];
+        retry = accept_one<P, CYC ? FORM_CYCLIC : FORM_STACKED>(a, it_item, static_cast<int>(meta & 0xffu),
+                                                                meta >> 8, room);
       }
+      const unsigned rm = __ballot_sync(FULL, retry);
+      __syncwarp();
+      if (retry) {
+        const int rp = nret + __popc(rm & ((1u << lane) - 1u));
+        s_ritem[wib][rp] = it_item;
+        s_rmeta[wib][rp] = meta;
+      }
+      nret += __popc(rm);
       pend = 0;
       __syncwarp();
     }
-    if (drained) break;
+    if (drained && nret == 0) break;
   }
 }
 
