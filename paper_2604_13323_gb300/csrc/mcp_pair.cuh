@@ -209,9 +209,10 @@ __device__ __forceinline__ bool pair_iter_f32(const A &a, int h, unsigned pm, fl
   return false;
 }
 
+constexpr int PAIR_REGS = 128;  // 4 blocks of 128 threads per SM; the spills sit in the FP64 paths
 template <int TPB>
 __host__ __device__ constexpr int pair_min_blocks() {
-  return 65536 / (TPB * 128) > 0 ? 65536 / (TPB * 128) : 1;
+  return 65536 / (TPB * PAIR_REGS) > 0 ? 65536 / (TPB * PAIR_REGS) : 1;
 }
 
 // The persistent loop of k_project_f32 with pairs as slots (16 per warp):

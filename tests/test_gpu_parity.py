@@ -230,6 +230,10 @@ def test_dual_segments_fp32_parity(mcproj):
     el, ora = eligible_mask(O, pts, wl.params)
     st = compare_projection(gpu, ora, wl.params.tol, oracle=O, eligible=el, min_eligible=0.5, sample_resid=4096)
     assert st["n"] == seg.total and st["conv_gpu"] > 0.99
+    # no pivot falls below the re-solve threshold on this workload, and a
+    # failed FP64 acceptance continues in FP32: no FP64 Newton step is taken
+    # (94 points used to finish with FP64 steps)
+    assert ((gpu[1] & mcproj.F_FP64_RESOLVE) != 0).sum() == 0
 
 
 def test_dual_check_fp32(mcproj):
