@@ -219,3 +219,34 @@ def test_arm_full_batch_in_the_benchmark_configuration(mcproj):
     assert st["conv_gpu"] > 0.99
     h_o, m_o = O.check(gpu[0])
     compare_collision(hit.cpu().numpy(), h_o, m_o)
+
+
+def test_dual_segments_in_the_benchmark_configuration(mcproj):
+    """The full uneven-segment dual-arm workload (262,240 points) as the
+    benchmark runs it: segment starts projected on the device, the launch
+    shape and threads per configuration autotuned on the first 65,536
+    materialised points, one persistent segment launch, then the collision
+    check; against the oracle on the same FP32 points."""
+    from tests.gpu_util import compare_collision, compare_projection, eligible_mask
+    wl = W.dual_arm_workload()
+    ex = wl.extra
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
+    O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
+    starts = P.project(dev(ex["raw_start"]), wl.params)[0]
+    delta = dev(ex["raw_dir"] * ex["step"])
+    length = dev(ex["lengths"], torch.int32)
+    s, d = starts.cpu(), delta.cpu()
+    t = torch.cat([torch.arange(int(ln), dtype=torch.float32) for ln in ex["lengths"]])
+    sid = torch.repeat_interleave(torch.arange(len(ex["lengths"])), torch.tensor(ex["lengths"], dtype=torch.long))
+    pts = torch.addcmul(s[:, sid], t[None, :], d[:, sid])
+    tpb, bps, chunk, fuse, tpc = P.autotune(pts[:, :65536].contiguous().cuda(), wl.params)
+    out, fl, it, r = P.project_segments(starts, delta, length, wl.params)
+    hit = P.check(out)
+    torch.cuda.synchronize()
+    gpu = (out.double().cpu().numpy(), fl.cpu().numpy(), it.cpu().numpy().astype(np.int32), r.cpu().numpy())
+    q0 = pts.double().numpy()
+    el, ora = eligible_mask(O, q0, wl.params)
+    st = compare_projection(gpu, ora, wl.params.tol, oracle=O, eligible=el, min_eligible=0.5, sample_resid=4096)
+    assert st["n"] == 262240 and st["conv_gpu"] > 0.99, (st, tpc)
+    h_o, m_o = O.check(gpu[0])
+    compare_collision(hit.cpu().numpy(), h_o, m_o)
