@@ -251,7 +251,11 @@ __global__ void k_resolve(const __grid_constant__ ResolveIn in, ResolveOut *out)
 
 // Obstacle preparation (one block): centroid of the obstacle centres (FP64),
 // then per obstacle sphere the FP32 records of the expanded overlap test in
-// the shifted frame: (-2c, |c|^2 - r^2), (-2r, 0, 0, 0); boxes shifted.
+// the shifted frame: (-2c, |c|^2 - r^2), (-2r, 0, 0, 0); after them, one
+// record of the same form per chunk of OBS_CHUNK consecutive obstacles: a
+// sphere around the chunk (centre the mean of its centres, radius the largest
+// |c_o - c| + r_o plus 1e-4 m, which keeps the FP32 test of the chunk
+// conservative); boxes shifted.
 __global__ void k_prep_obstacles(const double *obs, int n_obs, const double *box, int n_box, float *obs32,
                                  float *box32, double *origin) {
   __shared__ double part[3][256];
@@ -294,6 +298,32 @@ __global__ void k_prep_obstacles(const double *obs, int n_obs, const double *box
     obs32[8 * o + 5] = 0.f;
     obs32[8 * o + 6] = 0.f;
     obs32[8 * o + 7] = 0.f;
+  }
+  for (int k = t; k < obs_chunks(n_obs); k += blockDim.x) {
+    const int o0 = k * OBS_CHUNK, o1 = o0 + OBS_CHUNK < n_obs ? o0 + OBS_CHUNK : n_obs;
+    double mx = 0.0, my = 0.0, mz = 0.0;
+    for (int o = o0; o < o1; ++o) {
+      mx += obs[4 * o] - ox;
+      my += obs[4 * o + 1] - oy;
+      mz += obs[4 * o + 2] - oz;
+    }
+    mx /= (o1 - o0);
+    my /= (o1 - o0);
+    mz /= (o1 - o0);
+    double rad = 0.0;
+    for (int o = o0; o < o1; ++o) {
+      const double dx = obs[4 * o] - ox - mx, dy = obs[4 * o + 1] - oy - my, dz = obs[4 * o + 2] - oz - mz;
+      const double e = sqrt(dx * dx + dy * dy + dz * dz) + obs[4 * o + 3];
+      rad = e > rad ? e : rad;
+    }
+    rad += 1e-4;
+    float *rec = obs32 + 8 * (n_obs + k);
+    rec[0] = static_cast<float>(-2.0 * mx);
+    rec[1] = static_cast<float>(-2.0 * my);
+    rec[2] = static_cast<float>(-2.0 * mz);
+    rec[3] = static_cast<float>(mx * mx + my * my + mz * mz - rad * rad);
+    rec[4] = static_cast<float>(-2.0 * rad);
+    rec[5] = rec[6] = rec[7] = 0.f;
   }
   for (int b = t; b < n_box; b += blockDim.x) {
     box32[6 * b + 0] = static_cast<float>(box[6 * b + 0] - ox);
@@ -926,13 +956,41 @@ mcp_status mcp_load_obstacles(mcp_ctx *ctx, const double *spheres, int32_t n_sph
   ctx->obs_loaded = false;
   const size_t n_o = static_cast<size_t>(n_spheres > 0 ? n_spheres : 1);
   const size_t n_b = static_cast<size_t>(n_aabbs > 0 ? n_aabbs : 1);
-  MCP_CUDA(cudaMalloc(&ctx->d_obs32, n_o * 2 * sizeof(float4)), "cudaMalloc obstacles");
+  // spatial order (Morton code of the centres), so that the chunks of
+  // consecutive obstacles the check tests first are compact (scenes of more
+  // than 32 obstacles; smaller ones keep the caller's order); the verdicts do
+  // not depend on the order
+  std::vector<double> sorted(spheres ? spheres : nullptr, spheres ? spheres + 4 * static_cast<size_t>(n_spheres) : nullptr);
+  if (n_spheres > 32) {
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) lo[a] = hi[a] = spheres[a];
+    for (int o = 1; o < n_spheres; ++o)
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = std::min(lo[a], spheres[4 * o + a]);
+        hi[a] = std::max(hi[a], spheres[4 * o + a]);
+      }
+    std::vector<std::pair<uint32_t, int>> key(static_cast<size_t>(n_spheres));
+    for (int o = 0; o < n_spheres; ++o) {
+      uint32_t code = 0;
+      for (int a = 0; a < 3; ++a) {
+        const double u = hi[a] > lo[a] ? (spheres[4 * o + a] - lo[a]) / (hi[a] - lo[a]) : 0.0;
+        const uint32_t v = static_cast<uint32_t>(std::isfinite(u) ? std::min(std::max(u, 0.0), 1.0) * 1023.0 : 0.0);
+        for (int b = 0; b < 10; ++b) code |= ((v >> b) & 1u) << (3 * b + a);
+      }
+      key[static_cast<size_t>(o)] = {code, o};
+    }
+    std::stable_sort(key.begin(), key.end(), [](const auto &x, const auto &y) { return x.first < y.first; });
+    for (int o = 0; o < n_spheres; ++o)
+      for (int e = 0; e < 4; ++e) sorted[4 * static_cast<size_t>(o) + e] = spheres[4 * key[static_cast<size_t>(o)].second + e];
+  }
+  const size_t n_rec = n_o + static_cast<size_t>(obs_chunks(n_spheres));
+  MCP_CUDA(cudaMalloc(&ctx->d_obs32, n_rec * 2 * sizeof(float4)), "cudaMalloc obstacles");
   MCP_CUDA(cudaMalloc(&ctx->d_obs64, n_o * 4 * sizeof(double)), "cudaMalloc obstacles");
   MCP_CUDA(cudaMalloc(&ctx->d_box32, n_b * 6 * sizeof(float)), "cudaMalloc boxes");
   MCP_CUDA(cudaMalloc(&ctx->d_box64, n_b * 6 * sizeof(double)), "cudaMalloc boxes");
   if (!ctx->d_origin) MCP_CUDA(cudaMalloc(&ctx->d_origin, 3 * sizeof(double)), "cudaMalloc origin");
   if (n_spheres)
-    MCP_CUDA(cudaMemcpy(ctx->d_obs64, spheres, n_spheres * 4 * sizeof(double), cudaMemcpyHostToDevice), "copy");
+    MCP_CUDA(cudaMemcpy(ctx->d_obs64, sorted.data(), n_spheres * 4 * sizeof(double), cudaMemcpyHostToDevice), "copy");
   if (n_aabbs)
     MCP_CUDA(cudaMemcpy(ctx->d_box64, aabbs, n_aabbs * 6 * sizeof(double), cudaMemcpyHostToDevice), "copy");
   k_prep_obstacles<<<1, 256>>>(ctx->d_obs64, n_spheres, ctx->d_box64, n_aabbs, reinterpret_cast<float *>(ctx->d_obs32),

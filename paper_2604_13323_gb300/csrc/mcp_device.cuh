@@ -23,6 +23,10 @@ constexpr int MAXJ = 40;
 constexpr int MAXF = 8;
 constexpr int MAXC = 8;
 constexpr int MAXK = 24;
+// The collision check's broad phase first tests a bounding sphere of each
+// chunk of OBS_CHUNK consecutive obstacles (stored in spatial order).
+constexpr int OBS_CHUNK = 16;
+__host__ __device__ constexpr int obs_chunks(int n_obs) { return (n_obs + OBS_CHUNK - 1) / OBS_CHUNK; }
 
 enum : int { REV = 0, PRIS = 1 };
 enum : int {

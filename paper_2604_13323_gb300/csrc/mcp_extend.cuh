@@ -121,8 +121,8 @@ __device__ __noinline__ void project_lanes(const A &a, float (&q)[P::D], bool ac
 template <class P>
 __device__ __noinline__ bool collides_lane(const CheckData *chk, const float4 *s_pair, int n_obs, const float *s_box,
                                            int n_box, const double2 *tab, const float (&q)[P::D]) {
-  uint32_t t = 0;
-  return check_one_f32<P>(chk->m, chk->st, s_pair, n_obs, s_box, n_box, tab, q, t);
+  uint32_t t = 0;  // the flat broad phase: this kernel is bound by instruction fetch
+  return check_one_f32<P, false>(chk->m, chk->st, s_pair, n_obs, s_box, n_box, tab, q, t);
 }
 
 template <int D>

@@ -1075,8 +1075,12 @@ struct Rot9 {
 // with g = -2 c, gw = |c|^2 - r^2, g2 = -2 r (the expanded overlap test
 // below).  An odd count is padded with a record that never overlaps.
 __host__ __device__ constexpr int obs_pairs(int n_obs) { return (n_obs + 1) / 2; }
+// The records of the chunk spheres (one per OBS_CHUNK consecutive obstacles,
+// same form) follow the obstacles' pairs, also in pairs: one chunk pair per
+// 32 obstacles.
 __host__ __device__ constexpr size_t obs_smem_bytes(int n_obs, int n_box) {
-  return sizeof(float) * (12 * static_cast<size_t>(obs_pairs(n_obs)) + 6 * static_cast<size_t>(n_box));
+  return sizeof(float) * (12 * static_cast<size_t>(obs_pairs(n_obs)) + 12 * static_cast<size_t>(obs_pairs(obs_chunks(n_obs))) +
+                          6 * static_cast<size_t>(n_box));
 }
 // Obstacle o's five values from its pair.
 struct ObsRec {
@@ -1097,6 +1101,7 @@ __device__ __forceinline__ ObsRec obs_rec(const float4 *s_pair, int o) {
 // fmaf(x, gx, fmaf(y, gy, fmaf(z, gz, fmaf(r, g2, gw)))).  One out-of-line
 // copy serves every link of every kernel (inlined per link, the unrolled
 // broad phase made kernels with many links instruction-cache bound).
+template <bool CHUNKS>
 static __device__ __noinline__ bool link_hits_f32(const Rot9 Rr, V3<float> p, int s0, int e, const float *lb,
                                                   const SphereTable<float> &st, const float4 *s_pair, int n_obs,
                                                   const float *s_box, int n_box, uint32_t *tests_io) {
@@ -1115,25 +1120,50 @@ static __device__ __noinline__ bool link_hits_f32(const Rot9 Rr, V3<float> p, in
   const float kb = fmaf(bc.x, bc.x, fmaf(bc.y, bc.y, fmaf(bc.z, bc.z, -br * br)));
   const float2 bx2 = make_float2(bc.x, bc.x), by2 = make_float2(bc.y, bc.y), bz2 = make_float2(bc.z, bc.z),
                br2 = make_float2(br, br);
+  const float4 *s_chunk = s_pair + 3 * obs_pairs(n_obs);
+  // the bounding sphere's 4-FMA test against the records pr[pp] (two per pair)
+  auto pair_bits = [&](const float4 *pr, int pp) -> unsigned {
+    const float4 A = pr[3 * pp], B = pr[3 * pp + 1], C = pr[3 * pp + 2];
+    float2 v = __ffma2_rn(br2, make_float2(C.x, C.y), make_float2(B.z, B.w));
+    v = __ffma2_rn(bz2, make_float2(B.x, B.y), v);
+    v = __ffma2_rn(by2, make_float2(A.z, A.w), v);
+    v = __ffma2_rn(bx2, make_float2(A.x, A.y), v);
+    return (v.x < -kb ? 1u : 0u) | (v.y < -kb ? 2u : 0u);
+  };
   for (int o0 = 0; o0 < n_obs && !hit; o0 += 32) {
     const int cnt = min(32, n_obs - o0);
     const float4 *pr = s_pair + 3 * (o0 >> 1);
     unsigned cand = 0u;
-    auto pair_bits = [&](int pp) -> unsigned {
-      const float4 A = pr[3 * pp], B = pr[3 * pp + 1], C = pr[3 * pp + 2];
-      float2 v = __ffma2_rn(br2, make_float2(C.x, C.y), make_float2(B.z, B.w));
-      v = __ffma2_rn(bz2, make_float2(B.x, B.y), v);
-      v = __ffma2_rn(by2, make_float2(A.z, A.w), v);
-      v = __ffma2_rn(bx2, make_float2(A.x, A.y), v);
-      return (v.x < -kb ? 1u : 0u) | (v.y < -kb ? 2u : 0u);
-    };
-    if (cnt == 32) {  // full chunk: unrolled, compile-time bit positions
+    if (CHUNKS && n_obs > 32) {
+      // the two chunks of these 32 obstacles first (a chunk's sphere contains
+      // its obstacles, so an obstacle the bound overlaps lies in a chunk it
+      // overlaps)
+      const unsigned chunks = pair_bits(s_chunk, o0 >> 5);
+      tests += cnt > OBS_CHUNK ? 2u : 1u;
 #pragma unroll
-      for (int pp = 0; pp < 16; ++pp) cand |= pair_bits(pp) << (2 * pp);
-    } else {  // the padded record of an odd count never overlaps
-      for (int pp = 0; pp < obs_pairs(cnt); ++pp) cand |= pair_bits(pp) << (2 * pp);
+      for (int h = 0; h < 2; ++h) {
+        if (!((chunks >> h) & 1u)) continue;
+        const int c0 = h * OBS_CHUNK, cc = min(OBS_CHUNK, cnt - c0);
+        if (cc <= 0) continue;
+        if (cc == OBS_CHUNK) {  // full chunk: unrolled, compile-time bit positions
+#pragma unroll
+          for (int pp = 0; pp < OBS_CHUNK / 2; ++pp) cand |= pair_bits(pr, h * (OBS_CHUNK / 2) + pp) << (c0 + 2 * pp);
+        } else {  // the padded record of an odd count never overlaps
+          for (int pp = 0; pp < obs_pairs(cc); ++pp) cand |= pair_bits(pr, h * (OBS_CHUNK / 2) + pp) << (c0 + 2 * pp);
+        }
+        tests += static_cast<uint32_t>(cc);
+      }
+    } else {
+      // 32 obstacles or fewer: the chunks span the whole scene and rarely
+      // prune; every obstacle against the bound
+      if (cnt == 32) {  // full chunk: unrolled, compile-time bit positions
+#pragma unroll
+        for (int pp = 0; pp < 16; ++pp) cand |= pair_bits(pr, pp) << (2 * pp);
+      } else {  // the padded record of an odd count never overlaps
+        for (int pp = 0; pp < obs_pairs(cnt); ++pp) cand |= pair_bits(pr, pp) << (2 * pp);
+      }
+      tests += static_cast<uint32_t>(cnt);
     }
-    tests += static_cast<uint32_t>(cnt);
     if (!cand) continue;
     for (int sb = s0; sb < e && !hit; sb += SPH_BLOCK) {
       const int count = min(SPH_BLOCK, e - sb);
@@ -1182,7 +1212,9 @@ static __device__ __noinline__ bool link_hits_f32(const Rot9 Rr, V3<float> p, in
 // Collision verdict of one configuration q in the collision frame: model m
 // (root offsets shifted by the obstacle origin), spheres st, obstacle records
 // and boxes staged in shared memory.  `tests` counts the 4-FMA tests made.
-template <class P>
+// CHUNKS: test the chunk spheres first in scenes of more than 32 obstacles
+// (off where the code's size matters more than the tests it saves).
+template <class P, bool CHUNKS = true>
 __device__ __forceinline__ bool check_one_f32(const ModelT<float> &m, const SphereTable<float> &st,
                                               const float4 *s_pair, int n_obs, const float *s_box, int n_box,
                                               const double2 *tab, const float (&q)[P::D], uint32_t &tests) {
@@ -1190,8 +1222,8 @@ __device__ __forceinline__ bool check_one_f32(const ModelT<float> &m, const Sphe
   bool hit = false;
   {
     const Rot9 Ri{{1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f}};
-    hit = link_hits_f32(Ri, V3<float>{-m.shift[0], -m.shift[1], -m.shift[2]}, st.off[0], st.off[1], st.lb[MAXJ], st,
-                        s_pair, n_obs, s_box, n_box, &tests);
+    hit = link_hits_f32<CHUNKS>(Ri, V3<float>{-m.shift[0], -m.shift[1], -m.shift[2]}, st.off[0], st.off[1],
+                                st.lb[MAXJ], st, s_pair, n_obs, s_box, n_box, &tests);
   }
   Kin<P, float> k;
   if (!hit)
@@ -1203,27 +1235,34 @@ __device__ __forceinline__ bool check_one_f32(const ModelT<float> &m, const Sphe
             Rot9 Rr;
 #pragma unroll
             for (int i = 0; i < 9; ++i) Rr.r[i] = R[i];
-            hit = link_hits_f32(Rr, p, st.off[j + 1], st.off[j + 2], st.lb[j], st, s_pair, n_obs, s_box, n_box, &tests);
+            hit = link_hits_f32<CHUNKS>(Rr, p, st.off[j + 1], st.off[j + 2], st.lb[j], st, s_pair, n_obs, s_box, n_box,
+                                        &tests);
           }
         },
         [&]() { return hit; });
   return hit;
 }
 
-// Stages the FP32 obstacle records (in pairs, see obs_rec) and the boxes of
-// the collision frame in shared memory: s_pair holds obs_pairs(n_obs) x 3
-// float4, the boxes follow.  obs: [n_obs * 8] (gx, gy, gz, gw, g2, 0, 0, 0).
+// Stages the FP32 obstacle records (in pairs, see obs_rec), the chunk
+// records (in pairs, after them) and the boxes of the collision frame in
+// shared memory: s_pair holds obs_pairs(n_obs) x 3 float4, then
+// obs_pairs(obs_chunks(n_obs)) x 3 float4 of chunks, then the boxes.
+// obs: [(n_obs + obs_chunks(n_obs)) * 8] (gx, gy, gz, gw, g2, 0, 0, 0).
 __device__ __forceinline__ float *stage_obstacles(const float *obs, int n_obs, const float *box, int n_box,
                                                   float4 *s_pair) {
-  const int np = obs_pairs(n_obs);
+  const int np = obs_pairs(n_obs), nch = obs_chunks(n_obs), ncp = obs_pairs(nch);
   float *f = reinterpret_cast<float *>(s_pair);
-  for (int t = threadIdx.x; t < 12 * np; t += blockDim.x) {
-    const int pp = t / 12, c = t % 12, o = 2 * pp + (c & 1), field = c >> 1;  // gx gy gz gw g2 pad
+  for (int t = threadIdx.x; t < 12 * (np + ncp); t += blockDim.x) {
+    const bool chunk = t >= 12 * np;
+    const int u = chunk ? t - 12 * np : t;
+    const int pp = u / 12, c = u % 12, o = 2 * pp + (c & 1), field = c >> 1;  // gx gy gz gw g2 pad
+    const int n = chunk ? nch : n_obs;
+    const float *src = chunk ? obs + 8 * n_obs : obs;
     float v = 0.f;
-    if (field < 5) v = o < n_obs ? obs[8 * o + field] : (field == 3 ? 1e30f : 0.f);  // padding: gw huge
+    if (field < 5) v = o < n ? src[8 * o + field] : (field == 3 ? 1e30f : 0.f);  // padding: gw huge
     f[t] = v;
   }
-  float *s_box = f + 12 * np;
+  float *s_box = f + 12 * (np + ncp);
   for (int t = threadIdx.x; t < 6 * n_box; t += blockDim.x) s_box[t] = box[t];
   return s_box;
 }
