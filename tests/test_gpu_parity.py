@@ -396,3 +396,17 @@ def test_humanoid_fp64_plain_parity(mcproj):
     gpu = run_gpu(P, wl.q, wl.params, dtype=torch.float64)
     el, ora = eligible_mask(O, wl.q, wl.params, rel=1e-12, thr=1e-9)
     compare_projection(gpu, ora, wl.params.tol, q_tol=1e-6, oracle=O, eligible=el, min_eligible=0.8)
+
+
+def test_check_is_independent_of_obstacle_order(mcproj):
+    """The library stores the obstacles in its own spatial order and tests
+    chunks of them first: the verdicts do not depend on the order the caller
+    gives them in."""
+    wl = W.dual_arm_workload(total=10, n_random=4096)
+    q = dev(f32_exact(wl.q))
+    perm = np.random.default_rng(7).permutation(wl.obstacles.spheres.shape[0])
+    obs2 = W.Obstacles(spheres=np.ascontiguousarray(wl.obstacles.spheres[perm]), aabbs=wl.obstacles.aabbs)
+    a = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles).check(q)
+    b = mcproj.Projector(wl.robot, wl.constraints, obs2).check(q)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and 0 < int(a.sum()) < a.numel()
