@@ -827,6 +827,13 @@ def run_adjoint(args):
         p = wl.params
         P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles, device=local)
         Q0 = SH.initial_paths(P, pw["qa"], pw["qb"], pw["noise"], p)   # setup
+        # launch shape of the waypoints' projection: autotuned (setup, untimed)
+        # on the waypoints one descent step moves off the manifold
+        Q1 = P.project(Q0, p)[0]
+        _, g1 = P.path_length_grad(Q1, PATHS, WAYPOINTS)
+        P.path_step(Q1, P.vjp(Q1, g1)[0], PATHS, WAYPOINTS, 0.1, 0.05)
+        shorten_tuning = dict(zip(("tpb", "blocks_per_sm", "chunk", "fuse_check", "threads_per_config"),
+                                  P.autotune(Q1, p)))
         stats = {}
 
         def step():   # the graph-captured descent (the autograd one computes the same, more slowly)
@@ -900,7 +907,9 @@ def run_adjoint(args):
         fp32, fp64f = fm.projection(it)
         ach = fp32 / (parts["project"] * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s", "frac": ach / peak32,
-                "traffic": None, "kernel": "k_project_f32 (the waypoints' re-projection in one shortening step)",
+                "traffic": None,
+                "kernel": ("k_project_pair" if shorten_tuning["threads_per_config"] == 2 else "k_project_f32")
+                + " (the waypoints' re-projection in one shortening step)", "launch": shorten_tuning,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
                 "counted": "FP32 Newton-step and evaluation flops of the initial paths' projection"}
     e2e = None
