@@ -1093,8 +1093,10 @@ __device__ __forceinline__ ObsRec obs_rec(const float4 *s_pair, int o) {
 }
 
 // Spheres [s0, e) of one link placed by (R, p), with the link's bounding
-// sphere lb (local): the boxes, then the bounding sphere against chunks of 32
-// obstacles (broad phase, two obstacles per FP32x2 instruction), then the
+// sphere lb (local): the boxes, then, per 32 obstacles, the bounding sphere
+// against their two chunk spheres (CHUNKS, scenes of more than 32 obstacles)
+// and the obstacles of the chunks it overlaps (broad phase, two records per
+// FP32x2 instruction), then the
 // link's spheres in blocks of 8 against the candidate obstacles (narrow
 // phase, two spheres per instruction).  Every packed lane is an IEEE fma with
 // round-to-nearest, so each test is bit-identical to the scalar chain
@@ -1268,11 +1270,13 @@ __device__ __forceinline__ float *stage_obstacles(const float *obs, int n_obs, c
 }
 
 // FP32 check with a per-link broad phase: the link's bounding sphere is
-// tested against chunks of 32 obstacles (same 4-FMA test); only the obstacles
-// it overlaps are tested against the link's spheres.  The bound contains every
-// sphere of the link with a 1e-4 m margin, so no overlapping pair is skipped
-// and the verdict is that of the all-pairs test.  `pairs` counts every 4-FMA
-// test performed (broad and narrow).
+// tested against the chunk spheres (scenes of more than 32 obstacles), then
+// against the obstacles of the chunks it overlaps (same 4-FMA test); only the
+// obstacles it overlaps are tested against the link's spheres.  The bound
+// contains every sphere of the link, and a chunk's sphere every obstacle of
+// the chunk, each with a 1e-4 m margin, so no overlapping pair is skipped and
+// the verdict is that of the all-pairs test.  `pairs` counts every 4-FMA test
+// performed (chunks, broad and narrow).
 template <class P>
 __global__ void __launch_bounds__(128) k_check_f32(const __grid_constant__ CheckArgs<P, float> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
