@@ -389,8 +389,8 @@ def run_ours(args):
         if args.launch:   # a fixed shape (profiler runs reproduce the tuned one)
             vals = [int(v) for v in args.launch.split(",")]
             P.set_tuning(*vals)
-        else:   # segments: tuned on a batch of their materialised points (the same persistent kernel)
-            sample = q_in if seg_args is None else torch.tensor(cpu_q[:, :65536], dtype=dt, device=dev)
+        else:   # segments: tuned on a batch of all their materialised points (the same persistent kernel)
+            sample = q_in if seg_args is None else torch.tensor(cpu_q, dtype=dt, device=dev)
             vals = P.autotune(sample, wl.params)
         tuning = dict(zip(("tpb", "blocks_per_sm", "chunk", "fuse_check", "threads_per_config"), vals))
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
