@@ -172,7 +172,10 @@ mcp_status mcp_load_robot(mcp_ctx *ctx, const mcp_robot_desc *robot);
  * robot must be loaded first.  Synchronous (references are resolved on the device). */
 mcp_status mcp_load_constraints(mcp_ctx *ctx, const mcp_constraint_desc *cons, int32_t n);
 /* Loads (replaces) obstacle spheres [n * 4] (centre, radius) and axis-aligned
- * boxes [m * 6] (min xyz, max xyz); HOST memory, copied.  Synchronous. */
+ * boxes [m * 6] (min xyz, max xyz); HOST memory, copied.  Synchronous.
+ * MCP_ERR_ARG (the previous obstacles stay loaded) if a value is not finite.
+ * The library keeps the spheres in its own (spatial) order; verdicts do not
+ * depend on it. */
 mcp_status mcp_load_obstacles(mcp_ctx *ctx, const double *spheres, int32_t n_spheres, const double *aabbs,
                               int32_t n_aabbs);
 /* Returns the resolved constraint i (after q_ref handling): P, Q (12 each),

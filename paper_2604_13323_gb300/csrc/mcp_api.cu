@@ -944,6 +944,12 @@ mcp_status mcp_load_obstacles(mcp_ctx *ctx, const double *spheres, int32_t n_sph
     return fail(ctx, MCP_ERR_ARG, "obstacle counts %d / %d outside [0, %d] / [0, %d]", n_spheres, n_aabbs,
                 MCP_MAX_OBSTACLES, MCP_MAX_AABBS);
   if ((n_spheres && !spheres) || (n_aabbs && !aabbs)) return fail(ctx, MCP_ERR_ARG, "obstacle array is NULL");
+  // non-finite values would make a chunk's bounding sphere hide its other
+  // obstacles; rejected before anything is replaced
+  for (int64_t i = 0; i < 4 * static_cast<int64_t>(n_spheres); ++i)
+    if (!std::isfinite(spheres[i])) return fail(ctx, MCP_ERR_ARG, "obstacle sphere %lld is not finite", (long long)(i / 4));
+  for (int64_t i = 0; i < 6 * static_cast<int64_t>(n_aabbs); ++i)
+    if (!std::isfinite(aabbs[i])) return fail(ctx, MCP_ERR_ARG, "obstacle box %lld is not finite", (long long)(i / 6));
   DeviceGuard g(ctx->device);
   cudaFree(ctx->d_obs32);
   cudaFree(ctx->d_obs64);

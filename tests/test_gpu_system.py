@@ -250,3 +250,17 @@ def test_dual_segments_in_the_benchmark_configuration(mcproj):
     assert st["n"] == 262240 and st["conv_gpu"] > 0.99, (st, tpc)
     h_o, m_o = O.check(gpu[0])
     compare_collision(hit.cpu().numpy(), h_o, m_o)
+
+
+def test_non_finite_obstacles_are_rejected_and_keep_the_scene(mcproj):
+    wl = W.arm_workload(n=2048)
+    q = dev(f32_exact(wl.q))
+    P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
+    before = P.check(q).clone()
+    bad = wl.obstacles.spheres.copy()
+    bad[40, 3] = np.nan
+    with pytest.raises(mcproj.MCPError):
+        P.load_obstacles(W.Obstacles(spheres=bad, aabbs=wl.obstacles.aabbs))
+    after = P.check(q)
+    torch.cuda.synchronize()
+    assert torch.equal(before, after)
