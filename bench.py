@@ -233,15 +233,19 @@ def run_reference(args):
         return
     if args.workload == "extend":
         return run_reference_extend(args)
+    if args.workload == "vjp":
+        return run_reference_vjp(args)
     wl, q, wname, segs = make_workload(args.workload, 0)
     wname = apply_overrides(wl, wname, args)
-    if q is None:
-        from paper_2604_13323_gb300 import workloads as W
-        q = wl.extra["raw_start"]   # the oracle arm projects segment starts-like configurations
     from oracle import oracle as orc
     O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
     threads = orc.default_threads()
     p = wl.params
+    if q is None:   # segments: the starts projected by the oracle (setup), then the points on them
+        from paper_2604_13323_gb300 import workloads as W
+        ex = wl.extra
+        starts = O.project(ex["raw_start"], p.tol, p.max_iters, p.lam, threads=threads)[0]
+        q = W.segment_points(W.Segments(start=starts, delta=ex["raw_dir"] * ex["step"], length=ex["lengths"]))
     sample = min(q.shape[1], 8192)
     times, convs = [], []
     for s in range(args.warmup + args.steps):
@@ -264,6 +268,40 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{sample} configurations per step, projection + collision check"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_vjp(args):
+    """Reference arm of the VJP workload: the oracle's FP64 VJP at the
+    oracle-projected configurations (setup), 8192 per step."""
+    from oracle import oracle as orc
+    from paper_2604_13323_gb300 import workloads as W
+    wl = W.dual_arm_workload(total=10, n_random=VJP_N, batch_seed=1011)
+    p = wl.params
+    O = orc.Oracle(wl.robot, wl.constraints)
+    threads = orc.default_threads()
+    q_star = O.project(wl.q, p.tol, p.max_iters, p.lam, threads=threads)[0]
+    g = np.random.default_rng(1012).standard_normal((14, VJP_N))
+    sample = 8192
+    times = []
+    for s in range(args.warmup + args.steps):
+        sl = slice((s * sample) % VJP_N, (s * sample) % VJP_N + sample)
+        t0 = time.perf_counter()
+        O.vjp(q_star[:, sl], g[:, sl], threads=threads)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = sample * len(times) / total
+    unit = "VJPs/s"
+    line = {"impl": "reference", "metric": "vector-Jacobian products/sec at q* (dual-arm closed chain, 1 GB300)",
+            "value": value, "unit": unit, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"dual14_rel_vjp_{VJP_N}", "vjps_per_step": sample},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": threads, "kind": "oracle",
+                             "sample": f"{sample} VJPs per step"},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -969,10 +1007,9 @@ def run_adjoint(args):
 
 def main():
     args = parse()
-    if args.impl == "reference" and args.workload in ("vjp", "shorten"):
+    if args.impl == "reference" and args.workload == "shorten":
         if int(os.environ.get("RANK", "0")) == 0:
-            print(json.dumps({"impl": "reference", "unavailable": "the oracle's VJP is timed in this workload's "
-                              "cpu_baseline leg; the oracle has no path-shortening driver"}))
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle has no path-shortening driver"}))
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "extend":
