@@ -1,0 +1,44 @@
+"""The benchmark's reference arm (the FP64 oracle on the host cores): one JSON
+line per run with the contract's keys, on every workload the oracle covers,
+and nothing from ranks other than 0."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def run(workload, env=None):
+    e = dict(os.environ)
+    e.update(env or {})
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", workload, "--steps", "1",
+                        "--warmup", "1"], cwd=ROOT, env=e, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+@pytest.mark.parametrize("workload", ["arm", "dual_segments", "humanoid", "extend", "vjp", "sphere"])
+def test_reference_line(workload):
+    lines = run(workload)
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["steps"] == 1 and d["warmup"] == 1 and d["data"] == "synthetic"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    e2e = d["e2e"]
+    assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"]
+
+
+def test_reference_shortening_is_unavailable():
+    d = json.loads(run("shorten")[0])
+    assert d["impl"] == "reference" and "unavailable" in d
+
+
+def test_reference_other_ranks_print_nothing():
+    assert run("arm", {"RANK": "1", "WORLD_SIZE": "2"}) == []
