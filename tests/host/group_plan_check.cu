@@ -1,0 +1,119 @@
+// Host-side consistency check of the work plan of the group-cooperative
+// humanoid kernel (four lanes per configuration): every joint is placed by
+// forward kinematics exactly once with its parent available, every subtree
+// CoM sum comes after its children, every structurally nonzero Jacobian
+// segment (joint, constraint) and every nonzero Gram block is assigned to
+// exactly one lane with the right joint set, the refinement tasks and the dq
+// partition cover every joint once, and the Gram mask matches what the tasks
+// write.  Runs on the CPU (no kernel is launched); prints "<class>: N
+// problems" per class and exits with the total.
+#include <cstdio>
+#include <set>
+#include "../../paper_2604_13323_gb300/csrc/mcp_group.cuh"
+#include "../../paper_2604_13323_gb300/csrc/mcp_problems.cuh"
+using namespace mcp;
+template <class P> int check() {
+  GroupPlan<P> pl; const char *why = nullptr;
+  if (!make_group_plan<P>(pl, &why)) { printf("plan failed: %s\n", why); return 1; }
+  constexpr int D = P::D, NC = P::NC, K = kdim<P>();
+  int bad = 0;
+  printf("%s: n_fk=%d n_cb=%d n_cr=%d roots=%d n_j6=%d n_j2=%d n_dq=%d\n", P::name, pl.n_fk, pl.n_cb, pl.n_cr, pl.n_roots, pl.n_j6, pl.n_j2, pl.n_dq);
+  // FK: every joint stored exactly once; parents available
+  int stored[D] = {0};
+  for (int g = 0; g < GG; ++g) {
+    std::set<int> have; int prev = -1; int slot[2] = {-1, -1};
+    printf(" lane %d FK:", g);
+    for (int k = 0; k < GMAX_FK; ++k) {
+      int j = pl.fk_j[g][k]; if (j < 0) continue;
+      printf(" %d(p%d s%d w%d)", j, pl.fk_par[g][k], pl.fk_save[g][k], pl.fk_store[g][k]);
+      int p = P::parent(j), par = pl.fk_par[g][k];
+      if (par == 3 && p != -1) bad++, printf("[bad root]");
+      if (par == 0 && prev != p) bad++, printf("[bad prev]");
+      if ((par == 1 || par == 2) && slot[par - 1] != p) bad++, printf("[bad slot]");
+      if (pl.fk_save[g][k] >= 0) slot[pl.fk_save[g][k]] = j;
+      if (pl.fk_store[g][k]) stored[j]++;
+      prev = j; have.insert(j);
+      if (k >= pl.n_fk) bad++;
+    }
+    printf("\n");
+  }
+  for (int j = 0; j < D; ++j) if (stored[j] != 1) bad++, printf("joint %d stored %d\n", j, stored[j]);
+  // CoM: every joint exactly once in own/trunk lists; children processed before
+  int seen[D] = {0};
+  for (int g = 0; g < GG; ++g) { std::set<int> done; for (int k = 0; k < GMAX_CB; ++k) { int j = pl.cb_j[g][k]; if (j < 0) continue; seen[j]++; for (int h = 0; h < GMAX_CH; ++h) { int c = pl.child[j][h]; if (c >= 0 && !done.count(c)) bad++, printf("own child %d of %d not done on lane %d\n", c, j, g); } done.insert(j); if (k >= pl.n_cb) bad++; } }
+  { std::set<int> done; for (int k = 0; k < GMAX_CR; ++k) { int j = pl.cr_j[k]; if (j < 0) continue; seen[j]++; done.insert(j); if (k >= pl.n_cr) bad++; } }
+  for (int j = 0; j < D; ++j) if (seen[j] != 1) bad++, printf("joint %d in CoM lists %d times\n", j, seen[j]);
+  // segments: each (j,c) with col_sign != 0 exactly once; offsets in range, even
+  int segseen[NC][D] = {{0}};
+  for (int g = 0; g < GG; ++g) for (int k = 0; k < GMAX_JI; ++k) {
+    if (pl.j6_j[g][k] >= 0) { int j = pl.j6_j[g][k], c = pl.j6_c[g][k]; segseen[c][j]++; if (!grp_pose_like<P>(c)) bad++; if (k >= pl.n_j6) bad++; }
+    if (pl.j2_j[g][k] >= 0) { int j = pl.j2_j[g][k], c = pl.j2_c[g][k]; segseen[c][j]++; if (!grp_com_like<P>(c)) bad++; if (k >= pl.n_j2) bad++; }
+  }
+  constexpr int NJ = GrpState<P>::NJ;
+  for (int c = 0; c < NC; ++c) for (int j = 0; j < D; ++j) {
+    bool nz = col_sign<P>(c, j) != 0;
+    if (segseen[c][j] != (nz ? 1 : 0)) bad++, printf("seg (%d,%d) seen %d\n", j, c, segseen[c][j]);
+    if (nz && (pl.joff[c][j] < 0 || pl.joff[c][j] % 2 || pl.joff[c][j] + cdim(P::ckind(c)) > grp_nseg_floats<P>())) bad++, printf("joff bad\n");
+    if (!nz && pl.joff[c][j] != -1) bad++;
+  }
+  // dq joints exactly once
+  int dqs[D] = {0};
+  for (int g = 0; g < GG; ++g) for (int k = 0; k < GMAX_DQ; ++k) if (pl.dq_j[g][k] >= 0) { dqs[pl.dq_j[g][k]]++; if (k >= pl.n_dq) bad++; }
+  for (int j = 0; j < D; ++j) if (dqs[j] != 1) bad++, printf("dq joint %d: %d\n", j, dqs[j]);
+  // Gram: every nonzero lower block exactly once, joint lists = intersections
+  int blk[NC][NC] = {{0}};
+  for (int ph = 0; ph < 4; ++ph) {
+    printf(" phase %d: nt=%d len=", ph, pl.g_nt[ph]); for (int t = 0; t < GMAX_T; ++t) printf("%d ", pl.g_len[ph][t]); printf("\n");
+    for (int g = 0; g < GG; ++g) for (int t = 0; t < GMAX_T; ++t) {
+      GrpTask tk = pl.gt[ph][g][t]; if (tk.a < 0) continue;
+      if (t >= pl.g_nt[ph] || tk.n > pl.g_len[ph][t]) bad++;
+      printf("  lane %d task %d: (%d,%d) n=%d off=%d\n", g, t, tk.a, tk.b, tk.n, tk.off);
+      blk[tk.a][tk.b]++;
+      int ra = cdim(P::ckind(tk.a)), rb = cdim(P::ckind(tk.b));
+      if ((ph < 2) != (ra == 6) || ((ph % 2) == 0) != (rb == 6)) bad++, printf("shape\n");
+      if (roff<P>(tk.a) < roff<P>(tk.b)) bad++;
+      if (tk.off + tk.n > GMAX_POOL) bad++;
+      std::set<int> js; for (int s = 0; s < tk.n; ++s) js.insert(pl.pool[tk.off + s]);
+      for (int j = 0; j < D; ++j) { bool want = col_sign<P>(tk.a, j) && col_sign<P>(tk.b, j); if (want != (js.count(j) > 0)) bad++, printf("task joint set\n"); }
+    }
+  }
+  for (int a = 0; a < NC; ++a) for (int b = 0; b < NC; ++b) {
+    if (roff<P>(a) < roff<P>(b)) continue;
+    bool nz = false; for (int j = 0; j < D; ++j) nz |= col_sign<P>(a, j) && col_sign<P>(b, j);
+    if (a == b && grp_com_like<P>(a)) nz = false;  // dq-partition sum
+    if (blk[a][b] != (nz ? 1 : 0)) bad++, printf("block (%d,%d) %d\n", a, b, blk[a][b]);
+  }
+  // refinement tasks: each constraint once with its column set
+  int rs[NC] = {0};
+  for (int ph = 0; ph < 2; ++ph) for (int g = 0; g < GG; ++g) for (int t = 0; t < GMAX_T; ++t) {
+    GrpTask tk = pl.rt[ph][g][t]; if (tk.a < 0) continue; rs[tk.a]++;
+    if (t >= pl.r_nt[ph] || tk.n > pl.r_len[ph][t]) bad++;
+    std::set<int> js; for (int s = 0; s < tk.n; ++s) js.insert(pl.pool[tk.off + s]);
+    for (int j = 0; j < D; ++j) if ((col_sign<P>(tk.a, j) != 0) != (js.count(j) > 0)) bad++;
+  }
+  for (int c = 0; c < NC; ++c) if (rs[c] != (grp_pose_like<P>(c) ? 1 : 0)) bad++, printf("refinement %d\n", c);
+  // A mask: every entry written by a task is in the mask, every masked entry written
+  {
+    bool w[32][32] = {{false}};
+    for (int ph = 0; ph < 4; ++ph) for (int g = 0; g < GG; ++g) for (int t = 0; t < GMAX_T; ++t) {
+      GrpTask tk = pl.gt[ph][g][t]; if (tk.a < 0) continue;
+      for (int i = 0; i < cdim(P::ckind(tk.a)); ++i) for (int k = 0; k < cdim(P::ckind(tk.b)); ++k) {
+        int ii = roff<P>(tk.a) + i, kk = roff<P>(tk.b) + k; if (ii >= kk) w[ii][kk] = true; }
+    }
+    for (int c = 0; c < NC; ++c) if (grp_com_like<P>(c)) { int r0 = roff<P>(c); w[r0][r0] = w[r0 + 1][r0] = w[r0 + 1][r0 + 1] = true; }
+    int nm = 0;
+    for (int i = 0; i < K; ++i) for (int b = 0; b <= i; ++b) { bool m = (pl.amask[i] >> b) & 1; nm += m; if (m && !w[i][b]) bad++, printf("masked unwritten %d %d\n", i, b); }
+    printf(" amask entries %d of %d\n", nm, K * (K + 1) / 2);
+  }
+  // L columns
+  for (int i = 0; i < K; ++i) if (pl.lcol[i] != lcol_base<K>(i) || pl.lcol[i] % 4) bad++;
+  if (lcol_base<K>(K) > (int)(sizeof(GrpState<P>) )) bad++;
+  printf(" sizes: GrpState %zu B, Eval %zu B, A %d, Lc %d floats, NJ %d, shared %zu B, smem(W=2) %zu B, args %zu B\n",
+         sizeof(GrpState<P>), sizeof(typename GrpState<P>::Eval), GrpState<P>::K2, GrpState<P>::LC, NJ,
+         sizeof(GrpShared<P>), group_smem_bytes<P>(2), sizeof(GroupArgs<P>));
+  printf(" offsets: J %zu (mod8 %zu), u %zu (mod16 %zu), s.y %zu s.dq %zu, tables %zu\n", offsetof(GrpState<P>, J), offsetof(GrpState<P>, J) % 8, offsetof(GrpState<P>, u), offsetof(GrpState<P>, u) % 16,
+         offsetof(typename GrpState<P>::Solve, y), offsetof(typename GrpState<P>::Solve, dq), sizeof(GrpTables<P>));
+  printf(" %s: %d problems\n", P::name, bad);
+  return bad;
+}
+int main() { return check<ProbHumanoid36>() + check<ProbHumanoid36Hull>(); }
