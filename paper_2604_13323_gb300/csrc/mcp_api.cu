@@ -1555,7 +1555,7 @@ mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sam
       if (r > 0) times[r - 1] = ms;
     }
     if (e == cudaSuccess) {
-      std::sort(times, times + BURSTS - 1);
+      std::sort(times, times + (BURSTS - 1));
       med = times[(BURSTS - 1) / 2];
     }
     return e;

@@ -453,7 +453,7 @@ __device__ __forceinline__ void fk(const Ops &ops, const M &m, const T (&q)[P::D
     constexpr int pa = P::parent(j);
     constexpr int code = P::xrot(j);
     T Rpre[9];
-    V3<T> ppre{T(0), T(0), T(0)};
+    [[maybe_unused]] V3<T> ppre{T(0), T(0), T(0)};  // unused without positions
     if constexpr (pa < 0) {
       root_xrot<code>(m.X[j], Rpre);
       if constexpr (POS) ppre = load_p(m.X[j]);

@@ -639,7 +639,7 @@ __device__ __forceinline__ void grp_resid_phase(const GroupPlan<P> &pl, int ph, 
 template <class P, class A>
 __device__ __forceinline__ bool grp_iter(const A &a, const GrpTables<P> &tb, const GroupPlan<P> &pl,
                                          GrpState<P> &S, bool act, int &it, uint32_t &fl) {
-  constexpr int D = P::D, K = kdim<P>(), NC = P::NC;
+  constexpr int K = kdim<P>(), NC = P::NC;
   constexpr int MR = (K + GG - 1) / GG;  // rows per lane
   const int lane = threadIdx.x & 31;
   const int g = lane & (GG - 1);
