@@ -186,7 +186,12 @@ mcp_status mcp_get_constraint(const mcp_ctx *ctx, int32_t i, double *P, double *
  * q_in / q_out: [d * ld] float (precision 0) or double (precision 1); q_out may alias q_in.
  * flags [n] uint8 (MCP_F_*), iters [n] uint8 (steps applied), resid [n] double:
  * the FP64 Euclidean norm of F at the returned configuration.
- * On a divergence exit q_out holds the last iterate before the rejected step. */
+ * On a divergence exit q_out holds the last iterate before the rejected step.
+ * Precision 0: FP32 steps; a configuration is CONVERGED only when its FP64
+ * residual is below tol.  If the FP32 residual passed and the FP64 one did
+ * not, the configuration takes further FP32 steps while steps remain (then
+ * CAP | ACCEPT_FAIL); a Cholesky pivot below pivot_fp64 hands the remaining
+ * steps to FP64 (FP64_RESOLVE). */
 mcp_status mcp_project_batch(mcp_ctx *ctx, const mcp_project_params *p, int64_t n, int64_t ld, const void *q_in,
                              void *q_out, uint8_t *flags, uint8_t *iters, double *resid, mcp_stream stream);
 
