@@ -1470,7 +1470,9 @@ __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(con
     }
     const bool drained = !__any_sync(FULL, act) && qn >= qe && !more && nret == 0;
     // (4) FP64 acceptance in full warps (and, fused, the collision check of
-    // the accepted outputs: ALU work that overlaps other warps' FP64 passes)
+    // the accepted outputs: ALU work that overlaps other warps' FP64 passes);
+    // a failed acceptance with steps left is queued for one more FP32 step
+    // (an FP64 step on one lane would hold the FP64 pipe as long as 32 lanes)
     if (pend >= 32 || (drained && pend > 0)) {
       const int take = pend < 32 ? pend : 32;
       const bool room = nret + take <= RETRY_CAP;
