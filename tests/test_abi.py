@@ -49,3 +49,29 @@ def test_create_without_device_fails_cleanly(lib):
     h = ctypes.c_void_p()
     assert lib.mcp_create(0, ctypes.byref(h)) != 0
     assert not h.value
+
+
+def test_every_entry_point_rejects_a_null_context(lib):
+    """Bad arguments never abort: with no context every call returns
+    MCP_ERR_ARG (1) before touching memory or the GPU; destroy, the error
+    message and the launch count accept NULL."""
+    from paper_2604_13323_gb300 import mcproj
+    L = mcproj.load_library()
+    skip = {"mcp_create", "mcp_destroy", "mcp_last_error", "mcp_launch_count"}
+    for name in mcproj.EXPORTED:
+        if name in skip:
+            continue
+        fn = getattr(L, name)
+        args = []
+        for t in fn.argtypes:
+            if t in (ctypes.c_float, ctypes.c_double):
+                args.append(0.0)
+            elif t in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64):
+                args.append(0)
+            else:
+                args.append(None)
+        assert fn(*args) == 1, name
+    assert L.mcp_create(0, None) == 1
+    L.mcp_destroy(None)
+    assert L.mcp_last_error(None)
+    assert L.mcp_launch_count(None) == 0
