@@ -934,6 +934,86 @@ static int vjp_one(const or_robot *rb, const or_constraint *cons, int nc, const 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Gradient path shortening on the manifold: the consumer of the VJP above   */
+/* (the paper makes its log map differentiable so that the projection can   */
+/* serve gradient-based optimisation, Sec. IV-A).                            */
+/*                                                                           */
+/* A path is n_way waypoints q_0 .. q_{n_way-1} (columns w of a d x n_way    */
+/* block).  Its length is the sum of the Euclidean lengths of its edges,     */
+/*   L = sum_{w=0}^{n_way-2} |q_{w+1} - q_w|,                                */
+/* so dL/dq_w = e_w / |e_w| - e_{w+1} / |e_{w+1}| with e_w = q_w - q_{w-1}   */
+/* (an edge that does not exist, or has zero length, contributes nothing).  */
+/*                                                                           */
+/* One descent step from the waypoints Q:                                    */
+/*   1. P_w = project(Q_w) for every waypoint (ParallelProject above);       */
+/*   2. G = dL/dP at the projected path;                                     */
+/*   3. V_w = VJP(P_w, G_w) = G_w - J^T (J J^T)^{-1} J G_w, the gradient     */
+/*      pulled back through the projection (its tangent component);         */
+/*   4. Q_w = P_w - s_w eta V_w for the interior waypoints, where            */
+/*      s_w = min(1, max_step / max_j |eta V_w[j]|) clips the largest joint  */
+/*      move of a waypoint to max_step (max_step <= 0: no clipping); the     */
+/*      endpoints stay at P_0 and P_{n_way-1}.                               */
+/* After the last step the waypoints are projected once more.                */
+/* ------------------------------------------------------------------------ */
+static double path_length(int d, int n_way, const double *Q /* [n_way][d] */) {
+  double L = 0.0;
+  for (int w = 0; w + 1 < n_way; ++w) L += sqrt(dist2(d, Q + (w + 1) * d, Q + w * d));
+  return L;
+}
+
+static void path_gradient(int d, int n_way, const double *Q, double *G) {
+  for (int w = 0; w < n_way; ++w) {
+    double *g = G + w * d;
+    for (int j = 0; j < d; ++j) g[j] = 0.0;
+    if (w > 0) {   /* the edge into q_w: + e_w / |e_w| */
+      const double n = sqrt(dist2(d, Q + w * d, Q + (w - 1) * d));
+      if (n > 0.0)
+        for (int j = 0; j < d; ++j) g[j] += (Q[w * d + j] - Q[(w - 1) * d + j]) / n;
+    }
+    if (w + 1 < n_way) {   /* the edge out of q_w: - e_{w+1} / |e_{w+1}| */
+      const double n = sqrt(dist2(d, Q + (w + 1) * d, Q + w * d));
+      if (n > 0.0)
+        for (int j = 0; j < d; ++j) g[j] -= (Q[(w + 1) * d + j] - Q[w * d + j]) / n;
+    }
+  }
+}
+
+/* Shortens one path in place (Q [n_way][d]): `steps` descent steps, then the
+ * final projection.  L_out[0] = length of the input, L_out[1] = length of the
+ * result; flags / resid of the final projection per waypoint.  Returns 0 if
+ * the scratch could not be allocated. */
+static int shorten_one(const or_robot *rb, const or_constraint *cons, int nc, const or_params *p, int n_way,
+                       int steps, double eta, double max_step, double *Q, uint8_t *flags, double *resid,
+                       double *L_out) {
+  const int d = rb->nj;
+  double *G = (double *)malloc(sizeof(double) * (size_t)n_way * d);
+  if (!G) return 0;
+  L_out[0] = path_length(d, n_way, Q);
+  for (int s = 0; s <= steps; ++s) {
+    for (int w = 0; w < n_way; ++w) {   /* 1. project every waypoint */
+      int it = 0;
+      double r = 0.0;
+      int f = project_one(rb, cons, nc, p, Q + w * d, &it, &r);
+      flags[w] = (uint8_t)f;
+      resid[w] = r;
+    }
+    if (s == steps) break;   /* the final projection */
+    path_gradient(d, n_way, Q, G);   /* 2. */
+    for (int w = 1; w + 1 < n_way; ++w) {
+      double v[OR_MAXJ];
+      vjp_one(rb, cons, nc, Q + w * d, G + w * d, v);   /* 3. (NaN if J J^T is singular) */
+      double m = 0.0;
+      for (int j = 0; j < d; ++j) m = fmax(m, fabs(eta * v[j]));
+      const double sc = (max_step > 0.0 && m > max_step) ? max_step / m : 1.0;
+      for (int j = 0; j < d; ++j) Q[w * d + j] -= sc * eta * v[j];   /* 4. */
+    }
+  }
+  L_out[1] = path_length(d, n_way, Q);
+  free(G);
+  return 1;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Exported API (plain pointers; batches are SoA with leading dimension ld). */
 /* ------------------------------------------------------------------------ */
 
@@ -1053,6 +1133,11 @@ typedef struct {
   const double *q_t, *eps;
   int64_t ld_eps;
   int32_t *n_points, *winner;
+  /* path shortening: one job item is one path of n_way consecutive columns */
+  int n_way, steps;
+  double eta, max_step;
+  double *lengths;   /* [n_paths][2]: before, after */
+  int *failed;
   int mode;
 } or_job;
 
@@ -1061,7 +1146,8 @@ static void *job_run(void *arg) {
   const int d = jb->rb->nj;
   double q[OR_MAXJ], g[OR_MAXJ], v[OR_MAXJ];
   for (int64_t i = jb->i0; i < jb->i1; ++i) {
-    for (int j = 0; j < d; ++j) q[j] = jb->q_in[j * jb->ld + i];
+    if (jb->mode != 4)
+      for (int j = 0; j < d; ++j) q[j] = jb->q_in[j * jb->ld + i];
     if (jb->mode == 0) {
       int it = 0;
       double r = 0.0;
@@ -1074,6 +1160,20 @@ static void *job_run(void *arg) {
       double m = 0.0;
       jb->hit[i] = (uint8_t)check_one(jb->rb, q, jb->n_obs, jb->obs, jb->n_box, jb->box, &m);
       if (jb->margin) jb->margin[i] = m;
+    } else if (jb->mode == 4) {
+      /* path i: columns i * n_way .. (i + 1) * n_way - 1, gathered as [n_way][d] */
+      const int nw = jb->n_way;
+      double *Q = (double *)malloc(sizeof(double) * (size_t)nw * d);
+      if (!Q) { *jb->failed = 1; continue; }
+      const int64_t c0 = i * nw;
+      for (int w = 0; w < nw; ++w)
+        for (int j = 0; j < d; ++j) Q[w * d + j] = jb->q_in[j * jb->ld + c0 + w];
+      if (!shorten_one(jb->rb, jb->cons, jb->nc, jb->p, nw, jb->steps, jb->eta, jb->max_step, Q,
+                       jb->flags + c0, jb->resid + c0, jb->lengths + 2 * i))
+        *jb->failed = 1;
+      for (int w = 0; w < nw; ++w)
+        for (int j = 0; j < d; ++j) jb->q_out[j * jb->ld + c0 + w] = Q[w * d + j];
+      free(Q);
     } else if (jb->mode == 3) {
       double qt[OR_MAXJ], eps[OR_EXT_MAXN], qp[OR_MAXJ];
       for (int j = 0; j < d; ++j) qt[j] = jb->q_t[j * jb->ld + i];
@@ -1161,4 +1261,40 @@ void or_extend(const or_robot *rb, const or_constraint *cons, int nc, const or_p
   jb.q_in = q_s; jb.q_t = q_t; jb.eps = eps; jb.ld_eps = ld_eps; jb.q_out = q_proj; jb.flags = status;
   jb.n_points = n_points; jb.winner = winner; jb.mode = 3;
   run_jobs(jb, n_ext, nthreads);
+}
+
+/* Path length and its gradient for n_paths paths of n_way waypoints (SoA
+ * [d * ld], path p in columns p * n_way ..): L [n_paths], G [d * ld]. */
+void or_path_length_grad(int d, int64_t n_paths, int n_way, int64_t ld, const double *Q, double *L, double *G) {
+  double *B = (double *)malloc(sizeof(double) * (size_t)n_way * d * 2);
+  if (!B) return;
+  double *P = B, *Gp = B + (size_t)n_way * d;
+  for (int64_t p = 0; p < n_paths; ++p) {
+    for (int w = 0; w < n_way; ++w)
+      for (int j = 0; j < d; ++j) P[w * d + j] = Q[j * ld + p * n_way + w];
+    L[p] = path_length(d, n_way, P);
+    if (G) {
+      path_gradient(d, n_way, P, Gp);
+      for (int w = 0; w < n_way; ++w)
+        for (int j = 0; j < d; ++j) G[j * ld + p * n_way + w] = Gp[w * d + j];
+    }
+  }
+  free(B);
+}
+
+/* Gradient path shortening of n_paths paths (SoA [d * ld], path p in columns
+ * p * n_way ..): Q_out receives the final projected waypoints, flags / resid
+ * their final projection, lengths [n_paths][2] the length before and after.
+ * Returns 0 on success, 1 if scratch memory could not be allocated. */
+int or_shorten(const or_robot *rb, const or_constraint *cons, int nc, const or_params *p, int64_t n_paths,
+               int n_way, int64_t ld, const double *Q_in, int steps, double eta, double max_step, double *Q_out,
+               uint8_t *flags, double *resid, double *lengths, int nthreads) {
+  or_job jb;
+  int failed = 0;
+  memset(&jb, 0, sizeof(jb));
+  jb.rb = rb; jb.cons = cons; jb.nc = nc; jb.p = p; jb.ld = ld; jb.q_in = Q_in; jb.q_out = Q_out;
+  jb.flags = flags; jb.resid = resid; jb.n_way = n_way; jb.steps = steps; jb.eta = eta; jb.max_step = max_step;
+  jb.lengths = lengths; jb.failed = &failed; jb.mode = 4;
+  run_jobs(jb, n_paths, nthreads);
+  return failed;
 }

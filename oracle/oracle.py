@@ -76,6 +76,40 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_COUNT_SRC = os.path.join(_HERE, "count_ops.cpp")
+_COUNT_LIB = os.path.join(_OUT_DIR, "liboracle_count.so")
+_count_lib = None
+
+
+def build_count(force: bool = False) -> str:
+    """Compile the operation-counting build of the oracle (g++, the oracle's
+    C source included with `double` replaced by a counting wrapper)."""
+    with _lock:
+        newest = max(os.path.getmtime(_SRC), os.path.getmtime(_COUNT_SRC))
+        if force or not os.path.exists(_COUNT_LIB) or os.path.getmtime(_COUNT_LIB) < newest:
+            os.makedirs(_OUT_DIR, exist_ok=True)
+            tmp = _COUNT_LIB + f".tmp{os.getpid()}"
+            subprocess.check_call(["g++", "-std=c++17", "-O2", "-fPIC", "-shared", "-o", tmp, _COUNT_SRC, "-lm",
+                                   "-pthread"])
+            os.replace(tmp, _COUNT_LIB)
+    return _COUNT_LIB
+
+
+def _load_count():
+    global _count_lib
+    if _count_lib is None:
+        lib = ctypes.CDLL(build_count())
+        P = ctypes.POINTER
+        lib.oc_count.argtypes = [P(_Robot), P(_Constraint), ctypes.c_int, P(_Params), ctypes.c_int64, ctypes.c_int64,
+                                 _dp, _dp, ctypes.POINTER(ctypes.c_uint64)]
+        _count_lib = lib
+    return _count_lib
+
+
+# operation classes of the counting build: flops (add, mul, div) and special functions
+OP_NAMES = ("add", "mul", "div", "sqrt", "sincos", "atan2")
+
+
 def _load():
     global _lib
     if _lib is None:
@@ -99,6 +133,11 @@ def _load():
         lib.or_extend.argtypes = [P(_Robot), P(_Constraint), ctypes.c_int, P(_Params), P(_ExtParams), ctypes.c_int,
                                   _dp, ctypes.c_int, _dp, ctypes.c_int64, ctypes.c_int64, _dp, _dp, _dp,
                                   ctypes.c_int64, _dp, _u8p, _ip, _ip, ctypes.c_int]
+        lib.or_path_length_grad.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp]
+        lib.or_shorten.argtypes = [P(_Robot), P(_Constraint), ctypes.c_int, P(_Params), ctypes.c_int64, ctypes.c_int,
+                                   ctypes.c_int64, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _u8p,
+                                   _dp, _dp, ctypes.c_int]
+        lib.or_shorten.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -267,6 +306,46 @@ class Oracle:
                          _ptr(self._box), n, n, _ptr(q), _ptr(hit, _u8p), _ptr(margin), threads or default_threads())
         return hit, margin
 
+    def shorten(self, Q, n_paths, n_way, params, steps, eta=0.1, max_step=0.05, threads=None):
+        """Gradient path shortening on the manifold (FP64): `steps` descent
+        steps (project every waypoint, length gradient at the projections, its
+        VJP through the projection, clipped step of the interior waypoints),
+        then a final projection.  Q: [d, n_paths * n_way] waypoints.  Returns
+        (Q_final, flags, resid, lengths [n_paths, 2] before / after)."""
+        Q = _f64(Q)
+        d, ld = Q.shape
+        out = np.empty_like(Q)
+        flags = np.zeros(ld, np.uint8)
+        resid = np.zeros(ld)
+        lengths = np.zeros((n_paths, 2))
+        p = _Params(tol=params.tol, max_iters=params.max_iters, cyclic=int(bool(getattr(params, "cyclic", False))),
+                    lam=params.lam, alpha=getattr(params, "alpha", 1.0), max_step=params.max_step,
+                    outer=int(bool(getattr(params, "outer", False))))
+        if _load().or_shorten(ctypes.byref(self._robot), self._cons, self.nc, ctypes.byref(p), n_paths, n_way, ld,
+                              _ptr(Q), steps, eta, max_step, _ptr(out), _ptr(flags, _u8p), _ptr(resid),
+                              _ptr(lengths), threads or default_threads()):
+            raise MemoryError("oracle path shortening: scratch allocation failed")
+        return out, flags, resid, lengths
+
+    def count_ops(self, q, params, g=None):
+        """Operations the method performs per configuration (the counting
+        build of this oracle; structural zeros and signed unit factors are
+        free, as in traced straight-line code).  Returns a dict of arrays
+        [n, 6] (columns OP_NAMES): 'eval' = one evaluation of the stacked F,
+        'step' = one LM step (F and J, Gram, Cholesky, solves, J^T y,
+        update), 'vjp' = one VJP at q with upstream gradient g."""
+        q = _f64(q)
+        d, n = q.shape
+        g = _f64(g) if g is not None else np.zeros_like(q)
+        out = np.zeros((n, 18), np.uint64)
+        p = _Params(tol=params.tol, max_iters=params.max_iters, cyclic=int(bool(getattr(params, "cyclic", False))),
+                    lam=params.lam, alpha=getattr(params, "alpha", 1.0), max_step=params.max_step,
+                    outer=int(bool(getattr(params, "outer", False))))
+        _load_count().oc_count(ctypes.byref(self._robot), self._cons, self.nc, ctypes.byref(p), n, n, _ptr(q),
+                               _ptr(g), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+        out = out.astype(np.int64)
+        return {"eval": out[:, 0:6], "step": out[:, 6:12], "vjp": out[:, 12:18]}
+
     def vjp(self, q, g, threads=None):
         q = _f64(q)
         g = _f64(g)
@@ -276,6 +355,17 @@ class Oracle:
         _load().or_vjp(ctypes.byref(self._robot), self._cons, self.nc, n, n, _ptr(q), _ptr(g), _ptr(v),
                        _ptr(flags, _u8p), threads or default_threads())
         return v, flags
+
+
+def path_length_grad(Q, n_paths, n_way):
+    """Lengths [n_paths] and gradient [d, n] of waypoint paths (SoA, path p in
+    columns p * n_way ..): L = sum of |q_{w+1} - q_w|."""
+    Q = _f64(Q)
+    d, ld = Q.shape
+    L = np.zeros(n_paths)
+    G = np.zeros_like(Q)
+    _load().or_path_length_grad(d, n_paths, n_way, ld, _ptr(Q), _ptr(L), _ptr(G))
+    return L, G
 
 
 def so3_log(R3x3):

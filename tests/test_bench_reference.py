@@ -20,7 +20,7 @@ def run(workload, env=None):
     return [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
 
 
-@pytest.mark.parametrize("workload", ["arm", "dual_segments", "humanoid", "extend", "vjp", "sphere"])
+@pytest.mark.parametrize("workload", ["arm", "dual_segments", "humanoid", "extend", "vjp", "sphere", "shorten"])
 def test_reference_line(workload):
     lines = run(workload)
     assert len(lines) == 1
@@ -33,11 +33,6 @@ def test_reference_line(workload):
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"]
-
-
-def test_reference_shortening_is_unavailable():
-    d = json.loads(run("shorten")[0])
-    assert d["impl"] == "reference" and "unavailable" in d
 
 
 def test_reference_other_ranks_print_nothing():
