@@ -235,6 +235,8 @@ def run_reference(args):
         return run_reference_extend(args)
     if args.workload == "vjp":
         return run_reference_vjp(args)
+    if args.workload == "shorten":
+        return run_reference_shorten(args)
     wl, q, wname, segs = make_workload(args.workload, 0)
     wname = apply_overrides(wl, wname, args)
     from oracle import oracle as orc
@@ -301,6 +303,57 @@ def run_reference_vjp(args):
             "config": {"workload": f"dual14_rel_vjp_{VJP_N}", "vjps_per_step": sample},
             "cpu_baseline": {"value": value, "unit": unit, "cores": threads, "kind": "oracle",
                              "sample": f"{sample} VJPs per step"},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def oracle_initial_paths(O, pw, p, threads):
+    """The shortening workload's initial waypoints, built by the oracle the
+    way the GPU driver builds them: projected endpoints, linear interpolation
+    plus the seeded noise, projected."""
+    qa = O.project_params(pw["qa"], p, threads=threads)[0]
+    qb = O.project_params(pw["qb"], p, threads=threads)[0]
+    t = np.linspace(0.0, 1.0, pw["n_way"])
+    Q = (qa[:, :, None] + (qb - qa)[:, :, None] * t[None, None, :] + pw["noise"]).reshape(qa.shape[0], -1)
+    return O.project_params(Q, p, threads=threads)[0]
+
+
+def run_reference_shorten(args):
+    """Reference arm of the path-shortening workload: the oracle's FP64
+    descent (project, length gradient, VJP, clipped step; SHORTEN_STEPS steps)
+    on the host cores, SHORTEN_REF_PATHS paths of WAYPOINTS waypoints per
+    step (their initial waypoints built by the oracle, untimed)."""
+    from oracle import oracle as orc
+    from paper_2604_13323_gb300 import workloads as W
+    pw = W.path_workload(n_paths=PATHS, n_way=WAYPOINTS)
+    wl = pw["workload"]
+    p = wl.params
+    O = orc.Oracle(wl.robot, wl.constraints)
+    threads = orc.default_threads()
+    nb = SHORTEN_REF_PATHS
+    times, red = [], []
+    for s_ in range(args.warmup + args.steps):
+        sl = slice((s_ * nb) % PATHS, (s_ * nb) % PATHS + nb)
+        sub = {"qa": pw["qa"][:, sl], "qb": pw["qb"][:, sl], "noise": pw["noise"][:, sl], "n_way": WAYPOINTS}
+        Q0 = oracle_initial_paths(O, sub, p, threads)
+        t0 = time.perf_counter()
+        _, _, _, L = O.shorten(Q0, nb, WAYPOINTS, p, SHORTEN_STEPS, 0.1, 0.05, threads=threads)
+        dt = time.perf_counter() - t0
+        if s_ >= args.warmup:
+            times.append(dt)
+            red.append(float(np.mean(1.0 - L[:, 1] / L[:, 0])))
+    total = sum(times)
+    units = nb * WAYPOINTS * SHORTEN_STEPS
+    value = units * len(times) / total
+    unit = "waypoint-steps/s"
+    line = {"impl": "reference", "metric": "path-shortening waypoint steps/sec on the manifold (dual arm, 1 GB300)",
+            "value": value, "unit": unit, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"dual14_rel_shorten_{PATHS}x{WAYPOINTS}x{SHORTEN_STEPS}",
+                       "paths_per_step": nb, "mean_length_reduction": float(np.mean(red))},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": threads, "kind": "oracle",
+                             "sample": f"{nb} paths x {WAYPOINTS} waypoints x {SHORTEN_STEPS} descent steps per step"},
             "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -813,6 +866,7 @@ def run_extend(args):
 
 VJP_N = 65536          # projected dual-arm configurations per VJP step
 PATHS, WAYPOINTS, SHORTEN_STEPS = 4096, 64, 100
+SHORTEN_REF_PATHS = 64   # paths per step of the oracle's (reference arm) shortening
 
 
 def run_adjoint(args):
@@ -1007,10 +1061,7 @@ def run_adjoint(args):
 
 def main():
     args = parse()
-    if args.impl == "reference" and args.workload == "shorten":
-        if int(os.environ.get("RANK", "0")) == 0:
-            print(json.dumps({"impl": "reference", "unavailable": "the oracle has no path-shortening driver"}))
-    elif args.impl == "reference":
+    if args.impl == "reference":
         run_reference(args)
     elif args.workload == "extend":
         run_extend(args)
