@@ -8,13 +8,29 @@ Such configurations still converge to a valid point of the manifold, but
 *which* point is not a well-defined function of the start, so point-wise
 parity is only asserted on the configurations that are stable under such
 perturbations; validity (FP64 residual below tol) is asserted everywhere.
+
+The perturbation is the rounding scale of the precision the compared path
+computes in, applied as 8 random sign patterns.  FP32 path: 8 unit roundoffs
+(8 * 2^-24 ~ 5e-7).  One FP32 Newton step carries rounding of several unit
+roundoffs (the Gram entries sum d products, the Cholesky K rows, each iterate
+is rounded to FP32), so the compared path's iterates behave like starts
+perturbed at that scale; a start whose FP64 result moves by more than the
+point bar under such a perturbation has no answer that the path could
+reproduce to within the bar.  Plain FP64 path: 1e-14 (~90 unit roundoffs of
+FP64): it differs from the oracle not by the rounding of the same operations
+but by other ones (CUDA's sin / cos against libm's, FMA contraction, another
+order of products along the chain).  The threshold is the point bar itself
+(1e-4 rad for the FP32 path, 1e-8 for the plain FP64 one).
 """
 import numpy as np
 
 from . import oracle as orc
 
 
-def eligible_mask(o, q0, tol, max_iters, lam, max_step=0.0, rel=1e-6, thr=1e-5, reps=2, seed=0, cyclic=False,
+REL_FP32, REL_FP64 = 5e-7, 1e-14   # 8 unit roundoffs of FP32; ~90 of FP64
+
+
+def eligible_mask(o, q0, tol, max_iters, lam, max_step=0.0, rel=REL_FP32, thr=1e-4, reps=8, seed=0, cyclic=False,
                   stable_iters=False, stats=None, alpha=1.0, outer=False):
     """(mask, oracle result): mask[i] is True when `reps` random relative
     perturbations of size `rel` of start i move the oracle's result by <= thr

@@ -12,6 +12,12 @@ from oracle import parity
 Q_TOL = 1e-4
 FLAG_AGREE = 0.999
 CONTACT_BAND = 1e-5
+# the plain FP64 kernel against the FP64 oracle: both compute in FP64 but not
+# the same operations -- CUDA's sin / cos against libm's (each within an ulp,
+# not identical), FMA contraction, another order of the products along the
+# chain -- so their difference behaves like a start perturbation of ~100 unit
+# roundoffs (REL_FP64) rather than of a few; the point bar is 1e-8 rad
+Q_TOL_FP64 = 1e-8
 
 
 def f32_exact(q):
@@ -19,9 +25,16 @@ def f32_exact(q):
     return np.asarray(q, dtype=np.float32).astype(np.float64)
 
 
-def eligible_mask(oracle, q0, params, rel=1e-6, thr=1e-5, reps=2, seed=0, stable_iters=False, stats=None):
+def eligible_mask(oracle, q0, params, rel=None, thr=None, reps=8, seed=0, stable_iters=False, stats=None):
     """Configurations whose projection is a well-defined function of the start
-    (see oracle/parity.py).  Returns (mask, oracle result)."""
+    at the compared path's precision (see oracle/parity.py): by default 8
+    unit roundoffs of FP32 (FP64 for the plain FP64 path) against the point
+    bar (Q_TOL, Q_TOL_FP64).  Returns (mask, oracle result)."""
+    fp64 = getattr(params, "precision", 0) == 1
+    if rel is None:
+        rel = parity.REL_FP64 if fp64 else parity.REL_FP32
+    if thr is None:
+        thr = Q_TOL_FP64 if fp64 else Q_TOL
     return parity.eligible_mask(oracle, q0, params.tol, params.max_iters, params.lam, max_step=params.max_step,
                                 rel=rel, thr=thr, reps=reps, seed=seed, cyclic=bool(getattr(params, "cyclic", False)),
                                 stable_iters=stable_iters, stats=stats, alpha=getattr(params, "alpha", 1.0),

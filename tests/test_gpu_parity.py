@@ -1,11 +1,16 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Every case runs the same seeded inputs through both sides and compares them
-element by element: converged configurations to 1e-4 rad, the FP64 residual of
-each converged output below tol, convergence flags on >= 99.9 %, collision
-verdicts exactly outside a 1e-5 m contact band.  Sizes span several thread
-blocks with a ragged tail; the full workload sizes are included where the
-oracle finishes them in seconds.
+element by element: converged configurations to 1e-4 rad (the plain FP64
+kernel to 1e-8), the FP64 residual of each converged output below tol,
+convergence flags on >= 99.9 %, collision verdicts exactly outside a 1e-5 m
+contact band.  Points are compared on every start whose FP64 result is
+determined to within the point bar at the compared path's precision (it moves
+less than the bar under 8 random perturbations of 8 unit roundoffs); the
+fraction of such starts has a floor per workload, and every converged output,
+compared or not, must be a valid point of the manifold.  Sizes span several
+thread blocks with a ragged tail; the full workload sizes are included where
+the oracle finishes them in seconds.
 """
 import numpy as np
 import pytest
@@ -14,7 +19,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import oracle as orc  # noqa: E402
 from paper_2604_13323_gb300 import workloads as W  # noqa: E402
-from tests.gpu_util import compare_collision, compare_projection, eligible_mask, f32_exact  # noqa: E402
+from tests.gpu_util import Q_TOL, Q_TOL_FP64, compare_collision, compare_projection, eligible_mask, f32_exact  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -80,7 +85,9 @@ def test_arm_fp32_parity(mcproj, n, ld):
     O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
     gpu = run_gpu(P, q0, wl.params, ld=ld)
     el, ora = eligible_mask(O, q0, wl.params)
-    st = compare_projection(gpu, ora, wl.params.tol, oracle=O, eligible=el, min_eligible=0.5 if n > 100 else 0.0,
+    # uniform starts in the joint box: ~23 % of them pass near-singular J J^T on the way
+    # and their FP64 result moves by more than 1e-4 under FP32-scale perturbations
+    st = compare_projection(gpu, ora, wl.params.tol, oracle=O, eligible=el, min_eligible=0.75 if n > 100 else 0.0,
                             sample_resid=4096)
     assert st["conv_gpu"] > 0.99
 
@@ -88,47 +95,23 @@ def test_arm_fp32_parity(mcproj, n, ld):
 @pytest.mark.parametrize("steps", [1, 2])
 def test_arm_fp32_single_steps_all_configs(mcproj, steps):
     """One or two LM steps (cap = steps) from every start of the full batch,
-    compared relative to the size of the step.  A step through a nearly
-    singular J J^T + lambda I is ill-conditioned in any precision; such starts
-    are recognised by the oracle's own response to a perturbation of ~10 FP32
-    ulps, measured relative to the step (1e-5 (1 + |step|)).  The tolerance is
-    1e-4 relative to the step, or the forward-error bound of a least-norm step
-    solved in FP32, 16 eps32 kappa(J) (Higham, Accuracy and Stability of
-    Numerical Algorithms, ch. 20), where J at an iterate is ill-conditioned."""
+    compared with the oracle's steps to the 1e-4 rad point bar wherever the
+    FP64 result of those steps is determined to that bar at FP32 precision
+    (the default eligibility).  Starts whose step runs through a nearly
+    singular J J^T + lambda I are excluded by that test, not by the bar."""
     wl = W.arm_workload(n=65536)
     q0 = f32_exact(wl.q)
     p = W.Params(tol=1e-5, max_iters=steps, lam=1e-6)
     P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
     O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
     qg, fg, ig, rg = run_gpu(P, q0, p)
-    qo, fo, io, ro = O.project_params(q0, p)
-    step = np.abs(qo - q0).max(axis=0)
-    rng = np.random.default_rng(0)
-    dev_max = np.zeros(q0.shape[1])
-    for _ in range(2):
-        q1 = q0 * (1.0 + 1e-6 * rng.choice([-1.0, 1.0], size=q0.shape))
-        dev_max = np.maximum(dev_max, np.abs(O.project_params(q1, p)[0] - qo).max(axis=0))
-    el = dev_max <= 1e-5 * (1.0 + step)
-    same = ig == io
-    assert same.mean() > 0.999
-    # a pivot below the threshold hands the step to the FP64 re-solve: a different
-    # code path through a nearly singular system (steps of hundreds of radians)
-    fp32 = (fg & mcproj.F_FP64_RESOLVE) == 0
-    assert (~fp32).mean() < 1e-3
-    kappa = np.ones(q0.shape[1])
-    for t in range(steps):   # condition of J at every iterate the steps start from
-        qt = q0 if t == 0 else O.project_params(q0, W.Params(tol=p.tol, max_iters=t, lam=p.lam))[0]
-        for i in range(q0.shape[1]):
-            sv = np.linalg.svd(O.residual_jacobian(qt[:, i])[1], compute_uv=False)
-            kappa[i] = max(kappa[i], sv[0] / sv[-1])
-    rel = np.maximum(1e-4, 16 * np.finfo(np.float32).eps * kappa)
+    el, (qo, fo, io, ro) = eligible_mask(O, q0, p)
+    assert (ig == io).all()
+    assert ((fg & mcproj.F_FP64_RESOLVE) != 0).mean() < 1e-3
     err = np.abs(qg - qo).max(axis=0)
-    ok = err <= rel * (1.0 + step)
-    sel = same & el & fp32
-    assert (rel[sel] > 1e-4).mean() < 0.05
-    assert ok[sel].all(), (np.flatnonzero(~ok & sel)[:8], np.quantile(err[sel], [0.5, 0.99, 1.0]))
-    # large first steps through nearly singular systems are common from uniform starts
-    assert el.mean() > 0.6, el.mean()
+    assert (err[el] <= Q_TOL).all(), (np.flatnonzero(~(err <= Q_TOL) & el)[:8], err[el].max())
+    # one step from a uniform start is well determined more often than two
+    assert el.mean() > (0.88 if steps == 1 else 0.78), el.mean()
 
 
 def test_arm_fp64_plain_parity(mcproj):
@@ -137,27 +120,37 @@ def test_arm_fp64_plain_parity(mcproj):
     P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
     O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
     gpu = run_gpu(P, wl.q, wl.params, dtype=torch.float64)
-    el, ora = eligible_mask(O, wl.q, wl.params, rel=1e-12, thr=1e-9)
-    st = compare_projection(gpu, ora, wl.params.tol, q_tol=1e-6, oracle=O, eligible=el, min_eligible=0.8)
+    el, ora = eligible_mask(O, wl.q, wl.params)
+    st = compare_projection(gpu, ora, wl.params.tol, q_tol=Q_TOL_FP64, oracle=O, eligible=el, min_eligible=0.95)
     assert st["iters_equal"] > 0.999
 
 
 def test_arm_pose_fp32_parity(mcproj):
-    """6-D TSR (Eq. 1) on the 7-DoF arm, reference pose taken at a seeded q_ref."""
+    """6-D TSR (Eq. 1) on the 7-DoF arm, reference pose taken at a seeded q_ref;
+    starts q_ref + N(0, 0.3^2) (the noise of the humanoid's starts)."""
     wl = W.arm_workload(n=2048)
     rng = np.random.default_rng(5)
     q_ref = rng.uniform(-1.5, 1.5, 7)
     cons = [W.Constraint(W.C_POSE, frame_a=0, q_ref=q_ref)]
-    q0 = f32_exact(q_ref[:, None] + 0.1 * rng.standard_normal((7, 2048)))
+    q0 = f32_exact(q_ref[:, None] + 0.3 * rng.standard_normal((7, 2048)))
     P = mcproj.Projector(wl.robot, cons, wl.obstacles)
     O = orc.Oracle(wl.robot, cons, wl.obstacles)
     Pg, Qg, tg = P.constraint(0)
     Po, Qo, to = O.constraint_values(0)
     np.testing.assert_allclose(Pg, Po, atol=1e-14)
     gpu = run_gpu(P, q0, wl.params)
-    el, ora = eligible_mask(O, q0, wl.params)
-    st = compare_projection(gpu, ora, wl.params.tol, oracle=O, eligible=el, min_eligible=0.95)
-    assert st["conv_oracle"] > 0.95
+    selfd = {}
+    el, ora = eligible_mask(O, q0, wl.params, stats=selfd)
+    # A 7-DoF arm has one redundant DoF against a 6-D pose and these starts are
+    # up to a radian off: ~10 % of them are still converging slowly at the cap
+    # of 30 steps, and whether such a start is flagged CONVERGED at step 30
+    # flips in the oracle itself under an 8-ulp perturbation (~16 % of the
+    # starts change flag or count).  Flags are compared where the oracle's own
+    # flag is stable (>= 99.9 %); over all starts the disagreement may not
+    # exceed the oracle's own flip rate.
+    st = compare_projection(gpu, ora, wl.params.tol, oracle=O, eligible=el, min_eligible=0.78, stable_only=True,
+                            overall_flag_agree=1.0 - selfd["self_flip_rate"])
+    assert st["conv_oracle"] > 0.85
 
 
 def test_arm_check_fp32(mcproj):
@@ -206,7 +199,7 @@ def test_dual_batch_fp32_parity(mcproj):
     np.testing.assert_allclose(Pg, Po, atol=1e-14)
     gpu = run_gpu(P, q0, wl.params)
     el, ora = eligible_mask(O, q0, wl.params)
-    compare_projection(gpu, ora, wl.params.tol, oracle=O, eligible=el, min_eligible=0.95)
+    compare_projection(gpu, ora, wl.params.tol, oracle=O, eligible=el, min_eligible=0.99)
 
 
 def test_dual_segments_fp32_parity(mcproj):
@@ -228,7 +221,7 @@ def test_dual_segments_fp32_parity(mcproj):
     sid = torch.repeat_interleave(torch.arange(seg.length.shape[0]), torch.tensor(seg.length, dtype=torch.long))
     pts = torch.addcmul(s[:, sid], t[None, :], d[:, sid]).double().numpy()
     el, ora = eligible_mask(O, pts, wl.params)
-    st = compare_projection(gpu, ora, wl.params.tol, oracle=O, eligible=el, min_eligible=0.5, sample_resid=4096)
+    st = compare_projection(gpu, ora, wl.params.tol, oracle=O, eligible=el, min_eligible=0.9, sample_resid=4096)
     assert st["n"] == seg.total and st["conv_gpu"] > 0.99
     # no pivot falls below the re-solve threshold on this workload, and a
     # failed FP64 acceptance continues in FP32: no FP64 Newton step is taken
@@ -368,7 +361,7 @@ def test_humanoid_fp32_parity(mcproj):
         np.testing.assert_allclose(P.constraint(c)[2], O.constraint_values(c)[2], atol=1e-13)
     gpu = run_gpu(P, q0, wl.params, ld=4128)
     el, ora = eligible_mask(O, q0, wl.params)
-    st = compare_projection(gpu, ora, wl.params.tol, oracle=O, eligible=el, min_eligible=0.9, sample_resid=1024)
+    st = compare_projection(gpu, ora, wl.params.tol, oracle=O, eligible=el, min_eligible=0.98, sample_resid=1024)
     assert st["conv_gpu"] > 0.99
 
 
@@ -385,7 +378,7 @@ def test_humanoid_full_size_sampled(mcproj):
     idx = np.sort(np.random.default_rng(17).choice(q0.shape[1], 2048, replace=False))
     el, ora = eligible_mask(O, q0[:, idx], wl.params)
     compare_projection((qg[:, idx], fg[idx], ig[idx], rg[idx]), ora, wl.params.tol, oracle=O, eligible=el,
-                       min_eligible=0.9, sample_resid=512)
+                       min_eligible=0.98, sample_resid=512)
 
 
 def test_humanoid_fp64_plain_parity(mcproj):
@@ -394,8 +387,8 @@ def test_humanoid_fp64_plain_parity(mcproj):
     P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
     O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
     gpu = run_gpu(P, wl.q, wl.params, dtype=torch.float64)
-    el, ora = eligible_mask(O, wl.q, wl.params, rel=1e-12, thr=1e-9)
-    compare_projection(gpu, ora, wl.params.tol, q_tol=1e-6, oracle=O, eligible=el, min_eligible=0.8)
+    el, ora = eligible_mask(O, wl.q, wl.params)
+    compare_projection(gpu, ora, wl.params.tol, q_tol=Q_TOL_FP64, oracle=O, eligible=el, min_eligible=0.98)
 
 
 def test_check_is_independent_of_obstacle_order(mcproj):

@@ -18,7 +18,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import oracle as orc  # noqa: E402
 from paper_2604_13323_gb300 import workloads as W  # noqa: E402
-from tests.gpu_util import compare_collision, compare_projection, eligible_mask, f32_exact  # noqa: E402
+from tests.gpu_util import Q_TOL_FP64, compare_collision, compare_projection, eligible_mask, f32_exact  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -107,8 +107,8 @@ def test_task_fp64_plain_parity(mcproj, name, cyclic):
     P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
     gpu = run(P, wl.q, wl.params, dtype=torch.float64)
     selfst = {}
-    el, ora = eligible_mask(O, wl.q, wl.params, rel=1e-12, thr=1e-9, stable_iters=True, stats=selfst)
-    st = compare_projection(gpu, ora, wl.params.tol, q_tol=1e-6, oracle=O, eligible=el, min_eligible=0.7,
+    el, ora = eligible_mask(O, wl.q, wl.params, stable_iters=True, stats=selfst)
+    st = compare_projection(gpu, ora, wl.params.tol, q_tol=Q_TOL_FP64, oracle=O, eligible=el, min_eligible=0.7,
                             stable_only=True, **self_consistent_bars(selfst))
     assert st["iters_equal"] > 0.999, st
 
@@ -156,8 +156,8 @@ def test_humanoid_cyclic_fp64_plain_parity(mcproj):
     O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
     P = mcproj.Projector(wl.robot, wl.constraints, wl.obstacles)
     gpu = run(P, wl.q, wl.params, dtype=torch.float64)
-    el, ora = eligible_mask(O, wl.q, wl.params, rel=1e-12, thr=1e-9)
-    st = compare_projection(gpu, ora, wl.params.tol, q_tol=1e-6, oracle=O, eligible=el, min_eligible=0.5)
+    el, ora = eligible_mask(O, wl.q, wl.params)
+    st = compare_projection(gpu, ora, wl.params.tol, q_tol=Q_TOL_FP64, oracle=O, eligible=el, min_eligible=0.5)
     assert st["iters_equal"] > 0.99, st
 
 
@@ -196,6 +196,6 @@ def test_humanoid_hull_fp64_plain_parity(mcproj):
     O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
     gpu = run(P, wl.q, wl.params, dtype=torch.float64)
     selfst = {}
-    el, ora = eligible_mask(O, wl.q, wl.params, rel=1e-12, thr=1e-9, stable_iters=True, stats=selfst)
-    compare_projection(gpu, ora, wl.params.tol, q_tol=1e-6, oracle=O, eligible=el, min_eligible=0.7,
+    el, ora = eligible_mask(O, wl.q, wl.params, stable_iters=True, stats=selfst)
+    compare_projection(gpu, ora, wl.params.tol, q_tol=Q_TOL_FP64, oracle=O, eligible=el, min_eligible=0.7,
                        stable_only=True, **self_consistent_bars(selfst))
