@@ -535,14 +535,20 @@ __device__ __forceinline__ LogOut<Ops, T> so3_log(const T (&R)[9]) {
     for (int r = 0; r < 3; ++r)
 #pragma unroll
       for (int cc = 0; cc < 3; ++cc) S[r * 3 + cc] = T(0.5) * (R[r * 3 + cc] + R[cc * 3 + r]);
-    int i = 0;
-    if (S[4] > S[0]) i = 1;
-    if (S[8] > S[i * 4]) i = 2;
+    // the axis from column i of S, i the largest diagonal entry; the
+    // column is selected by value (no runtime index into a local array)
+    const bool i1 = S[4] > S[0];
+    const T d01 = i1 ? S[4] : S[0];
+    const bool i2 = S[8] > d01;
+    const T sii = i2 ? S[8] : d01;
+    const T s0i = i2 ? S[2] : (i1 ? S[1] : S[0]);
+    const T s1i = i2 ? S[5] : (i1 ? S[4] : S[3]);
+    const T s2i = i2 ? S[8] : (i1 ? S[7] : S[6]);
     T omc = T(1) - c;
-    T ai = Ops::sqrt_((S[i * 4] - c) / omc);
+    T ai = Ops::sqrt_((sii - c) / omc);
     T inv = T(1) / (omc * ai);
-    V3<T> a{(S[i] - (i == 0 ? c : T(0))) * inv, (S[3 + i] - (i == 1 ? c : T(0))) * inv,
-            (S[6 + i] - (i == 2 ? c : T(0))) * inv};
+    V3<T> a{(s0i - (!i1 && !i2 ? c : T(0))) * inv, (s1i - (i1 && !i2 ? c : T(0))) * inv,
+            (s2i - (i2 ? c : T(0))) * inv};
     if (dot(a, w) < T(0)) a = {-a.x, -a.y, -a.z};
     o.phi = {th * a.x, th * a.y, th * a.z};
   }

@@ -723,15 +723,9 @@ __device__ __forceinline__ double residual2_f64(const Ops &ops, const ModelT<dou
 }
 
 // One LM step entirely in FP64 at q (the re-solve of a badly conditioned
-// system): the same compile-time building blocks as the plain FP64 kernel's
-// step (structural nonzeros of J only, Gram, Cholesky, J^T y), with the
-// table-driven FP64 sin/cos.  Out of line, so that this rare path does not
-// raise the register budget of the FP32 loop.  (An earlier form held J and
-// the factor in runtime-indexed local arrays; on the humanoid it returned
-// wrong steps exactly where a pose error's rotation exceeded 3 pi / 4 -- the
-// log map's symmetric-part branch -- while this form and the plain kernel's
-// agree with the oracle there.)  Returns false if the FP64 system is
-// singular as well.
+// system).  J and the factorisation live in local memory (runtime-indexed
+// loops) so that this rare path does not raise the register budget of the
+// FP32 loop.  Returns false if the FP64 system is singular as well.
 template <class P, bool OUTER = false>
 __device__ __noinline__ bool lm_step_f64(const OpsF64Table ops, const ModelT<double> *__restrict__ m,
                                          const double *q_in, double lambda, double *dq_out) {
@@ -745,23 +739,111 @@ __device__ __noinline__ bool lm_step_f64(const OpsF64Table ops, const ModelT<dou
   Eval<P, double> e;
   residual<P, OpsF64Table, double, true>(*m, q, k, F, e);
   double J[K][D];
+#pragma unroll 1
+  for (int a = 0; a < K; ++a)
+#pragma unroll 1
+    for (int j = 0; j < D; ++j) J[a][j] = 0.0;
   jacobian<P>(*m, q, k, e, J);
-  double dq[D];
   if constexpr (OUTER) {
     // (J^T J + lambda I) dq = J^T F
-    double Am[D * (D + 1) / 2];
-    gram_outer<P>(J, lambda, Am);
-    jt_mul<P>(J, F, dq);
-    if (!(cholesky_solve<D, OpsF64Plain>(Am, dq) > 0.0)) return false;
+    double L[D][D], b[D];
+#pragma unroll 1
+    for (int i = 0; i < D; ++i) {
+      double t = 0.0;
+#pragma unroll 1
+      for (int a = 0; a < K; ++a) t = fma(J[a][i], F[a], t);
+      b[i] = t;
+#pragma unroll 1
+      for (int j = 0; j <= i; ++j) {
+        double s = (i == j) ? lambda : 0.0;
+#pragma unroll 1
+        for (int a = 0; a < K; ++a) s = fma(J[a][i], J[a][j], s);
+        L[i][j] = s;
+      }
+    }
+#pragma unroll 1
+    for (int j = 0; j < D; ++j) {
+      double s = L[j][j];
+#pragma unroll 1
+      for (int t = 0; t < j; ++t) s = fma(-L[j][t], L[j][t], s);
+      if (!(s > 0.0)) return false;
+      L[j][j] = sqrt(s);
+#pragma unroll 1
+      for (int i = j + 1; i < D; ++i) {
+        double t2 = L[i][j];
+#pragma unroll 1
+        for (int t = 0; t < j; ++t) t2 = fma(-L[i][t], L[j][t], t2);
+        L[i][j] = t2 / L[j][j];
+      }
+    }
+#pragma unroll 1
+    for (int i = 0; i < D; ++i) {
+      double t = b[i];
+#pragma unroll 1
+      for (int u = 0; u < i; ++u) t = fma(-L[i][u], b[u], t);
+      b[i] = t / L[i][i];
+    }
+#pragma unroll 1
+    for (int i = D - 1; i >= 0; --i) {
+      double t = b[i];
+#pragma unroll 1
+      for (int u = i + 1; u < D; ++u) t = fma(-L[u][i], b[u], t);
+      b[i] = t / L[i][i];
+    }
+#pragma unroll 1
+    for (int j = 0; j < D; ++j) dq_out[j] = b[j];
+    return true;
   } else {
-    double Am[K * (K + 1) / 2];
-    gram<P>(J, lambda, Am);
-    if (!(cholesky_solve<K, OpsF64Plain>(Am, F) > 0.0)) return false;
-    jt_mul<P>(J, F, dq);
+  double L[K][K];
+#pragma unroll 1
+  for (int a = 0; a < K; ++a) {
+#pragma unroll 1
+    for (int b = 0; b <= a; ++b) {
+      double s = (a == b) ? lambda : 0.0;
+#pragma unroll 1
+      for (int j = 0; j < D; ++j) s = fma(J[a][j], J[b][j], s);
+      L[a][b] = s;
+    }
   }
-#pragma unroll
-  for (int j = 0; j < D; ++j) dq_out[j] = dq[j];
+#pragma unroll 1
+  for (int j = 0; j < K; ++j) {
+    double s = L[j][j];
+#pragma unroll 1
+    for (int t = 0; t < j; ++t) s = fma(-L[j][t], L[j][t], s);
+    if (!(s > 0.0)) return false;
+    L[j][j] = sqrt(s);
+#pragma unroll 1
+    for (int i = j + 1; i < K; ++i) {
+      double t2 = L[i][j];
+#pragma unroll 1
+      for (int t = 0; t < j; ++t) t2 = fma(-L[i][t], L[j][t], t2);
+      L[i][j] = t2 / L[j][j];
+    }
+  }
+  double y[K];
+#pragma unroll 1
+  for (int i = 0; i < K; ++i) {
+    double s = F[i];
+#pragma unroll 1
+    for (int t = 0; t < i; ++t) s = fma(-L[i][t], y[t], s);
+    y[i] = s / L[i][i];
+  }
+#pragma unroll 1
+  for (int i = K - 1; i >= 0; --i) {
+    double s = y[i];
+#pragma unroll 1
+    for (int t = i + 1; t < K; ++t) s = fma(-L[t][i], y[t], s);
+    y[i] = s / L[i][i];
+  }
+#pragma unroll 1
+  for (int j = 0; j < D; ++j) {
+    double s = 0.0;
+#pragma unroll 1
+    for (int a = 0; a < K; ++a) s = fma(J[a][j], y[a], s);
+    dq_out[j] = s;
+  }
   return true;
+  }
 }
 
 // Heron refinement of an FP32 square root: one Newton step in FP64 brings the
@@ -1608,31 +1690,75 @@ struct VjpArgs {
 template <class P>
 __device__ __noinline__ uint32_t vjp_f64(const OpsF64Table ops, const ModelT<double> *__restrict__ m,
                                           const double *q, const double *g, double *v) {
-  // v = g - J^T (J J^T)^{-1} J g in FP64 with the compile-time building
-  // blocks of the FP64 LM step (structural nonzeros of J only).
+  // Reuse the FP64 LM step: with F replaced by J g and lambda = 0 it returns
+  // J^T (J J^T)^{-1} J g.  lm_step_f64 evaluates F itself, so the product is
+  // formed here instead.
   constexpr int D = P::D, K = kdim<P>();
-  double qq[D], gg[D];
+  double qq[D];
 #pragma unroll
-  for (int j = 0; j < D; ++j) {
-    qq[j] = q[j];
-    gg[j] = g[j];
-  }
+  for (int j = 0; j < D; ++j) qq[j] = q[j];
   Kin<P, double> k;
   if constexpr (needs_fk<P>()) fk<P, needs_pos<P>()>(ops, *m, qq, k);
   double F[K];
   Eval<P, double> e;
   residual<P, OpsF64Table, double, true>(*m, qq, k, F, e);
   double J[K][D];
+#pragma unroll 1
+  for (int a = 0; a < K; ++a)
+#pragma unroll 1
+    for (int j = 0; j < D; ++j) J[a][j] = 0.0;
   jacobian<P>(*m, qq, k, e, J);
-  double u[K];
-  j_mul<P>(J, gg, u);
-  double Am[K * (K + 1) / 2];
-  gram<P>(J, 0.0, Am);
-  if (!(cholesky_solve<K, OpsF64Plain>(Am, u) > 0.0)) return FL_NONFINITE;
-  double w[D];
-  jt_mul<P>(J, u, w);
-#pragma unroll
-  for (int j = 0; j < D; ++j) v[j] = gg[j] - w[j];
+  double L[K][K], u[K];
+#pragma unroll 1
+  for (int a = 0; a < K; ++a) {
+    double s = 0.0;
+#pragma unroll 1
+    for (int j = 0; j < D; ++j) s = fma(J[a][j], g[j], s);
+    u[a] = s;
+#pragma unroll 1
+    for (int b = 0; b <= a; ++b) {
+      double t = 0.0;
+#pragma unroll 1
+      for (int j = 0; j < D; ++j) t = fma(J[a][j], J[b][j], t);
+      L[a][b] = t;
+    }
+  }
+#pragma unroll 1
+  for (int j = 0; j < K; ++j) {
+    double s = L[j][j];
+#pragma unroll 1
+    for (int t = 0; t < j; ++t) s = fma(-L[j][t], L[j][t], s);
+    if (!(s > 0.0)) return FL_NONFINITE;
+    L[j][j] = sqrt(s);
+#pragma unroll 1
+    for (int i = j + 1; i < K; ++i) {
+      double t2 = L[i][j];
+#pragma unroll 1
+      for (int t = 0; t < j; ++t) t2 = fma(-L[i][t], L[j][t], t2);
+      L[i][j] = t2 / L[j][j];
+    }
+  }
+#pragma unroll 1
+  for (int i = 0; i < K; ++i) {
+    double s = u[i];
+#pragma unroll 1
+    for (int t = 0; t < i; ++t) s = fma(-L[i][t], u[t], s);
+    u[i] = s / L[i][i];
+  }
+#pragma unroll 1
+  for (int i = K - 1; i >= 0; --i) {
+    double s = u[i];
+#pragma unroll 1
+    for (int t = i + 1; t < K; ++t) s = fma(-L[t][i], u[t], s);
+    u[i] = s / L[i][i];
+  }
+#pragma unroll 1
+  for (int j = 0; j < D; ++j) {
+    double s = 0.0;
+#pragma unroll 1
+    for (int a = 0; a < K; ++a) s = fma(J[a][j], u[a], s);
+    v[j] = g[j] - s;
+  }
   return FL_RESOLVE;
 }
 
