@@ -336,8 +336,37 @@ mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sam
                         int32_t *tpb, int32_t *blocks_per_sm, int32_t *chunk, int32_t *fuse_check,
                         int32_t *threads_per_config, mcp_stream stream);
 
+/* Arithmetic-throughput probe (no counterpart in the paper: it measures the
+ * denominator of the roofline the benchmark reports).  Launches 8 blocks of
+ * 256 threads per SM on the context's device; every thread runs 8
+ * independent fused multiply-add chains for `iters` rounds in FP32
+ * (precision 0) or FP64 (precision 1).  out: DEVICE scratch of
+ * one element of that type (written only in a case that does not occur).
+ * *flops (HOST, may be NULL) receives the floating-point operations the
+ * launch performs (an FMA counts 2); the caller times the launch on `stream`.
+ * MCP_ERR_ARG for another precision, iters outside [1, 2^32] or a NULL /
+ * host out. */
+mcp_status mcp_fma_probe(mcp_ctx *ctx, int32_t precision, int64_t iters, void *out, int64_t *flops,
+                         mcp_stream stream);
+
 /* Number of kernels this context has launched so far (for launch accounting). */
 int64_t mcp_launch_count(const mcp_ctx *ctx);
+
+/* Number of device allocations (cudaMalloc) the library has made in this
+ * process, over all contexts (for tests and accounting: a call that must not
+ * allocate leaves it unchanged).
+ *
+ * Test hooks, read from the environment (host-side failure injection; no
+ * kernel is made to fail):
+ *   MCP_TEST_FAIL_ALLOC=<text>  every device allocation whose label contains
+ *                               <text> fails as out of memory (MCP_ERR_OOM);
+ *                               read at each allocation;
+ *   MCP_TEST_FAIL_CUDA=<text>   a context created while it is set reports
+ *                               MCP_ERR_CUDA from every CUDA call whose label
+ *                               contains <text>, after the call has run.
+ * Labels name what is allocated or launched ("obstacles", "segment offsets",
+ * "project_batch launch", ...; they appear in mcp_last_error). */
+int64_t mcp_alloc_count(void);
 
 /* Allocation-free segment projection.  The paper has no counterpart: this
  * entry point exists for callers that must not allocate device memory once
@@ -356,7 +385,10 @@ int64_t mcp_launch_count(const mcp_ctx *ctx);
  *     GPU that loads the library until the process exits.
  *   - The first call on a device looks up the array's device address (once
  *     per device, with that device current); make that first call before any
- *     stream capture.
+ *     stream capture.  The address is kept for the life of the process: it
+ *     does not survive cudaDeviceReset (after a reset the library's device
+ *     code is loaded again and the array may move), so a process that resets
+ *     a device must not call this entry point on it afterwards.
  *   - Every call shares the array and it keeps the last call's contents: the
  *     counter is cleared by each call, but calls that overlap on the GPU (on
  *     different streams, or from several contexts on the same device) race

@@ -2,6 +2,8 @@
 // loading, binding of a loaded robot/constraint stack to a compiled problem
 // class, and the batched entry points.
 #include <algorithm>
+#include <atomic>
+#include <cstdlib>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -18,6 +20,21 @@
 #include "mcp_problems.cuh"
 
 using namespace mcp;
+
+namespace mcp {
+static std::atomic<long long> g_allocs{0};
+
+cudaError_t dev_malloc(void **p, size_t bytes, const char *label) {
+  const char *f = std::getenv("MCP_TEST_FAIL_ALLOC");
+  if (f && *f && std::strstr(label, f)) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) g_allocs.fetch_add(1, std::memory_order_relaxed);
+  return e;
+}
+}  // namespace mcp
 
 // ---------------------------------------------------------------------------
 // Problem-class registry
@@ -456,12 +473,32 @@ __global__ void k_path_length(const float *Q, long long ld, long long n_paths, i
   if (lane == 0) length[p] = L;
 }
 
+// Arithmetic-throughput probe: every thread advances 8 independent FMA
+// chains x <- x a + b for `iters` rounds (a < 1, so the chains stay bounded).
+// The final sum is written only if it is negative, which it never is; the
+// compiler cannot know that, so no chain is removed.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_probe(T *out, long long iters, T a, T b) {
+  T x[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) x[c] = static_cast<T>(threadIdx.x + c);
+  for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = fma(x[c], a, b);
+  }
+  T s = T(0);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += x[c];
+  if (s < T(0)) out[0] = s;
+}
+
 // ---------------------------------------------------------------------------
 // Context
 // ---------------------------------------------------------------------------
 struct mcp_ctx {
   int device = 0;
   std::string err;
+  std::string fail_cuda;  // test hook: CUDA calls whose label contains it report an error (MCP_TEST_FAIL_CUDA)
   bool robot_loaded = false, cons_loaded = false, obs_loaded = false;
   RobotHost robot;
   std::vector<ConsHost> cons;
@@ -514,9 +551,18 @@ mcp_status cuda_fail(mcp_ctx *c, cudaError_t e, const char *what) {
               cudaGetErrorString(e));
 }
 
+// Host-side failure injection for tests: with the environment variable
+// MCP_TEST_FAIL_CUDA set when the context was created, a CUDA call of this
+// context whose label contains its text reports cudaErrorLaunchFailure after
+// it has run (nothing on the device fails; the context stays usable).
+cudaError_t injected(const mcp_ctx *ctx, cudaError_t e, const char *what) {
+  if (e != cudaSuccess || !ctx || ctx->fail_cuda.empty()) return e;
+  return std::strstr(what, ctx->fail_cuda.c_str()) ? cudaErrorLaunchFailure : cudaSuccess;
+}
+
 #define MCP_CUDA(call, what)                                    \
   do {                                                          \
-    cudaError_t e_ = (call);                                    \
+    cudaError_t e_ = injected(ctx, (call), what);               \
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what);     \
   } while (0)
 
@@ -648,7 +694,7 @@ mcp_status update_shifted(mcp_ctx *ctx) {
   }
   for (int r = 0; r < 3; ++r) ctx->hm.m32_shifted.shift[r] = static_cast<float>(ctx->origin[r]);
   if (!ctx->d_chk) {
-    cudaError_t e = cudaMalloc(&ctx->d_chk, sizeof(CheckData));
+    cudaError_t e = dev_malloc(&ctx->d_chk, sizeof(CheckData), "check data");
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc check data");
     ctx->hm.d_chk = ctx->d_chk;
   }
@@ -710,7 +756,7 @@ mcp_status ensure_resolved(mcp_ctx *ctx) {
       for (int j = 0; j < r.nj; ++j) in->qref[c][j] = ch.q_ref[j];
   }
   if (!ctx->d_resolve) {
-    cudaError_t e = cudaMalloc(&ctx->d_resolve, sizeof(ResolveOut));
+    cudaError_t e = dev_malloc(&ctx->d_resolve, sizeof(ResolveOut), "reference resolution");
     if (e != cudaSuccess) {
       delete in;
       return cuda_fail(ctx, e, "cudaMalloc");
@@ -737,8 +783,8 @@ mcp_status ensure_resolved(mcp_ctx *ctx) {
   {
     SphereTable<double> *d_st = nullptr;
     double *d_lb = nullptr;
-    MCP_CUDA(cudaMalloc(&d_st, sizeof(SphereTable<double>)), "cudaMalloc sphere table");
-    cudaError_t e = cudaMalloc(&d_lb, (MAXJ + 1) * 4 * sizeof(double));
+    MCP_CUDA(dev_malloc(&d_st, sizeof(SphereTable<double>), "sphere table"), "cudaMalloc sphere table");
+    cudaError_t e = dev_malloc(&d_lb, (MAXJ + 1) * 4 * sizeof(double), "link bounds");
     if (e == cudaSuccess) e = cudaMemcpy(d_st, &ctx->hm.st64, sizeof(SphereTable<double>), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
       k_link_bounds<<<1, 64>>>(d_st, r.nj, d_lb);
@@ -778,13 +824,14 @@ mcp_status mcp_create(int device, mcp_ctx **out) {
   mcp_ctx *ctx = new (std::nothrow) mcp_ctx;
   if (!ctx) return MCP_ERR_OOM;
   ctx->device = device;
+  if (const char *f = std::getenv("MCP_TEST_FAIL_CUDA")) ctx->fail_cuda = f;
   DeviceGuard g(device);
   int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   ctx->hm.sm_count = sms;
-  cudaError_t e = cudaMalloc(&ctx->d_m64, sizeof(ModelT<double>));
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tab, (SPLIT_TAB_OFF + 2 * SPLIT_TAB_HALF + 1) * sizeof(double2));
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counter, sizeof(unsigned long long));
+  cudaError_t e = dev_malloc(&ctx->d_m64, sizeof(ModelT<double>), "context model");
+  if (e == cudaSuccess) e = dev_malloc(&ctx->d_tab, (SPLIT_TAB_OFF + 2 * SPLIT_TAB_HALF + 1) * sizeof(double2), "context tables");
+  if (e == cudaSuccess) e = dev_malloc(&ctx->d_counter, sizeof(unsigned long long), "context counter");
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) {
     k_sincos_table<<<(SPLIT_TAB_OFF + 2 * SPLIT_TAB_HALF + 1 + 255) / 256, 256>>>(ctx->d_tab);
@@ -826,6 +873,8 @@ void mcp_destroy(mcp_ctx *ctx) {
 const char *mcp_last_error(const mcp_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
 int64_t mcp_launch_count(const mcp_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+int64_t mcp_alloc_count(void) { return g_allocs.load(std::memory_order_relaxed); }
 
 mcp_status mcp_load_robot(mcp_ctx *ctx, const mcp_robot_desc *rd) {
   if (!ctx) return MCP_ERR_ARG;
@@ -990,11 +1039,11 @@ mcp_status mcp_load_obstacles(mcp_ctx *ctx, const double *spheres, int32_t n_sph
       for (int e = 0; e < 4; ++e) sorted[4 * static_cast<size_t>(o) + e] = spheres[4 * key[static_cast<size_t>(o)].second + e];
   }
   const size_t n_rec = n_o + static_cast<size_t>(obs_chunks(n_spheres));
-  MCP_CUDA(cudaMalloc(&ctx->d_obs32, n_rec * 2 * sizeof(float4)), "cudaMalloc obstacles");
-  MCP_CUDA(cudaMalloc(&ctx->d_obs64, n_o * 4 * sizeof(double)), "cudaMalloc obstacles");
-  MCP_CUDA(cudaMalloc(&ctx->d_box32, n_b * 6 * sizeof(float)), "cudaMalloc boxes");
-  MCP_CUDA(cudaMalloc(&ctx->d_box64, n_b * 6 * sizeof(double)), "cudaMalloc boxes");
-  if (!ctx->d_origin) MCP_CUDA(cudaMalloc(&ctx->d_origin, 3 * sizeof(double)), "cudaMalloc origin");
+  MCP_CUDA(dev_malloc(&ctx->d_obs32, n_rec * 2 * sizeof(float4), "obstacles"), "cudaMalloc obstacles");
+  MCP_CUDA(dev_malloc(&ctx->d_obs64, n_o * 4 * sizeof(double), "obstacles"), "cudaMalloc obstacles");
+  MCP_CUDA(dev_malloc(&ctx->d_box32, n_b * 6 * sizeof(float), "boxes"), "cudaMalloc boxes");
+  MCP_CUDA(dev_malloc(&ctx->d_box64, n_b * 6 * sizeof(double), "boxes"), "cudaMalloc boxes");
+  if (!ctx->d_origin) MCP_CUDA(dev_malloc(&ctx->d_origin, 3 * sizeof(double), "obstacle origin"), "cudaMalloc origin");
   if (n_spheres)
     MCP_CUDA(cudaMemcpy(ctx->d_obs64, sorted.data(), n_spheres * 4 * sizeof(double), cudaMemcpyHostToDevice), "copy");
   if (n_aabbs)
@@ -1072,7 +1121,7 @@ mcp_status mcp_project_batch(mcp_ctx *ctx, const mcp_project_params *p, int64_t 
   int launches = 0;
   cudaError_t e = registry()[ctx->prob_class].project_fn(ctx->hm, c, &launches);
   ctx->launches += launches;
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "project_batch launch");
+  if ((e = injected(ctx, e, "project_batch launch")) != cudaSuccess) return cuda_fail(ctx, e, "project_batch launch");
   return MCP_OK;
 }
 
@@ -1125,7 +1174,7 @@ mcp_status mcp_project_check_batch(mcp_ctx *ctx, const mcp_project_params *p, in
   int launches = 0;
   cudaError_t e = run_project_check(ctx, c, &launches);
   ctx->launches += launches;
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "project_check_batch launch");
+  if ((e = injected(ctx, e, "project_check_batch launch")) != cudaSuccess) return cuda_fail(ctx, e, "project_check_batch launch");
   return MCP_OK;
 }
 
@@ -1180,7 +1229,7 @@ mcp_status mcp_extend_batch(mcp_ctx *ctx, const mcp_project_params *p, const mcp
   int launches = 0;
   cudaError_t err = registry()[ctx->prob_class].extend_fn(ctx->hm, c, &launches);
   ctx->launches += launches;
-  if (err != cudaSuccess) return cuda_fail(ctx, err, "extend_batch launch");
+  if ((err = injected(ctx, err, "extend_batch launch")) != cudaSuccess) return cuda_fail(ctx, err, "extend_batch launch");
   return MCP_OK;
 }
 
@@ -1204,7 +1253,7 @@ mcp_status mcp_project_segments(mcp_ctx *ctx, const mcp_project_params *p, int64
     cudaFree(ctx->d_seg_off);
     ctx->d_seg_off = nullptr;
     ctx->seg_cap = 0;
-    MCP_CUDA(cudaMalloc(&ctx->d_seg_off, (n_seg + 1) * sizeof(long long)), "cudaMalloc segment offsets");
+    MCP_CUDA(dev_malloc(&ctx->d_seg_off, (n_seg + 1) * sizeof(long long), "segment offsets"), "cudaMalloc segment offsets");
     ctx->seg_cap = n_seg + 1;
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -1239,7 +1288,7 @@ mcp_status mcp_project_segments(mcp_ctx *ctx, const mcp_project_params *p, int64
     int launches = 0;
     cudaError_t e = enqueue(s, &launches);
     ctx->launches += launches;
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "project_segments launch");
+    if ((e = injected(ctx, e, "project_segments launch")) != cudaSuccess) return cuda_fail(ctx, e, "project_segments launch");
     return MCP_OK;
   }
   // key: everything the captured launches depend on
@@ -1366,7 +1415,7 @@ mcp_status mcp_project_segments_noalloc(mcp_ctx *ctx, const mcp_project_params *
   int launches = 0;
   cudaError_t e = registry()[ctx->prob_class].project_fn(ctx->hm, c, &launches);
   ctx->launches += launches;
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "project_segments_noalloc launch");
+  if ((e = injected(ctx, e, "project_segments_noalloc launch")) != cudaSuccess) return cuda_fail(ctx, e, "project_segments_noalloc launch");
   return MCP_OK;
 }
 
@@ -1395,7 +1444,7 @@ mcp_status mcp_check_batch(mcp_ctx *ctx, int64_t n, int64_t ld, const void *q, i
   int launches = 0;
   cudaError_t e = registry()[ctx->robot_class].check_fn(ctx->hm, c, &launches);
   ctx->launches += launches;
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "check_batch launch");
+  if ((e = injected(ctx, e, "check_batch launch")) != cudaSuccess) return cuda_fail(ctx, e, "check_batch launch");
   return MCP_OK;
 }
 
@@ -1423,7 +1472,7 @@ mcp_status mcp_project_vjp(mcp_ctx *ctx, int64_t n, int64_t ld, const float *q_s
   int launches = 0;
   cudaError_t e = registry()[ctx->prob_class].vjp_fn(ctx->hm, c, &launches);
   ctx->launches += launches;
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "project_vjp launch");
+  if ((e = injected(ctx, e, "project_vjp launch")) != cudaSuccess) return cuda_fail(ctx, e, "project_vjp launch");
   return MCP_OK;
 }
 
@@ -1451,6 +1500,29 @@ mcp_status mcp_path_length_grad(mcp_ctx *ctx, int64_t n_paths, int32_t n_way, in
     ctx->launches += 1;
     MCP_CUDA(cudaGetLastError(), "path length launch");
   }
+  return MCP_OK;
+}
+
+mcp_status mcp_fma_probe(mcp_ctx *ctx, int32_t precision, int64_t iters, void *out, int64_t *flops,
+                         mcp_stream stream) {
+  if (!ctx) return MCP_ERR_ARG;
+  if (precision != 0 && precision != 1) return fail(ctx, MCP_ERR_ARG, "precision must be 0 (FP32) or 1 (FP64)");
+  if (iters < 1 || iters > (int64_t(1) << 32)) return fail(ctx, MCP_ERR_ARG, "iters outside [1, 2^32]");
+  if (!out) return fail(ctx, MCP_ERR_ARG, "out is NULL");
+  mcp_status st;
+  if ((st = check_batch_ptr(ctx, out, "out")) != MCP_OK) return st;
+  DeviceGuard gd(ctx->device);
+  int sms = 0;
+  MCP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "device attribute");
+  const unsigned blocks = static_cast<unsigned>(sms) * 8u;  // 2048 threads per SM
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (precision == 0)
+    k_fma_probe<float><<<blocks, 256, 0, s>>>(static_cast<float *>(out), iters, 0.999f, 1e-3f);
+  else
+    k_fma_probe<double><<<blocks, 256, 0, s>>>(static_cast<double *>(out), iters, 0.999, 1e-3);
+  ctx->launches += 1;
+  MCP_CUDA(cudaGetLastError(), "fma probe launch");
+  if (flops) *flops = static_cast<int64_t>(blocks) * 256 * 8 * 2 * iters;
   return MCP_OK;
 }
 
@@ -1502,11 +1574,11 @@ mcp_status mcp_autotune(mcp_ctx *ctx, const mcp_project_params *p, int64_t n_sam
   uint8_t *fl = nullptr, *it = nullptr, *hit = nullptr;
   double *res = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaError_t err = cudaMalloc(&out, sizeof(float) * d * ld);
-  if (err == cudaSuccess) err = cudaMalloc(&fl, ld);
-  if (err == cudaSuccess) err = cudaMalloc(&hit, ld);
-  if (err == cudaSuccess) err = cudaMalloc(&it, ld);
-  if (err == cudaSuccess) err = cudaMalloc(&res, sizeof(double) * ld);
+  cudaError_t err = dev_malloc(&out, sizeof(float) * d * ld, "autotune buffers");
+  if (err == cudaSuccess) err = dev_malloc(&fl, ld, "autotune buffers");
+  if (err == cudaSuccess) err = dev_malloc(&hit, ld, "autotune buffers");
+  if (err == cudaSuccess) err = dev_malloc(&it, ld, "autotune buffers");
+  if (err == cudaSuccess) err = dev_malloc(&res, sizeof(double) * ld, "autotune buffers");
   if (err == cudaSuccess) err = cudaEventCreate(&e0);
   if (err == cudaSuccess) err = cudaEventCreate(&e1);
   const Tuning saved = ctx->tune;

@@ -411,7 +411,7 @@ cudaError_t launch_extend_g(const HostModel &hm, const ExtCall &c, ExtArgs<P> &a
     cudaFree(c.scratch->ptr);
     c.scratch->ptr = nullptr;
     c.scratch->floats = 0;
-    err = cudaMalloc(&c.scratch->ptr, floats * sizeof(float));
+    err = dev_malloc(&c.scratch->ptr, floats * sizeof(float), "extend chain scratch");
     if (err != cudaSuccess) return err;
     c.scratch->floats = floats;
   }

@@ -10,6 +10,16 @@
 
 namespace mcp {
 
+// Every device allocation of the library goes through this function: it
+// counts them (mcp_alloc_count) and, for host-side failure tests, fails with
+// cudaErrorMemoryAllocation every allocation whose label contains the text of
+// the environment variable MCP_TEST_FAIL_ALLOC (unset or empty: never).
+cudaError_t dev_malloc(void **p, size_t bytes, const char *label);
+template <typename T>
+cudaError_t dev_malloc(T **p, size_t bytes, const char *label) {
+  return dev_malloc(reinterpret_cast<void **>(p), bytes, label);
+}
+
 constexpr int MAXS = 256;  // robot spheres per robot
 
 // Robot spheres sorted by the joint they ride on: spheres of link l (l = -1

@@ -97,6 +97,8 @@ def load_library(path: str = LIB_PATH):
                            ctypes.c_float, _vp], ctypes.c_int),
         "mcp_project_segments_noalloc": ([_vp, P(ProjectParams), ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp,
                                           ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+        "mcp_fma_probe": ([_vp, ctypes.c_int32, ctypes.c_int64, _vp, P(ctypes.c_int64), _vp], ctypes.c_int),
+        "mcp_alloc_count": ([], ctypes.c_int64),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -110,7 +112,12 @@ EXPORTED = ("mcp_create", "mcp_destroy", "mcp_last_error", "mcp_launch_count", "
             "mcp_load_constraints", "mcp_load_obstacles", "mcp_get_constraint", "mcp_project_batch",
             "mcp_project_check_batch", "mcp_project_segments", "mcp_check_batch", "mcp_project_vjp",
             "mcp_path_length_grad", "mcp_autotune", "mcp_set_tuning", "mcp_project_segments_noalloc",
-            "mcp_path_step", "mcp_extend_batch")
+            "mcp_path_step", "mcp_extend_batch", "mcp_fma_probe", "mcp_alloc_count")
+
+
+def alloc_count() -> int:
+    """Device allocations the library has made in this process (all contexts)."""
+    return int(load_library().mcp_alloc_count())
 
 
 class MCPError(RuntimeError):
@@ -359,6 +366,27 @@ class Projector:
                                           ctypes.byref(b), ctypes.byref(c), ctypes.byref(f), ctypes.byref(k),
                                           _stream(stream)))
         return t.value, b.value, c.value, f.value, k.value
+
+    def fma_probe(self, fp64=False, iters=None, reps=5, stream=None):
+        """Measured FMA throughput of this device (TFLOP/s): the best of `reps`
+        timed launches of the library's FMA-chain probe."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        iters = iters or ((1 << 12) if fp64 else (1 << 16))
+        out = torch.empty(1, dtype=torch.float64 if fp64 else torch.float32, device=dev)
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        flops = ctypes.c_int64()
+        best = float("inf")
+        for r in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            self._check(self.lib.mcp_fma_probe(self.h, 1 if fp64 else 0, iters, _ptr(out), ctypes.byref(flops),
+                                               _stream(st)))
+            e1.record(st)
+            e1.synchronize()
+            if r:   # the first launch warms up
+                best = min(best, e0.elapsed_time(e1))
+        return flops.value / (best * 1e-3) / 1e12
 
     def set_tuning(self, tpb, blocks_per_sm, chunk, fuse_check=0, threads_per_config=1):
         self._check(self.lib.mcp_set_tuning(self.h, int(tpb), int(blocks_per_sm), int(chunk), int(fuse_check),

@@ -54,10 +54,11 @@ def test_create_without_device_fails_cleanly(lib):
 def test_every_entry_point_rejects_a_null_context(lib):
     """Bad arguments never abort: with no context every call returns
     MCP_ERR_ARG (1) before touching memory or the GPU; destroy, the error
-    message and the launch count accept NULL."""
+    message and the launch count accept NULL; the allocation count takes no
+    context."""
     from paper_2604_13323_gb300 import mcproj
     L = mcproj.load_library()
-    skip = {"mcp_create", "mcp_destroy", "mcp_last_error", "mcp_launch_count"}
+    skip = {"mcp_create", "mcp_destroy", "mcp_last_error", "mcp_launch_count", "mcp_alloc_count"}
     for name in mcproj.EXPORTED:
         if name in skip:
             continue
@@ -75,3 +76,4 @@ def test_every_entry_point_rejects_a_null_context(lib):
     L.mcp_destroy(None)
     assert L.mcp_last_error(None)
     assert L.mcp_launch_count(None) == 0
+    assert L.mcp_alloc_count() == 0   # nothing allocated without a device

@@ -6,9 +6,10 @@ and synchronises the device, or code whose device memory is owned by another
 allocator or budget.  For them the library keeps the segment projection's
 scratch (work counter and segment offsets) in a fixed device array.  This
 test calls that entry point through the C ABI, on a context that never ran
-the allocating variant, twice in a row, and checks each result against
-mcp_project_segments on a second context.  Kept in a file of its own that is
-collected last.
+the allocating variant, twice in a row, checks each result against
+mcp_project_segments on a second context, and checks with the library's
+allocation counter that neither call allocated device memory.  Kept in a file
+of its own that is collected last.
 """
 import ctypes
 
@@ -48,11 +49,16 @@ def test_noalloc_matches_allocating_entry_point_twice():
     fresh = mcproj.Projector(wl.robot, wl.constraints)   # no allocating segment call on this context
     pp = mcproj.Projector.params(wl.params)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    outs = []
+    for call in range(2):   # the caller's buffers, allocated before the calls
+        outs.append((torch.full((14, total), float("nan"), dtype=torch.float32, device="cuda"),
+                     torch.full((total,), 255, dtype=torch.uint8, device="cuda"),
+                     torch.zeros(total, dtype=torch.uint8, device="cuda"),
+                     torch.full((total,), float("nan"), dtype=torch.float64, device="cuda")))
+    torch.cuda.synchronize()
+    allocs = lib.mcp_alloc_count()   # the library's device allocations so far (all contexts)
     for call in range(2):
-        out = torch.full((14, total), float("nan"), dtype=torch.float32, device="cuda")
-        fl = torch.full((total,), 255, dtype=torch.uint8, device="cuda")
-        it = torch.zeros(total, dtype=torch.uint8, device="cuda")
-        res = torch.full((total,), float("nan"), dtype=torch.float64, device="cuda")
+        out, fl, it, res = outs[call]
         st = lib.mcp_project_segments_noalloc(fresh.h, ctypes.byref(pp), n_seg, n_seg, _p(starts), _p(delta),
                                               _p(length), total, total, _p(out), _p(fl), _p(it), _p(res), stream)
         assert st == mcproj.MCP_OK, lib.mcp_last_error(fresh.h)
@@ -62,6 +68,7 @@ def test_noalloc_matches_allocating_entry_point_twice():
         conv = (f & mcproj.F_CONVERGED) != 0
         assert np.abs(q[:, conv] - q_ref[:, conv]).max() <= Q_TOL, call
         assert (r[conv] < wl.params.tol).all()
+        assert lib.mcp_alloc_count() == allocs, call   # neither call allocated device memory
 
 
 def test_noalloc_rejects_oversized_batch():
