@@ -4,12 +4,22 @@
 A step is one pass of the whole hot path over one batch: projection (FP32
 Newton/LM steps with FP64 acceptance, Alg. 2 ParallelProject) followed by the
 sphere collision check of every projected configuration (CollisionFree).
-The default workload is the 7-DoF arm with the end-effector orientation
-constraint, 65,536 configurations (tol 1e-5, cap 30, lambda 1e-6; 60 link
-spheres against 64 obstacle spheres).
+The default workload is the largest configuration that fits one GPU: the
+36-DoF humanoid (feet fixed in 6-D, hands in a fixed relative pose, centre of
+mass over the feet: 20 equations), 1,048,576 configurations, tol 1e-5, cap
+40, lambda 1e-6; 150 link spheres against 200 obstacle spheres and 6 boxes.
+Its line also carries:
+  * vs_plain_fp64: the plain per-configuration FP64 kernel projecting the same
+    configurations, and the ratio of the projection kernels' throughputs;
+  * sub_records: the 7-DoF arm (65,536), the dual-arm uneven segments
+    (262,240 points in one persistent launch), the VJP (65,536) and path
+    shortening (4,096 x 64 x 100), each with its own value and roofline;
+  * cpu_baseline: the FP64 oracle on the host cores, and under it the
+    whole-batch parity of the GPU's outputs against the oracle and the
+    oracle-counted algorithmic flops the roofline divides.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload arm|dual_arm|sphere] [--precision fp32|fp64]
+                    [--workload humanoid|arm|dual_segments|...] [--precision fp32|fp64]
 
 Prints one JSON line (rank 0).  Under torchrun each rank projects its own
 seeded batch of the same size (independent problems, no collective on the
@@ -53,7 +63,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="arm", choices=["arm", "dual_arm", "dual_segments", "sphere", "humanoid",
+    ap.add_argument("--workload", default="humanoid", choices=["arm", "dual_arm", "dual_segments", "sphere", "humanoid",
                                                           "arm_tray", "arm_peg", "arm_tsr", "dual_rod", "extend",
                                                           "humanoid_hull", "vjp", "shorten"])
     ap.add_argument("--cyclic", action="store_true",
@@ -66,6 +76,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=0,
                     help="use only the first N configurations (small cases for profilers; not a bench line)")
+    ap.add_argument("--shard", action="store_true",
+                    help="under torchrun: split ONE batch over the ranks (contiguous ranges, or whole segments "
+                         "balanced by length) and gather the outputs on the host (strong scaling); default: "
+                         "one batch per rank (replicas, weak scaling)")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="the headline workload only (no arm / dual-arm / VJP / shortening sub-records)")
+    ap.add_argument("--no-parity", action="store_true",
+                    help="skip the oracle's whole-batch parity and flop count (the CPU baseline still runs)")
     ap.add_argument("--profile", action="store_true",
                     help="fixed launch count for profilers: no time-padded warm-up, no CPU baseline, no e2e pass")
     return ap.parse_args()
@@ -169,61 +187,86 @@ def apply_overrides(wl, name, args):
     return name
 
 
-def _parity_vs_gpu(O, q0, p, out, fl, it, hit, margin, gpu):
-    """The GPU's outputs for the first configurations of the batch against
-    the oracle's, as the parity tests compare them: flags over all of them;
-    points (where both converged after the same number of steps) and
-    collision verdicts (outside the 1e-5 m contact band) over the starts whose
-    oracle result is stable under +-1e-6 relative perturbations (elsewhere the
-    oracle disagrees with itself by as much)."""
+def oracle_leg(wl, q, gpu=None, budget_s=10.0, whole_batch=True, reps=8):
+    """The benchmark's CPU-baseline leg, the one place it runs the FP64 oracle.
+
+    1. cpu_baseline: the oracle as it stands (projection + collision check,
+       all host cores) on contiguous chunks of the batch for ~budget_s.
+    2. parity (untimed, with the GPU's outputs `gpu` = (q [d, n], flags,
+       iters, hit)): the oracle projects the WHOLE batch, plus 8 perturbed
+       copies of it (8 unit roundoffs of FP32) that tell which starts have a
+       result determined to the 1e-4 rad point bar; reported over all of it:
+       flag agreement, equal step counts, the largest point error where the
+       result is determined, the share of converged outputs (both sides)
+       beyond 1e-4, collision verdicts outside the 1e-5 m contact band.
+    3. algorithmic flops: the operation-counting build of the oracle on a
+       sample of 256 configurations gives the flops of one evaluation of F and
+       of one LM step; with the ORACLE's step counts over the whole batch
+       (extra GPU steps earn nothing): FP32 = sum(iters) x step + n x eval,
+       FP64 = n x eval (the acceptance).  sin / cos / sqrt / atan2 are
+       special functions, counted apart.
+    Returns (cpu_baseline, parity or None, flops or None)."""
     from oracle import oracle as orc
     from oracle import parity as par
-    n = q0.shape[1]
-    qg, fg, ig, hg = (a[..., :n] for a in gpu)
-    el, _ = par.eligible_mask(O, q0, p.tol, p.max_iters, p.lam, max_step=p.max_step, cyclic=p.cyclic)
-    cg, co = (fg & orc.CONVERGED) != 0, (fl & orc.CONVERGED) != 0
-    both = cg & co
-    same = both & (ig == it) & el
-    err = np.abs(qg[:, same].astype(np.float64) - out[:, same]).max(axis=0) if same.any() else np.zeros(1)
-    band = both & el & (margin >= 1e-5)
-    return {"configs": int(n), "eligible": float(el.mean()), "flag_agree": float((cg == co).mean()),
-            "flag_agree_eligible": float((cg == co)[el].mean()) if el.any() else 1.0,
-            "iters_equal_eligible": float(same.sum() / max(1, (both & el).sum())),
-            "q_err_max_eligible": float(err.max()), "q_err_p999_eligible": float(np.quantile(err, 0.999)),
-            "hit_agree_outside_band": float(((hg != 0) == (hit != 0))[band].mean()) if band.any() else 1.0}
-
-
-def cpu_baseline(wl, q, budget_s=10.0, gpu=None):
-    """The FP64 oracle, as it stands, on the host cores: projection + check of
-    contiguous chunks of the workload until ~budget_s of wall time.  With the
-    GPU's outputs of the same batch (`gpu`: q [d, n], flags, iters, hit), the
-    first chunk is also compared with them."""
-    from oracle import oracle as orc
     O = orc.Oracle(wl.robot, wl.constraints, wl.obstacles)
     threads = orc.default_threads()
     p = wl.params
     chunk = 4096
     done = conv = 0
-    parity = None
     t0 = time.perf_counter()
     off = 0
     while time.perf_counter() - t0 < budget_s:
         sl = q[:, off:off + chunk]
         out, fl, it, r = O.project(sl, p.tol, p.max_iters, p.lam, max_step=p.max_step, cyclic=p.cyclic,
                                    threads=threads)
-        hit, margin = O.check(out, threads=threads)
-        if gpu is not None and parity is None and off == 0:
-            parity = _parity_vs_gpu(O, sl, p, out, fl, it, hit, margin, gpu)
+        O.check(out, threads=threads)
         conv += int(((fl & orc.CONVERGED) != 0).sum())
         done += sl.shape[1]
         off = (off + chunk) % q.shape[1]
     dt = time.perf_counter() - t0
-    res = {"value": conv / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+    cpu = {"value": conv / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
            "sample": f"{done} configurations (contiguous chunks of {chunk} of the bench batch), "
                      f"projection + collision check, FP64, {dt:.1f} s wall"}
-    if parity is not None:
-        res["parity_vs_gpu"] = parity
-    return res
+    if not whole_batch or gpu is None:
+        return cpu, None, None
+    t1 = time.perf_counter()
+    n = q.shape[1]
+    selfst = {}
+    el, (qo, fo, io, ro) = par.eligible_mask(O, q, p.tol, p.max_iters, p.lam, max_step=p.max_step,
+                                             cyclic=p.cyclic, reps=reps, stats=selfst)
+    qg, fg, ig, hg = gpu
+    cg, co = (fg & orc.CONVERGED) != 0, (fo & orc.CONVERGED) != 0
+    both = cg & co
+    same = both & (ig.astype(np.int64) == io)
+    err = np.abs(qg.astype(np.float64) - qo).max(axis=0)
+    cmp_ = same & el
+    hit_o, margin = O.check(qg.astype(np.float64), threads=threads)
+    band = margin >= 1e-5
+    parity = {"configs": int(n), "scope": "whole batch", "eligible": float(el.mean()),
+              "eligibility": f"oracle result moves <= 1e-4 under {reps} perturbations of 8 FP32 unit roundoffs",
+              "flag_agree": float((cg == co).mean()),
+              "flag_agree_eligible": float((cg == co)[el].mean()) if el.any() else 1.0,
+              "oracle_self_flip_rate": selfst.get("self_flip_rate"),
+              "iters_equal": float(same.sum() / max(1, both.sum())),
+              "compared": int(cmp_.sum()),
+              "q_err_max_eligible": float(err[cmp_].max()) if cmp_.any() else 0.0,
+              "q_err_p999_eligible": float(np.quantile(err[cmp_], 0.999)) if cmp_.any() else 0.0,
+              "eligible_beyond_1e-4": int((err[cmp_] > 1e-4).sum()),
+              "converged_beyond_1e-4": float((err[both] > 1e-4).mean()) if both.any() else 0.0,
+              "hit_agree_outside_band": float(((hg != 0) == (hit_o != 0))[band].mean()) if band.any() else 1.0,
+              "hit_excluded_band": int((~band).sum()),
+              "wall_s": round(time.perf_counter() - t1, 1)}
+    idx = np.linspace(0, n - 1, min(n, 256)).astype(np.int64)
+    cnt = O.count_ops(q[:, idx], p)
+    ev = cnt["eval"].mean(axis=0)
+    st = cnt["step"].mean(axis=0)
+    eval_f, step_f = float(ev[:3].sum()), float(st[:3].sum())
+    flops = {"fp32": float(io.sum()) * step_f + n * eval_f, "fp64": n * eval_f,
+             "per_step": step_f, "per_eval": eval_f, "oracle_mean_iters": float(io.mean()),
+             "special_per_step": dict(zip(orc.OP_NAMES[3:], [float(v) for v in st[3:]])),
+             "source": "operation-counting build of the oracle (256 sampled configurations) x the oracle's "
+                       "step counts over the whole batch"}
+    return cpu, parity, flops
 
 
 def run_reference(args):
@@ -390,26 +433,113 @@ def run_reference_extend(args):
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args):
+def init_dist():
+    """(world, rank, local rank, device) of this process; NCCL process group
+    for the replica aggregation under torchrun."""
     import torch
     import torch.distributed as dist
-
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    return world, rank, local, torch.device("cuda", local)
 
+
+def measured_peaks(local):
+    """FP32 and FP64 FMA throughput of this GPU, measured with the library's
+    FMA-chain probe (TFLOP/s), for the roofline's denominators."""
+    from paper_2604_13323_gb300 import mcproj
+    from paper_2604_13323_gb300 import workloads as W
+    P = mcproj.Projector(W.sphere_workload(n_pairs=2).robot, device=local)
+    try:
+        return {"fp32_fma": P.fma_probe(fp64=False), "fp64_fma": P.fma_probe(fp64=True),
+                "source": "mcp_fma_probe: 8 blocks of 256 threads per SM, 8 independent FMA chains per thread, "
+                          "best of 5 launches, CUDA events"}
+    finally:
+        P.close()
+
+
+def run_ours(args):
+    """The step on the requested workload; for the default (the humanoid, the
+    largest configuration that fits one GPU) the line also carries the arm,
+    the dual-arm segments, the VJP and path shortening as sub-records."""
+    import torch.distributed as dist
+    world, rank, local, dev = init_dist()
     from paper_2604_13323_gb300 import build as B
     B.build()
+    peaks = None if args.profile else measured_peaks(local)
+    env = {"world": world, "rank": rank, "local": local, "dev": dev, "peaks": peaks}
+    line = measure_batch(args, args.workload, env)
+    if line is not None and args.workload == "humanoid" and not (args.profile or args.batch or args.no_sub):
+        subs = {}
+        for w in ("arm", "dual_segments"):
+            subs[w] = compact(measure_batch(args, w, env, sub=True))
+        for w in ("vjp", "shorten"):
+            subs[w] = compact(run_adjoint(args, env, w, sub=True))
+        line["sub_records"] = subs
+    if line is not None and rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def compact(line):
+    """The parts of a workload's line kept as a sub-record of the headline."""
+    if line is None:
+        return None
+    keep = {k: line[k] for k in ("metric", "value", "unit", "ms_per_step", "dtype") if k in line}
+    keep["workload"] = line["config"]["workload"]
+    r = line.get("roofline") or {}
+    keep["roofline"] = {k: r[k] for k in ("kernel", "bound", "achieved", "peak", "frac", "fp64_frac",
+                                          "mixed_bound_frac") if k in r}
+    for k in ("vs_plain_fp64", "e2e"):
+        if line.get(k):
+            keep[k] = line[k]
+    for k in ("mean_length_reduction", "max_resid"):
+        if k in line.get("config", {}):
+            keep[k] = line["config"][k]
+    return keep
+
+
+def measure_batch(args, name, env, sub=False):
+    """One workload of the batch / segment projection: warm-up, the timed
+    steps (projection + collision check), the plain FP64 kernel on the same
+    configurations, end to end through the C ABI with host buffers, the
+    oracle leg (CPU baseline, whole-batch parity, counted flops) and the
+    roofline.  `sub`: a sub-record (no e2e, no oracle leg).  Returns the line
+    (rank 0) or None."""
+    import torch
+    world, rank, local, dev = env["world"], env["rank"], env["local"], env["dev"]
     from paper_2604_13323_gb300 import flops as FL
     from paper_2604_13323_gb300 import mcproj
     from paper_2604_13323_gb300 import workloads as W
 
-    wl, q_np, wname, segs = make_workload(args.workload, rank)
+    sharded = bool(args.shard) and world > 1
+    # replicas: each rank its own seeded batch; --shard: every rank the same
+    # batch, of which it projects its contiguous part
+    wl, q_np, wname, segs = make_workload(name, 0 if sharded else rank)
     wname = apply_overrides(wl, wname, args)
+    shard_info = None
+    if sharded:
+        from paper_2604_13323_gb300 import shard as SHD
+        if segs is None:
+            rr = SHD.batch_ranges(q_np.shape[1], world)
+            a_, b_ = rr[rank]
+            q_np = q_np[:, a_:b_]
+            shard_info = {"partition": "contiguous configuration ranges", "ranges": rr,
+                          "total": int(rr[-1][1])}
+        else:
+            lens = wl.extra["lengths"]
+            sr = SHD.segment_ranges(lens, world)
+            a_, b_ = sr[rank]
+            for key in ("raw_start", "raw_dir"):
+                wl.extra[key] = np.ascontiguousarray(wl.extra[key][:, a_:b_])
+            wl.extra["lengths"] = np.ascontiguousarray(lens[a_:b_])
+            pr = SHD.point_ranges(lens, sr)
+            shard_info = {"partition": "runs of whole segments balanced by their lengths", "ranges": pr,
+                          "segment_ranges": sr, "total": int(pr[-1][1])}
     if args.batch and q_np is not None:
         q_np = q_np[:, :args.batch]
         wname += f"_first{args.batch}"
@@ -476,7 +606,7 @@ def run_ours(args):
     # launch shape: the library's autotuner over threads per block, resident
     # blocks per SM and claim size, on this batch (setup, untimed)
     tuning = None
-    if not fp64 and not args.workload.startswith("humanoid"):
+    if not fp64 and not name.startswith("humanoid"):
         if args.launch:   # a fixed shape (profiler runs reproduce the tuned one)
             vals = [int(v) for v in args.launch.split(",")]
             P.set_tuning(*vals)
@@ -580,7 +710,7 @@ def run_ours(args):
         return done
 
     e2e_ms = []
-    if not args.profile:
+    if not (args.profile or sub):
         last = None
         for s_ in range(args.warmup):
             last = e2e_step(s_ % NB, last)
@@ -619,15 +749,44 @@ def run_ours(args):
         e2e["serial_value"] = e2e_c / (ser_max * 1e-3)
         e2e["serial_ms_per_step"] = ser_max
 
+    # ---- the plain per-configuration FP64 kernel on the same configurations ----
+    plain = None
+    if not fp64 and not args.profile:
+        plain = plain_fp64_run(P, wl, q_in, seg_args, n, d, dev, stream, flush, args, world)
+        if plain is not None:
+            mp32 = sum(t_proj) / len(t_proj)
+            fp32_proj_value = conv / (mp32 * 1e-3)
+            plain["fp32_projection"] = {"value": fp32_proj_value, "ms": mp32, "converged": conv}
+            plain["ratio_projection"] = fp32_proj_value / plain["value"] if plain["value"] > 0 else None
+
+    # ---- the oracle leg: CPU baseline, whole-batch parity, counted algorithmic flops ----
+    cpu = parity = oflops = None
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.profile or sub):
+        if seg_args is None:   # the oracle starts from the FP32 values the GPU projected
+            q_or = np.asarray(cpu_q, dtype=np.float32).astype(np.float64)
+        else:                  # the points formed in FP32 as the kernel forms them: start + t * delta
+            q_or = segment_points_f32(seg_args)
+        gpu_out = None
+        if not fp64:
+            gpu_out = (q_out.cpu().numpy(), flags.cpu().numpy(), iters.cpu().numpy(), hit.cpu().numpy())
+        cpu, parity, oflops = oracle_leg(wl, q_or, gpu=gpu_out, whole_batch=not fp64 and not args.no_parity)
+
     # ---- roofline of the dominant kernel ----
     fm = FL.FlopModel(wl.robot, wl.constraints, cyclic=bool(wl.params.cyclic))
-    fp32, fp64f = fm.projection(it_np)
+    if oflops is not None:
+        fp32, fp64f = oflops["fp32"], oflops["fp64"]
+        flop_src = oflops["source"]
+    else:
+        fp32, fp64f = fm.projection(it_np, sincos=False)
+        flop_src = "kernel-structure model (flops.py) without sin/cos, the kernel's own step counts"
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     clk = sampler.summary()
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak32 = sms * 128 * 2 * sm_max * 1e6 / 1e12        # FP32 FMA lanes x 2 flops x max clock
-    peak64 = 1.25                                         # nominal dense FP64, TFLOP/s
+    peaks = env.get("peaks") or {}
+    peak64 = peaks.get("fp64_fma") or 1.25                # measured DFMA chains, else the nominal figure
+    peak64_src = (peaks.get("source", "") + " (FP64)") if peaks.get("fp64_fma") else "nominal dense FP64"
     # one fused kernel: FP32 batch problems of the thread-per-configuration kernels
     one_kernel = fused and bool(tuning and tuning.get("fuse_check"))
     if fused and not one_kernel and sep_ms is not None:   # two launches: per-kernel times from the separate calls
@@ -639,7 +798,13 @@ def run_ours(args):
     # narrow phase); sphere transforms are not counted (conservative)
     check_flops = n * fm.fk_positions() + 8.0 * pairs_total
     check_roof = {"kernel": "k_check_f32", "pairs_per_config": pairs_total / n}
-    peak_src = "152 SMs x 128 FP32 lanes x 2 x max SM clock"
+    peak_src = f"{sms} SMs x 128 FP32 lanes x 2 x max SM clock (measured FFMA chains: " \
+               f"{peaks.get('fp32_fma', float('nan')):.1f} TFLOP/s)"
+    common = {"peak_source": peak_src, "fp64_peak": peak64, "fp64_peak_source": peak64_src,
+              "fp32_fma_measured": peaks.get("fp32_fma"), "flops_source": flop_src}
+    if oflops is not None:
+        common["flops_oracle"] = {k: oflops[k] for k in ("per_step", "per_eval", "oracle_mean_iters",
+                                                           "special_per_step")}
     if one_kernel:
         t = mp * 1e-3
         ach32 = (fp32 + check_flops) / t / 1e12
@@ -649,10 +814,9 @@ def run_ours(args):
                 "traffic": MEASURED_TRAFFIC.get((wname, "k_project_f32+check")),
                 "kernel": "k_project_f32 with the check fused (persistent: FP32 steps, FP64 acceptance, "
                           "collision check)",
-                "peak_source": peak_src, "fp64_achieved": ach64, "fp64_peak": peak64, "fp64_frac": ach64 / peak64,
-                "mixed_bound_frac": t_min / t,
+                "fp64_achieved": ach64, "fp64_frac": ach64 / peak64, "mixed_bound_frac": t_min / t,
                 "flops_per_config": {"fp32_projection": fp32 / n, "fp32_check": check_flops / n, "fp64": fp64f / n},
-                "check": check_roof}
+                "check": check_roof, **common}
         kernel_ms = {"project_check": mp}
     else:
         check_roof["achieved"] = check_flops / (mc * 1e-3) / 1e12
@@ -661,14 +825,14 @@ def run_ours(args):
             flops_proj = fp32 + fp64f   # the plain kernel does all of it in FP64
             ach = flops_proj / (mp * 1e-3) / 1e12
             roof = {"bound": "alu", "achieved": ach, "peak": peak64, "unit": "TFLOP/s", "frac": ach / peak64,
-                    "traffic": None, "kernel": "k_project_f64 (plain FP64)", "peak_source": "nominal FP64"}
+                    "traffic": None, "kernel": "k_project_f64 (plain FP64)", **common}
         else:
             ach32 = fp32 / (mp * 1e-3) / 1e12
             ach64 = fp64f / (mp * 1e-3) / 1e12
             # both pipes: the time the FP32 and FP64 work need at their peaks bounds the kernel
             t_min = max(fp32 / (peak32 * 1e12), fp64f / (peak64 * 1e12))
-            kshort = ("k_project_group" if args.workload.startswith("humanoid") and not wl.params.cyclic else
-                      "k_project_warp" if args.workload.startswith("humanoid") else
+            kshort = ("k_project_group" if name.startswith("humanoid") and not wl.params.cyclic else
+                      "k_project_warp" if name.startswith("humanoid") else
                       "k_project_pair" if tuning and tuning.get("threads_per_config") == 2 else "k_project_f32")
             roof = {"bound": "alu", "achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
                     "traffic": MEASURED_TRAFFIC.get((wname, kshort)),
@@ -677,10 +841,9 @@ def run_ours(args):
                         "k_project_warp": " (warp per configuration, cyclic sweeps)",
                         "k_project_pair": " (persistent, one lane per arm: FP32 steps + FP64 acceptance)",
                         "k_project_f32": " (persistent, FP32 steps + FP64 acceptance)"}[kshort],
-                    "peak_source": peak_src,
-                    "fp64_achieved": ach64, "fp64_peak": peak64, "fp64_frac": ach64 / peak64,
+                    "fp64_achieved": ach64, "fp64_frac": ach64 / peak64,
                     "mixed_bound_frac": t_min / (mp * 1e-3),
-                    "flops_per_config": {"fp32": fp32 / n, "fp64": fp64f / n}}
+                    "flops_per_config": {"fp32": fp32 / n, "fp64": fp64f / n}, **common}
         kernel_ms = {"project": mp, "check": mc}
         roof["check"] = check_roof
         if mc > mp and not fp64:   # the dominant kernel carries the headline roofline
@@ -690,38 +853,94 @@ def run_ours(args):
                     "peak_source": peak_src, "projection": roof}
     if sep_ms is not None:
         kernel_ms["separate_calls"] = sep_ms
-
-    cpu = None
-    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.profile):
-        if seg_args is None:   # the oracle starts from the FP32 values the GPU projected
-            q32 = np.asarray(cpu_q, dtype=np.float32).astype(np.float64)
-            gpu_out = (q_out[:, :4096].double().cpu().numpy(), flags[:4096].cpu().numpy(),
-                       iters[:4096].cpu().numpy(), hit[:4096].cpu().numpy())
-            cpu = cpu_baseline(wl, q32, gpu=gpu_out)
-        else:
-            cpu = cpu_baseline(wl, cpu_q)
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
-                "config": {"workload": wname, "batch": n, "dof": d, "k": wl.k, "tol": wl.params.tol,
-                           "source": "segments (persistent launch, CUDA graph)" if seg_args is not None else "batch",
-                           "cap": wl.params.max_iters, "lambda": wl.params.lam,
-                           "form": "cyclic" if wl.params.cyclic else "stacked",
-                           "precision": "fp64 plain" if fp64 else "fp32 + fp64 acceptance",
-                           "obstacles": int(wl.obstacles.spheres.shape[0]), "robot_spheres": wl.robot.n_spheres,
-                           "l2": "flushed between timed steps (512 MB write)",
-                           "parallelism": f"replicas x{world}", "converged_per_step": conv,
-                           "kernel_ms": kernel_ms, "mean_iters": float(it_np.mean()), "launch": tuning,
-                           "flag_fractions": {k: float(((fl_np & b) != 0).mean()) for k, b in
-                                              (("cap", mcproj.F_CAP), ("fp64_resolve", mcproj.F_FP64_RESOLVE),
-                                               ("accept_fail", mcproj.F_ACCEPT_FAIL),
-                                               ("nonfinite", mcproj.F_NONFINITE))}},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
-        print(json.dumps(line), flush=True)
+    if shard_info is not None:   # the host gather of every rank's outputs (after the timed region)
+        t_g = time.perf_counter()
+        full = SHD.gather_columns([q_out, flags, iters, resid, hit], shard_info["ranges"], shard_info["total"])
+        shard_info.update(gathered_columns=int(full[0].shape[-1]), gather_s=round(time.perf_counter() - t_g, 3),
+                          converged_gathered=int(((full[1] & mcproj.F_CONVERGED) != 0).sum()))
+        del shard_info["ranges"]
+    if cpu is not None and parity is not None:
+        cpu["parity_vs_gpu"] = parity
     P.close()
-    if world > 1:
-        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "strong" if sharded else "weak", "shard": shard_info,
+            "vs_baseline": None, "vs_plain_fp64": plain, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
+            "config": {"workload": wname, "batch": n, "dof": d, "k": wl.k, "tol": wl.params.tol,
+                       "source": "segments (persistent launch, CUDA graph)" if seg_args is not None else "batch",
+                       "cap": wl.params.max_iters, "lambda": wl.params.lam,
+                       "form": "cyclic" if wl.params.cyclic else "stacked",
+                       "precision": "fp64 plain" if fp64 else "fp32 + fp64 acceptance",
+                       "obstacles": int(wl.obstacles.spheres.shape[0]), "robot_spheres": wl.robot.n_spheres,
+                       "l2": "flushed between timed steps (512 MB write)",
+                       "parallelism": f"shard x{world}" if sharded else f"replicas x{world}",
+                       "converged_per_step": conv,
+                       "kernel_ms": kernel_ms, "mean_iters": float(it_np.mean()), "launch": tuning,
+                       "flag_fractions": {k: float(((fl_np & b) != 0).mean()) for k, b in
+                                          (("cap", mcproj.F_CAP), ("fp64_resolve", mcproj.F_FP64_RESOLVE),
+                                           ("accept_fail", mcproj.F_ACCEPT_FAIL),
+                                           ("nonfinite", mcproj.F_NONFINITE))}},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e if not sub else None, "gpu_launches": launches,
+            "clocks": clk}
+
+
+def segment_points_f32(seg_args):
+    """The segment points as the kernel forms them, start + t * delta in FP32
+    (one rounding), returned as FP64."""
+    import torch
+    starts, delta, length = (t.cpu() for t in seg_args)
+    t = torch.cat([torch.arange(int(ln), dtype=torch.float32) for ln in length.tolist()])
+    sid = torch.repeat_interleave(torch.arange(length.shape[0]), length.long())
+    return torch.addcmul(starts.float()[:, sid], t[None, :], delta.float()[:, sid]).double().numpy()
+
+
+def plain_fp64_run(P, wl, q_in, seg_args, n, d, dev, stream, flush, args, world, steps=3):
+    """The plain per-configuration FP64 kernel (FP64 FK, Jacobian, Cholesky,
+    CUDA's double-precision math; no FP32 step) projecting the same
+    configurations: converged projections per second of the projection
+    kernel alone, timed like the FP32 path (L2 flushed, CUDA events, warm-up
+    first).  The configurations are the FP32 inputs, widened."""
+    import copy
+    import torch
+    from paper_2604_13323_gb300 import mcproj
+    from paper_2604_13323_gb300 import workloads as W
+    p64 = copy.copy(wl.params)
+    p64.precision = W.PREC_FP64
+    out = torch.empty((d, n), dtype=torch.float64, device=dev)
+    fl = torch.empty(n, dtype=torch.uint8, device=dev)
+    it = torch.empty(n, dtype=torch.uint8, device=dev)
+    rs = torch.empty(n, dtype=torch.float64, device=dev)
+    if seg_args is not None:
+        sa = (seg_args[0].double(), seg_args[1].double(), seg_args[2])
+
+        def call():
+            P.project_segments(*sa, p64, total=n, out=out, flags=fl, iters=it, resid=rs, stream=stream)
+    else:
+        q64 = q_in.double()
+
+        def call():
+            P.project(q64, p64, out=out, flags=fl, iters=it, resid=rs, stream=stream)
+    try:
+        call()
+        torch.cuda.synchronize()
+    except mcproj.MCPError as e:
+        return {"unavailable": str(e)}
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = sum(ts) / len(ts)
+    conv = int((((fl.cpu().numpy() & mcproj.F_CONVERGED) != 0) & (rs.cpu().numpy() <= wl.params.tol)).sum())
+    ms_max, c_total = aggregate_replicas(ms, conv, world, dev)
+    return {"value": c_total / (ms_max * 1e-3), "unit": UNIT, "ms": ms_max, "converged": conv, "steps": steps,
+            "kernel": "k_project_f64 (plain FP64, one thread per configuration)"}
 
 
 EXT_N = 16384   # extensions per step of the extend workload
@@ -822,14 +1041,14 @@ def run_extend(args):
     sm_max = clk.get("sm_max_mhz") or 2070.0
     props = torch.cuda.get_device_properties(dev)
     peak32 = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
-    fp32 = total_steps * fm.iteration
+    fp32 = total_steps * fm.iteration_alg
     ach = fp32 / (ms * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s", "frac": ach / peak32,
             "traffic": MEASURED_TRAFFIC.get((f"dual14_rel_extend_{EXT_N}", "k_extend")),
             "kernel": "k_extend (8 lanes per extension, four per warp: particles, interpolation, bisection)",
             "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
-            "counted": "FP32 Newton steps of all projections x the step's flops (evaluations, FP64 "
-                       "acceptance and collision checks not counted)",
+            "counted": "FP32 Newton steps of all projections x the step's flops (kernel-structure model without "
+                       "sin/cos; evaluations, FP64 acceptance and collision checks not counted)",
             "newton_steps_per_step": total_steps}
     cpu = None
     if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.profile):
@@ -869,26 +1088,28 @@ PATHS, WAYPOINTS, SHORTEN_STEPS = 4096, 64, 100
 SHORTEN_REF_PATHS = 64   # paths per step of the oracle's (reference arm) shortening
 
 
-def run_adjoint(args):
+def run_adjoint(args, env=None, workload=None, sub=False):
     """The adjoint of the projection on the dual-arm closed chain: `vjp`
     times the VJP kernel v = g - J^T (J J^T)^{-1} J g on VJP_N projected
     configurations with g ~ N(0, 1) (one step = one call); `shorten` times
     gradient path shortening on the manifold (PATHS paths of WAYPOINTS
     waypoints, SHORTEN_STEPS steps of project -> length -> backward through
     the projection (VJP) -> clipped step; one bench step = one whole run) and
-    reports the mean length reduction and the largest FP64 residual."""
+    reports the mean length reduction and the largest FP64 residual.  With
+    `env` (a sub-record of the headline run) the process is set up already
+    and the line is returned instead of printed; `sub` skips the e2e pass and
+    the CPU baseline."""
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    from paper_2604_13323_gb300 import build as B
-    B.build()
+    standalone = env is None
+    if standalone:
+        world, rank, local, dev = init_dist()
+        from paper_2604_13323_gb300 import build as B
+        B.build()
+    else:
+        world, rank, local, dev = env["world"], env["rank"], env["local"], env["dev"]
+    workload = workload or args.workload
     from paper_2604_13323_gb300 import flops as FL
     from paper_2604_13323_gb300 import mcproj
     from paper_2604_13323_gb300 import shorten as SH
@@ -896,7 +1117,7 @@ def run_adjoint(args):
 
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    vjp_mode = args.workload == "vjp"
+    vjp_mode = workload == "vjp"
     extra = {}
     if vjp_mode:
         wl = W.dual_arm_workload(total=10, n_random=VJP_N, batch_seed=1011 + 1000 * rank)
@@ -966,11 +1187,12 @@ def run_adjoint(args):
     if vjp_mode:
         # one VJP evaluates F and J at q*, builds and factors J J^T, solves
         # twice (with the refinement) and forms g - J^T y: counted as one LM step
-        ach = VJP_N * fm.iteration / (ms * 1e-3) / 1e12
+        ach = VJP_N * fm.iteration_alg / (ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s", "frac": ach / peak32,
                 "traffic": None, "kernel": "k_vjp (thread per configuration, FP32 + FP64 re-solve below the pivot)",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
-                "counted": "one LM step's FP32 flops per VJP (FK, F, J, Gram, Cholesky, two solves, J^T y)"}
+                "counted": "one LM step's FP32 flops per VJP (FK, F, J, Gram, Cholesky, two solves, J^T y; "
+                           "kernel-structure model without sin/cos)"}
         vfl = vf.cpu().numpy()
         extra = {"vjp_flags_nonzero": float((vfl != 0).mean())}
     else:
@@ -996,16 +1218,17 @@ def run_adjoint(args):
         # the dominant call: the projection of the waypoints (FP32 steps of the
         # shortened points, a few per step, counted from the final projection)
         it = P.project(Qs, p)[2].cpu().numpy()
-        fp32, fp64f = fm.projection(it)
+        fp32, fp64f = fm.projection(it, sincos=False)
         ach = fp32 / (parts["project"] * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s", "frac": ach / peak32,
                 "traffic": None,
                 "kernel": ("k_project_pair" if shorten_tuning["threads_per_config"] == 2 else "k_project_f32")
                 + " (the waypoints' re-projection in one shortening step)", "launch": shorten_tuning,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
-                "counted": "FP32 Newton-step and evaluation flops of the initial paths' projection"}
+                "counted": "FP32 Newton-step and evaluation flops (kernel-structure model without sin/cos) of "
+                           "the final waypoints' projection"}
     e2e = None
-    if vjp_mode and not args.profile:   # q* and g from pinned host memory, v back, one step at a time
+    if vjp_mode and not (args.profile or sub):   # q* and g from pinned host memory, v back, one step at a time
         hq, hg = q_star.cpu().pin_memory(), g.cpu().pin_memory()
         hv = torch.empty(v.shape, dtype=v.dtype).pin_memory()
         e_ms = []
@@ -1025,7 +1248,7 @@ def run_adjoint(args):
         e2e = {"value": units_per_step * world / (e_max * 1e-3), "unit": unit,
                "h2d_bytes_per_step": 2 * hq.numel() * 4, "d2h_bytes_per_step": hv.numel() * 4}
     cpu = None
-    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.profile) and vjp_mode:
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.profile or sub) and vjp_mode:
         from oracle import oracle as orc
         O = orc.Oracle(wl.robot, wl.constraints)
         qn = q_star.double().cpu().numpy()
@@ -1053,10 +1276,14 @@ def run_adjoint(args):
                 "config": {"workload": name, "l2": "flushed between timed steps (512 MB write)",
                            "parallelism": f"replicas x{world}", **extra},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
-        print(json.dumps(line), flush=True)
+        if standalone:
+            print(json.dumps(line), flush=True)
+    else:
+        line = None
     P.close()
-    if world > 1:
+    if standalone and world > 1:
         dist.destroy_process_group()
+    return line
 
 
 def main():

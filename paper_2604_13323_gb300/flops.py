@@ -78,6 +78,13 @@ class FlopModel:
         if cyclic and len(self.cons) > 1:
             self.iteration = self.evaluation + 3 * self.d + sum(
                 FlopModel(robot, [c]).iteration for c in self.cons)
+        # sin / cos evaluations per forward kinematics (special functions: the
+        # algorithmic counts below leave their polynomial flops out)
+        self.n_sincos = int(sum(1 for j in range(self.d) if robot.type[j] == W.REVOLUTE)) if self.needs_fk else 0
+        n_fk_step = 1 + (len(self.cons) if cyclic and len(self.cons) > 1 else 0)
+        self.iteration_alg = self.iteration - SINCOS32 * self.n_sincos * n_fk_step
+        self.evaluation_alg = self.evaluation - SINCOS32 * self.n_sincos
+        self.acceptance_alg = self.acceptance - SINCOS64 * self.n_sincos
 
     def _fk(self, sincos):
         rb = self.rb
@@ -170,13 +177,14 @@ class FlopModel:
             r0 += kd
         return total, nz
 
-    def projection(self, iters):
-        """(FP32 flops, FP64 flops) of projecting configurations that took `iters` steps."""
+    def projection(self, iters, sincos=True):
+        """(FP32 flops, FP64 flops) of projecting configurations that took
+        `iters` steps; without the sin/cos polynomials if not `sincos`."""
         it = np.asarray(iters, dtype=np.float64)
         n = it.size
-        fp32 = float(it.sum()) * self.iteration + n * self.evaluation
-        fp64 = n * self.acceptance
-        return fp32, fp64
+        if sincos:
+            return float(it.sum()) * self.iteration + n * self.evaluation, n * self.acceptance
+        return float(it.sum()) * self.iteration_alg + n * self.evaluation_alg, n * self.acceptance_alg
 
     def fk_positions(self):
         """FP32 flops of the forward kinematics with translations (collision check)."""
