@@ -368,6 +368,17 @@ int64_t mcp_launch_count(const mcp_ctx *ctx);
  * "project_batch launch", ...; they appear in mcp_last_error). */
 int64_t mcp_alloc_count(void);
 
+/* Bounds-check status (no counterpart in the paper; a debugging aid).  A
+ * library built with -DMCP_CHECK_BOUNDS tests the index of every batch-array
+ * access of its persistent projection kernels against the array's extent;
+ * an access out of range is skipped and the source line of the first one is
+ * recorded (nothing traps).  *enabled (HOST, may be NULL) receives 1 for such
+ * a build, else 0; *first_line (HOST, may be NULL) the first line recorded
+ * since the last reset (0: none; always 0 without the checks).  reset != 0
+ * clears the record.  Synchronises the context's device.  MCP_ERR_ARG for a
+ * NULL context, MCP_ERR_CUDA if the synchronisation fails. */
+mcp_status mcp_bounds_status(const mcp_ctx *ctx, int32_t *enabled, uint32_t *first_line, int32_t reset);
+
 /* Allocation-free segment projection.  The paper has no counterpart: this
  * entry point exists for callers that must not allocate device memory once
  * they are running -- a real-time planning or control loop where a

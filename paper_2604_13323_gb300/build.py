@@ -34,25 +34,39 @@ def sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
         glob.glob(os.path.join(INCLUDE, "*.h"))
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    if not force and not _stale():
-        return LIB
+CHECKED_DIR = os.path.join(HERE, "_lib_checked")
+CHECKED_LIB = os.path.join(CHECKED_DIR, "libmcproj.so")
+
+
+def build_checked(force: bool = False) -> str:
+    """The bounds-checked debug variant (-DMCP_CHECK_BOUNDS) in its own
+    directory: every batch-array access of the persistent kernels tests its
+    index and records the first one out of range instead of touching memory
+    (see mcp_bounds_status)."""
+    return build(force=force, extra=["-DMCP_CHECK_BOUNDS"], out_dir=CHECKED_DIR)
+
+
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
+          out_dir: str = OUT_DIR) -> str:
+    lib = os.path.join(out_dir, "libmcproj.so")
+    if not force and not _stale(lib):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(OUT_DIR, exist_ok=True)
+    os.makedirs(out_dir, exist_ok=True)
     objs = []
     extra = list(extra or [])
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
@@ -64,12 +78,12 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
             objs.append(obj)
             if verbose and log:
                 sys.stderr.write(log)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     res = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -24,6 +24,22 @@ using namespace mcp;
 namespace mcp {
 static std::atomic<long long> g_allocs{0};
 
+// Readers of the per-module error words of the bounds-check mode (each
+// module of a -DMCP_CHECK_BOUNDS build registers one when it is loaded).
+static std::vector<unsigned int (*)(bool)> &bounds_readers() {
+  static std::vector<unsigned int (*)(bool)> r;
+  return r;
+}
+void register_bounds_reader(unsigned int (*reader)(bool)) { bounds_readers().push_back(reader); }
+unsigned int bounds_error_of_all_modules(bool reset) {
+  unsigned int first = 0;
+  for (auto *rd : bounds_readers()) {
+    const unsigned int v = rd(reset);
+    if (v && !first) first = v;
+  }
+  return first;
+}
+
 cudaError_t dev_malloc(void **p, size_t bytes, const char *label) {
   const char *f = std::getenv("MCP_TEST_FAIL_ALLOC");
   if (f && *f && std::strstr(label, f)) {
@@ -875,6 +891,22 @@ const char *mcp_last_error(const mcp_ctx *ctx) { return ctx ? ctx->err.c_str() :
 int64_t mcp_launch_count(const mcp_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
 int64_t mcp_alloc_count(void) { return g_allocs.load(std::memory_order_relaxed); }
+
+mcp_status mcp_bounds_status(const mcp_ctx *ctx, int32_t *enabled, uint32_t *first_line, int32_t reset) {
+  if (!ctx) return MCP_ERR_ARG;
+#ifdef MCP_CHECK_BOUNDS
+  DeviceGuard g(ctx->device);
+  if (cudaDeviceSynchronize() != cudaSuccess) return MCP_ERR_CUDA;
+  const unsigned int v = bounds_error_of_all_modules(reset != 0);
+  if (enabled) *enabled = 1;
+  if (first_line) *first_line = v;
+#else
+  (void)reset;
+  if (enabled) *enabled = 0;
+  if (first_line) *first_line = 0;
+#endif
+  return MCP_OK;
+}
 
 mcp_status mcp_load_robot(mcp_ctx *ctx, const mcp_robot_desc *rd) {
   if (!ctx) return MCP_ERR_ARG;

@@ -19,6 +19,42 @@
 
 namespace mcp {
 
+// ---------------------------------------------------------------------------
+// Bounds-check mode (debug builds compiled with -DMCP_CHECK_BOUNDS): the
+// persistent kernels test the index of every batch-array access against the
+// array's extent; an access out of range is skipped (loads read 0) and the
+// source line of the first one is recorded in this module's error word,
+// which mcp_bounds_status() reads.  Nothing traps.  In normal builds the test
+// is the constant true and costs nothing.
+// ---------------------------------------------------------------------------
+#ifdef MCP_CHECK_BOUNDS
+static __device__ unsigned int g_bounds_error;
+__device__ __forceinline__ bool in_bounds(long long i, long long n, int line) {
+  if (i >= 0 && i < n) return true;
+  atomicCAS(&g_bounds_error, 0u, static_cast<unsigned int>(line));
+  return false;
+}
+#define MCP_CHK(i, n) ::mcp::in_bounds((i), (n), __LINE__)
+// each module registers a reader of its own error word with the library
+unsigned int bounds_error_of_all_modules(bool reset);
+void register_bounds_reader(unsigned int (*reader)(bool));
+static unsigned int read_bounds_error(bool reset) {
+  unsigned int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_bounds_error, sizeof(v)) != cudaSuccess) v = ~0u;
+  if (reset) {
+    const unsigned int z = 0;
+    cudaMemcpyToSymbol(g_bounds_error, &z, sizeof(z));
+  }
+  return v;
+}
+struct BoundsRegistration {
+  BoundsRegistration() { register_bounds_reader(&read_bounds_error); }
+};
+static BoundsRegistration g_bounds_registration;
+#else
+#define MCP_CHK(i, n) true
+#endif
+
 constexpr int MAXJ = 40;
 constexpr int MAXF = 8;
 constexpr int MAXC = 8;

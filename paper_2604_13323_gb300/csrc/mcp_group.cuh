@@ -1163,7 +1163,7 @@ __global__ void __launch_bounds__(W * 32) k_project_group(const __grid_constant_
           it = static_cast<int>(meta & 0xffu);
           fl = ((meta >> 8) & ~(FL_INT_FP32CONV | FL_INT_NEEDS_F64)) | FL_INT_FORCE;
           act = true;
-          for (int j = g; j < D; j += GG) S.q[j] = a.q_out[j * a.ld_out + item];
+          for (int j = g; j < D; j += GG) S.q[j] = MCP_CHK(item, a.ld_out) ? a.q_out[j * a.ld_out + item] : 0.f;
         } else {
           const int rank = rank_all - from_r;
           long long cand = -1;
@@ -1174,7 +1174,7 @@ __global__ void __launch_bounds__(W * 32) k_project_group(const __grid_constant_
             act = true;
             it = 0;
             fl = 0;
-            for (int j = g; j < D; j += GG) S.q[j] = a.src.q[j * a.src.ld + item];
+            for (int j = g; j < D; j += GG) S.q[j] = MCP_CHK(item, a.src.ld) ? a.src.q[j * a.src.ld + item] : 0.f;
           }
         }
       }
@@ -1194,7 +1194,8 @@ __global__ void __launch_bounds__(W * 32) k_project_group(const __grid_constant_
     const unsigned fin = __ballot_sync(FULL, done) & lead;
     if (fin != 0u) {
       if (done) {
-        for (int j = g; j < D; j += GG) a.q_out[j * a.ld_out + item] = S.q[j];
+        if (MCP_CHK(item, a.ld_out))
+          for (int j = g; j < D; j += GG) a.q_out[j * a.ld_out + item] = S.q[j];
         if (g == 0) {
           const int pos = pend + __popc(fin & ((1u << lane) - 1u));
           s_item[wib][pos] = item;

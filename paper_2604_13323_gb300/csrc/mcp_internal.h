@@ -20,6 +20,10 @@ cudaError_t dev_malloc(T **p, size_t bytes, const char *label) {
   return dev_malloc(reinterpret_cast<void **>(p), bytes, label);
 }
 
+// Bounds-check mode: the per-module error readers (see mcp_device.cuh).
+void register_bounds_reader(unsigned int (*reader)(bool));
+unsigned int bounds_error_of_all_modules(bool reset);
+
 constexpr int MAXS = 256;  // robot spheres per robot
 
 // Robot spheres sorted by the joint they ride on: spheres of link l (l = -1

@@ -348,14 +348,16 @@ struct BatchSrc {
   __device__ __forceinline__ long long clamp_total(long long t) const { return t; }
   template <int D>
   __device__ __forceinline__ void load(long long item, T (&out)[D]) const {
+    const bool ok = MCP_CHK(item, ld);
 #pragma unroll
-    for (int j = 0; j < D; ++j) out[j] = q[j * ld + item];
+    for (int j = 0; j < D; ++j) out[j] = ok ? q[j * ld + item] : T(0);
   }
   // joints j0 .. j0 + N - 1 only
   template <int N>
   __device__ __forceinline__ void load_part(long long item, int j0, T (&out)[N]) const {
+    const bool ok = MCP_CHK(item, ld);
 #pragma unroll
-    for (int j = 0; j < N; ++j) out[j] = q[(j0 + j) * ld + item];
+    for (int j = 0; j < N; ++j) out[j] = ok ? q[(j0 + j) * ld + item] : T(0);
   }
 };
 
@@ -389,6 +391,13 @@ struct SegSrc {
   template <int N>
   __device__ __forceinline__ void load_part(long long item, int j0, T (&out)[N]) const {
     const int s = segment_of(item);
+    // the segment holds the item, and its start / delta columns exist
+    const bool ok = MCP_CHK(s, n) && MCP_CHK(s, ld) && MCP_CHK(item - __ldg(&off[s]), __ldg(&off[s + 1]) - __ldg(&off[s]));
+    if (!ok) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) out[j] = T(0);
+      return;
+    }
     const T t = static_cast<T>(item - __ldg(&off[s]));
 #pragma unroll
     for (int j = 0; j < N; ++j) out[j] = fma_(t, delta[(j0 + j) * ld + s], start[(j0 + j) * ld + s]);
@@ -967,7 +976,8 @@ __device__ __forceinline__ bool accept_one(const A &a, long long item, int it, u
   const ModelT<double> &m = *a.m64;
   float q[D];
 #pragma unroll
-  for (int j = 0; j < D; ++j) q[j] = a.q_out[j * a.ld_out + item];
+  const bool ok = MCP_CHK(item, a.ld_out);
+  for (int j = 0; j < D; ++j) q[j] = ok ? a.q_out[j * a.ld_out + item] : 0.f;
   double r2 = residual2_f64<P>(OpsF64Split{a.tab}, m, q);
   if (retry_ok && (fl & FL_INT_FP32CONV) && !(r2 < a.tol2_64) && r2 <= DBL_MAX && it < a.cap) return true;
   if (fl & (FL_INT_FP32CONV | FL_INT_NEEDS_F64)) {
@@ -986,7 +996,7 @@ __device__ __forceinline__ bool accept_one(const A &a, long long item, int it, u
       r2 = finish_f64<P, FORM>(a, qf, qdd, &it, &fl, r2, was_conv);
 #pragma unroll
       for (int j = 0; j < D; ++j) {
-        a.q_out[j * a.ld_out + item] = qf[j];
+        if (ok) a.q_out[j * a.ld_out + item] = qf[j];
         q[j] = qf[j];
       }
     }
@@ -997,9 +1007,11 @@ __device__ __forceinline__ bool accept_one(const A &a, long long item, int it, u
 #pragma unroll
   for (int j = 0; j < D; ++j)
     if (q[j] < a.m.lower[j] || q[j] > a.m.upper[j]) fl |= FL_LIMITS;
-  a.flags[item] = static_cast<uint8_t>(fl & 0xffu);
-  a.iters[item] = static_cast<uint8_t>(it > 255 ? 255 : it);
-  a.resid[item] = sqrt_refined(r2);
+  if (ok) {
+    a.flags[item] = static_cast<uint8_t>(fl & 0xffu);
+    a.iters[item] = static_cast<uint8_t>(it > 255 ? 255 : it);
+    a.resid[item] = sqrt_refined(r2);
+  }
   return false;
 }
 
@@ -1423,7 +1435,7 @@ __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(con
           fl = ((meta >> 8) & ~(FL_INT_FP32CONV | FL_INT_NEEDS_F64)) | FL_INT_FORCE;
           act = true;
 #pragma unroll
-          for (int j = 0; j < D; ++j) q[j] = a.q_out[j * a.ld_out + item];
+          for (int j = 0; j < D; ++j) q[j] = MCP_CHK(item, a.ld_out) ? a.q_out[j * a.ld_out + item] : 0.f;
         } else {
           const int rank = rank_all - from_r;
           long long cand = -1;
@@ -1459,7 +1471,8 @@ __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(con
     if (fin != 0u) {
       if (done) {
 #pragma unroll
-        for (int j = 0; j < D; ++j) a.q_out[j * a.ld_out + item] = q[j];
+        if (MCP_CHK(item, a.ld_out))
+          for (int j = 0; j < D; ++j) a.q_out[j * a.ld_out + item] = q[j];
         const int pos = pend + __popc(fin & ((1u << lane) - 1u));
         s_item[wib][pos] = item;
         s_meta[wib][pos] = static_cast<uint32_t>(it) | (fl << 8);
@@ -1488,10 +1501,11 @@ __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(con
           if (!retry) {
             float qc[D];
 #pragma unroll
-            for (int j = 0; j < D; ++j) qc[j] = a.q_out[j * a.ld_out + it_item];
+            const bool okc = MCP_CHK(it_item, a.ld_out);
+            for (int j = 0; j < D; ++j) qc[j] = okc ? a.q_out[j * a.ld_out + it_item] : 0.f;
             uint32_t tests = 0;
             const bool h = check_one_f32<P>(a.chk->m, a.chk->st, s_pair, a.n_obs, s_box, a.n_box, a.tab, qc, tests);
-            a.hit[it_item] = h ? 1 : 0;
+            if (okc) a.hit[it_item] = h ? 1 : 0;
             if (a.pairs) a.pairs[it_item] = tests;
           }
         }

@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(TPB, (pair_min_blocks<TPB>())) k_project_pair(
           fl = ((meta >> 8) & ~(FL_INT_FP32CONV | FL_INT_NEEDS_F64)) | FL_INT_FORCE;
           act = true;
 #pragma unroll
-          for (int j = 0; j < H; ++j) q[j] = a.q_out[(H * h + j) * a.ld_out + item];
+          for (int j = 0; j < H; ++j) q[j] = MCP_CHK(item, a.ld_out) ? a.q_out[(H * h + j) * a.ld_out + item] : 0.f;
         } else {
           const int rank = rank_all - from_r;
           long long cand = -1;
@@ -316,7 +316,8 @@ __global__ void __launch_bounds__(TPB, (pair_min_blocks<TPB>())) k_project_pair(
     if (fin != 0u) {
       if (done) {
 #pragma unroll
-        for (int j = 0; j < H; ++j) a.q_out[(H * h + j) * a.ld_out + item] = q[j];
+        if (MCP_CHK(item, a.ld_out))
+          for (int j = 0; j < H; ++j) a.q_out[(H * h + j) * a.ld_out + item] = q[j];
         if (h == 0) {
           const int pos = pend + __popc(fin & before);
           s_item[wib][pos] = item;
@@ -345,10 +346,11 @@ __global__ void __launch_bounds__(TPB, (pair_min_blocks<TPB>())) k_project_pair(
           if (!retry) {
             float qc[P::D];
 #pragma unroll
-            for (int j = 0; j < P::D; ++j) qc[j] = a.q_out[j * a.ld_out + it_item];
+            const bool okc = MCP_CHK(it_item, a.ld_out);
+            for (int j = 0; j < P::D; ++j) qc[j] = okc ? a.q_out[j * a.ld_out + it_item] : 0.f;
             uint32_t tests = 0;
             const bool hit = check_one_f32<P>(a.chk->m, a.chk->st, s_pair, a.n_obs, s_box, a.n_box, a.tab, qc, tests);
-            a.hit[it_item] = hit ? 1 : 0;
+            if (okc) a.hit[it_item] = hit ? 1 : 0;
             if (a.pairs) a.pairs[it_item] = tests;
           }
         }

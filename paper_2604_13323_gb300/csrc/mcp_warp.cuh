@@ -733,14 +733,14 @@ __global__ void __launch_bounds__(W * 32, 512 / (W * 32)) k_project_warp(const _
 #pragma unroll
         for (int s = 0; s < SL; ++s) {
           const int j = lane + 32 * s;
-          if (j < D) S.q[j] = a.q_out[j * a.ld_out + item];
+          if (j < D) S.q[j] = MCP_CHK(item, a.ld_out) ? a.q_out[j * a.ld_out + item] : 0.f;
         }
       } else {
         item = qn++;
 #pragma unroll
         for (int s = 0; s < SL; ++s) {
           const int j = lane + 32 * s;
-          if (j < D) S.q[j] = a.src.q[j * a.src.ld + item];
+          if (j < D) S.q[j] = MCP_CHK(item, a.src.ld) ? a.src.q[j * a.src.ld + item] : 0.f;
         }
       }
       __syncwarp();
@@ -754,7 +754,7 @@ __global__ void __launch_bounds__(W * 32, 512 / (W * 32)) k_project_warp(const _
 #pragma unroll
       for (int s = 0; s < SL; ++s) {
         const int j = lane + 32 * s;
-        if (j < D) a.q_out[j * a.ld_out + item] = S.q[j];
+        if (j < D && MCP_CHK(item, a.ld_out)) a.q_out[j * a.ld_out + item] = S.q[j];
       }
       if (lane == 0) {
         s_item[wib][pend] = item;

@@ -58,9 +58,11 @@ _lib = None
 
 
 def load_library(path: str = LIB_PATH):
-    """Loads libmcproj.so (built by paper_2604_13323_gb300.build)."""
+    """Loads libmcproj.so (built by paper_2604_13323_gb300.build); the default
+    library is loaded once per process, another path (the bounds-checked
+    build) is opened beside it."""
     global _lib
-    if _lib is not None:
+    if path == LIB_PATH and _lib is not None:
         return _lib
     if not os.path.exists(path):
         raise ImportError(f"{path} not found: build it with `python -m paper_2604_13323_gb300.build` "
@@ -99,12 +101,14 @@ def load_library(path: str = LIB_PATH):
                                           ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
         "mcp_fma_probe": ([_vp, ctypes.c_int32, ctypes.c_int64, _vp, P(ctypes.c_int64), _vp], ctypes.c_int),
         "mcp_alloc_count": ([], ctypes.c_int64),
+        "mcp_bounds_status": ([_vp, P(ctypes.c_int32), P(ctypes.c_uint32), ctypes.c_int32], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = res
-    _lib = lib
+    if path == LIB_PATH:
+        _lib = lib
     return lib
 
 
@@ -112,7 +116,7 @@ EXPORTED = ("mcp_create", "mcp_destroy", "mcp_last_error", "mcp_launch_count", "
             "mcp_load_constraints", "mcp_load_obstacles", "mcp_get_constraint", "mcp_project_batch",
             "mcp_project_check_batch", "mcp_project_segments", "mcp_check_batch", "mcp_project_vjp",
             "mcp_path_length_grad", "mcp_autotune", "mcp_set_tuning", "mcp_project_segments_noalloc",
-            "mcp_path_step", "mcp_extend_batch", "mcp_fma_probe", "mcp_alloc_count")
+            "mcp_path_step", "mcp_extend_batch", "mcp_fma_probe", "mcp_alloc_count", "mcp_bounds_status")
 
 
 def alloc_count() -> int:
@@ -144,11 +148,11 @@ class Projector:
     float64 for the plain FP64 path.
     """
 
-    def __init__(self, robot, constraints=(), obstacles=None, device: int = 0):
+    def __init__(self, robot, constraints=(), obstacles=None, device: int = 0, lib=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("mcproj needs a CUDA device; there is no CPU fallback")
-        self.lib = load_library()
+        self.lib = lib if lib is not None else load_library()
         self.device = device
         h = ctypes.c_void_p()
         st = self.lib.mcp_create(device, ctypes.byref(h))
@@ -247,6 +251,13 @@ class Projector:
         B = np.zeros(12)
         self._check(self.lib.mcp_get_constraint(self.h, i, None, None, None, B.ctypes.data_as(_dp)))
         return B
+
+    def bounds_status(self, reset=False):
+        """(enabled, first source line out of range or 0) of the bounds-check
+        mode (enabled only in the -DMCP_CHECK_BOUNDS build)."""
+        en, line = ctypes.c_int32(), ctypes.c_uint32()
+        self._check(self.lib.mcp_bounds_status(self.h, ctypes.byref(en), ctypes.byref(line), int(bool(reset))))
+        return en.value, line.value
 
     @property
     def launches(self) -> int:
