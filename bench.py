@@ -51,8 +51,6 @@ UNIT = "projections/s"
 # (workload, kernel); an entry is removed whenever its kernel changes.
 MEASURED_TRAFFIC = {
     ("arm7_axis_65536", "k_project_f32+check"): 1990656,                  # read 1.99 MB, write 0
-    ("dual14_rel_segments_262240", "k_project_pair"): 3543296 + 3374848,  # read 3.54 MB, write 3.37 MB
-    ("dual14_rel_extend_16384", "k_extend"): 3548160 + 1514496,           # read 3.55 MB, write 1.51 MB
 }
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 
