@@ -61,6 +61,26 @@ __host__ __device__ constexpr bool grp_supported() {
     if (!grp_pose_like<P>(c) && !grp_com_like<P>(c)) return false;
   return P::D <= 64 && kdim<P>() <= 4 * 5 && dfs_preorder<P>();
 }
+// Per-constraint data slots: the pose-like constraints (error frame G, point
+// x, log-map vector) and the support-hull ones (nearest-edge data) are stored
+// per kind, not per constraint, so that the shared state holds no unused rows.
+template <class P>
+__host__ __device__ constexpr int grp_pslot(int c) {
+  int n = 0;
+  for (int b = 0; b < c; ++b) n += grp_pose_like<P>(b) ? 1 : 0;
+  return n;
+}
+template <class P>
+__host__ __device__ constexpr int grp_hslot(int c) {
+  int n = 0;
+  for (int b = 0; b < c; ++b) n += P::ckind(b) == K_HULL ? 1 : 0;
+  return n;
+}
+template <class P>
+__host__ __device__ constexpr int grp_npose() { return grp_pslot<P>(P::NC); }
+template <class P>
+__host__ __device__ constexpr int grp_nhull() { return grp_hslot<P>(P::NC); }
+
 // Jacobian segments: (joint j, constraint c) with a structural nonzero, j-major
 template <class P>
 __host__ __device__ constexpr int grp_nseg_floats() {
@@ -70,6 +90,18 @@ __host__ __device__ constexpr int grp_nseg_floats() {
       if (col_sign<P>(c, j) != 0) n += cdim(P::ckind(c));
   return n;
 }
+// Floats of the 2-row (CoM-like) segments, which come first in the Jacobian's
+// space; the subtree moments C_j (3 floats per joint) are kept right after
+// them, where the 6-row segments are written once the 2-row ones are built.
+template <class P>
+__host__ __device__ constexpr int grp_cbase() {
+  int n = 0;
+  for (int j = 0; j < P::D; ++j)
+    for (int c = 0; c < P::NC; ++c)
+      if (col_sign<P>(c, j) != 0 && grp_com_like<P>(c)) n += cdim(P::ckind(c));
+  return (n + 3) & ~3;
+}
+
 // L by columns, each column padded to a multiple of 4 floats (16-byte loads)
 template <int K>
 __host__ __device__ constexpr int lcol_base(int k) {
@@ -111,6 +143,8 @@ struct GroupPlan {
   uint32_t amask[GG * 5];  // row i of J J^T: bit b set if rows i and b share a joint
                            // (the other entries are never written: structural zeros)
   int8_t chull[NC];     // constraint c is the support-hull kind
+  int8_t pslot[NC];     // slot of constraint c among the pose-like ones (-1: other kinds)
+  int8_t hslot[NC];     // slot of constraint c among the support-hull ones (-1: other kinds)
   // 5. Gram phases (6x6, 6x2, 2x6, 2x2 row-block pairs) and 7. refinement
   // phases (6-row, 2-row blocks): tasks per lane.  The diagonal blocks and
   // refinement rows of 2-row constraints (the CoM, over every joint) are
@@ -235,16 +269,20 @@ bool make_group_plan(GroupPlan<P> &pl, const char **why) {
     }
   }
   pl.n_roots = n_roots;
-  // segment offsets (every segment size is even: float2 loads)
+  // segment offsets (every segment size is even: float2 loads): the 2-row
+  // segments of the CoM-like constraints first, then the 6-row ones, so that
+  // the subtree moments can live where the 6-row segments go until the 2-row
+  // segments are built from them (grp_cbase)
   int off = 0;
-  for (int j = 0; j < D; ++j)
-    for (int c = 0; c < NC; ++c) {
-      pl.joff[c][j] = -1;
-      if (col_sign<P>(c, j) != 0) {
-        pl.joff[c][j] = static_cast<int16_t>(off);
-        off += cdim(P::ckind(c));
+  for (int pass = 0; pass < 2; ++pass)
+    for (int j = 0; j < D; ++j)
+      for (int c = 0; c < NC; ++c) {
+        if (pass == 0) pl.joff[c][j] = -1;
+        if (col_sign<P>(c, j) != 0 && grp_com_like<P>(c) == (pass == 0)) {
+          pl.joff[c][j] = static_cast<int16_t>(off);
+          off += cdim(P::ckind(c));
+        }
       }
-    }
   for (int i = 0; i < GG * 5; ++i) {
     pl.lcol[i] = static_cast<int16_t>(i < kdim<P>() ? lcol_base<kdim<P>()>(i) : 0);
     pl.amask[i] = 0u;
@@ -255,6 +293,8 @@ bool make_group_plan(GroupPlan<P> &pl, const char **why) {
   for (int c = 0; c < NC; ++c) {
     pl.croff[c] = static_cast<int8_t>(roff<P>(c));
     pl.chull[c] = static_cast<int8_t>(P::ckind(c) == K_HULL);
+    pl.pslot[c] = static_cast<int8_t>(grp_pose_like<P>(c) ? grp_pslot<P>(c) : -1);
+    pl.hslot[c] = static_cast<int8_t>(P::ckind(c) == K_HULL ? grp_hslot<P>(c) : -1);
   }
   // 4. segments: a limb's segments on its lane, the trunk's on the lane with
   // the fewest segments of that size
@@ -366,14 +406,15 @@ struct __align__(16) GrpState {
   static constexpr int NJ = (grp_nseg_floats<P>() + 3) & ~3;
   static constexpr int LC = lcol_base<K>(K);
   static constexpr int K2 = K * (K + 1) / 2;
-  struct Eval {         // FK and residual data, live until J is built
-    float zo[D][6];     // joint axis z and origin o (world)
-    float C[D][3];      // m_j c_j, then the subtree sum
-    float G[NC][9];     // rotation into the error frame
-    float x[NC][4];     // reference point of the translational rows
-    float phi[NC][4];   // log-map vector and J_l^-1 coefficient (w)
-    float hn[NC][2];    // support hull: normal of the nearest edge
-    int hmode[NC];      // support hull: 0 inside, 1 edge, 2 vertex
+  static constexpr int NPOSE = grp_npose<P>() > 0 ? grp_npose<P>() : 1;
+  static constexpr int NHULL = grp_nhull<P>() > 0 ? grp_nhull<P>() : 1;
+  struct Eval {           // FK and residual data, live until J is built
+    float zo[D][6];       // joint axis z and origin o (world)
+    float G[NPOSE][9];    // pose-like constraints: rotation into the error frame
+    float x[NPOSE][4];    // reference point of the translational rows
+    float phi[NPOSE][4];  // log-map vector and J_l^-1 coefficient (w)
+    float hn[NHULL][2];   // support hull: normal of the nearest edge
+    int hmode[NHULL];     // support hull: 0 inside, 1 edge, 2 vertex
   };
   struct Solve {         // after the Cholesky
     float Lc[LC];        // L by columns (rows k..K-1 of column k at lcol_base(k))
@@ -390,6 +431,11 @@ struct __align__(16) GrpState {
     Solve s;      // L's columns overwrite it (y, r, dq lie beyond A)
   } u;
   static_assert(NJ >= NF * 12, "task frames live in the Jacobian's space");
+  static_assert(NF * 12 <= grp_cbase<P>() || !needs_com<P>(), "task frames must not overlap the subtree moments");
+  static_assert(grp_cbase<P>() + 3 * D <= NJ || !needs_com<P>(), "subtree moments must fit the 6-row segments' space");
+  // the subtree moments C_j (m_j c_j, then the sum over the subtree), in the
+  // Jacobian's space until the 2-row segments are built
+  __device__ __forceinline__ float *C(int j) { return J + grp_cbase<P>() + 3 * j; }
   static_assert(LC >= K2, "y, r and dq must not overlap the Gram matrix");
 };
 
@@ -405,6 +451,17 @@ struct GrpTables {
   int8_t sgn[P::NC][P::D];  // column sign of joint j in constraint c
   int8_t pad[4 - (P::D * (P::NC + 1)) % 4];  // whole words
 };
+// Shared-memory stride between the states of consecutive configurations: an
+// odd number of 16-byte units, so that the eight configurations of a warp
+// start in eight different banks (with an even number the lanes of the eight
+// groups reading the same field of their state collide in one bank, up to
+// eight ways; measured: 43.7 ms instead of 32.3 ms on the full humanoid batch).
+template <class P>
+__host__ __device__ constexpr size_t grp_state_stride() {
+  constexpr size_t u = (sizeof(GrpState<P>) + 15) / 16;
+  return 16 * ((u % 2 == 0) ? u + 1 : u);
+}
+
 template <class P>
 GrpTables<P> make_grp_tables(const ModelT<float> &m) {
   GrpTables<P> t{};
@@ -479,15 +536,17 @@ __device__ __forceinline__ float grp_residual(const ModelT<float> &m, GrpState<P
   } else if constexpr (kind == K_HULL) {
     const float cx = tot[0] * m.inv_mass, cy = tot[1] * m.inv_mass;
     float px, py, nx, ny;
-    E.hmode[c] = polygon_nearest<float>(m.cB[c], static_cast<int>(m.ctgt[c][0]), cx, cy, px, py, nx, ny);
-    E.hn[c][0] = nx;
-    E.hn[c][1] = ny;
+    constexpr int hs = grp_hslot<P>(c);
+    E.hmode[hs] = polygon_nearest<float>(m.cB[c], static_cast<int>(m.ctgt[c][0]), cx, cy, px, py, nx, ny);
+    E.hn[hs][0] = nx;
+    E.hn[hs][1] = ny;
     const float f0 = cx - px, f1 = cy - py;
     S.F[r0] = f0;
     S.F[r0 + 1] = f1;
     return fmaf(f0, f0, f1 * f1);
   } else {
     static_assert(kind == K_POSE || kind == K_REL, "pose-like constraint expected");
+    constexpr int ps = grp_pslot<P>(c);
     float Pr[9], Rerr[9], G[9];
     load_R(m.cPinv[c], Pr);
     const V3<float> Pp = load_p(m.cPinv[c]);
@@ -529,14 +588,14 @@ __device__ __forceinline__ float grp_residual(const ModelT<float> &m, GrpState<P
     }
     const auto lg = so3_log<OpsF32, float>(Rerr);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) E.G[c][i] = G[i];
-    E.x[c][0] = xpt.x;
-    E.x[c][1] = xpt.y;
-    E.x[c][2] = xpt.z;
-    E.phi[c][0] = lg.phi.x;
-    E.phi[c][1] = lg.phi.y;
-    E.phi[c][2] = lg.phi.z;
-    E.phi[c][3] = jl_inv_beta<float>(lg.theta, lg.s, lg.c);
+    for (int i = 0; i < 9; ++i) E.G[ps][i] = G[i];
+    E.x[ps][0] = xpt.x;
+    E.x[ps][1] = xpt.y;
+    E.x[ps][2] = xpt.z;
+    E.phi[ps][0] = lg.phi.x;
+    E.phi[ps][1] = lg.phi.y;
+    E.phi[ps][2] = lg.phi.z;
+    E.phi[ps][3] = jl_inv_beta<float>(lg.theta, lg.s, lg.c);
     S.F[r0] = t.x;
     S.F[r0 + 1] = t.y;
     S.F[r0 + 2] = t.z;
@@ -710,7 +769,7 @@ __device__ __forceinline__ bool grp_iter(const A &a, const GrpTables<P> &tb, con
           const float mj = tb.mass[j];
 #pragma unroll
           for (int r = 0; r < 3; ++r)
-            E.C[j][r] = mj * fmaf(T[r * 4], cm[0], fmaf(T[r * 4 + 1], cm[1], fmaf(T[r * 4 + 2], cm[2], T[r * 4 + 3])));
+            S.C(j)[r] = mj * fmaf(T[r * 4], cm[0], fmaf(T[r * 4 + 1], cm[1], fmaf(T[r * 4 + 2], cm[2], T[r * 4 + 3])));
           static_for<P::NF>([&](auto FF) {
             constexpr int f = decltype(FF)::value;
             if (j == P::frame_link(f)) {
@@ -734,19 +793,19 @@ __device__ __forceinline__ bool grp_iter(const A &a, const GrpTables<P> &tb, con
     for (int k = 0; k < pl.n_cb; ++k) {
       const int j = pl.cb_j[g][k];
       if (act && j >= 0) {
-        float c0 = E.C[j][0], c1 = E.C[j][1], c2 = E.C[j][2];
+        float c0 = S.C(j)[0], c1 = S.C(j)[1], c2 = S.C(j)[2];
 #pragma unroll
         for (int h = 0; h < GMAX_CH; ++h) {
           const int cj = pl.child[j][h];
           if (cj >= 0) {
-            c0 += E.C[cj][0];
-            c1 += E.C[cj][1];
-            c2 += E.C[cj][2];
+            c0 += S.C(cj)[0];
+            c1 += S.C(cj)[1];
+            c2 += S.C(cj)[2];
           }
         }
-        E.C[j][0] = c0;
-        E.C[j][1] = c1;
-        E.C[j][2] = c2;
+        S.C(j)[0] = c0;
+        S.C(j)[1] = c1;
+        S.C(j)[2] = c2;
       }
     }
     __syncwarp();
@@ -754,28 +813,28 @@ __device__ __forceinline__ bool grp_iter(const A &a, const GrpTables<P> &tb, con
 #pragma unroll 1
       for (int k = 0; k < pl.n_cr; ++k) {
         const int j = pl.cr_j[k];
-        float c0 = E.C[j][0], c1 = E.C[j][1], c2 = E.C[j][2];
+        float c0 = S.C(j)[0], c1 = S.C(j)[1], c2 = S.C(j)[2];
 #pragma unroll
         for (int h = 0; h < GMAX_CH; ++h) {
           const int cj = pl.child[j][h];
           if (cj >= 0) {
-            c0 += E.C[cj][0];
-            c1 += E.C[cj][1];
-            c2 += E.C[cj][2];
+            c0 += S.C(cj)[0];
+            c1 += S.C(cj)[1];
+            c2 += S.C(cj)[2];
           }
         }
-        E.C[j][0] = c0;
-        E.C[j][1] = c1;
-        E.C[j][2] = c2;
+        S.C(j)[0] = c0;
+        S.C(j)[1] = c1;
+        S.C(j)[2] = c2;
       }
     }
     __syncwarp();
 #pragma unroll 1
     for (int k = 0; k < pl.n_roots; ++k) {
       const int rj = pl.roots[k];
-      tot[0] += E.C[rj][0];
-      tot[1] += E.C[rj][1];
-      tot[2] += E.C[rj][2];
+      tot[0] += S.C(rj)[0];
+      tot[1] += S.C(rj)[1];
+      tot[2] += S.C(rj)[2];
     }
   }
   // 3. residuals: constraint c on lane c mod 4
@@ -800,32 +859,8 @@ __device__ __forceinline__ bool grp_iter(const A &a, const GrpTables<P> &tb, con
   }
   const bool go = act && !done;
   __syncwarp();
-  // 4. Jacobian segments
-#pragma unroll 1
-  for (int k = 0; k < pl.n_j6; ++k) {
-    const int j = pl.j6_j[g][k];
-    if (go && j >= 0) {
-      const int c = pl.j6_c[g][k];
-      const float sg = static_cast<float>(tb.sgn[c][j]);
-      const V3<float> z{E.zo[j][0], E.zo[j][1], E.zo[j][2]};
-      const V3<float> o{E.zo[j][3], E.zo[j][4], E.zo[j][5]};
-      float G[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) G[i] = E.G[c][i];
-      const bool rev = tb.rev[j] != 0;
-      const V3<float> xp{E.x[c][0], E.x[c][1], E.x[c][2]};
-      const V3<float> v = rev ? cross(z, sub(xp, o)) : z;
-      const V3<float> vt = mulv(G, v);
-      const V3<float> w = jl_inv_apply(V3<float>{E.phi[c][0], E.phi[c][1], E.phi[c][2]}, E.phi[c][3], mulv(G, z));
-      float *dst = S.J + pl.joff[c][j];
-      dst[0] = sg * vt.x;
-      dst[1] = sg * vt.y;
-      dst[2] = sg * vt.z;
-      dst[3] = rev ? sg * w.x : 0.f;
-      dst[4] = rev ? sg * w.y : 0.f;
-      dst[5] = rev ? sg * w.z : 0.f;
-    }
-  }
+  // 4. Jacobian segments: the 2-row ones first (they read the subtree
+  // moments, which the 6-row segments overwrite)
 #pragma unroll 1
   for (int k = 0; k < pl.n_j2; ++k) {
     const int j = pl.j2_j[g][k];
@@ -836,24 +871,53 @@ __device__ __forceinline__ bool grp_iter(const A &a, const GrpTables<P> &tb, con
       const V3<float> o{E.zo[j][3], E.zo[j][4], E.zo[j][5]};
       const bool rev = tb.rev[j] != 0;
       const float Mj = tb.msub[j];
-      const V3<float> rr{fmaf(-Mj, o.x, E.C[j][0]), fmaf(-Mj, o.y, E.C[j][1]), fmaf(-Mj, o.z, E.C[j][2])};
+      const float *Cj = S.C(j);
+      const V3<float> rr{fmaf(-Mj, o.x, Cj[0]), fmaf(-Mj, o.y, Cj[1]), fmaf(-Mj, o.z, Cj[2])};
       const V3<float> d = cross(z, rr);
       const float fpr = Mj * m.inv_mass;
       float g0 = sg * (rev ? d.x * m.inv_mass : fpr * z.x);
       float g1 = sg * (rev ? d.y * m.inv_mass : fpr * z.y);
       if (pl.chull[c]) {  // inside: 0; on an edge: n n^T g; at a vertex: g
-        const int hm = E.hmode[c];
+        const int hs = pl.hslot[c];
+        const int hm = E.hmode[hs];
         if (hm == 0) {
           g0 = g1 = 0.f;
         } else if (hm == 1) {
-          const float sd = fmaf(E.hn[c][0], g0, E.hn[c][1] * g1);
-          g0 = E.hn[c][0] * sd;
-          g1 = E.hn[c][1] * sd;
+          const float sd = fmaf(E.hn[hs][0], g0, E.hn[hs][1] * g1);
+          g0 = E.hn[hs][0] * sd;
+          g1 = E.hn[hs][1] * sd;
         }
       }
       float *dst = S.J + pl.joff[c][j];
       dst[0] = g0;
       dst[1] = g1;
+    }
+  }
+  __syncwarp();
+#pragma unroll 1
+  for (int k = 0; k < pl.n_j6; ++k) {
+    const int j = pl.j6_j[g][k];
+    if (go && j >= 0) {
+      const int c = pl.j6_c[g][k];
+      const float sg = static_cast<float>(tb.sgn[c][j]);
+      const V3<float> z{E.zo[j][0], E.zo[j][1], E.zo[j][2]};
+      const V3<float> o{E.zo[j][3], E.zo[j][4], E.zo[j][5]};
+      float G[9];
+      const int ps = pl.pslot[c];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) G[i] = E.G[ps][i];
+      const bool rev = tb.rev[j] != 0;
+      const V3<float> xp{E.x[ps][0], E.x[ps][1], E.x[ps][2]};
+      const V3<float> v = rev ? cross(z, sub(xp, o)) : z;
+      const V3<float> vt = mulv(G, v);
+      const V3<float> w = jl_inv_apply(V3<float>{E.phi[ps][0], E.phi[ps][1], E.phi[ps][2]}, E.phi[ps][3], mulv(G, z));
+      float *dst = S.J + pl.joff[c][j];
+      dst[0] = sg * vt.x;
+      dst[1] = sg * vt.y;
+      dst[2] = sg * vt.z;
+      dst[3] = rev ? sg * w.x : 0.f;
+      dst[4] = rev ? sg * w.y : 0.f;
+      dst[5] = rev ? sg * w.z : 0.f;
     }
   }
   __syncwarp();
@@ -1100,11 +1164,11 @@ __device__ __forceinline__ bool grp_iter(const A &a, const GrpTables<P> &tb, con
 }
 
 template <class P, int W>
-__global__ void __launch_bounds__(W * 32) k_project_group(const __grid_constant__ GroupArgs<P> a) {
+__global__ void __launch_bounds__(W * 32, 1) k_project_group(const __grid_constant__ GroupArgs<P> a) {
   constexpr int D = P::D;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   GrpShared<P> &sh = *reinterpret_cast<GrpShared<P> *>(smem_raw);
-  GrpState<P> *ws = reinterpret_cast<GrpState<P> *>(smem_raw + ((sizeof(GrpShared<P>) + 15) & ~size_t(15)));
+  unsigned char *ws = smem_raw + ((sizeof(GrpShared<P>) + 15) & ~size_t(15));
   __shared__ long long s_item[W][40];  // parked configurations: < 32 + 8
   __shared__ uint32_t s_meta[W][40];
   __shared__ long long s_ritem[W][RETRY_CAP];  // sent back to the FP32 loop by the acceptance
@@ -1123,7 +1187,7 @@ __global__ void __launch_bounds__(W * 32) k_project_group(const __grid_constant_
   const int wib = threadIdx.x >> 5;
   const int g = lane & (GG - 1);
   const int grp = lane >> 2;
-  GrpState<P> &S = ws[wib * GCPW + grp];
+  GrpState<P> &S = *reinterpret_cast<GrpState<P> *>(ws + (wib * GCPW + grp) * grp_state_stride<P>());
   long long qn = 0, qe = 0;  // warp-local queue [qn, qe)
   bool more = true;
   bool act = false;
@@ -1238,7 +1302,7 @@ __global__ void __launch_bounds__(W * 32) k_project_group(const __grid_constant_
 
 template <class P>
 size_t group_smem_bytes(int W) {
-  return ((sizeof(GrpShared<P>) + 15) & ~size_t(15)) + static_cast<size_t>(W) * GCPW * sizeof(GrpState<P>);
+  return ((sizeof(GrpShared<P>) + 15) & ~size_t(15)) + static_cast<size_t>(W) * GCPW * grp_state_stride<P>();
 }
 
 template <class P>
@@ -1246,7 +1310,7 @@ cudaError_t launch_project_group(const HostModel &hm, const ProjCall &c, int *la
   static_assert(grp_supported<P>(), "the group kernel takes trees with pose-like and CoM-like constraints");
   if (c.total <= 0) return cudaSuccess;
   if (c.precision == 1 || c.segments || c.outer || c.cyclic) return cudaErrorNotSupported;
-  constexpr int W = 2;
+  constexpr int W = 10;  // one block per SM: 80 configurations, bounded by shared memory
   struct Planned {
     GroupPlan<P> plan;
     bool ok;

@@ -975,8 +975,8 @@ __device__ __forceinline__ bool accept_one(const A &a, long long item, int it, u
   constexpr int D = P::D;
   const ModelT<double> &m = *a.m64;
   float q[D];
-#pragma unroll
   const bool ok = MCP_CHK(item, a.ld_out);
+#pragma unroll
   for (int j = 0; j < D; ++j) q[j] = ok ? a.q_out[j * a.ld_out + item] : 0.f;
   double r2 = residual2_f64<P>(OpsF64Split{a.tab}, m, q);
   if (retry_ok && (fl & FL_INT_FP32CONV) && !(r2 < a.tol2_64) && r2 <= DBL_MAX && it < a.cap) return true;
@@ -1470,9 +1470,10 @@ __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(con
     const unsigned fin = __ballot_sync(FULL, done);
     if (fin != 0u) {
       if (done) {
+        if (MCP_CHK(item, a.ld_out)) {
 #pragma unroll
-        if (MCP_CHK(item, a.ld_out))
           for (int j = 0; j < D; ++j) a.q_out[j * a.ld_out + item] = q[j];
+        }
         const int pos = pend + __popc(fin & ((1u << lane) - 1u));
         s_item[wib][pos] = item;
         s_meta[wib][pos] = static_cast<uint32_t>(it) | (fl << 8);
@@ -1500,8 +1501,8 @@ __global__ void __launch_bounds__(TPB, (min_blocks<P, TPB>())) k_project_f32(con
         if constexpr (CHK) {
           if (!retry) {
             float qc[D];
-#pragma unroll
             const bool okc = MCP_CHK(it_item, a.ld_out);
+#pragma unroll
             for (int j = 0; j < D; ++j) qc[j] = okc ? a.q_out[j * a.ld_out + it_item] : 0.f;
             uint32_t tests = 0;
             const bool h = check_one_f32<P>(a.chk->m, a.chk->st, s_pair, a.n_obs, s_box, a.n_box, a.tab, qc, tests);

@@ -315,9 +315,10 @@ __global__ void __launch_bounds__(TPB, (pair_min_blocks<TPB>())) k_project_pair(
     const unsigned fin = __ballot_sync(FULL, done) & EVEN;
     if (fin != 0u) {
       if (done) {
+        if (MCP_CHK(item, a.ld_out)) {
 #pragma unroll
-        if (MCP_CHK(item, a.ld_out))
           for (int j = 0; j < H; ++j) a.q_out[(H * h + j) * a.ld_out + item] = q[j];
+        }
         if (h == 0) {
           const int pos = pend + __popc(fin & before);
           s_item[wib][pos] = item;
@@ -345,8 +346,8 @@ __global__ void __launch_bounds__(TPB, (pair_min_blocks<TPB>())) k_project_pair(
         if constexpr (CHK) {  // the collision check of the accepted output, one configuration per lane
           if (!retry) {
             float qc[P::D];
-#pragma unroll
             const bool okc = MCP_CHK(it_item, a.ld_out);
+#pragma unroll
             for (int j = 0; j < P::D; ++j) qc[j] = okc ? a.q_out[j * a.ld_out + it_item] : 0.f;
             uint32_t tests = 0;
             const bool hit = check_one_f32<P>(a.chk->m, a.chk->st, s_pair, a.n_obs, s_box, a.n_box, a.tab, qc, tests);
