@@ -51,6 +51,7 @@ UNIT = "projections/s"
 # (workload, kernel); an entry is removed whenever its kernel changes.
 MEASURED_TRAFFIC = {
     ("arm7_axis_65536", "k_project_f32+check"): 1990656,                  # read 1.99 MB, write 0
+    ("humanoid36_1048576", "k_project_group"): 240985088 + 136097280,     # read 241.0 MB, write 136.1 MB
 }
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 
