@@ -15,14 +15,18 @@
 //      the mass moments m_j c_j;
 //   2. subtree mass moments C_j = m_j c_j + sum over children, limbs first,
 //      then the trunk;
-//   3. residuals, constraint c on lane c mod 4; ||F|| by a group reduction;
+//   3. residuals, constraint c on lane c mod 4 (the pose and relative-pose
+//      constraints on one code path, so that their lanes run it together);
+//      ||F|| by a group reduction;
 //   4. the structural nonzeros of J, as (joint, constraint) segments spread
 //      over the lanes;
 //   5. the Gram matrix J J^T by blocks: each lane accumulates whole row-block
 //      pairs (6x6, 2x6, 2x2) over the joints both blocks share, in registers;
 //   6. Cholesky with rows i = 4m + g on lane g (registers), column k of L
 //      exchanged through shared memory (which keeps L by columns for the
-//      back substitution);
+//      back substitution); blocks of L that the symbolic factorisation
+//      proves zero (feet rows against hand columns) are skipped at compile
+//      time, in the factorisation and both substitutions;
 //   7. forward / back substitution, dq = J^T y, one refinement step
 //      (r = F - J dq - lambda y), alpha, MaxDistance, q <- q - dq.
 // Finished configurations are parked and accepted in FP64 32 at a time, one
@@ -110,6 +114,45 @@ __host__ __device__ constexpr int lcol_base(int k) {
   return o;
 }
 
+// Structural nonzeros of the Cholesky factor of A = J J^T + lambda I, row by
+// row (bit b of row i: L[i][b] may be nonzero).  The symbolic factorisation:
+// L[i][b] is nonzero where A[i][b] is (rows i and b of J share a joint) or
+// where L[i][j] and L[b][j] are both nonzero for some column j < b.
+template <class P>
+__host__ __device__ constexpr uint32_t l_row_pattern(int row) {
+  constexpr int K = kdim<P>();
+  uint64_t jm[MAXK] = {};  // joints of row i of J
+  for (int i = 0; i < K; ++i)
+    for (int j = 0; j < P::D; ++j)
+      if (jnz<P>(i, j)) jm[i] |= uint64_t(1) << j;
+  uint32_t nz[MAXK] = {};
+  for (int i = 0; i < K; ++i)
+    for (int b = 0; b <= i; ++b) {
+      bool v = (b == i) || (jm[i] & jm[b]) != 0;
+      for (int j = 0; j < b && !v; ++j) v = ((nz[i] >> j) & 1u) != 0 && ((nz[b] >> j) & 1u) != 0;
+      if (v) nz[i] |= 1u << b;
+    }
+  return nz[row];
+}
+template <class P, int I>
+struct LRow {
+  static constexpr uint32_t value = l_row_pattern<P>(I);
+};
+// Rows 4 mm .. 4 mm + 3 (one per lane of a group) all lie below row k and
+// are structurally zero in column k of L: the group skips their update.
+template <class P, int MM, int KC>
+__host__ __device__ constexpr bool l_col_block_zero() {
+  constexpr uint32_t m = LRow<P, GG * MM>::value | LRow<P, GG * MM + 1>::value | LRow<P, GG * MM + 2>::value |
+                         LRow<P, GG * MM + 3>::value;
+  return GG * MM > KC && ((m >> KC) & 1u) == 0u;
+}
+// Columns 4 mm .. 4 mm + 3 all lie left of column k and row k of L is
+// structurally zero in them.
+template <class P, int KR, int MM>
+__host__ __device__ constexpr bool l_row_seg_zero() {
+  return GG * MM + GG - 1 < KR && ((LRow<P, KR>::value >> (GG * MM)) & 0xFu) == 0u;
+}
+
 // Tasks of the Gram build and of the refinement residual: row blocks (a, b)
 // (b unused for the refinement) and a joint list pool[off, off + n).
 struct GrpTask {
@@ -145,6 +188,8 @@ struct GroupPlan {
   int8_t chull[NC];     // constraint c is the support-hull kind
   int8_t pslot[NC];     // slot of constraint c among the pose-like ones (-1: other kinds)
   int8_t hslot[NC];     // slot of constraint c among the support-hull ones (-1: other kinds)
+  int8_t crel[NC];      // pose-like constraint c is the relative pose of two frames
+  int8_t cfa[NC], cfb[NC];  // its frames (cfb: the relative pose's second frame, else cfa)
   // 5. Gram phases (6x6, 6x2, 2x6, 2x2 row-block pairs) and 7. refinement
   // phases (6-row, 2-row blocks): tasks per lane.  The diagonal blocks and
   // refinement rows of 2-row constraints (the CoM, over every joint) are
@@ -295,6 +340,9 @@ bool make_group_plan(GroupPlan<P> &pl, const char **why) {
     pl.chull[c] = static_cast<int8_t>(P::ckind(c) == K_HULL);
     pl.pslot[c] = static_cast<int8_t>(grp_pose_like<P>(c) ? grp_pslot<P>(c) : -1);
     pl.hslot[c] = static_cast<int8_t>(P::ckind(c) == K_HULL ? grp_hslot<P>(c) : -1);
+    pl.crel[c] = static_cast<int8_t>(P::ckind(c) == K_REL);
+    pl.cfa[c] = static_cast<int8_t>(grp_pose_like<P>(c) ? P::cfa(c) : 0);
+    pl.cfb[c] = static_cast<int8_t>(P::ckind(c) == K_REL ? P::cfb(c) : pl.cfa[c]);
   }
   // 4. segments: a limb's segments on its lane, the trunk's on the lane with
   // the fewest segments of that size
@@ -606,6 +654,75 @@ __device__ __forceinline__ float grp_residual(const ModelT<float> &m, GrpState<P
   }
 }
 
+// Residual of pose-like constraint c (run time: the pose and relative-pose
+// constraints of a stack run one code path, on their lanes at once) into
+// S.F, with the data the Jacobian needs; returns its squared norm.
+//   pose (Eq. 1):          G = P^-1_R,          R_err = G (R_a Q^-1_R),
+//                          x = p_a + R_a Q^-1_p, t = G x + P^-1_p;
+//   relative pose (Eq. 2): G = P^-1_R R_a^T,    R_err = G R_b,
+//                          x = p_b,             t = G (p_b - p_a) + P^-1_p.
+// Each product is formed with the operands the constraint's kind selects,
+// in the same order as for that kind alone.
+template <class P>
+__device__ __forceinline__ float grp_residual_pose(const ModelT<float> &m, GrpState<P> &S, const GroupPlan<P> &pl,
+                                                   int c) {
+  auto &E = S.u.e;
+  const float(*Tf)[12] = reinterpret_cast<const float(*)[12]>(S.J);
+  const bool rel = pl.crel[c] != 0;
+  const int r0 = pl.croff[c], ps = pl.pslot[c], fa = pl.cfa[c], fb = pl.cfb[c];
+  float Pr[9], Qr[9], Ra[9], Rb[9];
+  load_R(m.cPinv[c], Pr);
+  load_R(m.cQinv[c], Qr);
+  const V3<float> Pp = load_p(m.cPinv[c]);
+  const V3<float> Qp = load_p(m.cQinv[c]);
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      Ra[r * 3 + cc] = Tf[fa][r * 4 + cc];
+      Rb[r * 3 + cc] = Tf[fb][r * 4 + cc];
+    }
+  const V3<float> pa{Tf[fa][3], Tf[fa][7], Tf[fa][11]};
+  const V3<float> pb{Tf[fb][3], Tf[fb][7], Tf[fb][11]};
+  float X1[9], Y1[9], Z[9], X2[9], Y2[9], Rerr[9], G[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      X1[r * 3 + cc] = rel ? Pr[r * 3 + cc] : Ra[r * 3 + cc];
+      Y1[r * 3 + cc] = rel ? Ra[cc * 3 + r] : Qr[r * 3 + cc];
+    }
+  mul33(X1, Y1, Z);  // pose: R_a Q^-1_R; relative pose: G
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    X2[i] = rel ? Z[i] : Pr[i];
+    Y2[i] = rel ? Rb[i] : Z[i];
+    G[i] = rel ? Z[i] : Pr[i];
+  }
+  mul33(X2, Y2, Rerr);
+  const V3<float> xq = add_rot_t<7>(pa, Ra, Qp);
+  const V3<float> xpt{rel ? pb.x : xq.x, rel ? pb.y : xq.y, rel ? pb.z : xq.z};
+  const V3<float> tx = mulv(G, rel ? sub(pb, pa) : xq);
+  const V3<float> t{tx.x + Pp.x, tx.y + Pp.y, tx.z + Pp.z};
+  const auto lg = so3_log<OpsF32, float>(Rerr);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) E.G[ps][i] = G[i];
+  E.x[ps][0] = xpt.x;
+  E.x[ps][1] = xpt.y;
+  E.x[ps][2] = xpt.z;
+  E.phi[ps][0] = lg.phi.x;
+  E.phi[ps][1] = lg.phi.y;
+  E.phi[ps][2] = lg.phi.z;
+  E.phi[ps][3] = jl_inv_beta<float>(lg.theta, lg.s, lg.c);
+  S.F[r0] = t.x;
+  S.F[r0 + 1] = t.y;
+  S.F[r0 + 2] = t.z;
+  S.F[r0 + 3] = lg.phi.x;
+  S.F[r0 + 4] = lg.phi.y;
+  S.F[r0 + 5] = lg.phi.z;
+  return fmaf(t.x, t.x, fmaf(t.y, t.y, fmaf(t.z, t.z, fmaf(lg.phi.x, lg.phi.x, fmaf(lg.phi.y, lg.phi.y, lg.phi.z * lg.phi.z)))));
+}
+
 // Gram phase with row blocks of RA x RB rows: every lane runs its task slots;
 // each task accumulates sum_j seg(j, a) seg(j, b)^T over its joints in
 // registers and stores the lower-triangular part into S.u.A.
@@ -770,17 +887,18 @@ __device__ __forceinline__ bool grp_iter(const A &a, const GrpTables<P> &tb, con
 #pragma unroll
           for (int r = 0; r < 3; ++r)
             S.C(j)[r] = mj * fmaf(T[r * 4], cm[0], fmaf(T[r * 4 + 1], cm[1], fmaf(T[r * 4 + 2], cm[2], T[r * 4 + 3])));
+          int f = -1;  // the task frame on this link, if any (one copy of the composition)
           static_for<P::NF>([&](auto FF) {
-            constexpr int f = decltype(FF)::value;
-            if (j == P::frame_link(f)) {
-              float Fx[12], To[12];
-#pragma unroll
-              for (int e = 0; e < 12; ++e) Fx[e] = tb.fX[f][e];
-              compose34(T, Fx, To);
-#pragma unroll
-              for (int e = 0; e < 12; ++e) S.J[f * 12 + e] = To[e];
-            }
+            if (j == P::frame_link(decltype(FF)::value)) f = decltype(FF)::value;
           });
+          if (f >= 0) {
+            float Fx[12], To[12];
+#pragma unroll
+            for (int e = 0; e < 12; ++e) Fx[e] = tb.fX[f][e];
+            compose34(T, Fx, To);
+#pragma unroll
+            for (int e = 0; e < 12; ++e) S.J[f * 12 + e] = To[e];
+          }
         }
       }
     }
@@ -837,11 +955,19 @@ __device__ __forceinline__ bool grp_iter(const A &a, const GrpTables<P> &tb, con
       tot[2] += S.C(rj)[2];
     }
   }
-  // 3. residuals: constraint c on lane c mod 4
+  // 3. residuals: constraint c on lane c mod 4; the pose-like ones share one
+  // code path (run time), the others have their own (compile time)
   float r2p = 0.f;
+  if constexpr (grp_npose<P>() > 0) {
+#pragma unroll 1
+    for (int c = g; c < NC; c += GG)
+      if (act && pl.pslot[c] >= 0) r2p += grp_residual_pose<P>(m, S, pl, c);
+  }
   static_for<NC>([&](auto CC) {
     constexpr int c = decltype(CC)::value;
-    if (act && g == (c % GG)) r2p += grp_residual<P, c>(m, S, tot);
+    if constexpr (!grp_pose_like<P>(c)) {
+      if (act && g == (c % GG)) r2p += grp_residual<P, c>(m, S, tot);
+    }
   });
   const float r2 = grp_sum(r2p);
   bool done = false;
@@ -972,8 +1098,8 @@ __device__ __forceinline__ bool grp_iter(const A &a, const GrpTables<P> &tb, con
   }
   __syncwarp();
   float minpiv = FLT_MAX;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
+  static_for<K>([&](auto KK) {
+    constexpr int k = decltype(KK)::value;
     const int ow = k % GG, mk = k / GG;
     const float piv = __shfl_sync(FULL, L[mk][k], base + ow);
     minpiv = fminf(minpiv, piv);
@@ -996,16 +1122,18 @@ __device__ __forceinline__ bool grp_iter(const A &a, const GrpTables<P> &tb, con
       float cv[K];
 #pragma unroll
       for (int b = k + 1; b < K; ++b) cv[b] = go ? col[b - k] : 0.f;
+      static_for<MR>([&](auto MMc) {
+        constexpr int mm = decltype(MMc)::value;
+        if constexpr (mm >= (k + 1) / GG && !l_col_block_zero<P, mm, k>()) {
+          const int i = GG * mm + g;
+          const float lik = L[mm][k];
 #pragma unroll
-      for (int mm = (k + 1) / GG; mm < MR; ++mm) {
-        const int i = GG * mm + g;
-        const float lik = L[mm][k];
-#pragma unroll
-        for (int b = k + 1; b < GG * (mm + 1) && b < K; ++b)
-          if (i > k && b <= i) L[mm][b] = fmaf(-lik, cv[b], L[mm][b]);
-      }
+          for (int b = k + 1; b < GG * (mm + 1) && b < K; ++b)
+            if (i > k && b <= i) L[mm][b] = fmaf(-lik, cv[b], L[mm][b]);
+        }
+      });
     }
-  }
+  });
   if (go && !(minpiv >= a.pivot)) {  // includes NaN: this configuration continues in FP64
     fl |= FL_INT_NEEDS_F64;
     done = true;
@@ -1016,33 +1144,37 @@ __device__ __forceinline__ bool grp_iter(const A &a, const GrpTables<P> &tb, con
   for (int mm = 0; mm < MR; ++mm) colo[mm] = pl.lcol[(GG * mm + g) < K ? GG * mm + g : 0];
   // (L L^T)^{-1} b for rows held by the lanes (t[mm] = b_{4 mm + g})
   auto subst = [&](float (&t)[MR]) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {  // forward: L y = b
-      const int ow = k % GG, mk = k / GG;
+    static_for<K>([&](auto KK) {  // forward: L y = b
+      constexpr int k = decltype(KK)::value;
+      constexpr int ow = k % GG, mk = k / GG;
       const float yk = __shfl_sync(FULL, t[mk] * invd[mk], base + ow);
-#pragma unroll
-      for (int mm = mk; mm < MR; ++mm) {
-        const int i = GG * mm + g;
-        if (i == k) t[mm] = yk;
-        else if (i > k) t[mm] = fmaf(-L[mm][k], yk, t[mm]);
-      }
-    }
-#pragma unroll
-    for (int k = K - 1; k >= 0; --k) {  // back: L^T x = y, L[k][i] from column i
-      const int ow = k % GG, mk = k / GG;
-      const float xk = __shfl_sync(FULL, t[mk] * invd[mk], base + ow);
-#pragma unroll
-      for (int mm = 0; mm <= mk; ++mm) {
-        const int i = GG * mm + g;
-        if (i == k) {
-          t[mm] = xk;
-        } else if (i < k) {
-          // L[k][i]: row k of column i
-          const float l = go2 ? S.u.s.Lc[colo[mm] + (k - i)] : 0.f;
-          t[mm] = fmaf(-l, xk, t[mm]);
+      static_for<MR>([&](auto MMc) {
+        constexpr int mm = decltype(MMc)::value;
+        if constexpr (mm >= mk && !l_col_block_zero<P, mm, k>()) {
+          const int i = GG * mm + g;
+          if (i == k) t[mm] = yk;
+          else if (i > k) t[mm] = fmaf(-L[mm][k], yk, t[mm]);
         }
-      }
-    }
+      });
+    });
+    static_for<K>([&](auto KB) {  // back: L^T x = y, L[k][i] from column i
+      constexpr int k = K - 1 - decltype(KB)::value;
+      constexpr int ow = k % GG, mk = k / GG;
+      const float xk = __shfl_sync(FULL, t[mk] * invd[mk], base + ow);
+      static_for<MR>([&](auto MMc) {
+        constexpr int mm = decltype(MMc)::value;
+        if constexpr (mm <= mk && !l_row_seg_zero<P, k, mm>()) {
+          const int i = GG * mm + g;
+          if (i == k) {
+            t[mm] = xk;
+          } else if (i < k) {
+            // L[k][i]: row k of column i
+            const float l = go2 ? S.u.s.Lc[colo[mm] + (k - i)] : 0.f;
+            t[mm] = fmaf(-l, xk, t[mm]);
+          }
+        }
+      });
+    });
   };
   // dq = J^T y for the lane's dq joints (y from shared memory)
   auto jt_y = [&]() {
@@ -1071,64 +1203,62 @@ __device__ __forceinline__ bool grp_iter(const A &a, const GrpTables<P> &tb, con
       }
     }
   };
-  float t[MR];
+  // y = A^{-1} F, then one refinement step with the residual from J,
+  // r = F - J (J^T y) - lambda y: y += A^{-1} r.  Both passes run the same
+  // code (a loop, not two inlined copies).
+  float t[MR], ty[MR];
 #pragma unroll
   for (int mm = 0; mm < MR; ++mm) {
     const int i = GG * mm + g;
     t[mm] = (go2 && i < K) ? S.F[i] : 0.f;
+    ty[mm] = 0.f;
   }
-  subst(t);
-#pragma unroll
-  for (int mm = 0; mm < MR; ++mm) {
-    const int i = GG * mm + g;
-    if (go2 && i < K) S.u.s.y[i] = t[mm];
-  }
-  __syncwarp();
-  jt_y();
-  __syncwarp();
-  // one refinement step with the residual from J: r = F - J (J^T y) - lambda y
-  grp_resid_phase<6>(pl, 0, g, go2, a.lambda, S);
-  static_for<NC>([&](auto CC) {  // 2-row blocks: every joint, over the dq partition
-    constexpr int c = decltype(CC)::value;
-    if constexpr (grp_com_like<P>(c)) {
-      constexpr int r0 = roff<P>(c);
-      float s0 = 0.f, s1 = 0.f;
 #pragma unroll 1
-      for (int k = 0; k < pl.n_dq; ++k) {
-        const int j = pl.dq_j[g][k];
-        const int o = j >= 0 ? pl.joff[c][j] : -1;
-        if (go2 && o >= 0) {
-          const float2 v = lds2(S.J + o);
-          const float dj = S.u.s.dq[j];
-          s0 = fmaf(v.x, dj, s0);
-          s1 = fmaf(v.y, dj, s1);
+  for (int pass = 0; pass < 2; ++pass) {
+    subst(t);
+#pragma unroll
+    for (int mm = 0; mm < MR; ++mm) {
+      const int i = GG * mm + g;
+      ty[mm] += t[mm];
+      if (go2 && i < K) S.u.s.y[i] = ty[mm];
+    }
+    __syncwarp();
+    jt_y();
+    __syncwarp();
+    if (pass == 1) break;
+    grp_resid_phase<6>(pl, 0, g, go2, a.lambda, S);
+    static_for<NC>([&](auto CC) {  // 2-row blocks: every joint, over the dq partition
+      constexpr int c = decltype(CC)::value;
+      if constexpr (grp_com_like<P>(c)) {
+        constexpr int r0 = roff<P>(c);
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll 1
+        for (int k = 0; k < pl.n_dq; ++k) {
+          const int j = pl.dq_j[g][k];
+          const int o = j >= 0 ? pl.joff[c][j] : -1;
+          if (go2 && o >= 0) {
+            const float2 v = lds2(S.J + o);
+            const float dj = S.u.s.dq[j];
+            s0 = fmaf(v.x, dj, s0);
+            s1 = fmaf(v.y, dj, s1);
+          }
+        }
+        s0 = grp_sum(s0);
+        s1 = grp_sum(s1);
+        if (go2 && g == 0) {
+          S.u.s.r[r0] = fmaf(-a.lambda, S.u.s.y[r0], S.F[r0] - s0);
+          S.u.s.r[r0 + 1] = fmaf(-a.lambda, S.u.s.y[r0 + 1], S.F[r0 + 1] - s1);
         }
       }
-      s0 = grp_sum(s0);
-      s1 = grp_sum(s1);
-      if (go2 && g == 0) {
-        S.u.s.r[r0] = fmaf(-a.lambda, S.u.s.y[r0], S.F[r0] - s0);
-        S.u.s.r[r0 + 1] = fmaf(-a.lambda, S.u.s.y[r0 + 1], S.F[r0 + 1] - s1);
-      }
+    });
+    __syncwarp();
+#pragma unroll
+    for (int mm = 0; mm < MR; ++mm) {
+      const int i = GG * mm + g;
+      t[mm] = (go2 && i < K) ? S.u.s.r[i] : 0.f;
     }
-  });
-  __syncwarp();
-  float t2[MR];
-#pragma unroll
-  for (int mm = 0; mm < MR; ++mm) {
-    const int i = GG * mm + g;
-    t2[mm] = (go2 && i < K) ? S.u.s.r[i] : 0.f;
+    __syncwarp();
   }
-  subst(t2);
-  __syncwarp();
-#pragma unroll
-  for (int mm = 0; mm < MR; ++mm) {
-    const int i = GG * mm + g;
-    if (go2 && i < K) S.u.s.y[i] = t[mm] + t2[mm];
-  }
-  __syncwarp();
-  jt_y();
-  __syncwarp();
   // alpha, MaxDistance, update
   float s2p = 0.f;
 #pragma unroll 1
