@@ -40,16 +40,18 @@
 
 namespace mcp {
 
+// Limits of the work plan (the plan is copied into every block's shared
+// memory, so they are kept near what the humanoid classes need).
 constexpr int GG = 4;            // lanes per configuration
 constexpr int GCPW = 32 / GG;    // configurations per warp
-constexpr int GMAX_FK = 24;      // FK steps per lane
-constexpr int GMAX_CB = 24;      // own joints per lane (subtree moments)
+constexpr int GMAX_FK = 20;      // FK steps per lane
+constexpr int GMAX_CB = 16;      // own joints per lane (subtree moments)
 constexpr int GMAX_CR = 16;      // trunk joints
 constexpr int GMAX_CH = 4;       // children per joint
-constexpr int GMAX_JI = 32;      // Jacobian segments per lane and segment size
+constexpr int GMAX_JI = 16;      // Jacobian segments per lane and segment size
 constexpr int GMAX_DQ = 20;      // dq joints per lane
-constexpr int GMAX_T = 4;        // Gram / refinement tasks per lane and phase
-constexpr int GMAX_POOL = 640;   // joint lists of the tasks
+constexpr int GMAX_T = 2;        // Gram / refinement tasks per lane and phase
+constexpr int GMAX_POOL = 192;   // joint lists of the tasks
 
 template <class P>
 __host__ __device__ constexpr bool grp_pose_like(int c) {
@@ -106,11 +108,11 @@ __host__ __device__ constexpr int grp_cbase() {
   return (n + 3) & ~3;
 }
 
-// L by columns, each column padded to a multiple of 4 floats (16-byte loads)
+// L by columns, packed: rows k .. K-1 of column k from lcol_base(k)
 template <int K>
 __host__ __device__ constexpr int lcol_base(int k) {
   int o = 0;
-  for (int t = 0; t < k; ++t) o += (K - t + 3) & ~3;
+  for (int t = 0; t < k; ++t) o += K - t;
   return o;
 }
 
@@ -464,19 +466,18 @@ struct __align__(16) GrpState {
     float hn[NHULL][2];   // support hull: normal of the nearest edge
     int hmode[NHULL];     // support hull: 0 inside, 1 edge, 2 vertex
   };
-  struct Solve {         // after the Cholesky
+  struct Solve {         // after the Cholesky (the refinement's residual r overwrites F)
     float Lc[LC];        // L by columns (rows k..K-1 of column k at lcol_base(k))
     float y[KP];
-    float r[KP];
     float dq[DP];
   };
   float q[DP];
-  float F[KP];
+  float F[KP];  // F, then the refinement's residual r = F - J dq - lambda y
   float J[NJ];  // Jacobian segments; before they are built, the task frames (NF x 12)
   union alignas(16) {
     Eval e;
     float A[K2];  // Gram (packed lower triangle, row-major), read into registers before
-    Solve s;      // L's columns overwrite it (y, r, dq lie beyond A)
+    Solve s;      // L's columns overwrite it (y and dq lie beyond A)
   } u;
   static_assert(NJ >= NF * 12, "task frames live in the Jacobian's space");
   static_assert(NF * 12 <= grp_cbase<P>() || !needs_com<P>(), "task frames must not overlap the subtree moments");
@@ -484,7 +485,7 @@ struct __align__(16) GrpState {
   // the subtree moments C_j (m_j c_j, then the sum over the subtree), in the
   // Jacobian's space until the 2-row segments are built
   __device__ __forceinline__ float *C(int j) { return J + grp_cbase<P>() + 3 * j; }
-  static_assert(LC >= K2, "y, r and dq must not overlap the Gram matrix");
+  static_assert(LC >= K2, "y and dq must not overlap the Gram matrix");
 };
 
 // Model data the group kernel reads with runtime joint indices (shared memory).
@@ -803,7 +804,7 @@ __device__ __forceinline__ void grp_resid_phase(const GroupPlan<P> &pl, int ph, 
     if (go && tk.n > 0) {
       const int ra = pl.croff[tk.a];
 #pragma unroll
-      for (int i = 0; i < RA; ++i) S.u.s.r[ra + i] = fmaf(-lambda, S.u.s.y[ra + i], S.F[ra + i] - acc[i]);
+      for (int i = 0; i < RA; ++i) S.F[ra + i] = fmaf(-lambda, S.u.s.y[ra + i], S.F[ra + i] - acc[i]);
     }
   }
 }
@@ -1246,8 +1247,8 @@ __device__ __forceinline__ bool grp_iter(const A &a, const GrpTables<P> &tb, con
         s0 = grp_sum(s0);
         s1 = grp_sum(s1);
         if (go2 && g == 0) {
-          S.u.s.r[r0] = fmaf(-a.lambda, S.u.s.y[r0], S.F[r0] - s0);
-          S.u.s.r[r0 + 1] = fmaf(-a.lambda, S.u.s.y[r0 + 1], S.F[r0 + 1] - s1);
+          S.F[r0] = fmaf(-a.lambda, S.u.s.y[r0], S.F[r0] - s0);
+          S.F[r0 + 1] = fmaf(-a.lambda, S.u.s.y[r0 + 1], S.F[r0 + 1] - s1);
         }
       }
     });
@@ -1255,7 +1256,7 @@ __device__ __forceinline__ bool grp_iter(const A &a, const GrpTables<P> &tb, con
 #pragma unroll
     for (int mm = 0; mm < MR; ++mm) {
       const int i = GG * mm + g;
-      t[mm] = (go2 && i < K) ? S.u.s.r[i] : 0.f;
+      t[mm] = (go2 && i < K) ? S.F[i] : 0.f;
     }
     __syncwarp();
   }
@@ -1299,9 +1300,9 @@ __global__ void __launch_bounds__(W * 32, 1) k_project_group(const __grid_consta
   extern __shared__ __align__(16) unsigned char smem_raw[];
   GrpShared<P> &sh = *reinterpret_cast<GrpShared<P> *>(smem_raw);
   unsigned char *ws = smem_raw + ((sizeof(GrpShared<P>) + 15) & ~size_t(15));
-  __shared__ long long s_item[W][40];  // parked configurations: < 32 + 8
+  __shared__ int s_item[W][40];  // parked configurations: < 32 + 8 (the launcher keeps totals below 2^31)
   __shared__ uint32_t s_meta[W][40];
-  __shared__ long long s_ritem[W][RETRY_CAP];  // sent back to the FP32 loop by the acceptance
+  __shared__ int s_ritem[W][RETRY_CAP];  // sent back to the FP32 loop by the acceptance
   __shared__ uint32_t s_rmeta[W][RETRY_CAP];
   {
     static_assert(sizeof(GrpTables<P>) % 4 == 0 && sizeof(GroupPlan<P>) % 4 == 0, "word copies");
@@ -1392,7 +1393,7 @@ __global__ void __launch_bounds__(W * 32, 1) k_project_group(const __grid_consta
           for (int j = g; j < D; j += GG) a.q_out[j * a.ld_out + item] = S.q[j];
         if (g == 0) {
           const int pos = pend + __popc(fin & ((1u << lane) - 1u));
-          s_item[wib][pos] = item;
+          s_item[wib][pos] = static_cast<int>(item);
           s_meta[wib][pos] = static_cast<uint32_t>(it) | (fl << 8);
         }
         act = false;
@@ -1419,7 +1420,7 @@ __global__ void __launch_bounds__(W * 32, 1) k_project_group(const __grid_consta
       __syncwarp();
       if (retry) {
         const int rp = nret + __popc(rm & ((1u << lane) - 1u));
-        s_ritem[wib][rp] = it_item;
+        s_ritem[wib][rp] = static_cast<int>(it_item);
         s_rmeta[wib][rp] = meta;
       }
       nret += __popc(rm);
@@ -1440,7 +1441,8 @@ cudaError_t launch_project_group(const HostModel &hm, const ProjCall &c, int *la
   static_assert(grp_supported<P>(), "the group kernel takes trees with pose-like and CoM-like constraints");
   if (c.total <= 0) return cudaSuccess;
   if (c.precision == 1 || c.segments || c.outer || c.cyclic) return cudaErrorNotSupported;
-  constexpr int W = 10;  // one block per SM: 80 configurations, bounded by shared memory
+  if (c.total > 0x7fffffffLL) return cudaErrorInvalidValue;  // parked indices are 32-bit
+  constexpr int W = 11;  // one block per SM: 88 configurations, bounded by shared memory
   struct Planned {
     GroupPlan<P> plan;
     bool ok;

@@ -106,7 +106,7 @@ template <class P> int check() {
     printf(" amask entries %d of %d\n", nm, K * (K + 1) / 2);
   }
   // L columns
-  for (int i = 0; i < K; ++i) if (pl.lcol[i] != lcol_base<K>(i) || pl.lcol[i] % 4) bad++;
+  for (int i = 0; i < K; ++i) if (pl.lcol[i] != lcol_base<K>(i)) bad++;
   if (lcol_base<K>(K) > (int)(sizeof(GrpState<P>) )) bad++;
   printf(" sizes: GrpState %zu B, Eval %zu B, A %d, Lc %d floats, NJ %d, shared %zu B, smem(W=2) %zu B, args %zu B\n",
          sizeof(GrpState<P>), sizeof(typename GrpState<P>::Eval), GrpState<P>::K2, GrpState<P>::LC, NJ,
