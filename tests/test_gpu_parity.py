@@ -252,7 +252,7 @@ def test_dual_vjp(mcproj):
     v = v.cpu().numpy()
     v_o, f_o = O.vjp(qs.astype(np.float64), g)
     rel = np.linalg.norm(v - v_o, axis=0) / np.linalg.norm(v_o, axis=0)
-    assert np.quantile(rel[conv], 0.999) < 1e-4 and rel[conv].max() < 1e-3, rel.max()
+    assert rel[conv].max() < 1e-4, rel[conv].max()
 
 
 # ---------------------------------------------------------------------------

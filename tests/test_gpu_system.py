@@ -100,7 +100,8 @@ def test_segments_inside_caller_graph(mcproj):
 
 def test_vjp_matches_finite_differences_of_oracle_projection(mcproj):
     """g^T dPi/dq at the GPU's projected points, by central differences of the
-    FP64 oracle's projection (h = 1e-4, lambda = 0, tight tolerance)."""
+    FP64 oracle's projection (h = 1e-4, lambda = 0, tight tolerance), on all
+    16 configurations of the batch."""
     wl = W.adjoint_workload(n=16)
     P = mcproj.Projector(wl.robot, wl.constraints)
     O = orc.Oracle(wl.robot, wl.constraints)
@@ -108,17 +109,16 @@ def test_vjp_matches_finite_differences_of_oracle_projection(mcproj):
     g = f32_exact(wl.extra["g"][:, :16])
     v, _ = P.vjp(qs, dev(g))
     torch.cuda.synchronize()
+    assert ((fl.cpu().numpy() & 1) != 0).all()
     qs, v = qs.cpu().numpy().astype(np.float64), v.cpu().numpy()
-    h = 1e-4
-    for i in range(4):
-        D = np.zeros((14, 14))
-        for j in range(14):
-            e = np.zeros(14)
-            e[j] = h
-            pp = O.project(np.stack([qs[:, i] + e, qs[:, i] - e], 1), 1e-13, 80, 0.0)[0]
-            D[:, j] = (pp[:, 0] - pp[:, 1]) / (2 * h)
+    h, d, n = 1e-4, qs.shape[0], qs.shape[1]
+    E = np.eye(d) * h
+    cols = np.concatenate([np.concatenate([qs[:, [i]] + E, qs[:, [i]] - E], 1) for i in range(n)], 1)
+    pp = O.project(cols, 1e-13, 80, 0.0)[0].reshape(d, n, 2, d)   # [row, config, +/-, perturbed joint]
+    for i in range(n):
+        D = (pp[:, i, 0, :] - pp[:, i, 1, :]) / (2 * h)             # D[:, j] = dPi / dq_j
         ref = g[:, i] @ D
-        assert np.linalg.norm(v[:, i] - ref) / np.linalg.norm(ref) < 1e-4
+        assert np.linalg.norm(v[:, i] - ref) / np.linalg.norm(ref) < 1e-4, i
 
 
 def test_autograd_project_backward_is_vjp(mcproj):
