@@ -1289,8 +1289,16 @@ __device__ __forceinline__ float *stage_obstacles(const float *obs, int n_obs, c
 // the chunk, each with a 1e-4 m margin, so no overlapping pair is skipped and
 // the verdict is that of the all-pairs test.  `pairs` counts every 4-FMA test
 // performed (chunks, broad and narrow).
+// Resident blocks of 128 threads the check asks for: trees of more than 14
+// joints are capped at 128 registers (4 blocks, 16 warps per SM; the
+// humanoid's check: 2.37 -> 2.15 ms per 1,048,576 configurations, its
+// 142-register build allowing 12 warps); the arms' check was slower capped.
 template <class P>
-__global__ void __launch_bounds__(128) k_check_f32(const __grid_constant__ CheckArgs<P, float> a) {
+__host__ __device__ constexpr int check_min_blocks() {
+  return P::D > 14 ? 4 : 1;
+}
+template <class P>
+__global__ void __launch_bounds__(128, (check_min_blocks<P>())) k_check_f32(const __grid_constant__ CheckArgs<P, float> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4 *s_pair = reinterpret_cast<float4 *>(smem_raw);  // 3 float4 per pair of obstacles
   const float *s_box = stage_obstacles(a.obs, a.n_obs, a.box, a.n_box, s_pair);
