@@ -4,9 +4,11 @@
 // CoM sum comes after its children, every structurally nonzero Jacobian
 // segment (joint, constraint) and every nonzero Gram block is assigned to
 // exactly one lane with the right joint set, the refinement tasks and the dq
-// partition cover every joint once, and the Gram mask matches what the tasks
-// write.  Runs on the CPU (no kernel is launched); prints "<class>: N
+// partition cover every joint once, the Gram mask matches what the tasks
+// write, and the compile-time zero pattern of the Cholesky factor (the blocks
+// the kernel skips) matches a double-precision factor.  Runs on the CPU (no kernel is launched); prints "<class>: N
 // problems" per class and exits with the total.
+#include <cmath>
 #include <cstdio>
 #include <set>
 #include "../../paper_2604_13323_gb300/csrc/mcp_group.cuh"
@@ -104,6 +106,30 @@ template <class P> int check() {
     int nm = 0;
     for (int i = 0; i < K; ++i) for (int b = 0; b <= i; ++b) { bool m = (pl.amask[i] >> b) & 1; nm += m; if (m && !w[i][b]) bad++, printf("masked unwritten %d %d\n", i, b); }
     printf(" amask entries %d of %d\n", nm, K * (K + 1) / 2);
+  }
+  // The compile-time pattern of L (blocks the kernel skips): a Cholesky in
+  // double of J J^T + lambda I, J random on its structural nonzeros, has an
+  // exact zero wherever the pattern has one, and the pattern is no wider than
+  // the factor (every entry it keeps is nonzero in this factor).
+  {
+    unsigned long long x = 0x9E3779B97F4A7C15ull;
+    auto rnd = [&]() { x ^= x << 13; x ^= x >> 7; x ^= x << 17; return (double)(x >> 11) / 9007199254740992.0 - 0.5; };
+    double J[32][64] = {{0}}, A[32][32] = {{0}}, Lm[32][32] = {{0}};
+    for (int i = 0; i < K; ++i) for (int j = 0; j < D; ++j) if (jnz<P>(i, j)) J[i][j] = rnd();
+    for (int i = 0; i < K; ++i) for (int b = 0; b < K; ++b) { double t = 0; for (int j = 0; j < D; ++j) t += J[i][j] * J[b][j]; A[i][b] = t + (i == b ? 1e-6 : 0.0); }
+    for (int k = 0; k < K; ++k) {
+      double d = A[k][k]; for (int j = 0; j < k; ++j) d -= Lm[k][j] * Lm[k][j];
+      Lm[k][k] = std::sqrt(d);
+      for (int i = k + 1; i < K; ++i) { double t = A[i][k]; for (int j = 0; j < k; ++j) t -= Lm[i][j] * Lm[k][j]; Lm[i][k] = t / Lm[k][k]; }
+    }
+    int zeros = 0;
+    for (int i = 0; i < K; ++i) for (int b = 0; b <= i; ++b) {
+      const bool nzp = (l_row_pattern<P>(i) >> b) & 1u;
+      if (!nzp && Lm[i][b] != 0.0) bad++, printf("L[%d][%d] = %g outside the pattern\n", i, b, Lm[i][b]);
+      if (nzp && Lm[i][b] == 0.0) bad++, printf("L[%d][%d] kept by the pattern but zero\n", i, b);
+      zeros += !nzp;
+    }
+    printf(" L pattern: %d structural zeros of %d\n", zeros, K * (K + 1) / 2);
   }
   // L columns
   for (int i = 0; i < K; ++i) if (pl.lcol[i] != lcol_base<K>(i)) bad++;
