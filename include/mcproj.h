@@ -191,7 +191,9 @@ mcp_status mcp_get_constraint(const mcp_ctx *ctx, int32_t i, double *P, double *
  * residual is below tol.  If the FP32 residual passed and the FP64 one did
  * not, the configuration takes further FP32 steps while steps remain (then
  * CAP | ACCEPT_FAIL); a Cholesky pivot below pivot_fp64 hands the remaining
- * steps to FP64 (FP64_RESOLVE). */
+ * steps to FP64 (FP64_RESOLVE).  The humanoid classes' FP32 kernel takes at
+ * most 2^31 - 1 configurations per call (MCP_ERR_CUDA, invalid argument,
+ * beyond: its parked indices are 32-bit). */
 mcp_status mcp_project_batch(mcp_ctx *ctx, const mcp_project_params *p, int64_t n, int64_t ld, const void *q_in,
                              void *q_out, uint8_t *flags, uint8_t *iters, double *resid, mcp_stream stream);
 
