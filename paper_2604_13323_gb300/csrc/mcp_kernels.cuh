@@ -1105,7 +1105,7 @@ __device__ __forceinline__ ObsRec obs_rec(const float4 *s_pair, int o) {
 }
 
 // Spheres [s0, e) of one link placed by (R, p), with the link's bounding
-// sphere lb (local): the boxes, then, per 32 obstacles, the bounding sphere
+// sphere lb (local): the boxes the bound overlaps, then, per 32 obstacles, the bounding sphere
 // against their two chunk spheres (CHUNKS, scenes of more than 32 obstacles)
 // and the obstacles of the chunks it overlaps (broad phase, two records per
 // FP32x2 instruction), then the
@@ -1123,14 +1123,18 @@ static __device__ __noinline__ bool link_hits_f32(const Rot9 Rr, V3<float> p, in
   const float(&R)[9] = Rr.r;
   uint32_t tests = *tests_io;
   bool hit = false;
-  if (n_box > 0) {
-    for (int s = s0; s < e && !hit; ++s) {
-      const V3<float> c = add_rot_t<7>(p, R, V3<float>{st.s[s][0], st.s[s][1], st.s[s][2]});
-      if (box_hits<float>(c, st.s[s][3], s_box, n_box)) hit = true;
-    }
-  }
   const V3<float> bc = add_rot_t<7>(p, R, V3<float>{lb[0], lb[1], lb[2]});
   const float br = lb[3];
+  // boxes: the link's spheres against a box only where the link's bounding
+  // sphere (which contains them) overlaps it
+  for (int b = 0; b < n_box && !hit; ++b) {
+    const float *bx = s_box + 6 * b;
+    if (!box_hits<float>(bc, br, bx, 1)) continue;
+    for (int s = s0; s < e && !hit; ++s) {
+      const V3<float> c = add_rot_t<7>(p, R, V3<float>{st.s[s][0], st.s[s][1], st.s[s][2]});
+      if (box_hits<float>(c, st.s[s][3], bx, 1)) hit = true;
+    }
+  }
   const float kb = fmaf(bc.x, bc.x, fmaf(bc.y, bc.y, fmaf(bc.z, bc.z, -br * br)));
   const float2 bx2 = make_float2(bc.x, bc.x), by2 = make_float2(bc.y, bc.y), bz2 = make_float2(bc.z, bc.z),
                br2 = make_float2(br, br);
