@@ -480,9 +480,12 @@ struct NoStop {
 // p_j)` is called right after joint j is placed, and joints after `stop()`
 // becomes true are skipped, so consumers can use each link's pose while it is
 // live (the collision check does) instead of keeping the whole tree.
-template <class P, bool POS, class Ops, typename T, class Visit = NoVisit, class Stop = NoStop, class M = ModelT<T>>
-__device__ __forceinline__ void fk(const Ops &ops, const M &m, const T (&q)[P::D], Kin<P, T> &k,
-                                   const Visit &visit = Visit{}, const Stop &stop = Stop{}) {
+// COM: accumulate the mass moment sum_j m_j c_j (its x and y, all that the
+// CoM constraints read) for problems with a CoM constraint; the collision
+// check, which only needs the link poses, leaves it out.
+template <class P, bool POS, bool COM, class Ops, typename T, class Visit, class Stop, class M>
+__device__ __forceinline__ void fk_impl(const Ops &ops, const M &m, const T (&q)[P::D], Kin<P, T> &k,
+                                        const Visit &visit, const Stop &stop) {
   static_for<P::D>([&](auto JJ) {
     constexpr int j = decltype(JJ)::value;
     if (stop()) return;
@@ -498,7 +501,7 @@ __device__ __forceinline__ void fk(const Ops &ops, const M &m, const T (&q)[P::D
       if constexpr (POS) ppre = add_rot_t<P::xtmask(j)>(k.p[pa], k.R[pa], load_p(m.X[j]));
     }
     k.z[j] = col(Rpre, 2);
-    if constexpr (j == 0 && POS && needs_com<P>()) k.mc = V3<T>{T(0), T(0), T(0)};
+    if constexpr (j == 0 && COM) k.mc = V3<T>{T(0), T(0), T(0)};
     if constexpr (P::jtype(j) == REV) {
       T s, c;
       ops.sincos(q[j], s, c);
@@ -512,9 +515,10 @@ __device__ __forceinline__ void fk(const Ops &ops, const M &m, const T (&q)[P::D
       for (int i = 0; i < 9; ++i) k.R[j][i] = Rpre[i];
       if constexpr (POS) k.p[j] = {fma_(q[j], Rpre[2], ppre.x), fma_(q[j], Rpre[5], ppre.y), fma_(q[j], Rpre[8], ppre.z)};
     }
-    if constexpr (POS && needs_com<P>()) {
-      const V3<T> ci = add_rot_t<7>(k.p[j], k.R[j], V3<T>{m.com[j][0], m.com[j][1], m.com[j][2]});
-      k.mc = {fma_(m.mass[j], ci.x, k.mc.x), fma_(m.mass[j], ci.y, k.mc.y), fma_(m.mass[j], ci.z, k.mc.z)};
+    if constexpr (COM) {  // x and y of c_j = p_j + R_j com_j (the order of add_rot_t)
+      const T cx = fma_(k.R[j][2], m.com[j][2], fma_(k.R[j][1], m.com[j][1], fma_(k.R[j][0], m.com[j][0], k.p[j].x)));
+      const T cy = fma_(k.R[j][5], m.com[j][2], fma_(k.R[j][4], m.com[j][1], fma_(k.R[j][3], m.com[j][0], k.p[j].y)));
+      k.mc = {fma_(m.mass[j], cx, k.mc.x), fma_(m.mass[j], cy, k.mc.y), T(0)};
     }
     visit(JJ, k.R[j], k.p[j]);
   });
@@ -525,6 +529,17 @@ __device__ __forceinline__ void fk(const Ops &ops, const M &m, const T (&q)[P::D
     apply_xrot<P::frot(f)>(k.R[l], m.fX[f], k.fR[f]);
     if constexpr (POS) k.fp[f] = add_rot_t<P::ftmask(f)>(k.p[l], k.R[l], load_p(m.fX[f]));
   });
+}
+template <class P, bool POS, class Ops, typename T, class Visit = NoVisit, class Stop = NoStop, class M = ModelT<T>>
+__device__ __forceinline__ void fk(const Ops &ops, const M &m, const T (&q)[P::D], Kin<P, T> &k,
+                                   const Visit &visit = Visit{}, const Stop &stop = Stop{}) {
+  fk_impl<P, POS, POS && needs_com<P>(), Ops, T, Visit, Stop, M>(ops, m, q, k, visit, stop);
+}
+// Link poses only (no mass moment): the collision check.
+template <class P, class Ops, typename T, class Visit, class Stop, class M = ModelT<T>>
+__device__ __forceinline__ void fk_links(const Ops &ops, const M &m, const T (&q)[P::D], Kin<P, T> &k,
+                                         const Visit &visit, const Stop &stop) {
+  fk_impl<P, true, false, Ops, T, Visit, Stop, M>(ops, m, q, k, visit, stop);
 }
 
 // ---------------------------------------------------------------------------

@@ -1245,7 +1245,7 @@ __device__ __forceinline__ bool check_one_f32(const ModelT<float> &m, const Sphe
   }
   Kin<P, float> k;
   if (!hit)
-    fk<P, true>(
+    fk_links<P>(
         ops, m, q, k,
         [&](auto JJ, const float (&R)[9], V3<float> p) {
           constexpr int j = decltype(JJ)::value;
@@ -1346,7 +1346,7 @@ __global__ void __launch_bounds__(128) k_check_f64(const __grid_constant__ Check
   }
   Kin<P, double> k;
   if (!hit)
-    fk<P, true>(
+    fk_links<P>(
         ops, a.m, q, k,
         [&](auto JJ, const double (&R)[9], V3<double> p) {
           constexpr int j = decltype(JJ)::value;
