@@ -12,7 +12,9 @@
 //   1. FK along the kinematic tree: every lane walks the joints of the chains
 //      it owns (limbs, assigned by longest-first scheduling) and the shared
 //      trunk (computed by every lane), storing the joint axes and origins and
-//      the mass moments m_j c_j;
+//      the mass moments m_j c_j; a prismatic chain at the root (the floating
+//      base's translations) is placed in closed form, its rotations being
+//      constant;
 //   2. subtree mass moments C_j = m_j c_j + sum over children, limbs first,
 //      then the trunk;
 //   3. residuals, constraint c on lane c mod 4 (the pose and relative-pose
@@ -52,6 +54,7 @@ constexpr int GMAX_JI = 16;      // Jacobian segments per lane and segment size
 constexpr int GMAX_DQ = 20;      // dq joints per lane
 constexpr int GMAX_T = 2;        // Gram / refinement tasks per lane and phase
 constexpr int GMAX_POOL = 192;   // joint lists of the tasks
+constexpr int GMAX_PRE = 3;      // prismatic root joints placed in closed form
 
 template <class P>
 __host__ __device__ constexpr bool grp_pose_like(int c) {
@@ -200,6 +203,7 @@ struct GroupPlan {
   GrpTask rt[2][GG][GMAX_T];
   int8_t pool[GMAX_POOL];
   int n_fk, n_cb, n_cr, n_roots, n_j6, n_j2, n_dq;
+  int n_pre;  // leading FK steps of every lane placed in closed form (a prismatic root chain)
   int g_nt[4], g_len[4][GMAX_T];  // per phase: task slots, longest list per slot
   int r_nt[2], r_len[2][GMAX_T];
 };
@@ -285,6 +289,20 @@ bool make_group_plan(GroupPlan<P> &pl, const char **why) {
     n_fk = std::max(n_fk, static_cast<int>(js.size()));
   }
   pl.n_fk = n_fk;
+  // prismatic root prefix: joints 0 .. n_pre-1, prismatic, each the child of
+  // the one before, at the head of every lane's schedule, with no transform
+  // saved and no task frame among them
+  {
+    int n = 0;
+    while (n < GMAX_PRE && n < D && P::jtype(n) == PRIS && P::parent(n) == n - 1) ++n;
+    for (int f = 0; f < P::NF; ++f) n = std::min(n, P::frame_link(f) < n ? P::frame_link(f) : n);
+    for (int g = 0; g < GG; ++g)
+      for (int k = 0; k < n; ++k)
+        if (pl.fk_j[g][k] != k || pl.fk_save[g][k] >= 0) n = k;
+    for (int g = 0; g < GG; ++g)
+      if (n > 0 && pl.fk_j[g][n] >= 0 && pl.fk_par[g][n] != 0) n = 0;
+    pl.n_pre = n;
+  }
   // 2. subtree moments
   int n_cb = 0;
   for (int g = 0; g < GG; ++g) {
@@ -498,6 +516,14 @@ struct GrpTables {
   float msub[P::D];
   int8_t rev[P::D];
   int8_t sgn[P::NC][P::D];  // column sign of joint j in constraint c
+  // the prismatic root chain in closed form (for its first GMAX_PRE joints):
+  // with q = 0 joint i's frame sits at pre_c[i] with rotation R_i; its axis
+  // is pre_a[i] = R_i e_z, so its origin is pre_c[i] + sum_{k <= i} q_k pre_a[k];
+  // pre_mc[i] = m_i R_i com_i; pre_R = the rotation after the last of them
+  float pre_R[GMAX_PRE][9];
+  float pre_a[GMAX_PRE][3];
+  float pre_c[GMAX_PRE][3];
+  float pre_mc[GMAX_PRE][3];
   int8_t pad[4 - (P::D * (P::NC + 1)) % 4];  // whole words
 };
 // Shared-memory stride between the states of consecutive configurations: an
@@ -512,8 +538,29 @@ __host__ __device__ constexpr size_t grp_state_stride() {
 }
 
 template <class P>
-GrpTables<P> make_grp_tables(const ModelT<float> &m) {
+GrpTables<P> make_grp_tables(const ModelT<float> &m, const ModelT<double> &m64) {
   GrpTables<P> t{};
+  {  // the prismatic root chain, in FP64 then rounded
+    double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, c[3] = {0, 0, 0};
+    for (int i = 0; i < GMAX_PRE && i < P::D && P::jtype(i) == PRIS && P::parent(i) == i - 1; ++i) {
+      const double *X = m64.X[i];
+      double Rn[9], cn[3];
+      for (int r = 0; r < 3; ++r) {
+        cn[r] = c[r] + R[r * 3] * X[3] + R[r * 3 + 1] * X[7] + R[r * 3 + 2] * X[11];
+        for (int cc = 0; cc < 3; ++cc)
+          Rn[r * 3 + cc] = R[r * 3] * X[cc] + R[r * 3 + 1] * X[4 + cc] + R[r * 3 + 2] * X[8 + cc];
+      }
+      for (int e = 0; e < 9; ++e) R[e] = Rn[e];
+      for (int r = 0; r < 3; ++r) c[r] = cn[r];
+      for (int e = 0; e < 9; ++e) t.pre_R[i][e] = static_cast<float>(R[e]);
+      for (int r = 0; r < 3; ++r) {
+        t.pre_a[i][r] = static_cast<float>(R[r * 3 + 2]);
+        t.pre_c[i][r] = static_cast<float>(c[r]);
+        t.pre_mc[i][r] = static_cast<float>(m64.mass[i] * (R[r * 3] * m64.com[i][0] + R[r * 3 + 1] * m64.com[i][1] +
+                                                           R[r * 3 + 2] * m64.com[i][2]));
+      }
+    }
+  }
   for (int j = 0; j < P::D; ++j) {
     for (int e = 0; e < 12; ++e) t.X[j][e] = m.X[j][e];
     for (int r = 0; r < 3; ++r) t.com[j][r] = m.com[j][r];
@@ -829,8 +876,46 @@ __device__ __forceinline__ bool grp_iter(const A &a, const GrpTables<P> &tb, con
     float T[12], S0[12], S1[12];
 #pragma unroll
     for (int e = 0; e < 12; ++e) T[e] = S0[e] = S1[e] = 0.f;
+    // the prismatic root chain in closed form: constant rotations, origins
+    // pre_c[i] + sum_{k <= i} q_k pre_a[k]
+    const int n_pre = pl.n_pre;
+    if (n_pre > 0 && act) {
+      float o0 = 0.f, o1 = 0.f, o2 = 0.f;
+#pragma unroll
+      for (int i = 0; i < GMAX_PRE; ++i) {
+        if (i < n_pre) {
+          const float qi = S.q[i];
+          o0 = fmaf(qi, tb.pre_a[i][0], o0);
+          o1 = fmaf(qi, tb.pre_a[i][1], o1);
+          o2 = fmaf(qi, tb.pre_a[i][2], o2);
+          const float x0 = tb.pre_c[i][0] + o0, x1 = tb.pre_c[i][1] + o1, x2 = tb.pre_c[i][2] + o2;
+          if (pl.fk_store[g][i]) {
+            E.zo[i][0] = tb.pre_a[i][0];
+            E.zo[i][1] = tb.pre_a[i][1];
+            E.zo[i][2] = tb.pre_a[i][2];
+            E.zo[i][3] = x0;
+            E.zo[i][4] = x1;
+            E.zo[i][5] = x2;
+            const float mi = tb.mass[i];
+            S.C(i)[0] = fmaf(mi, x0, tb.pre_mc[i][0]);
+            S.C(i)[1] = fmaf(mi, x1, tb.pre_mc[i][1]);
+            S.C(i)[2] = fmaf(mi, x2, tb.pre_mc[i][2]);
+          }
+          if (i == n_pre - 1) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+#pragma unroll
+              for (int cc = 0; cc < 3; ++cc) T[r * 4 + cc] = tb.pre_R[i][r * 3 + cc];
+            }
+            T[3] = x0;
+            T[7] = x1;
+            T[11] = x2;
+          }
+        }
+      }
+    }
 #pragma unroll 1
-    for (int k = 0; k < pl.n_fk; ++k) {
+    for (int k = n_pre; k < pl.n_fk; ++k) {
       const int j = pl.fk_j[g][k];
       if (act && j >= 0) {
         const int par = pl.fk_par[g][k];
@@ -1457,7 +1542,7 @@ cudaError_t launch_project_group(const HostModel &hm, const ProjCall &c, int *la
   cudaError_t err = cudaMemsetAsync(c.counter, 0, sizeof(unsigned long long), c.stream);
   if (err != cudaSuccess) return err;
   a.m = hm.m32;
-  a.t = make_grp_tables<P>(hm.m32);
+  a.t = make_grp_tables<P>(hm.m32, hm.m64);
   a.pl = pp.plan;
   a.m64 = hm.d_m64;
   a.tab = hm.d_tab;

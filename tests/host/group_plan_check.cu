@@ -5,8 +5,9 @@
 // segment (joint, constraint) and every nonzero Gram block is assigned to
 // exactly one lane with the right joint set, the refinement tasks and the dq
 // partition cover every joint once, the Gram mask matches what the tasks
-// write, and the compile-time zero pattern of the Cholesky factor (the blocks
-// the kernel skips) matches a double-precision factor.  Runs on the CPU (no kernel is launched); prints "<class>: N
+// write, the compile-time zero pattern of the Cholesky factor (the blocks
+// the kernel skips) matches a double-precision factor, and the prismatic root
+// prefix placed in closed form matches a step-by-step composition.  Runs on the CPU (no kernel is launched); prints "<class>: N
 // problems" per class and exits with the total.
 #include <cmath>
 #include <cstdio>
@@ -40,6 +41,55 @@ template <class P> int check() {
     printf("\n");
   }
   for (int j = 0; j < D; ++j) if (stored[j] != 1) bad++, printf("joint %d stored %d\n", j, stored[j]);
+  // the prismatic root prefix placed in closed form: a chain of prismatic
+  // joints from the root, at the head of every lane's schedule, nothing saved
+  // in it and no task frame on it; the step after it continues from it
+  printf(" prismatic prefix: %d joints\n", pl.n_pre);
+  if (pl.n_pre < 0 || pl.n_pre > GMAX_PRE) bad++;
+  for (int k = 0; k < pl.n_pre; ++k) {
+    if (P::jtype(k) != PRIS || P::parent(k) != k - 1) bad++, printf("prefix joint %d\n", k);
+    for (int g = 0; g < GG; ++g) if (pl.fk_j[g][k] != k || pl.fk_save[g][k] >= 0) bad++, printf("prefix step %d lane %d\n", k, g);
+  }
+  for (int f = 0; f < P::NF; ++f) if (P::frame_link(f) < pl.n_pre) bad++;
+  for (int g = 0; g < GG; ++g) if (pl.n_pre > 0 && pl.fk_j[g][pl.n_pre] >= 0 && pl.fk_par[g][pl.n_pre] != 0) bad++;
+  // its constants against a step-by-step composition of a random model
+  if (pl.n_pre > 0) {
+    static ModelT<double> m64{};
+    static ModelT<float> m32{};
+    unsigned long long x = 0x2545F4914F6CDD1Dull;
+    auto rnd = [&]() { x ^= x << 13; x ^= x >> 7; x ^= x << 17; return (double)(x >> 11) / 9007199254740992.0 - 0.5; };
+    for (int j = 0; j < D; ++j) {
+      const double a = 3.0 * rnd(), c = std::cos(a), s_ = std::sin(a);   // a rotation about x, then a translation
+      const double Xr[12] = {1, 0, 0, rnd(), 0, c, -s_, rnd(), 0, s_, c, rnd()};
+      for (int e = 0; e < 12; ++e) m64.X[j][e] = Xr[e];
+      m64.mass[j] = 1.0 + rnd();
+      for (int r = 0; r < 3; ++r) m64.com[j][r] = 0.1 * rnd();
+    }
+    const GrpTables<P> tb = make_grp_tables<P>(m32, m64);
+    double q[GMAX_PRE];
+    for (int i = 0; i < GMAX_PRE; ++i) q[i] = rnd();
+    double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, pp[3] = {0, 0, 0}, acc[3] = {0, 0, 0};
+    for (int i = 0; i < pl.n_pre; ++i) {
+      double Rn[9], pn[3];   // T_i = T_{i-1} X_i Tz(q_i)
+      for (int r = 0; r < 3; ++r) {
+        for (int cc = 0; cc < 3; ++cc) Rn[r * 3 + cc] = R[r * 3] * m64.X[i][cc] + R[r * 3 + 1] * m64.X[i][4 + cc] + R[r * 3 + 2] * m64.X[i][8 + cc];
+        pn[r] = pp[r] + R[r * 3] * m64.X[i][3] + R[r * 3 + 1] * m64.X[i][7] + R[r * 3 + 2] * m64.X[i][11];
+      }
+      for (int r = 0; r < 3; ++r) pn[r] += q[i] * Rn[r * 3 + 2];
+      for (int e = 0; e < 9; ++e) R[e] = Rn[e];
+      for (int r = 0; r < 3; ++r) pp[r] = pn[r];
+      double err = 0;
+      for (int r = 0; r < 3; ++r) {
+        acc[r] += q[i] * tb.pre_a[i][r];
+        err = std::max(err, std::fabs(tb.pre_c[i][r] + acc[r] - pp[r]));
+        err = std::max(err, std::fabs(tb.pre_a[i][r] - R[r * 3 + 2]));
+        const double mc = m64.mass[i] * (R[r * 3] * m64.com[i][0] + R[r * 3 + 1] * m64.com[i][1] + R[r * 3 + 2] * m64.com[i][2]);
+        err = std::max(err, std::fabs(tb.pre_mc[i][r] - mc));
+      }
+      for (int e = 0; e < 9; ++e) err = std::max(err, std::fabs(tb.pre_R[i][e] - R[e]));
+      if (err > 1e-6) bad++, printf("prefix joint %d constants off by %g\n", i, err);
+    }
+  }
   // CoM: every joint exactly once in own/trunk lists; children processed before
   int seen[D] = {0};
   for (int g = 0; g < GG; ++g) { std::set<int> done; for (int k = 0; k < GMAX_CB; ++k) { int j = pl.cb_j[g][k]; if (j < 0) continue; seen[j]++; for (int h = 0; h < GMAX_CH; ++h) { int c = pl.child[j][h]; if (c >= 0 && !done.count(c)) bad++, printf("own child %d of %d not done on lane %d\n", c, j, g); } done.insert(j); if (k >= pl.n_cb) bad++; } }
